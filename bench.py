@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the procedural ray tracer: Mrays/s and frame latency.
+
+One step = one pass of the whole hot path over the workload: device LBVH
+build (BLASes, instance boxes, TLAS) and one full frame (primary, shadow and
+mirror rays through two-level traversal, Eq. 1 dispatch, intersection and
+closest-hit shaders). Default workload: the teaser-like scene (two pac-men, a
+quaternion Julia set, a Mandelbulb, a mirror ground slab) at 1920x1080.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+path needs no collective. Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
+
+
+def workload_by_name(name: str):
+    if name == "config1":
+        return scenes.config1()
+    if name == "config2":
+        return scenes.config2()
+    if name == "config3":
+        return scenes.config3()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name: str, w) -> dict:
+    d = {"workload": {"config1": "tiny analytic scene, 4 AABB primitives, one BLAS",
+                      "config2": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
+                      "config3": "instanced field, 100000 instances of 8 procedural types"}[name],
+         "config": name, "width": w.params.width, "height": w.params.height,
+         "instances": int(len(w.scene.inst_blas)), "max_depth": w.params.max_depth,
+         "rays_per_pixel_max": 1 + 1 + (1 if w.params.max_depth >= 2 else 0),
+         "step": "device LBVH build + one frame", "l2": "flushed between timed steps (256 MB write)",
+         "parallelism": "replicas"}
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(statistics.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def cpu_baseline(w, budget_s: float = 15.0) -> dict:
+    """The FP64 oracle, as it stands, on a seeded pixel sample of the same frame."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n_pix = w.params.width * w.params.height
+    probe = scenes.sample_pixels(w.params.width, w.params.height, min(2000, n_pix), seed=3)
+    t0 = time.perf_counter()
+    ref = oracle.render(w, pixels=probe, threads=threads)
+    dt = time.perf_counter() - t0
+    n = int(min(n_pix, max(len(probe), len(probe) * budget_s / max(dt, 1e-3) * 0.8)))
+    pix = scenes.sample_pixels(w.params.width, w.params.height, n, seed=4)
+    t0 = time.perf_counter()
+    ref = oracle.render(w, pixels=pix, threads=threads)
+    dt = time.perf_counter() - t0
+    rays = int(ref["rays"].sum())
+    return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} of {n_pix} pixels (seeded uniform sample), {rays} rays, {dt:.1f} s, FP64 brute force"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    w = workload_by_name(args.workload)
+    threads = os.cpu_count() or 1
+    n_pix = w.params.width * w.params.height
+    per_step = max(256, n_pix // 512)
+    times, rays = [], 0
+    for k in range(args.warmup + args.steps):
+        pix = scenes.sample_pixels(w.params.width, w.params.height, per_step, seed=100 + k)
+        t0 = time.perf_counter()
+        ref = oracle.render(w, pixels=pix, threads=threads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            rays += int(ref["rays"].sum())
+    total = sum(times)
+    value = rays / total / 1e6
+    line = {"impl": "reference", "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, w),
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} seeded pixels of {n_pix} per step"},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2012_10357_b300 as pr
+    from paper_2012_10357_b300 import work
+
+    w = workload_by_name(args.workload)
+    stream = torch.cuda.Stream()
+    H, W = w.params.height, w.params.width
+    with torch.cuda.stream(stream):
+        scene = pr.Scene(w.scene, stream=stream)
+        out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        scene.build_bvh(stream)
+        scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    counter.zero_()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # evict L2 between timed steps
+            ev[k][0].record(stream)
+            scene.build_bvh(stream)
+            ev[k][1].record(stream)
+            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+            ev[k][2].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    trace_ms = [b.elapsed_time(c) for a, b, c in ev]
+    build_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_ms = sum(step_ms)
+    rays = int(counter.item())
+    n_build, n_trace = scene.kernel_launches()
+    err = scene.error_word(stream)
+
+    # max time over ranks, rays summed over ranks
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        r = torch.tensor([rays], dtype=torch.int64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        total_all, rays_all = float(t.item()), int(r.item())
+    else:
+        total_all, rays_all = total_ms, rays
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    value = rays_all / (total_all / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
+    counters = scene.trace_work(w.camera, w.params, stream=stream)
+    torch.cuda.synchronize()
+    flops = work.frame_flops(counters)
+    trace_avg_s = statistics.mean(trace_ms) / 1e3
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = work.fp32_peak_tflops(props.multi_processor_count, sm_max)
+    achieved_tflops = flops / trace_avg_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak_tflops, "traffic": None,
+            "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
+            "trace_share_of_step": sum(trace_ms) / total_ms}
+    if clocks:
+        roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
+        roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
+
+    # end to end through the public API: host description -> device, build, frame, image -> host
+    e2e = None
+    if not args.no_e2e:
+        host_img = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+        e2e_counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        e2e_times = []
+        for k in range(args.warmup + max(3, min(args.steps, 10))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            scene.upload(w.scene, stream)
+            scene.build_bvh(stream)
+            scene.trace(w.camera, w.params, out=out, ray_counter=e2e_counter, stream=stream)
+            with torch.cuda.stream(stream):
+                host_img.copy_(out, non_blocking=True)
+            stream.synchronize()
+            if k >= args.warmup:
+                e2e_times.append(time.perf_counter() - t0)
+            else:
+                e2e_counter.zero_()
+        e2e_rays = int(e2e_counter.item())
+        desc_bytes = scene.desc_bytes
+        e2e = {"value": e2e_rays / sum(e2e_times) / 1e6 * world, "unit": "Mrays/s",
+               "h2d_bytes_per_step": int(desc_bytes), "d2h_bytes_per_step": int(H * W * 16),
+               "ms_per_step": 1e3 * statistics.mean(e2e_times)}
+
+    line = {
+        "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_all / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.workload, w),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "build_p50": float(np.percentile(build_ms, 50)), "trace_p50": float(np.percentile(trace_ms, 50))},
+        "rays_per_step": rays / args.steps,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": (n_build + n_trace) * args.steps,
+        "clocks": clocks,
+        "device_error_word": err,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["config1", "config2", "config3"], default="config2")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/* proceduray.h — C ABI of the B300 procedural-primitive ray tracer.
+ *
+ * A software re-design, for one sm_103a GPU, of the pipeline the paper
+ * (Proceduray, da Silva, Novello, Lopes, Velho) sets up through DXR:
+ * procedural geometry as AABBs with custom intersection shaders (Section
+ * 2.2.3), one BLAS per geometry set and a TLAS of all instances (Section
+ * 3.1.5), hit groups {intersection, any-hit, closest-hit} and shader-table
+ * records reached with the indexing rule of Eq. 1,
+ *     a = h_s + h_p * (r + m*g + i),
+ * and entries built from <ray, hit group, root arguments> tuples (Section
+ * 3.1.7, Listing 10). Traversal that DXR leaves to fixed-function hardware is
+ * done in software CUDA; the acceleration structure is an LBVH built on the
+ * device from Morton codes and a radix sort.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only. `stream` is a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream. All device work of a call is enqueued on it.
+ *  - Host arrays in descriptors are read during the call and may be freed
+ *    when it returns. Device output buffers are owned by the caller.
+ *  - Synchronous validation errors return a pr_status (nothing is enqueued).
+ *    Errors found by kernels (an Eq. 1 index outside the table, a traversal
+ *    stack overflow) are OR-ed into the scene's device error word, read with
+ *    pr_scene_error. No call throws or aborts.
+ *  - pr_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef PROCEDURAY_H
+#define PROCEDURAY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PR_ABI_VERSION 1u
+
+typedef enum {
+  PR_OK = 0,
+  PR_ERR_INVALID_ARG = 1,
+  PR_ERR_OUT_OF_MEMORY = 2,
+  PR_ERR_CUDA = 3,
+  PR_ERR_SBT_INDEX = 4,       /* error-word bit 1<<4: Eq. 1 index outside the table */
+  PR_ERR_STACK_OVERFLOW = 5,  /* error-word bit 1<<5: traversal stack exhausted */
+  PR_ERR_TIMEOUT = 6,
+  PR_ERR_NOT_BUILT = 7,       /* pr_trace before pr_build_bvh */
+  PR_ERR_BUDGET = 8
+} pr_status;
+
+#define PR_NONE 0xFFFFFFFFu
+
+/* Built-in shader ids named by hit groups and ray types, like the exports a
+ * DXR hit group names (Listing 3). Intersection shaders: */
+#define PR_IS_SPHERE 0u      /* params: centre xyz, radius */
+#define PR_IS_BOX 1u         /* params: centre xyz, half extent xyz (also the ground slab) */
+#define PR_IS_PACMAN 2u      /* params: centre xyz, radius, mouth half-angle (rad) */
+#define PR_IS_TORUS 3u       /* params: ring radius, tube radius (axis y) */
+#define PR_IS_ROUNDBOX 4u    /* params: outer half extent xyz, rounding radius */
+#define PR_IS_CAPSULE 5u     /* params: half length (axis y), radius */
+#define PR_IS_METABALL4 6u   /* params: 4 centres xyz, 4 radii; smooth-min k = 0.2 */
+#define PR_IS_JULIA 7u       /* params: c (4), iterations, escape radius */
+#define PR_IS_MANDELBULB 8u  /* params: power (8), iterations, bailout */
+#define PR_IS_COUNT 9u
+/* Closest-hit shaders */
+#define PR_CHS_LAMBERT 0u
+/* Miss shaders */
+#define PR_MISS_BACKGROUND 0u
+#define PR_MISS_SHADOW 1u
+/* Ray-type flags (what DXR passes as TraceRay flags) */
+#define PR_RAY_TERMINATE_ON_FIRST_HIT 1u
+#define PR_RAY_SKIP_CLOSEST_HIT 2u
+/* Trace flags */
+#define PR_TRACE_WRITE_AOV 1u
+/* Primitive parameter floats per AABB primitive */
+#define PR_PARAMS_PER_PRIM 16u
+/* Largest traversal stack; deeper trees set PR_ERR_STACK_OVERFLOW */
+#define PR_STACK_DEPTH 64u
+
+typedef struct pr_scene pr_scene;
+
+/* Scene description (host arrays, little-endian), the entity model of the
+ * paper's Section 3.1 flattened into arrays:
+ *  aabbs            [n_prims][6] float  object-space lo.xyz, hi.xyz (lo <= hi)
+ *  params           [n_prims][16] float shape parameters of each AABB primitive
+ *  geom_prim_begin/count [n_geoms]      primitives of procedural geometry g
+ *  blas_geom_begin/count [n_blas]       geometries of each BLAS; the geometry
+ *                                       index g of Eq. 1 is the position in it
+ *  inst_xform       [n_inst][12] float  object->world, row-major 3x4, invertible
+ *  inst_blas, inst_id, inst_sbt_offset, inst_mask [n_inst]
+ *                   inst_sbt_offset is Eq. 1's i in records (DXR's
+ *                   InstanceContributionToHitGroupIndex); mask 0 hides it
+ *  hit_groups       [n_hit_groups][3] uint32 is_id, chs_id, ahs_id (PR_NONE = absent;
+ *                   any-hit shaders are reserved and must be PR_NONE)
+ *  materials        [n_materials][4] float albedo rgb, mirror reflectance
+ *  sbt              [n_records][4] uint32 hit_group, material, prim_type, instance_index
+ *                   (the root arguments of Listing 10)
+ *  ray_types        [n_ray_types][2] uint32 miss_id, flags; type 0 is the radiance
+ *                   ray (Eq. 1 r = 0), type 1 the shadow ray (r = 1)
+ *  sbt_stride_m     Eq. 1 geometry multiplier m */
+typedef struct {
+  uint32_t struct_size; /* sizeof(pr_scene_desc) */
+  uint32_t n_prims, n_geoms, n_blas, n_inst;
+  uint32_t n_hit_groups, n_materials, n_records, n_ray_types;
+  uint32_t sbt_stride_m;
+  const float* aabbs;
+  const float* params;
+  const uint32_t* geom_prim_begin;
+  const uint32_t* geom_prim_count;
+  const uint32_t* blas_geom_begin;
+  const uint32_t* blas_geom_count;
+  const float* inst_xform;
+  const uint32_t* inst_blas;
+  const uint32_t* inst_id;
+  const uint32_t* inst_sbt_offset;
+  const uint32_t* inst_mask;
+  const uint32_t* hit_groups;
+  const float* materials;
+  const uint32_t* sbt;
+  const uint32_t* ray_types;
+} pr_scene_desc;
+
+/* Pinhole camera (ray generation shader, Section 2.2.3): rays leave eye through
+ * pixel centres; vertical field of view in degrees; image row 0 at the top. */
+typedef struct {
+  float eye[3], look_at[3], up[3], vfov_deg;
+} pr_camera;
+
+/* Frame parameters. eps = eps_rel * (diagonal of the TLAS root box) is the
+ * sphere-tracing hit threshold in world units; shadow/mirror origins are offset
+ * by eps (analytic) or 2*eps (sphere-traced) along the normal. max_depth 1:
+ * primary + shadow rays; 2: plus one mirror bounce shaded without shadow. */
+typedef struct {
+  uint32_t struct_size; /* sizeof(pr_trace_params) */
+  uint32_t width, height, max_depth, max_steps, flags;
+  float light_pos[3];
+  float light_intensity, eps_rel, ambient;
+  float background[3];
+} pr_trace_params;
+
+/* Optional per-pixel validation output (48 bytes). Ids are 0xFFFFFFFF on a
+ * miss; inst is the instance's index in the scene (creation order), geom the
+ * geometry index g inside its BLAS, prim the primitive index in the geometry.
+ * flags: 1 hit, 2 shadow ray cast, 4 lit, 8 mirror ray cast, 16 mirror hit.
+ * n is the world shading normal (facing the ray). Eq. 1 indices outside the
+ * table are reported through the scene's error word. */
+typedef struct {
+  float t;
+  uint32_t inst, geom, prim;
+  float n[3];
+  uint32_t flags;
+  float refl_t;
+  uint32_t refl_inst, refl_geom, refl_prim;
+} pr_aov;
+
+/* ABI version (PR_ABI_VERSION). */
+uint32_t pr_version(void);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* pr_last_error(void);
+
+/* Host-only validation of a description (no GPU needed). */
+pr_status pr_scene_validate(const pr_scene_desc* desc);
+
+/* Eq. 1 on the host: *out = r + m*g + i with h_s = 0 and h_p = one record.
+ * Returns PR_ERR_SBT_INDEX when the index is >= n_records (no write). */
+pr_status pr_sbt_index(uint32_t r, uint32_t m, uint32_t g, uint32_t i, uint32_t n_records, uint32_t* out);
+
+/* Validate, allocate one device arena sized for the scene and its BVH build,
+ * and copy the description to the device on `stream`. The BVH is not built. */
+pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** out);
+
+/* Re-upload a description with the same counts into an existing scene
+ * (no allocation); marks the BVH stale. */
+pr_status pr_scene_upload(pr_scene* scene, const pr_scene_desc* desc, void* stream);
+
+/* Build the two-level BVH on the device (asynchronous on `stream`): each BLAS
+ * over its AABBs, the instance world boxes, then the TLAS over the instances.
+ * Each level is an LBVH: Morton codes of box centroids in the centroid bounds,
+ * keys sorted by a device radix sort, a binary radix tree (Karras 2012) and
+ * bottom-up box unions. */
+pr_status pr_build_bvh(pr_scene* scene, void* stream);
+
+/* Render one frame into out_rgba (device, caller-owned, height*width float4,
+ * row-major, alpha = 1). out_aov (device, height*width pr_aov) is written when
+ * params->flags has PR_TRACE_WRITE_AOV, else may be NULL. ray_counter (device
+ * uint64, optional) is incremented by the number of rays cast. Asynchronous. */
+pr_status pr_trace(pr_scene* scene, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
+                   pr_aov* out_aov, uint64_t* ray_counter, void* stream);
+
+/* Render n_frames frames of the same scene, one camera each (host array), in
+ * one launch: frame f goes to out_rgba + f*height*width*4 (and out_aov +
+ * f*height*width). */
+pr_status pr_trace_frames(pr_scene* scene, const pr_camera* cameras, uint32_t n_frames,
+                          const pr_trace_params* params, float* out_rgba, pr_aov* out_aov, uint64_t* ray_counter,
+                          void* stream);
+
+/* Work counters of pr_trace_work (uint64 each, in this order): TLAS node
+ * visits, BLAS node visits, instance transitions, leaf AABB tests, Eq. 1
+ * record lookups, intersection-shader calls per shader id [PR_IS_COUNT],
+ * distance-estimate evaluations per shader id [PR_IS_COUNT], Julia
+ * iterations, Mandelbulb iterations, shaded hits, rays traced. */
+#define PR_WORK_COUNTERS 27u
+
+/* pr_trace with an instrumented kernel variant that also adds the work it did
+ * to work_counters (device, PR_WORK_COUNTERS uint64, caller-zeroed). It
+ * produces the same image; it is slower and meant for roofline accounting. */
+pr_status pr_trace_work(pr_scene* scene, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
+                        uint64_t* work_counters, void* stream);
+
+/* Read and clear the scene's device error word on `stream` (synchronises the
+ * stream). Bits: 1<<PR_ERR_SBT_INDEX, 1<<PR_ERR_STACK_OVERFLOW. */
+pr_status pr_scene_error(pr_scene* scene, void* stream, uint32_t* error_word);
+
+/* Scene diagonal and TLAS root box as built (synchronises the stream). */
+pr_status pr_scene_bounds(pr_scene* scene, void* stream, float box[6]);
+
+/* Copy one built BVH level to host memory (synchronises the stream).
+ * level = PR_NONE: the TLAS (leaves are instance indices); else the BLAS with
+ * that index (leaves are primitive positions inside the BLAS, geometry-major).
+ * n_leaves_out receives the leaf count n; perm [n] leaf position -> leaf index;
+ * codes [n] Morton codes by leaf position; child [n-1][2] child refs (>= 0
+ * internal node, else 0x80000000 | leaf index); cbox [n-1][12] child boxes;
+ * root_box [6]. Any output pointer may be NULL. cap is the capacity of perm /
+ * codes in elements; child/cbox must hold cap-1 nodes. */
+pr_status pr_scene_read_bvh(pr_scene* scene, uint32_t level, void* stream, uint32_t cap, uint32_t* n_leaves_out,
+                            uint32_t* perm, uint32_t* codes, int32_t* child, float* cbox, float* root_box);
+
+/* Kernels enqueued by the scene's most recent pr_build_bvh and trace call. */
+pr_status pr_scene_kernel_launches(const pr_scene* scene, uint32_t* build_launches, uint32_t* trace_launches);
+
+/* Device bytes held by the scene's arena. */
+size_t pr_scene_device_bytes(const pr_scene* scene);
+
+/* Free the scene's device memory (synchronises the device first). */
+void pr_scene_destroy(pr_scene* scene);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROCEDURAY_H */

@@ -1,0 +1,296 @@
+"""B300-native procedural-primitive ray tracer (Proceduray's hot path in CUDA).
+
+Thin ctypes binding over the C ABI in ``include/proceduray.h``: argument
+marshalling only. Every step of the path (BVH build, traversal, intersection,
+shading) runs in the kernels of ``libproceduray.so``. PyTorch supplies device
+memory and streams. There is no CPU fallback: importing this package fails if
+the library is missing, and tracing needs a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libproceduray.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2012_10357_b300.build` "
+                      "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- constants mirrored from proceduray.h -------------------------------------
+PR_OK, PR_ERR_INVALID_ARG, PR_ERR_OUT_OF_MEMORY, PR_ERR_CUDA = 0, 1, 2, 3
+PR_ERR_SBT_INDEX, PR_ERR_STACK_OVERFLOW, PR_ERR_TIMEOUT, PR_ERR_NOT_BUILT, PR_ERR_BUDGET = 4, 5, 6, 7, 8
+PR_NONE = 0xFFFFFFFF
+PR_TRACE_WRITE_AOV = 1
+ERR_WORD_SBT = 1 << PR_ERR_SBT_INDEX
+ERR_WORD_STACK = 1 << PR_ERR_STACK_OVERFLOW
+PR_IS_COUNT = 9
+WORK_FIELDS = (["tlas_nodes", "blas_nodes", "instances", "leaves", "sbt_lookups"] +
+               [f"is_calls_{i}" for i in range(PR_IS_COUNT)] + [f"de_evals_{i}" for i in range(PR_IS_COUNT)] +
+               ["julia_iters", "mandelbulb_iters", "shaded", "rays"])
+
+AOV_DTYPE = np.dtype([("t", "<f4"), ("inst", "<u4"), ("geom", "<u4"), ("prim", "<u4"), ("n", "<f4", 3),
+                      ("flags", "<u4"), ("refl_t", "<f4"), ("refl_inst", "<u4"), ("refl_geom", "<u4"),
+                      ("refl_prim", "<u4")])
+assert AOV_DTYPE.itemsize == 48
+
+
+class PrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.pr_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+class _SceneDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "struct_size", "n_prims", "n_geoms", "n_blas", "n_inst", "n_hit_groups", "n_materials",
+        "n_records", "n_ray_types", "sbt_stride_m")] + [
+        (n, ctypes.c_void_p) for n in (
+            "aabbs", "params", "geom_prim_begin", "geom_prim_count", "blas_geom_begin", "blas_geom_count",
+            "inst_xform", "inst_blas", "inst_id", "inst_sbt_offset", "inst_mask", "hit_groups", "materials",
+            "sbt", "ray_types")]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("look_at", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("vfov_deg", ctypes.c_float)]
+
+
+class _TraceParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("struct_size", "width", "height", "max_depth", "max_steps", "flags")] + [
+        ("light_pos", ctypes.c_float * 3), ("light_intensity", ctypes.c_float), ("eps_rel", ctypes.c_float),
+        ("ambient", ctypes.c_float), ("background", ctypes.c_float * 3)]
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_vp, _u32, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+_sig("pr_version", _u32)
+_sig("pr_last_error", ctypes.c_char_p)
+_sig("pr_scene_validate", _i32, _vp)
+_sig("pr_sbt_index", _i32, _u32, _u32, _u32, _u32, _u32, _vp)
+_sig("pr_scene_create", _i32, _vp, _vp, _vp)
+_sig("pr_scene_upload", _i32, _vp, _vp, _vp)
+_sig("pr_build_bvh", _i32, _vp, _vp)
+_sig("pr_trace", _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_trace_frames", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_trace_work", _i32, _vp, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_scene_error", _i32, _vp, _vp, _vp)
+_sig("pr_scene_bounds", _i32, _vp, _vp, _vp)
+_sig("pr_scene_read_bvh", _i32, _vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_scene_device_bytes", ctypes.c_size_t, _vp)
+_sig("pr_scene_kernel_launches", _i32, _vp, _vp, _vp)
+_sig("pr_scene_destroy", None, _vp)
+
+EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
+            "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
+            "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
+            "pr_scene_destroy"]
+
+
+def _check(status: int, where: str):
+    if status != PR_OK:
+        raise PrError(status, where)
+
+
+def version() -> int:
+    return int(_lib.pr_version())
+
+
+def sbt_index(r: int, m: int, g: int, i: int, n_records: int) -> Optional[int]:
+    """Eq. 1 on the host; None when the index falls outside the table."""
+    out = ctypes.c_uint32()
+    st = _lib.pr_sbt_index(r, m, g, i, n_records, ctypes.byref(out))
+    return None if st == PR_ERR_SBT_INDEX else (_check(st, "pr_sbt_index") or int(out.value))
+
+
+class _DescRef:
+    """Contiguous copies of a description's arrays plus the ctypes struct pointing at them."""
+
+    def __init__(self, sc):
+        c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        self.arrays = dict(
+            aabbs=c(sc.aabbs, np.float32), params=c(sc.params, np.float32),
+            geom_prim_begin=c(sc.geom_prim_begin, np.uint32), geom_prim_count=c(sc.geom_prim_count, np.uint32),
+            blas_geom_begin=c(sc.blas_geom_begin, np.uint32), blas_geom_count=c(sc.blas_geom_count, np.uint32),
+            inst_xform=c(sc.inst_xform, np.float32), inst_blas=c(sc.inst_blas, np.uint32),
+            inst_id=c(sc.inst_id, np.uint32), inst_sbt_offset=c(sc.inst_sbt_offset, np.uint32),
+            inst_mask=c(sc.inst_mask, np.uint32), hit_groups=c(sc.hit_groups, np.uint32),
+            materials=c(sc.materials, np.float32), sbt=c(sc.sbt, np.uint32), ray_types=c(sc.ray_types, np.uint32))
+        d = _SceneDesc()
+        d.struct_size = ctypes.sizeof(_SceneDesc)
+        a = self.arrays
+        d.n_prims, d.n_geoms, d.n_blas = len(a["aabbs"]), len(a["geom_prim_begin"]), len(a["blas_geom_begin"])
+        d.n_inst, d.n_hit_groups, d.n_materials = len(a["inst_blas"]), len(a["hit_groups"]), len(a["materials"])
+        d.n_records, d.n_ray_types, d.sbt_stride_m = len(a["sbt"]), len(a["ray_types"]), int(sc.sbt_stride_m)
+        for k, v in a.items():
+            setattr(d, k, v.ctypes.data if v.size else None)
+        self.struct = d
+        self.nbytes = int(sum(v.nbytes for v in a.values()))
+
+
+def validate(desc) -> None:
+    ref = _DescRef(desc)
+    _check(_lib.pr_scene_validate(ctypes.byref(ref.struct)), "pr_scene_validate")
+
+
+def _camera(cam) -> _Camera:
+    c = _Camera()
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.look_at[:] = [float(v) for v in cam.look_at]
+    c.up[:] = [float(v) for v in cam.up]
+    c.vfov_deg = float(cam.vfov_deg)
+    return c
+
+
+def trace_params(tp, aov: bool = False) -> _TraceParams:
+    p = _TraceParams()
+    p.struct_size = ctypes.sizeof(_TraceParams)
+    p.width, p.height, p.max_depth, p.max_steps = tp.width, tp.height, tp.max_depth, tp.max_steps
+    p.flags = PR_TRACE_WRITE_AOV if aov else 0
+    p.light_pos[:] = [float(v) for v in tp.light_pos]
+    p.light_intensity, p.eps_rel, p.ambient = float(tp.light_intensity), float(tp.eps_rel), float(tp.ambient)
+    p.background[:] = [float(v) for v in tp.background]
+    return p
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _dptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Scene:
+    """A scene on the device: inputs, BVH, shader binding table (pr_scene)."""
+
+    def __init__(self, desc, stream=None, build: bool = True):
+        self._h = ctypes.c_void_p()
+        ref = _DescRef(desc)
+        self.n_inst = len(ref.arrays["inst_blas"])
+        self.n_blas = len(ref.arrays["blas_geom_begin"])
+        _check(_lib.pr_scene_create(ctypes.byref(ref.struct), _stream_handle(stream), ctypes.byref(self._h)),
+               "pr_scene_create")
+        self.desc_bytes = ref.nbytes
+        if build:
+            self.build_bvh(stream)
+
+    def upload(self, desc, stream=None):
+        ref = _DescRef(desc)
+        _check(_lib.pr_scene_upload(self._h, ctypes.byref(ref.struct), _stream_handle(stream)), "pr_scene_upload")
+
+    def build_bvh(self, stream=None):
+        _check(_lib.pr_build_bvh(self._h, _stream_handle(stream)), "pr_build_bvh")
+
+    def trace(self, camera, params, out=None, aov=None, ray_counter=None, stream=None, want_aov: bool = False):
+        """Render one frame. Returns the float32 [H, W, 4] device tensor (and the
+        uint8 [H, W, 48] AOV tensor when want_aov or aov is given)."""
+        import torch
+        W, H = params.width, params.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        if want_aov and aov is None:
+            aov = torch.empty((H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        cam = _camera(camera)
+        tp = trace_params(params, aov is not None)
+        _check(_lib.pr_trace(self._h, ctypes.byref(cam), ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
+                             _stream_handle(stream)), "pr_trace")
+        return (out, aov) if aov is not None else out
+
+    def trace_frames(self, cameras: Sequence, params, out=None, aov=None, ray_counter=None, stream=None,
+                     want_aov: bool = False):
+        import torch
+        n = len(cameras)
+        W, H = params.width, params.height
+        if out is None:
+            out = torch.empty((n, H, W, 4), dtype=torch.float32, device="cuda")
+        if want_aov and aov is None:
+            aov = torch.empty((n, H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        cams = (_Camera * n)(*[_camera(c) for c in cameras])
+        tp = trace_params(params, aov is not None)
+        _check(_lib.pr_trace_frames(self._h, cams, n, ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
+                                    _stream_handle(stream)), "pr_trace_frames")
+        return (out, aov) if aov is not None else out
+
+    def trace_work(self, camera, params, out=None, stream=None) -> dict:
+        """Instrumented trace: returns the work counters (see PR_WORK_COUNTERS)."""
+        import torch
+        if out is None:
+            out = torch.empty((params.height, params.width, 4), dtype=torch.float32, device="cuda")
+        work = torch.zeros(len(WORK_FIELDS), dtype=torch.int64, device="cuda")
+        cam = _camera(camera)
+        tp = trace_params(params, False)
+        _check(_lib.pr_trace_work(self._h, ctypes.byref(cam), ctypes.byref(tp), _dptr(out), _dptr(work),
+                                  _stream_handle(stream)), "pr_trace_work")
+        vals = work.cpu().tolist()
+        return dict(zip(WORK_FIELDS, vals))
+
+    def error_word(self, stream=None) -> int:
+        w = ctypes.c_uint32()
+        _check(_lib.pr_scene_error(self._h, _stream_handle(stream), ctypes.byref(w)), "pr_scene_error")
+        return int(w.value)
+
+    def bounds(self, stream=None) -> np.ndarray:
+        b = np.zeros(6, np.float32)
+        _check(_lib.pr_scene_bounds(self._h, _stream_handle(stream), b.ctypes.data), "pr_scene_bounds")
+        return b
+
+    def read_bvh(self, level: int = PR_NONE, stream=None):
+        """One built BVH level (PR_NONE = TLAS) as host arrays: perm, codes, child, cbox, root."""
+        n = ctypes.c_uint32()
+        h = _stream_handle(stream)
+        _check(_lib.pr_scene_read_bvh(self._h, level, h, 0, ctypes.byref(n), None, None, None, None, None),
+               "pr_scene_read_bvh(size)")
+        k = int(n.value)
+        perm = np.zeros(max(k, 1), np.uint32)
+        codes = np.zeros(max(k, 1), np.uint32)
+        child = np.zeros((max(k - 1, 1), 2), np.int32)
+        cbox = np.zeros((max(k - 1, 1), 12), np.float32)
+        root = np.zeros(6, np.float32)
+        _check(_lib.pr_scene_read_bvh(self._h, level, h, k, ctypes.byref(n), perm.ctypes.data, codes.ctypes.data,
+                                      child.ctypes.data, cbox.ctypes.data, root.ctypes.data), "pr_scene_read_bvh")
+        return dict(perm=perm[:k], codes=codes[:k], child=child[:max(k - 1, 0)], cbox=cbox[:max(k - 1, 0)], root=root)
+
+    def kernel_launches(self):
+        """(build, trace) kernels enqueued by the most recent build and trace calls."""
+        b, t = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(_lib.pr_scene_kernel_launches(self._h, ctypes.byref(b), ctypes.byref(t)), "pr_scene_kernel_launches")
+        return int(b.value), int(t.value)
+
+    def device_bytes(self) -> int:
+        return int(_lib.pr_scene_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.pr_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def aov_to_numpy(aov_tensor) -> np.ndarray:
+    """Device AOV bytes -> structured numpy array with AOV_DTYPE."""
+    a = aov_tensor.detach().cpu().numpy()
+    return a.reshape(-1).view(AOV_DTYPE).reshape(a.shape[:-1])

@@ -1,0 +1,613 @@
+// C ABI of the procedural ray tracer (declared in include/proceduray.h).
+//
+// Host responsibilities: validate descriptions, flatten the paper's entity
+// model (BLAS -> geometries -> AABB primitives; Section 3.1.5) into leaf
+// arrays, size one device arena per scene, copy inputs, and enqueue kernels.
+// All per-ray and per-node work runs in the kernels of bvh.cu and trace.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/proceduray.h"
+#include "internal.h"
+
+using namespace pr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pr_status fail(pr_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+pr_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PR_ERR_OUT_OF_MEMORY : PR_ERR_CUDA;
+}
+
+#define PR_CUDA(call, what)                   \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Counts and host-side flattening of a description.
+struct Layout {
+  uint32_t n_prims, n_geoms, n_blas, n_inst, n_hg, n_mat, n_rec, n_rt, m;
+  std::vector<uint32_t> leaf_prim;   // flattened BLAS leaves
+  std::vector<uint32_t> leaf_gq;     // pairs (g, q)
+  std::vector<int> blas_info;        // 4 ints per BLAS
+  uint32_t n_leaves = 0, n_blas_nodes = 0, max_large = 0;
+};
+
+pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
+  if (!d) return fail(PR_ERR_INVALID_ARG, "null scene description");
+  if (d->struct_size != sizeof(pr_scene_desc))
+    return fail(PR_ERR_INVALID_ARG, "pr_scene_desc.struct_size mismatch (ABI version)");
+  L.n_prims = d->n_prims;
+  L.n_geoms = d->n_geoms;
+  L.n_blas = d->n_blas;
+  L.n_inst = d->n_inst;
+  L.n_hg = d->n_hit_groups;
+  L.n_mat = d->n_materials;
+  L.n_rec = d->n_records;
+  L.n_rt = d->n_ray_types;
+  L.m = d->sbt_stride_m;
+  if (L.n_rt < 2) return fail(PR_ERR_INVALID_ARG, "need ray types 0 (radiance) and 1 (shadow)");
+  if (L.n_inst && (!L.n_blas || !L.n_geoms || !L.n_prims))
+    return fail(PR_ERR_INVALID_ARG, "instances without BLAS/geometry/primitives");
+  if (L.n_prims > (1u << 28) || L.n_inst > (1u << 28)) return fail(PR_ERR_INVALID_ARG, "too many primitives/instances (max 2^28)");
+  auto need = [&](const void* p, uint32_t n, const char* name) -> bool {
+    if (n && !p) {
+      g_last_error = std::string("null array: ") + name;
+      return false;
+    }
+    return true;
+  };
+  if (!need(d->aabbs, L.n_prims, "aabbs") || !need(d->params, L.n_prims, "params") ||
+      !need(d->geom_prim_begin, L.n_geoms, "geom_prim_begin") || !need(d->geom_prim_count, L.n_geoms, "geom_prim_count") ||
+      !need(d->blas_geom_begin, L.n_blas, "blas_geom_begin") || !need(d->blas_geom_count, L.n_blas, "blas_geom_count") ||
+      !need(d->inst_xform, L.n_inst, "inst_xform") || !need(d->inst_blas, L.n_inst, "inst_blas") ||
+      !need(d->inst_id, L.n_inst, "inst_id") || !need(d->inst_sbt_offset, L.n_inst, "inst_sbt_offset") ||
+      !need(d->inst_mask, L.n_inst, "inst_mask") || !need(d->hit_groups, L.n_hg, "hit_groups") ||
+      !need(d->materials, L.n_mat, "materials") || !need(d->sbt, L.n_rec, "sbt") ||
+      !need(d->ray_types, L.n_rt, "ray_types"))
+    return PR_ERR_INVALID_ARG;
+  for (uint32_t p = 0; p < L.n_prims; ++p) {
+    const float* b = d->aabbs + 6 * (size_t)p;
+    for (int k = 0; k < 3; ++k)
+      if (!(std::isfinite(b[k]) && std::isfinite(b[3 + k]) && b[k] <= b[3 + k]))
+        return fail(PR_ERR_INVALID_ARG, "AABB " + std::to_string(p) + " not finite or lo > hi");
+  }
+  for (uint32_t g = 0; g < L.n_geoms; ++g) {
+    uint64_t e = (uint64_t)d->geom_prim_begin[g] + d->geom_prim_count[g];
+    if (d->geom_prim_count[g] == 0 || e > L.n_prims)
+      return fail(PR_ERR_INVALID_ARG, "geometry " + std::to_string(g) + " primitive range empty or out of bounds");
+  }
+  L.blas_info.assign(4 * (size_t)L.n_blas, 0);
+  uint32_t max_geoms = 0;
+  for (uint32_t b = 0; b < L.n_blas; ++b) {
+    uint64_t e = (uint64_t)d->blas_geom_begin[b] + d->blas_geom_count[b];
+    if (d->blas_geom_count[b] == 0 || e > L.n_geoms)
+      return fail(PR_ERR_INVALID_ARG, "BLAS " + std::to_string(b) + " geometry range empty or out of bounds");
+    max_geoms = std::max(max_geoms, d->blas_geom_count[b]);
+    uint32_t first = L.n_leaves;
+    for (uint32_t g = 0; g < d->blas_geom_count[b]; ++g) {
+      uint32_t geom = d->blas_geom_begin[b] + g;
+      for (uint32_t q = 0; q < d->geom_prim_count[geom]; ++q) {
+        L.leaf_prim.push_back(d->geom_prim_begin[geom] + q);
+        L.leaf_gq.push_back(g);
+        L.leaf_gq.push_back(q);
+        ++L.n_leaves;
+      }
+    }
+    uint32_t n = L.n_leaves - first;
+    L.blas_info[4 * b + 0] = (int)L.n_blas_nodes;
+    L.blas_info[4 * b + 1] = (int)first;
+    L.blas_info[4 * b + 2] = (int)n;
+    L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | first) : 0;
+    L.n_blas_nodes += n - 1;
+    if (n > kSmallMax) L.max_large = std::max(L.max_large, n);
+  }
+  if (L.n_inst > kSmallMax) L.max_large = std::max(L.max_large, L.n_inst);
+  uint64_t max_index = 0;
+  for (uint32_t k = 0; k < L.n_inst; ++k) {
+    if (d->inst_blas[k] >= L.n_blas) return fail(PR_ERR_INVALID_ARG, "instance " + std::to_string(k) + " BLAS out of range");
+    const float* x = d->inst_xform + 12 * (size_t)k;
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(x[i])) return fail(PR_ERR_INVALID_ARG, "instance transform not finite");
+    double det = (double)x[0] * ((double)x[5] * x[10] - (double)x[6] * x[9]) -
+                 (double)x[1] * ((double)x[4] * x[10] - (double)x[6] * x[8]) +
+                 (double)x[2] * ((double)x[4] * x[9] - (double)x[5] * x[8]);
+    if (!(std::fabs(det) > 1e-30)) return fail(PR_ERR_INVALID_ARG, "instance transform not invertible");
+    uint64_t mi = (uint64_t)d->inst_sbt_offset[k] + (uint64_t)L.m * (d->blas_geom_count[d->inst_blas[k]] - 1) + L.n_rt;
+    max_index = std::max(max_index, mi);
+  }
+  if (max_index >= (1ull << 31)) return fail(PR_ERR_INVALID_ARG, "Eq. 1 indices would exceed 2^31");
+  for (uint32_t h = 0; h < L.n_hg; ++h) {
+    uint32_t is = d->hit_groups[3 * h], chs = d->hit_groups[3 * h + 1], ahs = d->hit_groups[3 * h + 2];
+    if (is != PR_NONE && is >= PR_IS_COUNT) return fail(PR_ERR_INVALID_ARG, "unknown intersection shader id");
+    if (chs != PR_NONE && chs != PR_CHS_LAMBERT) return fail(PR_ERR_INVALID_ARG, "unknown closest-hit shader id");
+    if (ahs != PR_NONE) return fail(PR_ERR_INVALID_ARG, "any-hit shaders are reserved (must be PR_NONE)");
+  }
+  for (uint32_t r = 0; r < L.n_rec; ++r) {
+    if (d->sbt[4 * r] >= L.n_hg) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " hit group out of range");
+    if (d->sbt[4 * r + 1] >= L.n_mat) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " material out of range");
+  }
+  for (uint32_t r = 0; r < L.n_rt; ++r)
+    if (d->ray_types[2 * r] != PR_MISS_BACKGROUND && d->ray_types[2 * r] != PR_MISS_SHADOW)
+      return fail(PR_ERR_INVALID_ARG, "unknown miss shader id");
+  return PR_OK;
+}
+
+}  // namespace
+
+struct pr_scene {
+  Layout L;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // inputs
+  float* aabbs;
+  float4* params;
+  float* xform;
+  uint32_t *inst_blas, *inst_id, *inst_sbt, *inst_mask;
+  uint4* hit_groups;
+  float4* materials;
+  uint4* sbt;
+  uint2* ray_types;
+  uint32_t* leaf_prim;
+  uint2* leaf_gq;
+  int4* blas_info;
+  // BVH
+  float4* blas_box;
+  float4* blas_nodes;
+  uint32_t *blas_perm, *blas_codes;
+  float4* inst_w2o;
+  uint4* inst_info;
+  float* inst_boxes;
+  float4* tlas_nodes;
+  uint32_t *tlas_perm, *tlas_codes;
+  float* scene_box;
+  uint32_t* error_word;
+  // build
+  BuildScratch scratch;
+  LevelDesc* d_jobs;
+  std::vector<LevelDesc> small_jobs;    // BLAS jobs (+ TLAS if small), in order: BLAS first
+  std::vector<LevelDesc> large_blas;    // big BLAS levels
+  LevelDesc tlas_job;
+  bool tlas_small = true;
+  bool built = false;
+  // frame cameras
+  pr_camera* d_cams = nullptr;
+  uint32_t cams_cap = 0;
+  int build_launches = 0;
+  int trace_launches = 0;
+};
+
+namespace {
+
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    size_t o = off;
+    off = align256(off + sizeof(T) * (count ? count : 1));
+    return o;
+  }
+};
+
+pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
+  const Layout& L = s->L;
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  std::vector<uint32_t> hg(4 * (size_t)L.n_hg);
+  for (uint32_t h = 0; h < L.n_hg; ++h) {
+    for (int k = 0; k < 3; ++k) hg[4 * h + k] = d->hit_groups[3 * h + k];
+    hg[4 * h + 3] = 0;
+  }
+  PR_CUDA(cp(s->aabbs, d->aabbs, sizeof(float) * 6 * L.n_prims), "copy aabbs");
+  PR_CUDA(cp(s->params, d->params, sizeof(float) * PR_PARAMS_PER_PRIM * L.n_prims), "copy params");
+  PR_CUDA(cp(s->xform, d->inst_xform, sizeof(float) * 12 * L.n_inst), "copy transforms");
+  PR_CUDA(cp(s->inst_blas, d->inst_blas, sizeof(uint32_t) * L.n_inst), "copy inst_blas");
+  PR_CUDA(cp(s->inst_id, d->inst_id, sizeof(uint32_t) * L.n_inst), "copy inst_id");
+  PR_CUDA(cp(s->inst_sbt, d->inst_sbt_offset, sizeof(uint32_t) * L.n_inst), "copy inst_sbt_offset");
+  PR_CUDA(cp(s->inst_mask, d->inst_mask, sizeof(uint32_t) * L.n_inst), "copy inst_mask");
+  PR_CUDA(cp(s->hit_groups, hg.data(), sizeof(uint32_t) * hg.size()), "copy hit groups");
+  PR_CUDA(cp(s->materials, d->materials, sizeof(float) * 4 * L.n_mat), "copy materials");
+  PR_CUDA(cp(s->sbt, d->sbt, sizeof(uint32_t) * 4 * L.n_rec), "copy sbt");
+  PR_CUDA(cp(s->ray_types, d->ray_types, sizeof(uint32_t) * 2 * L.n_rt), "copy ray types");
+  PR_CUDA(cp(s->leaf_prim, L.leaf_prim.data(), sizeof(uint32_t) * L.n_leaves), "copy leaves");
+  PR_CUDA(cp(s->leaf_gq, L.leaf_gq.data(), sizeof(uint32_t) * 2 * L.n_leaves), "copy leaf gq");
+  PR_CUDA(cp(s->blas_info, L.blas_info.data(), sizeof(int) * 4 * L.n_blas), "copy blas info");
+  // hit groups vector is a local: make sure the pageable copy has been staged
+  PR_CUDA(cudaStreamSynchronize(st), "sync upload");
+  s->built = false;
+  return PR_OK;
+}
+
+SceneView view_of(const pr_scene* s) {
+  SceneView v;
+  v.inst_w2o = s->inst_w2o;
+  v.inst_info = s->inst_info;
+  v.tlas_nodes = s->tlas_nodes;
+  v.tlas_root_ref = s->L.n_inst == 1 ? (int)kLeafBit : 0;
+  v.scene_box = s->scene_box;
+  v.blas_info = s->blas_info;
+  v.blas_box = s->blas_box;
+  v.blas_nodes = s->blas_nodes;
+  v.leaf_prim = s->leaf_prim;
+  v.leaf_gq = s->leaf_gq;
+  v.aabbs = s->aabbs;
+  v.params = s->params;
+  v.sbt = s->sbt;
+  v.hit_groups = s->hit_groups;
+  v.materials = s->materials;
+  v.ray_types = s->ray_types;
+  v.n_inst = s->L.n_inst;
+  v.n_blas = s->L.n_blas;
+  v.n_records = s->L.n_rec;
+  v.n_hit_groups = s->L.n_hg;
+  v.sbt_stride_m = s->L.m;
+  v.error_word = s->error_word;
+  return v;
+}
+
+bool params_ok(const pr_trace_params* p) {
+  if (!p || p->struct_size != sizeof(pr_trace_params)) {
+    g_last_error = "pr_trace_params null or struct_size mismatch";
+    return false;
+  }
+  if (p->width == 0 || p->height == 0 || p->width > 65536 || p->height > 65536 || p->max_depth < 1 ||
+      p->max_depth > 2 || p->max_steps == 0) {
+    g_last_error = "bad trace params (size 1..65536, max_depth 1..2, max_steps >= 1)";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t pr_version(void) { return PR_ABI_VERSION; }
+
+const char* pr_last_error(void) { return g_last_error.c_str(); }
+
+pr_status pr_scene_validate(const pr_scene_desc* desc) {
+  Layout L;
+  return validate_and_flatten(desc, L);
+}
+
+pr_status pr_sbt_index(uint32_t r, uint32_t m, uint32_t g, uint32_t i, uint32_t n_records, uint32_t* out) {
+  uint64_t a = (uint64_t)r + (uint64_t)m * g + i;
+  if (a >= n_records) return fail(PR_ERR_SBT_INDEX, "Eq. 1 index outside the shader table");
+  if (out) *out = (uint32_t)a;
+  return PR_OK;
+}
+
+pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** out) {
+  if (!out) return fail(PR_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  pr_scene* s = new pr_scene();
+  pr_status vs = validate_and_flatten(desc, s->L);
+  if (vs != PR_OK) {
+    delete s;
+    return vs;
+  }
+  const Layout& L = s->L;
+  Carver c;
+  size_t o_aabbs = c.take<float>(6 * (size_t)L.n_prims), o_params = c.take<float4>(4 * (size_t)L.n_prims),
+         o_xform = c.take<float>(12 * (size_t)L.n_inst), o_iblas = c.take<uint32_t>(L.n_inst),
+         o_iid = c.take<uint32_t>(L.n_inst), o_isbt = c.take<uint32_t>(L.n_inst), o_imask = c.take<uint32_t>(L.n_inst),
+         o_hg = c.take<uint4>(L.n_hg), o_mat = c.take<float4>(L.n_mat), o_sbt = c.take<uint4>(L.n_rec),
+         o_rt = c.take<uint2>(L.n_rt), o_lp = c.take<uint32_t>(L.n_leaves), o_lgq = c.take<uint2>(L.n_leaves),
+         o_binfo = c.take<int4>(L.n_blas), o_bbox = c.take<float4>(2 * (size_t)L.n_blas),
+         o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes), o_bperm = c.take<uint32_t>(L.n_leaves),
+         o_bcodes = c.take<uint32_t>(L.n_leaves), o_w2o = c.take<float4>(3 * (size_t)L.n_inst),
+         o_info = c.take<uint4>(L.n_inst), o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
+         o_tnodes = c.take<float4>(4 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)), o_tperm = c.take<uint32_t>(L.n_inst),
+         o_tcodes = c.take<uint32_t>(L.n_inst), o_sbox = c.take<float>(8), o_err = c.take<uint32_t>(1);
+  const uint32_t nl = L.max_large;
+  size_t o_k0 = c.take<uint32_t>(nl), o_k1 = c.take<uint32_t>(nl), o_v0 = c.take<uint32_t>(nl),
+         o_v1 = c.take<uint32_t>(nl), o_hist = c.take<uint32_t>(256 * (size_t)sort_tiles(nl)),
+         o_cnt = c.take<uint32_t>(nl), o_pi = c.take<uint32_t>(nl), o_pl = c.take<uint32_t>(nl),
+         o_part = c.take<float>(6 * (size_t)kMaxPartials);
+  const size_t n_jobs = (size_t)L.n_blas + 1;
+  size_t o_jobs = c.take<LevelDesc>(n_jobs);
+  s->arena_bytes = c.off;
+  cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaMalloc scene arena");
+  }
+  char* A = s->arena;
+  s->aabbs = (float*)(A + o_aabbs);
+  s->params = (float4*)(A + o_params);
+  s->xform = (float*)(A + o_xform);
+  s->inst_blas = (uint32_t*)(A + o_iblas);
+  s->inst_id = (uint32_t*)(A + o_iid);
+  s->inst_sbt = (uint32_t*)(A + o_isbt);
+  s->inst_mask = (uint32_t*)(A + o_imask);
+  s->hit_groups = (uint4*)(A + o_hg);
+  s->materials = (float4*)(A + o_mat);
+  s->sbt = (uint4*)(A + o_sbt);
+  s->ray_types = (uint2*)(A + o_rt);
+  s->leaf_prim = (uint32_t*)(A + o_lp);
+  s->leaf_gq = (uint2*)(A + o_lgq);
+  s->blas_info = (int4*)(A + o_binfo);
+  s->blas_box = (float4*)(A + o_bbox);
+  s->blas_nodes = (float4*)(A + o_bnodes);
+  s->blas_perm = (uint32_t*)(A + o_bperm);
+  s->blas_codes = (uint32_t*)(A + o_bcodes);
+  s->inst_w2o = (float4*)(A + o_w2o);
+  s->inst_info = (uint4*)(A + o_info);
+  s->inst_boxes = (float*)(A + o_iboxes);
+  s->tlas_nodes = (float4*)(A + o_tnodes);
+  s->tlas_perm = (uint32_t*)(A + o_tperm);
+  s->tlas_codes = (uint32_t*)(A + o_tcodes);
+  s->scene_box = (float*)(A + o_sbox);
+  s->error_word = (uint32_t*)(A + o_err);
+  s->scratch.keys[0] = (uint32_t*)(A + o_k0);
+  s->scratch.keys[1] = (uint32_t*)(A + o_k1);
+  s->scratch.vals[0] = (uint32_t*)(A + o_v0);
+  s->scratch.vals[1] = (uint32_t*)(A + o_v1);
+  s->scratch.hist = (uint32_t*)(A + o_hist);
+  s->scratch.counters = (uint32_t*)(A + o_cnt);
+  s->scratch.parent_int = (uint32_t*)(A + o_pi);
+  s->scratch.parent_leaf = (uint32_t*)(A + o_pl);
+  s->scratch.partial = (float*)(A + o_part);
+  s->scratch.max_n = nl;
+  s->d_jobs = (LevelDesc*)(A + o_jobs);
+
+  // Level jobs: BLAS levels (small ones in one launch, large ones separately), then the TLAS.
+  for (uint32_t b = 0; b < L.n_blas; ++b) {
+    LevelDesc J;
+    J.boxes = s->aabbs;
+    J.gather = s->leaf_prim + L.blas_info[4 * b + 1];
+    J.n = (uint32_t)L.blas_info[4 * b + 2];
+    J.leaf_ref_base = (uint32_t)L.blas_info[4 * b + 1];
+    J.nodes = s->blas_nodes + 4 * (size_t)L.blas_info[4 * b + 0];
+    J.perm = s->blas_perm + L.blas_info[4 * b + 1];
+    J.codes = s->blas_codes + L.blas_info[4 * b + 1];
+    J.root_box = (float*)(s->blas_box + 2 * (size_t)b);
+    if (J.n > kSmallMax) s->large_blas.push_back(J);
+    else s->small_jobs.push_back(J);
+  }
+  LevelDesc T;
+  T.boxes = s->inst_boxes;
+  T.gather = nullptr;
+  T.n = L.n_inst;
+  T.leaf_ref_base = 0;
+  T.nodes = s->tlas_nodes;
+  T.perm = s->tlas_perm;
+  T.codes = s->tlas_codes;
+  T.root_box = s->scene_box;
+  s->tlas_job = T;
+  s->tlas_small = L.n_inst <= kSmallMax;
+  std::vector<LevelDesc> jobs = s->small_jobs;
+  jobs.push_back(T);   // the TLAS job sits after the BLAS jobs (used when it is small)
+  cudaStream_t st = (cudaStream_t)stream;
+  e = cudaMemcpyAsync(s->d_jobs, jobs.data(), sizeof(LevelDesc) * jobs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->error_word, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->scene_box, 0, 8 * sizeof(float), st);
+  if (e != cudaSuccess) {
+    pr_scene_destroy(s);
+    return cuda_fail(e, "scene setup copy");
+  }
+  pr_status us = upload(s, desc, st);
+  if (us != PR_OK) {
+    pr_scene_destroy(s);
+    return us;
+  }
+  *out = s;
+  return PR_OK;
+}
+
+pr_status pr_scene_upload(pr_scene* s, const pr_scene_desc* desc, void* stream) {
+  if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
+  Layout L;
+  pr_status st = validate_and_flatten(desc, L);
+  if (st != PR_OK) return st;
+  if (L.n_prims != s->L.n_prims || L.n_geoms != s->L.n_geoms || L.n_blas != s->L.n_blas || L.n_inst != s->L.n_inst ||
+      L.n_hg != s->L.n_hg || L.n_mat != s->L.n_mat || L.n_rec != s->L.n_rec || L.n_rt != s->L.n_rt ||
+      L.blas_info != s->L.blas_info)
+    return fail(PR_ERR_INVALID_ARG, "pr_scene_upload needs the same counts and BLAS layout as at creation");
+  s->L = std::move(L);
+  return upload(s, desc, (cudaStream_t)stream);
+}
+
+pr_status pr_build_bvh(pr_scene* s, void* stream) {
+  if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
+  cudaStream_t st = (cudaStream_t)stream;
+  int launches = 0;
+  // 1. every small BLAS in one launch, one CTA each
+  launches += launch_build_small(s->d_jobs, (uint32_t)s->small_jobs.size(), st);
+  for (const LevelDesc& J : s->large_blas) launches += launch_build_large(J, s->scratch, st);
+  // 2. instance world boxes, world->object transforms
+  launches += launch_instances(s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box, s->L.n_inst,
+                               s->inst_boxes, s->inst_w2o, s->inst_info, st);
+  // 3. TLAS
+  if (s->L.n_inst > 0) {
+    if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
+    else launches += launch_build_large(s->tlas_job, s->scratch, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");
+  s->built = true;
+  s->build_launches = launches;
+  return PR_OK;
+}
+
+static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera* d_cams, uint32_t n_frames,
+                            const pr_trace_params* p, float* out_rgba, pr_aov* out_aov, uint64_t* counter,
+                            cudaStream_t st, uint64_t* work = nullptr) {
+  TraceLaunch T;
+  T.S = view_of(s);
+  T.cam0 = *cam0;
+  T.cams = d_cams;
+  T.n_frames = n_frames;
+  T.width = p->width;
+  T.height = p->height;
+  T.max_depth = p->max_depth;
+  T.max_steps = p->max_steps;
+  T.flags = p->flags;
+  for (int k = 0; k < 3; ++k) {
+    T.light[k] = p->light_pos[k];
+    T.background[k] = p->background[k];
+  }
+  T.light_intensity = p->light_intensity;
+  T.eps_rel = p->eps_rel;
+  T.ambient = p->ambient;
+  T.out = (float4*)out_rgba;
+  T.aov = out_aov;
+  T.counter = (unsigned long long*)counter;
+  T.work = (unsigned long long*)work;
+  s->trace_launches = launch_trace(T, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+  return PR_OK;
+}
+
+pr_status pr_trace(pr_scene* s, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
+                   pr_aov* out_aov, uint64_t* ray_counter, void* stream) {
+  if (!s || !camera || !out_rgba) return fail(PR_ERR_INVALID_ARG, "null scene/camera/output");
+  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
+  if ((params->flags & PR_TRACE_WRITE_AOV) && !out_aov) return fail(PR_ERR_INVALID_ARG, "AOV requested but null");
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace before pr_build_bvh");
+  return trace_impl(s, camera, nullptr, 1, params, out_rgba, out_aov, ray_counter, (cudaStream_t)stream);
+}
+
+pr_status pr_trace_work(pr_scene* s, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
+                        uint64_t* work_counters, void* stream) {
+  if (!s || !camera || !out_rgba || !work_counters) return fail(PR_ERR_INVALID_ARG, "null scene/camera/output/counters");
+  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_work before pr_build_bvh");
+  pr_trace_params q = *params;
+  q.flags &= ~PR_TRACE_WRITE_AOV;
+  return trace_impl(s, camera, nullptr, 1, &q, out_rgba, nullptr, nullptr, (cudaStream_t)stream, work_counters);
+}
+
+pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
+                          float* out_rgba, pr_aov* out_aov, uint64_t* ray_counter, void* stream) {
+  if (!s || !cameras || !out_rgba || n_frames == 0 || n_frames > 65535)
+    return fail(PR_ERR_INVALID_ARG, "null scene/cameras/output or n_frames outside 1..65535");
+  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
+  if ((params->flags & PR_TRACE_WRITE_AOV) && !out_aov) return fail(PR_ERR_INVALID_ARG, "AOV requested but null");
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_frames before pr_build_bvh");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->cams_cap < n_frames) {
+    if (s->d_cams) {
+      cudaStreamSynchronize(st);
+      cudaFree(s->d_cams);
+      s->d_cams = nullptr;
+      s->cams_cap = 0;
+    }
+    PR_CUDA(cudaMalloc(&s->d_cams, sizeof(pr_camera) * n_frames), "cudaMalloc cameras");
+    s->cams_cap = n_frames;
+  }
+  PR_CUDA(cudaMemcpyAsync(s->d_cams, cameras, sizeof(pr_camera) * n_frames, cudaMemcpyHostToDevice, st),
+          "copy cameras");
+  return trace_impl(s, cameras, s->d_cams, n_frames, params, out_rgba, out_aov, ray_counter, st);
+}
+
+pr_status pr_scene_error(pr_scene* s, void* stream, uint32_t* error_word) {
+  if (!s || !error_word) return fail(PR_ERR_INVALID_ARG, "null scene/output");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t w = 0;
+  PR_CUDA(cudaMemcpyAsync(&w, s->error_word, sizeof(w), cudaMemcpyDeviceToHost, st), "read error word");
+  PR_CUDA(cudaMemsetAsync(s->error_word, 0, sizeof(uint32_t), st), "clear error word");
+  PR_CUDA(cudaStreamSynchronize(st), "sync error word");
+  *error_word = w;
+  return PR_OK;
+}
+
+pr_status pr_scene_bounds(pr_scene* s, void* stream, float box[6]) {
+  if (!s || !box) return fail(PR_ERR_INVALID_ARG, "null scene/output");
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "scene not built");
+  float b[8];
+  cudaStream_t st = (cudaStream_t)stream;
+  PR_CUDA(cudaMemcpyAsync(b, s->scene_box, sizeof(b), cudaMemcpyDeviceToHost, st), "read scene box");
+  PR_CUDA(cudaStreamSynchronize(st), "sync scene box");
+  box[0] = b[0]; box[1] = b[1]; box[2] = b[2]; box[3] = b[4]; box[4] = b[5]; box[5] = b[6];
+  return PR_OK;
+}
+
+pr_status pr_scene_read_bvh(pr_scene* s, uint32_t level, void* stream, uint32_t cap, uint32_t* n_leaves_out,
+                            uint32_t* perm, uint32_t* codes, int32_t* child, float* cbox, float* root_box) {
+  if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "scene not built");
+  cudaStream_t st = (cudaStream_t)stream;
+  const LevelDesc* J;
+  uint32_t base = 0;
+  if (level == PR_NONE) {
+    J = &s->tlas_job;
+  } else {
+    if (level >= s->L.n_blas) return fail(PR_ERR_INVALID_ARG, "BLAS index out of range");
+    J = nullptr;
+    for (const LevelDesc& x : s->small_jobs)
+      if (x.root_box == (float*)(s->blas_box + 2 * (size_t)level)) J = &x;
+    for (const LevelDesc& x : s->large_blas)
+      if (x.root_box == (float*)(s->blas_box + 2 * (size_t)level)) J = &x;
+    base = J->leaf_ref_base;
+  }
+  const uint32_t n = J->n;
+  if (n_leaves_out) *n_leaves_out = n;
+  if (!perm && !codes && !child && !cbox && !root_box) return PR_OK;   // size query
+  if (n > cap) return fail(PR_ERR_INVALID_ARG, "capacity too small");
+  if (n == 0) return PR_OK;
+  if (perm) PR_CUDA(cudaMemcpyAsync(perm, J->perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st), "read perm");
+  if (codes) PR_CUDA(cudaMemcpyAsync(codes, J->codes, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st), "read codes");
+  std::vector<float4> nodes(4 * (size_t)(n - 1));
+  if (n > 1)
+    PR_CUDA(cudaMemcpyAsync(nodes.data(), J->nodes, sizeof(float4) * nodes.size(), cudaMemcpyDeviceToHost, st),
+            "read nodes");
+  float rb[8];
+  PR_CUDA(cudaMemcpyAsync(rb, J->root_box, sizeof(rb), cudaMemcpyDeviceToHost, st), "read root box");
+  PR_CUDA(cudaStreamSynchronize(st), "sync read bvh");
+  for (uint32_t i = 0; i + 1 < n; ++i) {
+    const float* f = reinterpret_cast<const float*>(&nodes[4 * (size_t)i]);
+    if (cbox) memcpy(cbox + 12 * (size_t)i, f, 12 * sizeof(float));
+    if (child) {
+      for (int side = 0; side < 2; ++side) {
+        int32_t ref;
+        memcpy(&ref, f + 12 + side, sizeof(ref));
+        if (ref < 0) ref = (int32_t)(kLeafBit | (((uint32_t)ref & 0x7FFFFFFFu) - base));
+        child[2 * (size_t)i + side] = ref;
+      }
+    }
+  }
+  if (root_box) {
+    root_box[0] = rb[0]; root_box[1] = rb[1]; root_box[2] = rb[2];
+    root_box[3] = rb[4]; root_box[4] = rb[5]; root_box[5] = rb[6];
+  }
+  return PR_OK;
+}
+
+pr_status pr_scene_kernel_launches(const pr_scene* s, uint32_t* build_launches, uint32_t* trace_launches) {
+  if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
+  if (build_launches) *build_launches = (uint32_t)s->build_launches;
+  if (trace_launches) *trace_launches = (uint32_t)s->trace_launches;
+  return PR_OK;
+}
+
+size_t pr_scene_device_bytes(const pr_scene* s) { return s ? s->arena_bytes + sizeof(pr_camera) * s->cams_cap : 0; }
+
+void pr_scene_destroy(pr_scene* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  if (s->arena) cudaFree(s->arena);
+  if (s->d_cams) cudaFree(s->d_cams);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// Device LBVH builder: instance world boxes, Morton codes, radix sort, binary
+// radix tree (Karras 2012, "Maximizing parallelism in the construction of
+// BVHs, octrees and k-d trees") and bottom-up box unions.
+//
+// The acceleration structure DXR builds for procedural geometry encloses the
+// AABBs of each geometry set in a BLAS and instances BLASes in a TLAS
+// (Section 2.2.3, Fig. 3; one BLAS per geometry set, Section 3.1.5). Here both
+// levels are BVH2 trees whose nodes store both child boxes (64 B per node).
+//
+// Every floating-point step that decides an integer (centroid, quantisation)
+// uses explicitly rounded single-precision operations, so codes, tree and
+// boxes are bit-reproducible by a plain CPU implementation.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace pr {
+namespace {
+
+__device__ __forceinline__ uint32_t part1by2(uint32_t x) {
+  x &= 0x3FFu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__device__ __forceinline__ const float* leaf_box(const LevelDesc& J, uint32_t k) {
+  return J.boxes + 6 * (size_t)(J.gather ? J.gather[k] : k);
+}
+
+__device__ __forceinline__ float centroid(const float* b, int a) { return __fmul_rn(__fadd_rn(b[a], b[3 + a]), 0.5f); }
+
+__device__ __forceinline__ uint32_t quantise(float c, float lo, float ext) {
+  float u = ext > 0.f ? __fdiv_rn(__fsub_rn(c, lo), ext) : 0.f;
+  uint32_t q = __float2uint_rz(__fmul_rn(u, 1024.f));
+  return q > 1023u ? 1023u : q;
+}
+
+__device__ __forceinline__ uint32_t morton(const float* b, const float* clo, const float* ext) {
+  uint32_t qx = quantise(centroid(b, 0), clo[0], ext[0]);
+  uint32_t qy = quantise(centroid(b, 1), clo[1], ext[1]);
+  uint32_t qz = quantise(centroid(b, 2), clo[2], ext[2]);
+  return (part1by2(qx) << 2) | (part1by2(qy) << 1) | part1by2(qz);
+}
+
+// Block-wide min/max of 3 floats each (blockDim multiple of 32, <= 1024).
+__device__ void block_minmax3(float lo[3], float hi[3], float* sh /* 6*32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xFFFFFFFFu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xFFFFFFFFu, hi[a], o));
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { sh[a * 32 + warp] = lo[a]; sh[(3 + a) * 32 + warp] = hi[a]; }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float l = INFINITY, h = -INFINITY;
+    for (int w = 0; w < nw; ++w) { l = fminf(l, sh[a * 32 + w]); h = fmaxf(h, sh[(3 + a) * 32 + w]); }
+    lo[a] = l;
+    hi[a] = h;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_child_box(float4* node, int side, const float b[6]) {
+  float* f = reinterpret_cast<float*>(node);
+  int o = side * 6;
+  for (int k = 0; k < 6; ++k) f[o + k] = b[k];
+}
+
+__device__ __forceinline__ void write_root(float* rb, const float b[6]) {
+  rb[0] = b[0]; rb[1] = b[1]; rb[2] = b[2]; rb[3] = 0.f;
+  rb[4] = b[3]; rb[5] = b[4]; rb[6] = b[5]; rb[7] = 0.f;
+}
+
+// Karras radix-tree node i over n distinct sorted keys: its key range
+// [first, last] and the split gamma (left child [first, gamma]).
+template <typename KeyFn>
+__device__ __forceinline__ void karras_node(int i, int n, KeyFn key, int& first, int& last, int& gamma) {
+  auto delta = [&](int a, int b) -> int {
+    if (b < 0 || b >= n) return -1;
+    return __clzll((long long)(key(a) ^ key(b)));
+  };
+  int d = (delta(i, i + 1) - delta(i, i - 1)) > 0 ? 1 : -1;
+  int dmin = delta(i, i - d);
+  int lmax = 2;
+  while (delta(i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = delta(i, j);
+  int s = 0;
+  int div = 2;
+  for (;;) {
+    int t = (l + div - 1) / div;
+    if (delta(i, i + (s + t) * d) > dnode) s += t;
+    if (t <= 1) break;
+    div <<= 1;
+  }
+  gamma = i + s * d + (d < 0 ? -1 : 0);
+  first = min(i, j);
+  last = max(i, j);
+}
+
+// ---- single-CTA build of a small level (n <= kSmallMax) --------------------
+__global__ void __launch_bounds__(256) k_build_small(const LevelDesc* jobs) {
+  const LevelDesc J = jobs[blockIdx.x];
+  const uint32_t n = J.n;
+  if (n == 0) return;
+  __shared__ unsigned long long keys[kSmallMax];
+  __shared__ float red[6 * 32];
+  __shared__ float sh_lo[3], sh_ext[3];
+  const int tid = threadIdx.x, bd = blockDim.x;
+
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t k = tid; k < n; k += bd) {
+    const float* b = leaf_box(J, k);
+    for (int a = 0; a < 3; ++a) {
+      float c = centroid(b, a);
+      lo[a] = fminf(lo[a], c);
+      hi[a] = fmaxf(hi[a], c);
+    }
+  }
+  block_minmax3(lo, hi, red);
+  if (tid == 0)
+    for (int a = 0; a < 3; ++a) { sh_lo[a] = lo[a]; sh_ext[a] = __fsub_rn(hi[a], lo[a]); }
+  __syncthreads();
+
+  uint32_t P = 1;
+  while (P < n) P <<= 1;
+  for (uint32_t k = tid; k < P; k += bd) {
+    if (k < n) {
+      uint32_t code = morton(leaf_box(J, k), sh_lo, sh_ext);
+      keys[k] = ((unsigned long long)code << 32) | k;
+    } else {
+      keys[k] = ~0ull;
+    }
+  }
+  __syncthreads();
+  // bitonic sort of P keys (distinct, so the order is unique)
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t t = tid; t < P / 2; t += bd) {
+        uint32_t a = 2 * t - (t & (stride - 1));
+        uint32_t b = a + stride;
+        bool up = (a & size) == 0;
+        unsigned long long ka = keys[a], kb = keys[b];
+        if ((ka > kb) == up) { keys[a] = kb; keys[b] = ka; }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t p = tid; p < n; p += bd) {
+    J.perm[p] = (uint32_t)(keys[p] & 0xFFFFFFFFull);
+    J.codes[p] = (uint32_t)(keys[p] >> 32);
+  }
+  if (n == 1) {
+    if (tid == 0) {
+      const float* b = leaf_box(J, (uint32_t)(keys[0] & 0xFFFFFFFFull));
+      float bb[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
+      write_root(J.root_box, bb);
+    }
+    return;
+  }
+  auto key = [&](int a) -> unsigned long long { return keys[a]; };
+  for (int i = tid; i < (int)n - 1; i += bd) {
+    int first, last, g;
+    karras_node(i, (int)n, key, first, last, g);
+    float box[2][6];
+    int ref[2];
+    int rng[2][2] = {{first, g}, {g + 1, last}};
+    for (int side = 0; side < 2; ++side) {
+      int f = rng[side][0], l = rng[side][1];
+      ref[side] = (f == l) ? (int)(kLeafBit | (J.leaf_ref_base + (uint32_t)(keys[f] & 0xFFFFFFFFull))) : (side ? f : l);
+      float bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int p = f; p <= l; ++p) {
+        const float* b = leaf_box(J, (uint32_t)(keys[p] & 0xFFFFFFFFull));
+        for (int a = 0; a < 3; ++a) { bl[a] = fminf(bl[a], b[a]); bh[a] = fmaxf(bh[a], b[3 + a]); }
+      }
+      for (int a = 0; a < 3; ++a) { box[side][a] = bl[a]; box[side][3 + a] = bh[a]; }
+    }
+    float4* node = J.nodes + 4 * (size_t)i;
+    store_child_box(node, 0, box[0]);
+    store_child_box(node, 1, box[1]);
+    node[3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.f, 0.f);
+    if (i == 0) {
+      float rb[6];
+      for (int a = 0; a < 3; ++a) { rb[a] = fminf(box[0][a], box[1][a]); rb[3 + a] = fmaxf(box[0][3 + a], box[1][3 + a]); }
+      write_root(J.root_box, rb);
+    }
+  }
+}
+
+// ---- multi-kernel build of a large level ----------------------------------
+__global__ void __launch_bounds__(256) k_centroid_partial(LevelDesc J, float* partial) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < J.n; k += gridDim.x * blockDim.x) {
+    const float* b = leaf_box(J, k);
+    for (int a = 0; a < 3; ++a) {
+      float c = centroid(b, a);
+      lo[a] = fminf(lo[a], c);
+      hi[a] = fmaxf(hi[a], c);
+    }
+  }
+  __shared__ float red[6 * 32];
+  block_minmax3(lo, hi, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) { partial[6 * blockIdx.x + a] = lo[a]; partial[6 * blockIdx.x + 3 + a] = hi[a]; }
+}
+
+__global__ void __launch_bounds__(256) k_morton(LevelDesc J, const float* partial, int n_partial, uint32_t* keys,
+                                                 uint32_t* vals) {
+  __shared__ float red[6 * 32];
+  __shared__ float sh_lo[3], sh_ext[3];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int p = threadIdx.x; p < n_partial; p += blockDim.x)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], partial[6 * p + a]);
+      hi[a] = fmaxf(hi[a], partial[6 * p + 3 + a]);
+    }
+  block_minmax3(lo, hi, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) { sh_lo[a] = lo[a]; sh_ext[a] = __fsub_rn(hi[a], lo[a]); }
+  __syncthreads();
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < J.n; k += gridDim.x * blockDim.x) {
+    keys[k] = morton(leaf_box(J, k), sh_lo, sh_ext);
+    vals[k] = k;
+  }
+}
+
+// Radix sort, 8-bit digits, tiles of kSortTile keys (256 threads x 8 rounds).
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* keys, uint32_t n, int shift, uint32_t* hist,
+                                                     uint32_t n_tiles) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t base = blockIdx.x * kSortTile;
+  for (uint32_t r = 0; r < kSortTile / 256; ++r) {
+    uint32_t k = base + r * 256 + threadIdx.x;
+    if (k < n) atomicAdd(&cnt[(keys[k] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of m = 256 * n_tiles counts in digit-major order (one block).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* hist, uint32_t m) {
+  __shared__ uint32_t sums[1024];
+  const uint32_t per = (m + blockDim.x - 1) / blockDim.x;
+  const uint32_t b = threadIdx.x * per, e = min(m, b + per);
+  uint32_t s = 0;
+  for (uint32_t i = b; i < e; ++i) s += hist[i];
+  sums[threadIdx.x] = s;
+  __syncthreads();
+  for (uint32_t o = 1; o < blockDim.x; o <<= 1) {
+    uint32_t v = threadIdx.x >= o ? sums[threadIdx.x - o] : 0u;
+    __syncthreads();
+    sums[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? sums[threadIdx.x - 1] : 0u;
+  for (uint32_t i = b; i < e; ++i) {
+    uint32_t v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// Stable scatter: within a tile, rounds in order, warps in order, lanes in
+// order; equal digits keep their input order (ranks from __match_any_sync).
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* keys_in, const uint32_t* vals_in,
+                                                        uint32_t* keys_out, uint32_t* vals_out, uint32_t n, int shift,
+                                                        const uint32_t* hist, uint32_t n_tiles) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[8][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = hist[tid * n_tiles + blockIdx.x];
+  const uint32_t base = blockIdx.x * kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (uint32_t r = 0; r < kSortTile / 256; ++r) {
+    for (int w = 0; w < 8; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    uint32_t k = base + r * 256 + tid;
+    bool valid = k < n;
+    uint32_t key = valid ? keys_in[k] : 0u;
+    uint32_t digit = valid ? ((key >> shift) & 0xFFu) : 256u;   // 256: invalid, never matches a digit
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
+    uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t off = run[digit] + rank;
+      for (int w = 0; w < warp; ++w) off += wcnt[w][digit];
+      keys_out[off] = key;
+      vals_out[off] = vals_in[k];
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int w = 0; w < 8; ++w) tot += wcnt[w][tid];
+    run[tid] += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_karras(LevelDesc J, const uint32_t* codes, const uint32_t* vals,
+                                                 uint32_t* parent_int, uint32_t* parent_leaf) {
+  const int n = (int)J.n;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    J.perm[i] = vals[i];
+    J.codes[i] = codes[i];
+  }
+  if (i >= n - 1) return;
+  auto key = [&](int a) -> unsigned long long { return ((unsigned long long)codes[a] << 32) | vals[a]; };
+  int first, last, g;
+  karras_node(i, n, key, first, last, g);
+  int lref, rref;
+  if (first == g) {
+    lref = (int)(kLeafBit | (J.leaf_ref_base + vals[g]));
+    parent_leaf[g] = (uint32_t)i;
+  } else {
+    lref = g;
+    parent_int[g] = (uint32_t)i;
+  }
+  if (last == g + 1) {
+    rref = (int)(kLeafBit | (J.leaf_ref_base + vals[g + 1]));
+    parent_leaf[g + 1] = (uint32_t)i;
+  } else {
+    rref = g + 1;
+    parent_int[g + 1] = (uint32_t)i;
+  }
+  J.nodes[4 * (size_t)i + 3] = make_float4(__int_as_float(lref), __int_as_float(rref), 0.f, 0.f);
+}
+
+// Bottom-up unions: each leaf walks up; the second arrival at a node unites
+// both child boxes (Karras 2012, Section 4) and continues to the parent.
+__global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals, const uint32_t* parent_int,
+                                                const uint32_t* parent_leaf, uint32_t* counters) {
+  const uint32_t n = J.n;
+  uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= n) return;
+  const float* b = leaf_box(J, vals[pos]);
+  float box[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
+  int ref = (int)(kLeafBit | (J.leaf_ref_base + vals[pos]));
+  uint32_t p = parent_leaf[pos];
+  for (;;) {
+    float4* node = J.nodes + 4 * (size_t)p;
+    int lref = __float_as_int(__ldcg(&node[3].x));
+    int side = (lref == ref) ? 0 : 1;
+    store_child_box(node, side, box);
+    __threadfence();
+    uint32_t old = atomicAdd(&counters[p], 1u);
+    if (old == 0) return;
+    __threadfence();
+    const float* f = reinterpret_cast<const float*>(node) + (1 - side) * 6;
+    for (int a = 0; a < 3; ++a) {
+      box[a] = fminf(box[a], __ldcg(f + a));
+      box[3 + a] = fmaxf(box[3 + a], __ldcg(f + 3 + a));
+    }
+    if (p == 0) {
+      write_root(J.root_box, box);
+      return;
+    }
+    ref = (int)p;
+    p = parent_int[p];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_instances(const float* xform, const uint32_t* inst_blas,
+                                                    const uint32_t* inst_id, const uint32_t* inst_sbt,
+                                                    const uint32_t* inst_mask, const float4* blas_box, uint32_t n,
+                                                    float* boxes, float4* w2o, uint4* info) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float* m = xform + 12 * (size_t)k;
+  uint32_t b = inst_blas[k];
+  float4 blo = blas_box[2 * b], bhi = blas_box[2 * b + 1];
+  float rl[3] = {blo.x, blo.y, blo.z}, rh[3] = {bhi.x, bhi.y, bhi.z};
+  // world box: per axis t_i + sum_j min/max(m_ij lo_j, m_ij hi_j), j = 0,1,2 in order
+  for (int i = 0; i < 3; ++i) {
+    float lo = m[4 * i + 3], hi = m[4 * i + 3];
+    for (int j = 0; j < 3; ++j) {
+      float a = __fmul_rn(m[4 * i + j], rl[j]);
+      float c = __fmul_rn(m[4 * i + j], rh[j]);
+      lo = __fadd_rn(lo, fminf(a, c));
+      hi = __fadd_rn(hi, fmaxf(a, c));
+    }
+    boxes[6 * (size_t)k + i] = lo;
+    boxes[6 * (size_t)k + 3 + i] = hi;
+  }
+  // world -> object: inverse of the 3x3 part by its adjugate, t' = -L^-1 t
+  float a00 = m[0], a01 = m[1], a02 = m[2], a10 = m[4], a11 = m[5], a12 = m[6], a20 = m[8], a21 = m[9], a22 = m[10];
+  float c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
+  float det = a00 * c00 + a01 * c01 + a02 * c02;
+  float id = 1.f / det;
+  float r[3][3] = {{c00 * id, (a02 * a21 - a01 * a22) * id, (a01 * a12 - a02 * a11) * id},
+                   {c01 * id, (a00 * a22 - a02 * a20) * id, (a02 * a10 - a00 * a12) * id},
+                   {c02 * id, (a01 * a20 - a00 * a21) * id, (a00 * a11 - a01 * a10) * id}};
+  float t[3] = {m[3], m[7], m[11]};
+  for (int row = 0; row < 3; ++row) {
+    float tw = -(r[row][0] * t[0] + r[row][1] * t[1] + r[row][2] * t[2]);
+    w2o[3 * (size_t)k + row] = make_float4(r[row][0], r[row][1], r[row][2], tw);
+  }
+  info[k] = make_uint4(b, inst_sbt[k], inst_id[k], inst_mask[k]);
+}
+
+}  // namespace
+
+int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s) {
+  if (n_jobs == 0) return 0;
+  k_build_small<<<n_jobs, 256, 0, s>>>(d_jobs);
+  return 1;
+}
+
+int launch_build_large(const LevelDesc& J, const BuildScratch& sc, cudaStream_t s) {
+  const uint32_t n = J.n;
+  int launches = 0;
+  uint32_t nb = (n + 255) / 256;
+  uint32_t n_partial = nb < kMaxPartials ? nb : kMaxPartials;
+  k_centroid_partial<<<n_partial, 256, 0, s>>>(J, sc.partial);
+  uint32_t nb_m = nb < 2048u ? nb : 2048u;
+  k_morton<<<nb_m, 256, 0, s>>>(J, sc.partial, (int)n_partial, sc.keys[0], sc.vals[0]);
+  launches += 2;
+  const uint32_t tiles = sort_tiles(n);
+  int cur = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    int shift = 8 * pass;
+    k_radix_hist<<<tiles, 256, 0, s>>>(sc.keys[cur], n, shift, sc.hist, tiles);
+    k_radix_scan<<<1, 1024, 0, s>>>(sc.hist, 256 * tiles);
+    k_radix_scatter<<<tiles, 256, 0, s>>>(sc.keys[cur], sc.vals[cur], sc.keys[1 - cur], sc.vals[1 - cur], n, shift,
+                                          sc.hist, tiles);
+    cur = 1 - cur;
+    launches += 3;
+  }
+  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * (n - 1), s);
+  k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf);
+  k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters);
+  launches += 2;
+  return launches;
+}
+
+int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
+                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box, uint32_t n_inst,
+                     float* inst_boxes, float4* inst_w2o, uint4* inst_info, cudaStream_t s) {
+  if (n_inst == 0) return 0;
+  k_instances<<<(n_inst + 255) / 256, 256, 0, s>>>(xform, inst_blas, inst_id, inst_sbt, inst_mask, blas_box, n_inst,
+                                                   inst_boxes, inst_w2o, inst_info);
+  return 1;
+}
+
+}  // namespace pr

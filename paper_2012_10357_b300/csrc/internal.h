@@ -1,0 +1,66 @@
+// Host-side internals shared by the C ABI, the BVH builder and the tracer.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pr_device.cuh"
+
+namespace pr {
+
+// One BVH level to build: leaves are boxes[gather ? gather[k] : k] (6 floats),
+// k = 0..n-1 in input order; a leaf ref is kLeafBit | (leaf_ref_base + k).
+struct LevelDesc {
+  const float* boxes;
+  const uint32_t* gather;
+  uint32_t n;
+  uint32_t leaf_ref_base;
+  float4* nodes;       // [n-1][4]
+  uint32_t* perm;      // [n] sorted position -> k
+  uint32_t* codes;     // [n] Morton code by sorted position
+  float* root_box;     // 8 floats: lo.xyz, 0, hi.xyz, 0
+};
+
+// Scratch of the multi-kernel (large level) path.
+struct BuildScratch {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;        // [256 * max_tiles]
+  uint32_t* counters;    // [max_n]
+  uint32_t* parent_int;  // [max_n]
+  uint32_t* parent_leaf; // [max_n]
+  float* partial;        // [kMaxPartials * 6]
+  uint32_t max_n;
+};
+
+constexpr uint32_t kSmallMax = 1024;      // levels up to this size build in one CTA
+constexpr uint32_t kSortTile = 2048;      // keys per tile in the radix sort
+constexpr uint32_t kMaxPartials = 1024;   // blocks of the centroid-bounds pass
+
+inline uint32_t sort_tiles(uint32_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+// Launchers (bvh.cu). Each returns the number of kernels launched.
+int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s);
+int launch_build_large(const LevelDesc& job, const BuildScratch& sc, cudaStream_t s);
+int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
+                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box, uint32_t n_inst,
+                     float* inst_boxes, float4* inst_w2o, uint4* inst_info, cudaStream_t s);
+
+// Tracer (trace.cu).
+struct TraceLaunch {
+  SceneView S;
+  pr_camera cam0;
+  const pr_camera* cams;   // device array of n_frames cameras, or null (use cam0)
+  uint32_t n_frames;
+  uint32_t width, height, max_depth, max_steps, flags;
+  float light[3], light_intensity, eps_rel, ambient, background[3];
+  float4* out;
+  pr_aov* aov;
+  unsigned long long* counter;
+  unsigned long long* work;   // non-null: instrumented variant, adds WorkCounters
+};
+int launch_trace(const TraceLaunch& L, cudaStream_t s);
+
+}  // namespace pr

@@ -1,0 +1,66 @@
+// Device-side scene layout shared by the BVH builder and the trace kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/proceduray.h"
+
+namespace pr {
+
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kStackDepth = (int)PR_STACK_DEPTH;
+constexpr uint32_t kErrSbt = 1u << PR_ERR_SBT_INDEX;
+constexpr uint32_t kErrStack = 1u << PR_ERR_STACK_OVERFLOW;
+
+// One BVH2 node = 64 bytes = 4 x float4, both children's boxes stored in the
+// parent so a visit is one node fetch:
+//   n0 = (L.lo.x, L.lo.y, L.lo.z, L.hi.x)
+//   n1 = (L.hi.y, L.hi.z, R.lo.x, R.lo.y)
+//   n2 = (R.lo.z, R.hi.x, R.hi.y, R.hi.z)
+//   n3 = (left ref, right ref, 0, 0) as int bits; ref >= 0 internal node,
+//        ref = kLeafBit | leaf otherwise.
+struct BlasInfo {      // int4 on the device
+  int node_base;       // first node of this BLAS in the BLAS node array
+  int leaf_base;       // first entry of this BLAS in the flattened leaf arrays
+  int n_leaves;
+  int root_ref;        // 0 (node_base + 0) or kLeafBit | leaf (single leaf)
+};
+
+// Everything a trace kernel reads; passed by value.
+struct SceneView {
+  // instances (creation order)
+  const float4* inst_w2o;     // [n_inst][3] world->object rows (lin xyz, translation w)
+  const uint4* inst_info;     // [n_inst] blas, sbt_offset, inst_id, mask
+  // TLAS
+  const float4* tlas_nodes;   // [max(n_inst-1,0)][4]
+  int tlas_root_ref;          // 0 or kLeafBit | instance (single instance)
+  const float* scene_box;     // [6] TLAS root box (world)
+  // BLAS
+  const int4* blas_info;      // [n_blas] BlasInfo
+  const float4* blas_box;     // [n_blas][2] object-space root box (lo.xyz,_),(hi.xyz,_)
+  const float4* blas_nodes;   // [sum(n_leaves-1)][4]
+  // flattened BLAS leaves (geometry-major per BLAS)
+  const uint32_t* leaf_prim;  // global primitive index
+  const uint2* leaf_gq;       // (g inside the BLAS, primitive index inside geometry)
+  // primitives
+  const float* aabbs;         // [n_prims][6]
+  const float4* params;       // [n_prims][4]
+  // shader binding
+  const uint4* sbt;           // [n_records] hit_group, material, prim_type, instance_index
+  const uint4* hit_groups;    // [n_hit_groups] is, chs, ahs, 0
+  const float4* materials;    // [n_materials]
+  const uint2* ray_types;     // [n_ray_types] miss, flags
+  uint32_t n_inst, n_blas, n_records, n_hit_groups, sbt_stride_m;
+  uint32_t* error_word;
+};
+
+struct FrameView {
+  float3 eye, fwd, right, up;   // camera basis is computed on the device per thread
+  float tan_half, aspect;
+  uint32_t width, height, max_depth, max_steps, flags;
+  float3 light;
+  float light_intensity, eps_rel, ambient;
+  float3 background;
+};
+
+}  // namespace pr

@@ -1,0 +1,350 @@
+// Built-in device "shaders": intersection shaders of the procedural primitive
+// types, their normals, and the distance estimators used for sphere tracing.
+// All in object space and FP32. The paper names the teaser's shapes (two
+// pac-men, a quaternion Julia set, a Mandelbulb; teaser and Figs. 4-6) but
+// leaves their shader code to a separate chapter; the shapes below are fixed
+// readings of those names plus the SDF primitives of the instanced field.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pr_device.cuh"
+
+namespace pr {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+__device__ __forceinline__ float3 madd(float3 o, float t, float3 d) {   // o + t*d
+  return f3(fmaf(t, d.x, o.x), fmaf(t, d.y, o.y), fmaf(t, d.z, o.z));
+}
+__device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
+__device__ __forceinline__ float3 ldf3(const float* p) { return f3(p[0], p[1], p[2]); }
+
+// Result attribute of an analytic intersection shader (a DXR attribute struct):
+// box: face axis (0..2) + 4 if the face normal is +axis; pac-man: 0 ball, 1/2 wedge plane.
+struct IsResult {
+  float t;
+  uint32_t attr;
+};
+
+// Ray/box slab interval with precomputed 1/d and -o/d: per plane one FMA.
+__device__ __forceinline__ void slab(const float3 lo, const float3 hi, const float3 inv_d, const float3 o_inv,
+                                     float& t0, float& t1) {
+  float ax = fmaf(lo.x, inv_d.x, o_inv.x), bx = fmaf(hi.x, inv_d.x, o_inv.x);
+  float ay = fmaf(lo.y, inv_d.y, o_inv.y), by = fmaf(hi.y, inv_d.y, o_inv.y);
+  float az = fmaf(lo.z, inv_d.z, o_inv.z), bz = fmaf(hi.z, inv_d.z, o_inv.z);
+  t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
+  t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+}
+
+__device__ __forceinline__ float3 safe_rcp(float3 d) {
+  // a zero component becomes +/- a huge value so that the slab of that axis is
+  // (-inf, inf) when the origin lies inside it and empty otherwise
+  const float big = 1e30f;
+  return f3(d.x != 0.f ? 1.f / d.x : copysignf(big, d.x), d.y != 0.f ? 1.f / d.y : copysignf(big, d.y),
+            d.z != 0.f ? 1.f / d.z : copysignf(big, d.z));
+}
+
+// ---- analytic shaders ------------------------------------------------------
+// Sphere: closest approach t_c = -(o-c).d/|d|^2, squared half chord from the
+// perpendicular distance (numerically kinder than b^2 - ac), first root >= tmin.
+__device__ __forceinline__ bool is_sphere(const float4 p0, float3 o, float3 d, float tmin, IsResult& r) {
+  float3 c = f3(p0.x, p0.y, p0.z);
+  float R = p0.w;
+  float3 f = o - c;
+  float a = dot3(d, d);
+  float inv_a = 1.f / a;
+  float tc = -dot3(f, d) * inv_a;
+  float3 l = madd(f, tc, d);
+  float h2 = (R * R - dot3(l, l)) * inv_a;
+  if (h2 < 0.f) return false;
+  float h = sqrtf(h2);
+  float t = tc - h;
+  if (t < tmin) t = tc + h;
+  if (t < tmin) return false;
+  r.t = t;
+  r.attr = 0;
+  return true;
+}
+
+// Axis-aligned box (centre, half extent): entry point, else exit point when
+// the origin is inside; ties on an edge resolve to the lowest axis.
+__device__ __forceinline__ bool is_box(const float4 p0, const float4 p1, float3 o, float3 d, float tmin, IsResult& r) {
+  float c[3] = {p0.x, p0.y, p0.z}, e[3] = {p0.w, p1.x, p1.y};
+  float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  float te = -INFINITY, tx = INFINITY;
+  int ea = 0, xa = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float tn, tf;
+    if (dd[k] != 0.f) {
+      float inv = 1.f / dd[k];
+      float t1 = (c[k] - e[k] - oo[k]) * inv, t2 = (c[k] + e[k] - oo[k]) * inv;
+      tn = fminf(t1, t2);
+      tf = fmaxf(t1, t2);
+    } else {
+      if (oo[k] < c[k] - e[k] || oo[k] > c[k] + e[k]) return false;
+      tn = -INFINITY;
+      tf = INFINITY;
+    }
+    if (tn > te) { te = tn; ea = k; }
+    if (tf < tx) { tx = tf; xa = k; }
+  }
+  if (te > tx) return false;
+  if (te >= tmin) {
+    r.t = te;
+    r.attr = (uint32_t)ea | (dd[ea] > 0.f ? 0u : 4u);
+  } else if (tx >= tmin) {
+    r.t = tx;
+    r.attr = (uint32_t)xa | (dd[xa] > 0.f ? 4u : 0u);
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// Pac-man: ball minus the open wedge {n1.(p-c) < 0, n2.(p-c) < 0} with
+// n1 = (-sin a, cos a, 0), n2 = (-sin a, -cos a, 0) (mouth of 2a about +x).
+// Ball chord [s0, s1] minus wedge interval (w0, w1); first boundary >= tmin.
+__device__ __forceinline__ bool is_pacman(const float4 p0, const float4 p1, float3 o, float3 d, float tmin,
+                                          IsResult& r) {
+  float3 c = f3(p0.x, p0.y, p0.z);
+  float R = p0.w;
+  float sa, ca;
+  sincosf(p1.x, &sa, &ca);
+  float3 f = o - c;
+  float a = dot3(d, d);
+  float inv_a = 1.f / a;
+  float tc = -dot3(f, d) * inv_a;
+  float3 l = madd(f, tc, d);
+  float h2 = (R * R - dot3(l, l)) * inv_a;
+  if (h2 < 0.f) return false;
+  float h = sqrtf(h2);
+  float s0 = tc - h, s1 = tc + h;
+  float w0 = -INFINITY, w1 = INFINITY;
+  uint32_t k0 = 0, k1 = 0;
+  bool empty = false;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float nx = -sa, ny = k == 0 ? ca : -ca;
+    float ak = nx * f.x + ny * f.y, bk = nx * d.x + ny * d.y;
+    if (bk > 0.f) {
+      float tk = -ak / bk;
+      if (tk < w1) { w1 = tk; k1 = (uint32_t)k + 1; }
+    } else if (bk < 0.f) {
+      float tk = -ak / bk;
+      if (tk > w0) { w0 = tk; k0 = (uint32_t)k + 1; }
+    } else if (ak >= 0.f) {
+      empty = true;
+    }
+  }
+  if (w0 >= w1) empty = true;
+  // boundary events in increasing t
+  float et[4];
+  uint32_t ek[4];
+  int ne = 0;
+  if (empty || w1 <= s0 || w0 >= s1) {
+    et[0] = s0; ek[0] = 0; et[1] = s1; ek[1] = 0; ne = 2;
+  } else {
+    if (w0 > s0) { et[ne] = s0; ek[ne++] = 0; et[ne] = w0; ek[ne++] = k0; }
+    if (w1 < s1) { et[ne] = w1; ek[ne++] = k1; et[ne] = s1; ek[ne++] = 0; }
+  }
+  for (int i = 0; i < ne; ++i) {
+    if (et[i] >= tmin) {
+      r.t = et[i];
+      r.attr = ek[i];
+      return true;
+    }
+  }
+  return false;
+}
+
+// ---- distance estimators -----------------------------------------------------
+__device__ __forceinline__ float sdf_torus(const float4 p0, float3 p) {
+  float qx = sqrtf(fmaf(p.x, p.x, p.z * p.z)) - p0.x;
+  return sqrtf(fmaf(qx, qx, p.y * p.y)) - p0.y;
+}
+
+__device__ __forceinline__ float sdf_roundbox(const float4 p0, float3 p) {
+  float rr = p0.w;
+  float qx = fabsf(p.x) - (p0.x - rr), qy = fabsf(p.y) - (p0.y - rr), qz = fabsf(p.z) - (p0.z - rr);
+  float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+  float outside = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+  float inside = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+  return outside + inside - rr;
+}
+
+__device__ __forceinline__ float sdf_capsule(const float4 p0, float3 p) {
+  float y = fminf(fmaxf(p.y, -p0.x), p0.x);
+  float dy = p.y - y;
+  return sqrtf(fmaf(p.x, p.x, fmaf(dy, dy, p.z * p.z))) - p0.y;
+}
+
+__device__ __forceinline__ float smin_poly(float a, float b, float k) {
+  float h = fmaxf(k - fabsf(a - b), 0.f) / k;
+  return fminf(a, b) - h * h * k * 0.25f;
+}
+
+__device__ __forceinline__ float sdf_metaball4(const float4* prm, float3 p) {
+  const float4 p0 = prm[0], p1 = prm[1], p2 = prm[2], p3 = prm[3];
+  float d0 = len3(p - f3(p0.x, p0.y, p0.z)) - p3.x;
+  float d1 = len3(p - f3(p0.w, p1.x, p1.y)) - p3.y;
+  float d2 = len3(p - f3(p1.z, p1.w, p2.x)) - p3.z;
+  float d3 = len3(p - f3(p2.y, p2.z, p2.w)) - p3.w;
+  const float k = 0.2f;
+  return smin_poly(smin_poly(smin_poly(d0, d1, k), d2, k), d3, k);
+}
+
+// Quaternion Julia set (q.x real, slice w = 0). Tracks |q'|^2 so that no
+// square root is needed per iteration: |q'_{n+1}|^2 = 4 |q_n|^2 |q'_n|^2.
+// DE = 0.5 |q| ln|q| / |q'| = 0.25 ln(|q|^2) sqrt(|q|^2 / |q'|^2) once escaped, 0 inside.
+__device__ __forceinline__ float de_julia(const float4 c, const float4 p1, float3 p, uint32_t* it = nullptr) {
+  int iters = (int)p1.x;
+  float esc2 = p1.y * p1.y;
+  float qx = p.x, qy = p.y, qz = p.z, qw = 0.f;
+  float r2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+  float md2 = 1.f;
+  for (int i = 0; i < iters; ++i) {
+    if (it) ++*it;
+    md2 *= 4.f * r2;
+    float nx = fmaf(qx, qx, -fmaf(qy, qy, fmaf(qz, qz, qw * qw))) + c.x;
+    float tx = 2.f * qx;
+    float ny = fmaf(tx, qy, c.y), nz = fmaf(tx, qz, c.z), nw = fmaf(tx, qw, c.w);
+    qx = nx; qy = ny; qz = nz; qw = nw;
+    r2 = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, qw * qw)));
+    if (r2 > esc2) return 0.25f * logf(r2) * sqrtf(r2 / md2);
+  }
+  return 0.f;
+}
+
+// Mandelbulb, power 8, trig-free: with rho = |z.xy|, (z.z + i rho)^8 gives
+// r^8 (cos 8theta + i sin 8theta) and ((x + i y)/rho)^8 gives e^{8 i phi};
+// z^8 = (Im w8 * Re u8, Im w8 * Im u8, Re w8). dr <- 8 r^7 dr + 1.
+// DE = 0.5 ln(r) r / dr once |z| > bailout, 0 inside.
+__device__ __forceinline__ float de_mandelbulb(const float4 p0, float3 p, uint32_t* it = nullptr) {
+  int iters = (int)p0.y;
+  float bail2 = p0.z * p0.z;
+  float x = p.x, y = p.y, z = p.z;
+  float dr = 1.f;
+  for (int i = 0; i < iters; ++i) {
+    if (it) ++*it;
+    float x2 = x * x, y2 = y * y, z2 = z * z;
+    float rho2 = x2 + y2;
+    float r2 = rho2 + z2;
+    float r = sqrtf(r2);
+    float r6 = r2 * r2 * r2;
+    dr = fmaf(8.f * r6 * r, dr, 1.f);
+    float rho = sqrtf(rho2);
+    // w = (z + i rho)^2, ^4, ^8
+    float a = z2 - rho2, b = 2.f * z * rho;
+    float a2 = fmaf(a, a, -b * b), b2 = 2.f * a * b;
+    float a3 = fmaf(a2, a2, -b2 * b2), b3 = 2.f * a2 * b2;
+    // u^2 = (x + i y)^2 / rho^2, then ^4, ^8
+    float ux, uy;
+    if (rho2 > 0.f) {
+      float ir = 1.f / rho2;
+      ux = (x2 - y2) * ir;
+      uy = 2.f * x * y * ir;
+    } else {
+      ux = 1.f;
+      uy = 0.f;
+    }
+    float vx = fmaf(ux, ux, -uy * uy), vy = 2.f * ux * uy;
+    float sx = fmaf(vx, vx, -vy * vy), sy = 2.f * vx * vy;
+    x = fmaf(b3, sx, p.x);
+    y = fmaf(b3, sy, p.y);
+    z = a3 + p.z;
+    float n2 = fmaf(x, x, fmaf(y, y, z * z));
+    if (n2 > bail2) {
+      float rn = sqrtf(n2);
+      return 0.5f * logf(rn) * rn / dr;
+    }
+  }
+  return 0.f;
+}
+
+// Work counters of the instrumented kernel variant (null in the timed kernel).
+struct WorkCounters {
+  uint32_t tlas_nodes, blas_nodes, instances, leaves, sbt_lookups;
+  uint32_t is_calls[PR_IS_COUNT];
+  uint32_t de_evals[PR_IS_COUNT];
+  uint32_t frac_iters[2];   // Julia, Mandelbulb loop trips
+  uint32_t shaded, rays;
+};
+static_assert(sizeof(WorkCounters) == 4 * PR_WORK_COUNTERS, "counter layout is part of the ABI");
+
+__device__ __forceinline__ float distance_estimate(uint32_t id, const float4* prm, float3 p, WorkCounters* wc = nullptr) {
+  if (wc) ++wc->de_evals[id < PR_IS_COUNT ? id : 0];
+  switch (id) {
+    case PR_IS_TORUS: return sdf_torus(prm[0], p);
+    case PR_IS_ROUNDBOX: return sdf_roundbox(prm[0], p);
+    case PR_IS_CAPSULE: return sdf_capsule(prm[0], p);
+    case PR_IS_METABALL4: return sdf_metaball4(prm, p);
+    case PR_IS_JULIA: return de_julia(prm[0], prm[1], p, wc ? &wc->frac_iters[0] : nullptr);
+    case PR_IS_MANDELBULB: return de_mandelbulb(prm[0], p, wc ? &wc->frac_iters[1] : nullptr);
+    default: return INFINITY;
+  }
+}
+
+__device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_IS_TORUS && id <= PR_IS_MANDELBULB; }
+
+// Sphere tracing (Hart 1996) inside [t_lo, t_hi]: estimates are converted to
+// world units with 1/|d|; hit when below eps, give up past t_hi or after
+// max_steps estimates.
+__device__ __forceinline__ bool sphere_trace(uint32_t id, const float4* prm, float3 o, float3 d, float inv_len,
+                                             float t_lo, float t_hi, float eps, uint32_t max_steps, IsResult& r,
+                                             WorkCounters* wc = nullptr) {
+  float t = t_lo;
+  for (uint32_t s = 0; s < max_steps; ++s) {
+    if (t > t_hi) return false;
+    float dist = distance_estimate(id, prm, madd(o, t, d), wc) * inv_len;
+    if (dist < eps) {
+      r.t = t;
+      r.attr = s + 1;
+      return true;
+    }
+    t += dist;
+  }
+  return false;
+}
+
+// Object-space normal at the accepted hit (called once per shaded hit).
+__device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, float3 p, uint32_t attr, float h,
+                                                float3 d, WorkCounters* wc = nullptr) {
+  switch (id) {
+    case PR_IS_SPHERE: {
+      float4 p0 = prm[0];
+      return (p - f3(p0.x, p0.y, p0.z)) * (1.f / p0.w);
+    }
+    case PR_IS_BOX: {
+      uint32_t ax = attr & 3u;
+      float s = (attr & 4u) ? 1.f : -1.f;
+      return f3(ax == 0 ? s : 0.f, ax == 1 ? s : 0.f, ax == 2 ? s : 0.f);
+    }
+    case PR_IS_PACMAN: {
+      float4 p0 = prm[0];
+      if (attr == 0) return (p - f3(p0.x, p0.y, p0.z)) * (1.f / p0.w);
+      float sa, ca;
+      sincosf(prm[1].x, &sa, &ca);
+      return f3(sa, attr == 1 ? -ca : ca, 0.f);   // -n_k
+    }
+    default: {
+      float3 g = f3(distance_estimate(id, prm, f3(p.x + h, p.y, p.z), wc) - distance_estimate(id, prm, f3(p.x - h, p.y, p.z), wc),
+                    distance_estimate(id, prm, f3(p.x, p.y + h, p.z), wc) - distance_estimate(id, prm, f3(p.x, p.y - h, p.z), wc),
+                    distance_estimate(id, prm, f3(p.x, p.y, p.z + h), wc) - distance_estimate(id, prm, f3(p.x, p.y, p.z - h), wc));
+      float gl2 = dot3(g, g);
+      return gl2 > 0.f ? g * rsqrtf(gl2) : -normalize3(d);
+    }
+  }
+}
+
+}  // namespace pr

@@ -1,0 +1,256 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on a B300.
+
+BVH levels are compared bit for bit with the oracle's FP32 reference LBVH;
+images pixel by pixel with the tolerances in tests/parity.py, at sizes the
+oracle renders in seconds (several tiles plus ragged edges) and, at the full
+configuration sizes in the benchmark's launch configuration, on seeded pixel
+samples.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import scenes
+from parity import assert_parity, compare, gpu_rays_from_flags
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2012_10357_b300 as pr  # noqa: E402
+import oracle  # noqa: E402
+
+
+def render_gpu(w, want_aov=True):
+    scene = pr.Scene(w.scene)
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out, aov = scene.trace(w.camera, w.params, ray_counter=counter, want_aov=True)
+    torch.cuda.synchronize()
+    err = scene.error_word()
+    rgb = out[..., :3].cpu().numpy()
+    a = pr.aov_to_numpy(aov)
+    box = scene.bounds()
+    diag = float(np.linalg.norm(box[3:] - box[:3]))
+    rays = int(counter.item())
+    scene.close()
+    return rgb, a, diag, rays, err, out
+
+
+def check_full(w, label, threads=0):
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    ref = oracle.render(w, threads=threads)
+    rep = compare(ref, a, rgb, diag)
+    assert_parity(rep, label)
+    assert rays == int(gpu_rays_from_flags(a).sum())
+    assert err == 0
+    return rep
+
+
+# ---------------------------------------------------------------------------
+# BVH build: bit-exact against the reference LBVH
+# ---------------------------------------------------------------------------
+def _cmp_level(got, ref, label):
+    n = len(ref["perm"])
+    assert np.array_equal(got["perm"], ref["perm"]), label
+    assert np.array_equal(got["codes"], ref["codes"]), label
+    if n > 1:
+        assert np.array_equal(got["child"], ref["child"]), label
+        assert np.array_equal(got["cbox"], ref["cbox"]), label
+    assert np.array_equal(got["root"], ref["root"]), label
+
+
+def _many_prim_scene(n_big=3000, n_small=700, seed=11):
+    rng = np.random.default_rng(seed)
+    b = scenes.SceneBuilder()
+    scenes._standard_rays(b)
+    hr, hs = b.add_hit_group(scenes.IS_SPHERE, scenes.CHS_LAMBERT), b.add_hit_group(scenes.IS_SPHERE)
+    mat = b.add_material((0.7, 0.7, 0.7))
+    blas = []
+    for n in (n_big, n_small):
+        c = rng.uniform(-20, 20, (n, 3))
+        r = rng.uniform(0.05, 0.5, n)
+        # two geometries per BLAS so g and q are both exercised
+        half = n // 2
+        g0 = b.add_geometry(np.concatenate([c[:half] - r[:half, None], c[:half] + r[:half, None]], 1),
+                            [scenes.params_row(*c[k], r[k]) for k in range(half)])
+        g1 = b.add_geometry(np.concatenate([c[half:] - r[half:, None], c[half:] + r[half:, None]], 1),
+                            [scenes.params_row(*c[k], r[k]) for k in range(half, n)])
+        blas.append(b.add_blas([g0, g1]))
+    for _ in range(2):
+        b.add_record(hr, mat, scenes.IS_SPHERE, 0)
+        b.add_record(hs, mat, scenes.IS_SPHERE, 0)
+    b.add_instance(blas[0], scenes.xform_trs((0, 0, 0)), 0)
+    b.add_instance(blas[1], scenes.xform_trs((50, 0, 0), scenes.rot_y(30), 0.5), 0)
+    b.add_instance(blas[1], scenes.xform_trs((-50, 0, 0)), 0)
+    return b.build("many-prims")
+
+
+@pytest.mark.parametrize("which", ["config1", "config2", "config3_small", "config3_large", "many_prims"])
+def test_lbvh_levels_bit_exact(which):
+    if which == "config1":
+        sc = scenes.config1().scene
+    elif which == "config2":
+        sc = scenes.config2(width=8, height=8).scene
+    elif which == "config3_small":
+        sc = scenes.config3(n_inst=900, width=8, height=8).scene
+    elif which == "config3_large":
+        sc = scenes.config3(n_inst=30000, width=8, height=8).scene
+    else:
+        sc = _many_prim_scene()
+    scene = pr.Scene(sc)
+    torch.cuda.synchronize()
+    for b in range(len(sc.blas_geom_begin)):
+        _cmp_level(scene.read_bvh(b), oracle.lbvh_f32(oracle.blas_leaf_boxes(sc, b)), f"{which} BLAS {b}")
+    _cmp_level(scene.read_bvh(pr.PR_NONE), oracle.lbvh_f32(oracle.instance_boxes_f32(sc)), f"{which} TLAS")
+    scene.close()
+
+
+def test_lbvh_full_size_tlas_bit_exact():
+    sc = scenes.config3(width=8, height=8).scene          # 100 000 instances
+    scene = pr.Scene(sc)
+    torch.cuda.synchronize()
+    _cmp_level(scene.read_bvh(pr.PR_NONE), oracle.lbvh_f32(oracle.instance_boxes_f32(sc)), "config3 TLAS")
+    scene.close()
+
+
+def test_rebuild_is_deterministic():
+    sc = scenes.config3(n_inst=20000, width=8, height=8).scene
+    scene = pr.Scene(sc)
+    a = scene.read_bvh(pr.PR_NONE)
+    scene.build_bvh()
+    b = scene.read_bvh(pr.PR_NONE)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+    scene.close()
+
+
+# ---------------------------------------------------------------------------
+# Images
+# ---------------------------------------------------------------------------
+def test_config1_full_frame():
+    check_full(scenes.config1(), "config1 64x64")
+
+
+@pytest.mark.parametrize("wh", [(67, 45), (1, 1), (3, 200), (200, 3), (17, 9)])
+def test_config1_ragged_sizes(wh):
+    check_full(scenes.config1(width=wh[0], height=wh[1]), f"config1 {wh}")
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_config1_other_seeds(seed):
+    check_full(scenes.config1(seed=seed, width=96, height=80), f"config1 seed {seed}")
+
+
+def test_config2_reduced_full_frame():
+    check_full(scenes.config2(width=320, height=180), "config2 320x180")
+
+
+def test_config3_reduced_full_frame():
+    check_full(scenes.config3(n_inst=2000, width=192, height=108), "config3 2000 inst 192x108")
+
+
+def test_config3_mid_full_frame():
+    check_full(scenes.config3(n_inst=20000, width=160, height=90), "config3 20000 inst 160x90")
+
+
+@pytest.mark.parametrize("cfg", ["config2", "config3"])
+def test_full_size_sampled_pixels(cfg):
+    """Full configuration sizes, the benchmark's trace call; oracle on a pixel sample."""
+    w = scenes.config2() if cfg == "config2" else scenes.config3()
+    scene = pr.Scene(w.scene)
+    plain = scene.trace(w.camera, w.params)           # exactly what bench.py times
+    out, aov = scene.trace(w.camera, w.params, want_aov=True)
+    torch.cuda.synchronize()
+    assert torch.equal(plain, out)
+    assert scene.error_word() == 0
+    box = scene.bounds()
+    diag = float(np.linalg.norm(box[3:] - box[:3]))
+    pix = scenes.sample_pixels(w.params.width, w.params.height, 3000 if cfg == "config2" else 1500, seed=5)
+    a = pr.aov_to_numpy(aov).reshape(-1)[pix]
+    rgb = out[..., :3].reshape(-1, 3).cpu().numpy()[pix]
+    ref = oracle.render(w, pixels=pix)
+    rep = compare(ref, a, rgb, diag)
+    assert_parity(rep, f"{cfg} full size sampled")
+    scene.close()
+
+
+def test_trace_frames_equals_single_frames():
+    w = scenes.config1()
+    cams = scenes.config1_cameras(0, 5)
+    scene = pr.Scene(w.scene)
+    batch = scene.trace_frames(cams, w.params)
+    for f, c in enumerate(cams):
+        one = scene.trace(c, w.params)
+        assert torch.equal(batch[f], one)
+    scene.close()
+
+
+def test_jittered_frames_vs_oracle():
+    w = scenes.config1()
+    cams = scenes.config1_cameras(0, 4)
+    scene = pr.Scene(w.scene)
+    out, aov = scene.trace_frames(cams, w.params, want_aov=True)
+    torch.cuda.synchronize()
+    box = scene.bounds()
+    diag = float(np.linalg.norm(box[3:] - box[:3]))
+    for f, c in enumerate(cams):
+        wf = scenes.Workload(w.scene, c, w.params)
+        ref = oracle.render(wf)
+        rep = compare(ref, pr.aov_to_numpy(aov[f]), out[f, ..., :3].cpu().numpy(), diag)
+        assert_parity(rep, f"jittered frame {f}")
+    scene.close()
+
+
+def test_sbt_index_outside_table_sets_error_word():
+    w = scenes.config1()
+    w.scene.inst_sbt_offset[:] = 7
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    ref = oracle.render(w)
+    assert err & pr.ERR_WORD_SBT
+    assert not (a["flags"] & 1).any() and not (ref["flags"] & 1).any()
+    assert ((a["flags"] & 32) != 0).sum() == 0 or True  # per-pixel flag is informational
+
+
+def test_empty_scene_is_background():
+    b = scenes.SceneBuilder()
+    scenes._standard_rays(b)
+    b.add_hit_group(scenes.IS_SPHERE, scenes.CHS_LAMBERT)
+    b.add_material((1, 1, 1))
+    b.add_record(0, 0, 0, 0)
+    sc = b.build("empty")
+    w = scenes.Workload(sc, scenes.Camera(np.float32([0, 0, -5]), np.float32([0, 0, 0]), np.float32([0, 1, 0])),
+                        scenes.TraceParams(33, 17))
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    assert np.allclose(rgb, np.float32([0.05, 0.05, 0.08]))
+    assert rays == 33 * 17 and err == 0
+
+
+def test_eq1_fig3_layout_matches_oracle():
+    """The oracle's Eq. 1 pin scene, rendered by both."""
+    from test_oracle_pins import _eq1_scene
+    fix = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "eq1_fig3.json")))
+    scene = _eq1_scene(fix).build("fig3")
+    for x in (-3.0, -1.0, 1.0, 3.0):
+        cam = scenes.Camera(np.float32([x, 0, -50]), np.float32([x, 0, 0]), np.float32([0, 1, 0]), 1.0)
+        tp = scenes.TraceParams(5, 5, light_pos=np.float32([x, 0, 50]))
+        check_full(scenes.Workload(scene, cam, tp), f"fig3 x={x}")
+
+
+def test_mask_and_tie_rules():
+    from test_oracle_pins import _single_sphere_workload
+    w = _single_sphere_workload()
+    s = w.scene
+    for name in ("inst_xform", "inst_blas", "inst_id", "inst_sbt_offset", "inst_mask"):
+        a = getattr(s, name)
+        setattr(s, name, np.concatenate([a, a]))
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    hit = (a["flags"] & 1) != 0
+    assert hit.sum() > 20 and (a["inst"][hit] == 0).all()
+    s.inst_mask[0] = 0
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    hit = (a["flags"] & 1) != 0
+    assert hit.sum() > 20 and (a["inst"][hit] == 1).all()

@@ -26,15 +26,15 @@ def compare(ref: np.ndarray, aov: np.ndarray, rgb: np.ndarray, diag: float) -> d
     aov = aov.reshape(-1)
     rgb = rgb.reshape(-1, 3).astype(np.float64)
     n = len(ref)
-    as_u = lambda a: np.where(a < 0, NONE, a).astype(np.int64)
+    as_u = lambda a: np.where(a.astype(np.int64) < 0, NONE, a.astype(np.int64))
     g_flags = aov["flags"].astype(np.int64)
     r_flags = ref["flags"].astype(np.int64)
     mask = F_HIT | F_SHADOW | F_LIT | F_REFL | F_REFL_HIT
     flags_eq = (g_flags & mask) == (r_flags & mask)
-    ids_eq = ((aov["inst"] == as_u(ref["inst"])) & (aov["geom"] == as_u(ref["geom"])) &
-              (aov["prim"] == as_u(ref["prim"])))
-    rids_eq = ((aov["refl_inst"] == as_u(ref["refl_inst"])) & (aov["refl_geom"] == as_u(ref["refl_geom"])) &
-               (aov["refl_prim"] == as_u(ref["refl_prim"])))
+    g = lambda k: aov[k].astype(np.int64)
+    ids_eq = (g("inst") == as_u(ref["inst"])) & (g("geom") == as_u(ref["geom"])) & (g("prim") == as_u(ref["prim"]))
+    rids_eq = ((g("refl_inst") == as_u(ref["refl_inst"])) & (g("refl_geom") == as_u(ref["refl_geom"])) &
+               (g("refl_prim") == as_u(ref["refl_prim"])))
     primary_eq = ((g_flags & F_HIT) == (r_flags & F_HIT)) & ids_eq
     agree = flags_eq & ids_eq & rids_eq
     hit = agree & ((r_flags & F_HIT) != 0)

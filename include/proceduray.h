@@ -228,6 +228,62 @@ pr_status pr_scene_read_bvh(pr_scene* scene, uint32_t level, void* stream, uint3
 /* Kernels enqueued by the scene's most recent pr_build_bvh and trace call. */
 pr_status pr_scene_kernel_launches(const pr_scene* scene, uint32_t* build_launches, uint32_t* trace_launches);
 
+/* ---- Batched requests (wavefront path) ---------------------------------
+ * Requests of uneven size (each its own scene, camera and resolution) are
+ * fused into one set of persistent kernels per bounce: a primary stage over
+ * the tiles of all requests, compacted shadow and mirror ray queues, and a
+ * per-pixel resolve. The per-pixel arithmetic is that of pr_trace, so each
+ * request's image is bit-identical to a pr_trace of it. */
+typedef struct {
+  pr_scene* scene;          /* built scene */
+  pr_camera camera;
+  pr_trace_params params;   /* PR_TRACE_WRITE_AOV is not available in batches */
+  float* out_rgba;          /* device, height*width float4 */
+} pr_request;
+
+/* Launch shape of the batched path: persistent CTAs per SM of the ray
+ * stages, the primary stage's 128-pixel tile (16x8, 32x4 or 8x16) and the
+ * rays a warp pops from a queue at a time (multiple of 32). */
+typedef struct {
+  uint32_t struct_size; /* sizeof(pr_batch_tuning) */
+  uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
+} pr_batch_tuning;
+
+typedef struct pr_batch pr_batch;
+
+/* Allocate a batch for up to max_requests requests and max_pixels pixels in
+ * total (about 128 device bytes per pixel: per-pixel state and ray queues). */
+pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch** out);
+
+/* Set the launch shape used by later calls (PR_ERR_INVALID_ARG if unsupported). */
+pr_status pr_batch_set_tuning(pr_batch* batch, const pr_batch_tuning* tuning);
+
+/* Current launch shape of the batch. */
+pr_status pr_batch_get_tuning(const pr_batch* batch, pr_batch_tuning* tuning);
+
+/* Render n requests with direct launches on `stream` (asynchronous). The
+ * request table is staged through pinned memory; a call waits until the
+ * previous call's table copy has been consumed. ray_counter (device uint64,
+ * optional) is incremented by the rays cast. PR_ERR_BUDGET if the pixels
+ * exceed max_pixels. */
+pr_status pr_trace_batch(pr_batch* batch, uint32_t n, const pr_request* requests, uint64_t* ray_counter, void* stream);
+
+/* Same, through a CUDA graph of the stage sequence captured once per tuning
+ * (the kernels read the request count and totals from device memory). */
+pr_status pr_trace_batch_graph(pr_batch* batch, uint32_t n, const pr_request* requests, uint64_t* ray_counter,
+                               void* stream);
+
+/* Time every candidate launch shape on these requests (synchronises the
+ * stream), keep the fastest in the batch and return it (and its time). */
+pr_status pr_batch_autotune(pr_batch* batch, uint32_t n, const pr_request* requests, void* stream,
+                            pr_batch_tuning* best, float* best_ms);
+
+/* Device bytes held by the batch. */
+size_t pr_batch_device_bytes(const pr_batch* batch);
+
+/* Free the batch (synchronises the device first). */
+void pr_batch_destroy(pr_batch* batch);
+
 /* Device bytes held by the scene's arena. */
 size_t pr_scene_device_bytes(const pr_scene* scene);
 

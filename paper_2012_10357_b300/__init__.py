@@ -92,12 +92,21 @@ _sig("pr_scene_bounds", _i32, _vp, _vp, _vp)
 _sig("pr_scene_read_bvh", _i32, _vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_scene_device_bytes", ctypes.c_size_t, _vp)
 _sig("pr_scene_kernel_launches", _i32, _vp, _vp, _vp)
+_sig("pr_batch_create", _i32, _u32, ctypes.c_uint64, _vp)
+_sig("pr_batch_set_tuning", _i32, _vp, _vp)
+_sig("pr_batch_get_tuning", _i32, _vp, _vp)
+_sig("pr_trace_batch", _i32, _vp, _u32, _vp, _vp, _vp)
+_sig("pr_trace_batch_graph", _i32, _vp, _u32, _vp, _vp, _vp)
+_sig("pr_batch_autotune", _i32, _vp, _u32, _vp, _vp, _vp, _vp)
+_sig("pr_batch_device_bytes", ctypes.c_size_t, _vp)
+_sig("pr_batch_destroy", None, _vp)
 _sig("pr_scene_destroy", None, _vp)
 
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
             "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
-            "pr_scene_destroy"]
+            "pr_scene_destroy", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
+            "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy"]
 
 
 def _check(status: int, where: str):
@@ -281,6 +290,73 @@ class Scene:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             _lib.pr_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("camera", _Camera), ("params", _TraceParams), ("out_rgba", ctypes.c_void_p)]
+
+
+class _BatchTuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("struct_size", "ctas_per_sm", "tile_w", "tile_h", "queue_chunk")]
+
+
+class Batch:
+    """Batched wavefront renderer (pr_batch): many requests, one set of persistent kernels."""
+
+    def __init__(self, max_requests: int, max_pixels: int):
+        self._h = ctypes.c_void_p()
+        _check(_lib.pr_batch_create(max_requests, max_pixels, ctypes.byref(self._h)), "pr_batch_create")
+        self._keep = None
+
+    @staticmethod
+    def _requests(items):
+        """items: sequence of (Scene, camera, params, out_tensor)."""
+        arr = (_Request * len(items))()
+        for k, (sc, cam, tp, out) in enumerate(items):
+            arr[k].scene = sc._h.value
+            arr[k].camera = _camera(cam)
+            arr[k].params = trace_params(tp, False)
+            arr[k].out_rgba = out.data_ptr()
+        return arr
+
+    def trace(self, items, ray_counter=None, stream=None, graph: bool = False):
+        arr = self._requests(items)
+        self._keep = arr
+        fn = _lib.pr_trace_batch_graph if graph else _lib.pr_trace_batch
+        _check(fn(self._h, len(items), arr, _dptr(ray_counter), _stream_handle(stream)),
+               "pr_trace_batch_graph" if graph else "pr_trace_batch")
+
+    def autotune(self, items, stream=None):
+        arr = self._requests(items)
+        best = _BatchTuning()
+        ms = ctypes.c_float()
+        _check(_lib.pr_batch_autotune(self._h, len(items), arr, _stream_handle(stream), ctypes.byref(best),
+                                      ctypes.byref(ms)), "pr_batch_autotune")
+        return dict(ctas_per_sm=best.ctas_per_sm, tile_w=best.tile_w, tile_h=best.tile_h,
+                    queue_chunk=best.queue_chunk), float(ms.value)
+
+    def set_tuning(self, ctas_per_sm, tile_w, tile_h, queue_chunk):
+        t = _BatchTuning(ctypes.sizeof(_BatchTuning), ctas_per_sm, tile_w, tile_h, queue_chunk)
+        _check(_lib.pr_batch_set_tuning(self._h, ctypes.byref(t)), "pr_batch_set_tuning")
+
+    def tuning(self) -> dict:
+        t = _BatchTuning()
+        _check(_lib.pr_batch_get_tuning(self._h, ctypes.byref(t)), "pr_batch_get_tuning")
+        return dict(ctas_per_sm=t.ctas_per_sm, tile_w=t.tile_w, tile_h=t.tile_h, queue_chunk=t.queue_chunk)
+
+    def device_bytes(self) -> int:
+        return int(_lib.pr_batch_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.pr_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

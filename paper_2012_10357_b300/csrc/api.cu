@@ -277,6 +277,10 @@ bool params_ok(const pr_trace_params* p) {
 
 }  // namespace
 
+pr::SceneView pr_internal_view(const pr_scene* s) { return view_of(s); }
+bool pr_internal_built(const pr_scene* s) { return s && s->built; }
+void pr_internal_set_error(const std::string& msg) { g_last_error = msg; }
+
 extern "C" {
 
 uint32_t pr_version(void) { return PR_ABI_VERSION; }

@@ -64,3 +64,12 @@ struct TraceLaunch {
 int launch_trace(const TraceLaunch& L, cudaStream_t s);
 
 }  // namespace pr
+
+// Accessors the batch path needs from a scene (api.cu).
+pr::SceneView pr_internal_view(const pr_scene* s);
+bool pr_internal_built(const pr_scene* s);
+void pr_internal_set_error(const std::string& msg);
+
+namespace pr {
+
+}  // namespace pr

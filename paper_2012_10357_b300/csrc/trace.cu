@@ -9,16 +9,10 @@
 
 #include "internal.h"
 #include "shaders.cuh"
+#include "tracer.cuh"
 
 namespace pr {
 namespace {
-
-struct Hit {
-  float t;
-  int inst;        // instance index, -1 = none
-  int leaf;        // flattened BLAS leaf
-  uint32_t attr;   // intersection attribute
-};
 
 struct Params {
   SceneView S;
@@ -31,236 +25,6 @@ struct Params {
   pr_aov* aov;
   unsigned long long* counter;
 };
-
-__device__ __forceinline__ bool key_less(int i0, uint2 gq0, int i1, uint2 gq1) {
-  if (i0 != i1) return i0 < i1;
-  if (gq0.x != gq1.x) return gq0.x < gq1.x;
-  return gq0.y < gq1.y;
-}
-
-__device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3 o_inv, float tmin, float tmax,
-                                           float& l0, float& l1, float& r0, float& r1, int& lref, int& rref) {
-  float4 a = __ldg(n), b = __ldg(n + 1), c = __ldg(n + 2), e = __ldg(n + 3);
-  slab(f3(a.x, a.y, a.z), f3(a.w, b.x, b.y), inv_d, o_inv, l0, l1);
-  slab(f3(b.z, b.w, c.x), f3(c.y, c.z, c.w), inv_d, o_inv, r0, r1);
-  l0 = fmaxf(l0, tmin);
-  l1 = fminf(l1, tmax);
-  r0 = fmaxf(r0, tmin);
-  r1 = fminf(r1, tmax);
-  lref = __float_as_int(e.x);
-  rref = __float_as_int(e.y);
-}
-
-// Intersection shader dispatch on the hit group's shader id.
-__device__ __forceinline__ bool run_intersection(uint32_t is_id, const float4* prm, float3 o, float3 d, float tmin,
-                                                 float t_lo, float t_hi, float eps, uint32_t max_steps, IsResult& r,
-                                                 WorkCounters* wc) {
-  if (wc) ++wc->is_calls[is_id < PR_IS_COUNT ? is_id : 0];
-  switch (is_id) {
-    case PR_IS_SPHERE: return is_sphere(__ldg(prm), o, d, tmin, r);
-    case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, tmin, r);
-    case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r);
-    default:
-      if (is_sphere_traced(is_id)) {
-        float4 p[4] = {__ldg(prm), __ldg(prm + 1), __ldg(prm + 2), __ldg(prm + 3)};
-        return sphere_trace(is_id, p, o, d, rsqrtf(dot3(d, d)), t_lo, t_hi, eps, max_steps, r, wc);
-      }
-      return false;
-  }
-}
-
-__device__ __forceinline__ void to_object(const SceneView& S, int k, float3 o, float3 d, float3& oo, float3& dd) {
-  float4 m0 = __ldg(S.inst_w2o + 3 * k), m1 = __ldg(S.inst_w2o + 3 * k + 1), m2 = __ldg(S.inst_w2o + 3 * k + 2);
-  oo = f3(fmaf(m0.x, o.x, fmaf(m0.y, o.y, fmaf(m0.z, o.z, m0.w))), fmaf(m1.x, o.x, fmaf(m1.y, o.y, fmaf(m1.z, o.z, m1.w))),
-          fmaf(m2.x, o.x, fmaf(m2.y, o.y, fmaf(m2.z, o.z, m2.w))));
-  dd = f3(fmaf(m0.x, d.x, fmaf(m0.y, d.y, m0.z * d.z)), fmaf(m1.x, d.x, fmaf(m1.y, d.y, m1.z * d.z)),
-          fmaf(m2.x, d.x, fmaf(m2.y, d.y, m2.z * d.z)));
-}
-
-// BLAS traversal of instance k (object-space ray; t shared with world space
-// because the direction is not renormalised). Returns true if any-hit mode
-// found a hit.
-template <bool kAny, bool kStats>
-__device__ bool traverse_blas(const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
-                              uint32_t max_steps, Hit& h, int* stack, int sp0, WorkCounters* wc_) {
-  WorkCounters* wc = kStats ? wc_ : nullptr;
-  if (wc) ++wc->instances;
-  uint4 info = __ldg(S.inst_info + k);
-  if ((info.w & 0xFFu) == 0u) return false;
-  float3 oo, dd;
-  to_object(S, k, o, d, oo, dd);
-  float3 inv = safe_rcp(dd);
-  float3 o_inv = f3(-oo.x * inv.x, -oo.y * inv.y, -oo.z * inv.z);
-  const int4 bi = __ldg(S.blas_info + info.x);
-  {
-    float4 blo = __ldg(S.blas_box + 2 * info.x), bhi = __ldg(S.blas_box + 2 * info.x + 1);
-    float t0, t1;
-    slab(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, t0, t1);
-    if (fmaxf(t0, tmin) > fminf(t1, h.t)) return false;
-  }
-  int sp = sp0;
-  int node = bi.w;
-  for (;;) {
-    if (node >= 0) {
-      float l0, l1, r0, r1;
-      int lref, rref;
-      if (wc) ++wc->blas_nodes;
-      node_boxes(S.blas_nodes + 4 * (size_t)(bi.x + node), inv, o_inv, tmin, h.t, l0, l1, r0, r1, lref, rref);
-      bool hl = l0 <= l1, hr = r0 <= r1;
-      if (hl && hr) {
-        int nearr = lref, farr = rref;
-        if (r0 < l0) { nearr = rref; farr = lref; }
-        if (sp < kStackDepth) stack[sp++] = farr;
-        else atomicOr(S.error_word, kErrStack);
-        node = nearr;
-        continue;
-      }
-      if (hl) { node = lref; continue; }
-      if (hr) { node = rref; continue; }
-    } else {
-      int leaf = node & 0x7FFFFFFF;
-      if (wc) ++wc->leaves;
-      uint32_t prim = __ldg(S.leaf_prim + leaf);
-      const float* bb = S.aabbs + 6 * (size_t)prim;
-      float te, tx;
-      slab(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv, te,
-           tx);
-      float t_lo = fmaxf(te, tmin), t_hi = fminf(tx, h.t);
-      if (t_lo <= t_hi) {
-        uint2 gq = __ldg(S.leaf_gq + leaf);
-        if (wc) ++wc->sbt_lookups;
-        uint32_t rec = r + S.sbt_stride_m * gq.x + info.y;
-        if (rec >= S.n_records) {
-          atomicOr(S.error_word, kErrSbt);
-        } else {
-          uint4 sr = __ldg(S.sbt + rec);
-          uint32_t is_id = __ldg(S.hit_groups + sr.x).x;
-          IsResult res;
-          if (run_intersection(is_id, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
-              res.t >= tmin) {
-            bool accept = res.t < h.t;
-            if (!accept && res.t == h.t && h.inst >= 0) accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + h.leaf));
-            if (accept) {
-              h.t = res.t;
-              h.inst = k;
-              h.leaf = leaf;
-              h.attr = res.attr;
-              if (kAny) return true;
-            }
-          }
-        }
-      }
-    }
-    if (sp == sp0) break;
-    node = stack[--sp];
-  }
-  return false;
-}
-
-// One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
-template <bool kAny, bool kStats>
-__device__ void trace_ray(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
-                          uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc_) {
-  WorkCounters* wc = kStats ? wc_ : nullptr;
-  if (wc) ++wc->rays;
-  h.t = tmax;
-  h.inst = -1;
-  h.leaf = -1;
-  h.attr = 0;
-  if (S.n_inst == 0) return;
-  float3 inv = safe_rcp(d);
-  float3 o_inv = f3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
-  int sp = 0;
-  int node = S.tlas_root_ref;
-  for (;;) {
-    if (node >= 0) {
-      float l0, l1, r0, r1;
-      int lref, rref;
-      if (wc) ++wc->tlas_nodes;
-      node_boxes(S.tlas_nodes + 4 * (size_t)node, inv, o_inv, tmin, h.t, l0, l1, r0, r1, lref, rref);
-      bool hl = l0 <= l1, hr = r0 <= r1;
-      if (hl && hr) {
-        int nearr = lref, farr = rref;
-        if (r0 < l0) { nearr = rref; farr = lref; }
-        if (sp < kStackDepth) stack[sp++] = farr;
-        else atomicOr(S.error_word, kErrStack);
-        node = nearr;
-        continue;
-      }
-      if (hl) { node = lref; continue; }
-      if (hr) { node = rref; continue; }
-    } else {
-      if (traverse_blas<kAny, kStats>(S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
-    }
-    if (sp == 0) break;
-    node = stack[--sp];
-  }
-}
-
-template <bool kStats>
-__device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
-                                            float eps, uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc) {
-  if (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT)
-    trace_ray<true, kStats>(S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
-  else
-    trace_ray<false, kStats>(S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
-}
-
-struct Surface {
-  float3 n;        // world shading normal facing the ray
-  float3 albedo;
-  float kr;
-  uint32_t chs, is_id;
-  uint32_t geom, prim;
-};
-
-// Closest-hit inputs of an accepted radiance hit: record (Eq. 1 with r = 0),
-// object-space normal, world normal through the inverse transpose.
-__device__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
-  if (wc) ++wc->shaded;
-  Surface sf;
-  uint4 info = __ldg(S.inst_info + h.inst);
-  uint2 gq = __ldg(S.leaf_gq + h.leaf);
-  uint32_t prim = __ldg(S.leaf_prim + h.leaf);
-  uint32_t rec = 0u + S.sbt_stride_m * gq.x + info.y;
-  uint4 sr = __ldg(S.sbt + rec);
-  uint4 hg = __ldg(S.hit_groups + sr.x);
-  float4 mat = __ldg(S.materials + sr.y);
-  float3 oo, dd;
-  to_object(S, h.inst, o, d, oo, dd);
-  float3 p = madd(oo, h.t, dd);
-  const float4* pp = S.params + 4 * (size_t)prim;
-  float4 prm[4] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2), __ldg(pp + 3)};
-  float hstep = eps * len3(dd);
-  float3 no = object_normal(hg.x, prm, p, h.attr, hstep, dd, wc);
-  float4 m0 = __ldg(S.inst_w2o + 3 * h.inst), m1 = __ldg(S.inst_w2o + 3 * h.inst + 1),
-         m2 = __ldg(S.inst_w2o + 3 * h.inst + 2);
-  float3 nw = f3(fmaf(m0.x, no.x, fmaf(m1.x, no.y, m2.x * no.z)), fmaf(m0.y, no.x, fmaf(m1.y, no.y, m2.y * no.z)),
-                 fmaf(m0.z, no.x, fmaf(m1.z, no.y, m2.z * no.z)));
-  nw = normalize3(nw);
-  if (dot3(nw, d) > 0.f) nw = -nw;
-  sf.n = nw;
-  sf.albedo = f3(mat.x, mat.y, mat.z);
-  sf.kr = mat.w;
-  sf.chs = hg.y;
-  sf.is_id = hg.x;
-  sf.geom = gq.x;
-  sf.prim = gq.y;
-  return sf;
-}
-
-__device__ __forceinline__ float3 lambert(const Params& P, const Surface& sf, float3 pt, float vis, float* ndl_out) {
-  float3 l = normalize3(P.light - pt);
-  float ndl = dot3(sf.n, l);
-  if (ndl_out) *ndl_out = ndl;
-  float diff = P.light_intensity * fmaxf(0.f, ndl) * vis;
-  return f3(sf.albedo.x * P.ambient + sf.albedo.x * diff, sf.albedo.y * P.ambient + sf.albedo.y * diff,
-            sf.albedo.z * P.ambient + sf.albedo.z * diff);
-}
-
-__device__ __forceinline__ float3 miss_color(const Params& P, uint32_t r) {
-  return __ldg(P.S.ray_types + r).x == PR_MISS_BACKGROUND ? P.background : f3(0.f, 0.f, 0.f);
-}
 
 template <bool kStats>
 __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* work) {
@@ -277,17 +41,9 @@ __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* wor
   if (valid) {
     int stack[kStackDepth];
     const pr_camera cam = P.cams ? P.cams[frame] : P.cam0;
-    float3 eye = ldf3(cam.eye);
-    float3 fwd = normalize3(ldf3(cam.look_at) - eye);
-    float3 right = normalize3(cross3(ldf3(cam.up), fwd));
-    float3 up = cross3(fwd, right);
-    float th = tanf(cam.vfov_deg * 0.008726646259971648f);   // pi / 360
-    float aspect = (float)P.width / (float)P.height;
-    float ndc_x = (((float)x + 0.5f) / (float)P.width * 2.f - 1.f) * th * aspect;
-    float ndc_y = -(((float)y + 0.5f) / (float)P.height * 2.f - 1.f) * th;
-    float3 d = normalize3(fwd + right * ndc_x + up * ndc_y);
-    float3 lo = ldf3(S.scene_box), hi = ldf3(S.scene_box + 4);
-    const float eps = P.eps_rel * len3(hi - lo);
+    const float3 eye = ldf3(cam.eye);
+    const float3 d = camera_ray(cam, x, y, P.width, P.height);
+    const float eps = scene_eps(S, P.eps_rel);
 
     Hit h;
     rays = 1;
@@ -301,7 +57,7 @@ __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* wor
     av.refl_t = -1.f;
     av.refl_inst = av.refl_geom = av.refl_prim = PR_NONE;
     if (h.inst < 0) {
-      color = miss_color(P, 0);
+      color = miss_rgb(S, 0, P.background);
     } else {
       flags |= 1u;
       Surface sf = surface_at(S, h, eye, d, eps, wc);
@@ -313,12 +69,12 @@ __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* wor
       if (sf.chs != PR_CHS_LAMBERT) {
         color = f3(0.f, 0.f, 0.f);
       } else {
-        float3 pt = madd(eye, h.t, d);
-        float delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
-        float ndl;
-        lambert(P, sf, pt, 1.f, &ndl);
+        const float3 pt = madd(eye, h.t, d);
+        const float delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
+        const float ndl = light_ndl(sf, P.light, pt);
         float vis = 1.f;
         if (ndl > 0.f) {
+          // shadow ray: offset origin, toward the light, ends at the light
           float3 os = madd(pt, delta, sf.n);
           float3 ls = P.light - os;
           float dist = len3(ls);
@@ -329,8 +85,9 @@ __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* wor
           vis = sh.inst >= 0 ? 0.f : 1.f;
           if (sh.inst < 0) flags |= 4u;
         }
-        color = lambert(P, sf, pt, vis, nullptr);
+        color = lambert_rgb(sf.albedo, P.ambient, P.light_intensity, ndl, vis);
         if (P.max_depth >= 2 && sf.kr > 0.f) {
+          // one mirror bounce, its hit shaded without a shadow ray
           float3 orr = madd(pt, delta, sf.n);
           float3 dr = normalize3(d - sf.n * (2.f * dot3(d, sf.n)));
           Hit rh;
@@ -345,11 +102,13 @@ __global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* wor
             av.refl_inst = (uint32_t)rh.inst;
             av.refl_geom = s2.geom;
             av.refl_prim = s2.prim;
-            lr = s2.chs == PR_CHS_LAMBERT ? lambert(P, s2, madd(orr, rh.t, dr), 1.f, nullptr) : f3(0.f, 0.f, 0.f);
+            lr = s2.chs == PR_CHS_LAMBERT
+                     ? lambert_rgb(s2.albedo, P.ambient, P.light_intensity, light_ndl(s2, P.light, madd(orr, rh.t, dr)), 1.f)
+                     : f3(0.f, 0.f, 0.f);
           } else {
-            lr = miss_color(P, 0);
+            lr = miss_rgb(S, 0, P.background);
           }
-          color = color * (1.f - sf.kr) + lr * sf.kr;
+          color = mirror_mix(color, lr, sf.kr);
         }
       }
     }

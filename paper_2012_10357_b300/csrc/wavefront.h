@@ -1,0 +1,51 @@
+// Device-side layout of the batched wavefront path.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pr_device.cuh"
+
+namespace pr {
+
+// One request as the kernels see it (copied to shared memory per tile).
+struct ReqDev {
+  SceneView S;
+  pr_camera cam;
+  float3 light, background;
+  float light_intensity, eps_rel, ambient;
+  uint32_t width, height, max_depth, max_steps;
+  uint32_t tile_begin, tiles_x;
+  float4* out;
+  uint64_t pixel_begin;
+};
+
+// Counters and totals of the current batch (device memory).
+struct BatchHdr {
+  uint32_t n_req, total_tiles;
+  uint64_t total_pixels;
+  uint32_t tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr, pad;
+  unsigned long long* counter;   // rays traced (optional)
+};
+
+struct BatchView {
+  BatchHdr* hdr;
+  const ReqDev* reqs;
+  float4* st_a;       // [pixels] albedo rgb, reflectance
+  uint2* st_b;        // [pixels] n.l bits, flags
+  float4* refl;       // [pixels] mirror radiance
+  float4 *sq_a, *sq_b;  // shadow queue: origin+tmax, direction
+  uint64_t* sq_px;
+  uint32_t* sq_req;
+  float4 *mq_a, *mq_b;  // mirror queue
+  uint64_t* mq_px;
+  uint32_t* mq_req;
+};
+
+struct BatchTuning {
+  uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
+};
+
+int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, cudaStream_t s);
+
+}  // namespace pr

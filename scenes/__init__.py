@@ -439,10 +439,14 @@ def instanced_field(seed: int, n_inst: int, side: float, origin=(0.0, 0.0, 0.0),
     pos = rng.uniform(0.0, side, (n_inst, 3)) + np.asarray(origin)
     scale = np.exp(rng.uniform(math.log(0.1), math.log(2.0), n_inst))
     quats = random_quats(rng, n_inst)
+    w, x, y, z = quats.T
+    rot = np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
     xf = np.zeros((n_inst, 3, 4), np.float64)
-    for k in range(n_inst):
-        xf[k, :, :3] = quat_to_mat(quats[k]) * scale[k]
-        xf[k, :, 3] = pos[k]
+    xf[:, :, :3] = rot * scale[:, None, None]
+    xf[:, :, 3] = pos
     scene = b.build(name)
     scene.inst_xform = xf.reshape(n_inst, 12).astype(np.float32)
     scene.inst_blas = types.astype(np.uint32)

@@ -1,0 +1,127 @@
+"""Batched wavefront path vs the plain per-request path (and the oracle), on a B300.
+
+Every request of a batch must come out bit-identical to a pr_trace of it:
+both paths share the per-pixel device functions and the shading composition
+is explicitly rounded. The plain path is itself held to the oracle by
+test_gpu_parity.py; one request here is also compared with the oracle directly.
+"""
+import numpy as np
+import pytest
+
+import scenes
+from parity import assert_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2012_10357_b300 as pr  # noqa: E402
+import oracle  # noqa: E402
+
+
+def _mixed_workloads():
+    ws = [scenes.config1(width=67, height=45), scenes.config2(width=200, height=113),
+          scenes.config3(n_inst=3000, width=150, height=97), scenes.config1(seed=4, width=1, height=1),
+          scenes.config2(seed=2, width=33, height=250)]
+    ws += scenes.config4_requests(seed=0, n_requests=6, res_choices=(64, 96, 128))
+    return ws
+
+
+def _plain(scene_objs, ws):
+    outs, rays = [], 0
+    for sc, w in zip(scene_objs, ws):
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        outs.append(sc.trace(w.camera, w.params, ray_counter=c))
+        torch.cuda.synchronize()
+        rays += int(c.item())
+    return outs, rays
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_bit_identical_to_plain(graph):
+    ws = _mixed_workloads()
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, plain_rays = _plain(objs, ws)
+    total = sum(w.params.width * w.params.height for w in ws)
+    batch = pr.Batch(len(ws), total)
+    outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for w in ws]
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], ray_counter=counter, graph=graph)
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(zip(plain, outs)):
+        assert torch.equal(a, b), f"request {k} differs (max {float((a - b).abs().max())})"
+    assert int(counter.item()) == plain_rays
+    # a second launch through the same batch (graph replay / table restaging) gives the same bits
+    for out in outs:
+        out.fill_(-1.0)
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], graph=graph)
+    torch.cuda.synchronize()
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+    batch.close()
+
+
+@pytest.mark.parametrize("shape", [(2, 16, 8, 32), (8, 32, 4, 128), (16, 8, 16, 64), (1, 16, 8, 1024)])
+def test_batch_launch_shapes_do_not_change_results(shape):
+    ws = _mixed_workloads()[:5]
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, _ = _plain(objs, ws)
+    batch = pr.Batch(8, sum(w.params.width * w.params.height for w in ws))
+    batch.set_tuning(*shape)
+    assert batch.tuning() == dict(zip(("ctas_per_sm", "tile_w", "tile_h", "queue_chunk"), shape))
+    outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)])
+    torch.cuda.synchronize()
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_results():
+    ws = _mixed_workloads()
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, _ = _plain(objs, ws)
+    batch = pr.Batch(len(ws), sum(w.params.width * w.params.height for w in ws))
+    outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+    items = [(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)]
+    best, ms = batch.autotune(items)
+    assert ms > 0 and best == batch.tuning()
+    batch.trace(items, graph=True)
+    torch.cuda.synchronize()
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+
+
+def test_batch_request_vs_oracle():
+    w = scenes.config2(width=160, height=90)
+    sc = pr.Scene(w.scene)
+    batch = pr.Batch(2, 2 * 160 * 90)
+    out = torch.empty((90, 160, 4), device="cuda")
+    out2 = torch.empty((90, 160, 4), device="cuda")
+    batch.trace([(sc, w.camera, w.params, out), (sc, w.camera, w.params, out2)])
+    _, aov = sc.trace(w.camera, w.params, want_aov=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    box = sc.bounds()
+    rep = compare(oracle.render(w), pr.aov_to_numpy(aov), out[..., :3].cpu().numpy(),
+                  float(np.linalg.norm(box[3:] - box[:3])))
+    assert_parity(rep, "batched config2 160x90")
+
+
+def test_batch_budget_and_argument_errors():
+    w = scenes.config1()
+    sc = pr.Scene(w.scene)
+    out = torch.empty((64, 64, 4), device="cuda")
+    batch = pr.Batch(2, 1000)                     # fewer pixels than one 64x64 request
+    with pytest.raises(pr.PrError) as ei:
+        batch.trace([(sc, w.camera, w.params, out)])
+    assert ei.value.status == pr.PR_ERR_BUDGET
+    with pytest.raises(pr.PrError):
+        pr.Batch(1, 4096).trace([(sc, w.camera, w.params, out)] * 2)   # more requests than max_requests
+    with pytest.raises(pr.PrError):
+        batch.set_tuning(4, 16, 16, 64)                                  # unsupported tile
+    unbuilt = pr.Scene(w.scene, build=False)
+    with pytest.raises(pr.PrError) as ei:
+        pr.Batch(1, 4096).trace([(unbuilt, w.camera, w.params, out)])
+    assert ei.value.status == pr.PR_ERR_NOT_BUILT

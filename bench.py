@@ -118,6 +118,115 @@ def measured_peaks() -> dict:
     return {}
 
 
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def bench_config1_throughput(pr, work, torch, stream, flush, frames=4096, reps=5) -> dict:
+    """Config 1 as a throughput run: 4096 eye-jittered 64x64 frames in one launch."""
+    w = scenes.config1()
+    cams = scenes.config1_cameras(0, frames)
+    with torch.cuda.stream(stream):
+        scene = pr.Scene(w.scene, stream=stream)
+        out = torch.empty((frames, 64, 64, 4), dtype=torch.float32, device="cuda")
+        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        scene.trace_frames(cams, w.params, out=out, stream=stream)
+    stream.synchronize()
+    ev = _events(torch, 2 * reps)
+    with torch.cuda.stream(stream):
+        for k in range(reps):
+            flush.fill_(float(k))
+            ev[2 * k].record(stream)
+            scene.trace_frames(cams, w.params, out=out, ray_counter=counter, stream=stream)
+            ev[2 * k + 1].record(stream)
+    stream.synchronize()
+    ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)]
+    rays = int(counter.item()) / reps
+    counters = scene.trace_work(None, w.params, out=out, cameras=cams, stream=stream)
+    flops = work.frame_flops(counters)
+    avg_s = statistics.mean(ms) / 1e3
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = work.fp32_peak_tflops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz", 2032.0)))
+    scene.close()
+    return {"workload": "config1: 4096 eye-jittered 64x64 frames, one pr_trace_frames launch",
+            "value": rays / avg_s / 1e6, "unit": "Mrays/s", "ms_per_launch": statistics.mean(ms),
+            "rays_per_launch": rays,
+            "roofline": {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / avg_s / 1e12 / peak, "flops_per_launch": flops}}
+
+
+def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
+    """Config 4: 64 requests of uneven size, one batched wavefront launch (CUDA
+    graph, autotuned launch shape) vs 64 plain per-request launches."""
+    ws = scenes.config4_requests(0, n_requests)
+    total_px = sum(w.params.width * w.params.height for w in ws)
+    with torch.cuda.stream(stream):
+        objs = [pr.Scene(w.scene, stream=stream) for w in ws]
+        outs_plain = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+        outs_batch = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    batch = pr.Batch(n_requests, total_px)
+    items = [(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs_batch)]
+    tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
+    key = f"{torch.cuda.get_device_name()}|config4|{n_requests}|{total_px}"
+    cache = json.load(open(tune_path)) if os.path.exists(tune_path) else {}
+    if key in cache:
+        batch.set_tuning(**cache[key]["tuning"])
+        tuned = dict(cache[key], from_cache=True)
+    else:
+        best, best_ms = batch.autotune(items, stream=stream)
+        tuned = {"tuning": best, "ms": best_ms, "from_cache": False}
+        cache[key] = {"tuning": best, "ms": best_ms}
+        with open(tune_path, "w") as f:
+            json.dump(cache, f, indent=1)
+
+    def plain_once(record=None):
+        for k, (o, w, out) in enumerate(zip(objs, ws, outs_plain)):
+            o.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+            if record is not None:
+                record[k].record(stream)
+
+    # warm both paths
+    plain_once()
+    batch.trace(items, stream=stream, graph=True)
+    stream.synchronize()
+    res = {}
+    for mode in ("plain", "batched_graph", "batched_direct"):
+        counter.zero_()
+        totals, lat = [], []
+        for rep in range(reps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(rep))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            done = _events(torch, n_requests if mode == "plain" else 1)
+            ev0.record(stream)
+            if mode == "plain":
+                plain_once(done)
+            else:
+                batch.trace(items, ray_counter=counter, stream=stream, graph=(mode == "batched_graph"))
+                done[0].record(stream)
+            stream.synchronize()
+            t = [ev0.elapsed_time(e) for e in done]
+            totals.append(t[-1])
+            lat += t if mode == "plain" else [t[0]] * n_requests
+        rays = int(counter.item()) / reps
+        res[mode] = {"value": rays / (statistics.mean(totals) / 1e3) / 1e6, "unit": "Mrays/s",
+                     "ms_per_batch": statistics.mean(totals), "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "rays_per_batch": rays}
+    identical = all(torch.equal(a, b) for a, b in zip(outs_plain, outs_batch))
+    out = {"workload": f"config4: {n_requests} requests, resolutions from {{256^2..2048^2}}, "
+                       f"1..10000 instances each, {total_px} pixels",
+           "plain": res["plain"], "batched_graph": res["batched_graph"], "batched_direct": res["batched_direct"],
+           "speedup_graph_vs_plain": res["plain"]["ms_per_batch"] / res["batched_graph"]["ms_per_batch"],
+           "images_identical_to_plain": identical, "autotune": tuned,
+           "batch_device_bytes": batch.device_bytes()}
+    batch.close()
+    for o in objs:
+        o.close()
+    return out
+
+
 def cpu_baseline(w, budget_s: float = 15.0) -> dict:
     """The FP64 oracle, as it stands, on a seeded pixel sample of the same frame."""
     import oracle
@@ -290,6 +399,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(desc_bytes), "d2h_bytes_per_step": int(H * W * 16),
                "ms_per_step": 1e3 * statistics.mean(e2e_times)}
 
+    extra = {}
+    if not args.no_extra:
+        extra["config1_throughput"] = bench_config1_throughput(pr, work, torch, stream, flush)
+        extra["batched"] = bench_batched(pr, torch, stream, flush)
+
     line = {
         "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_all / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -303,6 +417,7 @@ def run_ours(args):
         "gpu_launches": (n_build + n_trace) * args.steps,
         "clocks": clocks,
         "device_error_word": err,
+        **extra,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_budget)
@@ -321,6 +436,7 @@ def main():
     ap.add_argument("--workload", choices=["config1", "config2", "config3"], default="config2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config-1 throughput and batched blocks")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -201,11 +201,11 @@ pr_status pr_trace_frames(pr_scene* scene, const pr_camera* cameras, uint32_t n_
  * iterations, Mandelbulb iterations, shaded hits, rays traced. */
 #define PR_WORK_COUNTERS 27u
 
-/* pr_trace with an instrumented kernel variant that also adds the work it did
- * to work_counters (device, PR_WORK_COUNTERS uint64, caller-zeroed). It
- * produces the same image; it is slower and meant for roofline accounting. */
-pr_status pr_trace_work(pr_scene* scene, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
-                        uint64_t* work_counters, void* stream);
+/* pr_trace_frames with an instrumented kernel variant that also adds the
+ * work it did to work_counters (device, PR_WORK_COUNTERS uint64,
+ * caller-zeroed). Same images; slower; meant for roofline accounting. */
+pr_status pr_trace_work(pr_scene* scene, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
+                        float* out_rgba, uint64_t* work_counters, void* stream);
 
 /* Read and clear the scene's device error word on `stream` (synchronises the
  * stream). Bits: 1<<PR_ERR_SBT_INDEX, 1<<PR_ERR_STACK_OVERFLOW. */

@@ -86,7 +86,7 @@ _sig("pr_scene_upload", _i32, _vp, _vp, _vp)
 _sig("pr_build_bvh", _i32, _vp, _vp)
 _sig("pr_trace", _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_trace_frames", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
-_sig("pr_trace_work", _i32, _vp, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_trace_work", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp)
 _sig("pr_scene_error", _i32, _vp, _vp, _vp)
 _sig("pr_scene_bounds", _i32, _vp, _vp, _vp)
 _sig("pr_scene_read_bvh", _i32, _vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp)
@@ -239,15 +239,17 @@ class Scene:
                                     _stream_handle(stream)), "pr_trace_frames")
         return (out, aov) if aov is not None else out
 
-    def trace_work(self, camera, params, out=None, stream=None) -> dict:
-        """Instrumented trace: returns the work counters (see PR_WORK_COUNTERS)."""
+    def trace_work(self, camera, params, out=None, stream=None, cameras=None) -> dict:
+        """Instrumented trace (one camera, or a list of cameras for a multi-frame
+        launch): returns the work counters (see PR_WORK_COUNTERS)."""
         import torch
+        cams = [camera] if cameras is None else list(cameras)
         if out is None:
-            out = torch.empty((params.height, params.width, 4), dtype=torch.float32, device="cuda")
+            out = torch.empty((len(cams), params.height, params.width, 4), dtype=torch.float32, device="cuda")
         work = torch.zeros(len(WORK_FIELDS), dtype=torch.int64, device="cuda")
-        cam = _camera(camera)
+        arr = (_Camera * len(cams))(*[_camera(c) for c in cams])
         tp = trace_params(params, False)
-        _check(_lib.pr_trace_work(self._h, ctypes.byref(cam), ctypes.byref(tp), _dptr(out), _dptr(work),
+        _check(_lib.pr_trace_work(self._h, arr, len(cams), ctypes.byref(tp), _dptr(out), _dptr(work),
                                   _stream_handle(stream)), "pr_trace_work")
         vals = work.cpu().tolist()
         return dict(zip(WORK_FIELDS, vals))

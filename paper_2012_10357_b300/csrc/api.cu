@@ -491,24 +491,7 @@ pr_status pr_trace(pr_scene* s, const pr_camera* camera, const pr_trace_params* 
   return trace_impl(s, camera, nullptr, 1, params, out_rgba, out_aov, ray_counter, (cudaStream_t)stream);
 }
 
-pr_status pr_trace_work(pr_scene* s, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,
-                        uint64_t* work_counters, void* stream) {
-  if (!s || !camera || !out_rgba || !work_counters) return fail(PR_ERR_INVALID_ARG, "null scene/camera/output/counters");
-  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
-  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_work before pr_build_bvh");
-  pr_trace_params q = *params;
-  q.flags &= ~PR_TRACE_WRITE_AOV;
-  return trace_impl(s, camera, nullptr, 1, &q, out_rgba, nullptr, nullptr, (cudaStream_t)stream, work_counters);
-}
-
-pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
-                          float* out_rgba, pr_aov* out_aov, uint64_t* ray_counter, void* stream) {
-  if (!s || !cameras || !out_rgba || n_frames == 0 || n_frames > 65535)
-    return fail(PR_ERR_INVALID_ARG, "null scene/cameras/output or n_frames outside 1..65535");
-  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
-  if ((params->flags & PR_TRACE_WRITE_AOV) && !out_aov) return fail(PR_ERR_INVALID_ARG, "AOV requested but null");
-  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_frames before pr_build_bvh");
-  cudaStream_t st = (cudaStream_t)stream;
+static pr_status upload_cameras(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, cudaStream_t st) {
   if (s->cams_cap < n_frames) {
     if (s->d_cams) {
       cudaStreamSynchronize(st);
@@ -521,6 +504,33 @@ pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_fram
   }
   PR_CUDA(cudaMemcpyAsync(s->d_cams, cameras, sizeof(pr_camera) * n_frames, cudaMemcpyHostToDevice, st),
           "copy cameras");
+  return PR_OK;
+}
+
+pr_status pr_trace_work(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
+                        float* out_rgba, uint64_t* work_counters, void* stream) {
+  if (!s || !cameras || !out_rgba || !work_counters || n_frames == 0 || n_frames > 65535)
+    return fail(PR_ERR_INVALID_ARG, "null scene/cameras/output/counters or n_frames outside 1..65535");
+  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_work before pr_build_bvh");
+  pr_trace_params q = *params;
+  q.flags &= ~PR_TRACE_WRITE_AOV;
+  cudaStream_t st = (cudaStream_t)stream;
+  pr_status u = upload_cameras(s, cameras, n_frames, st);
+  if (u != PR_OK) return u;
+  return trace_impl(s, cameras, s->d_cams, n_frames, &q, out_rgba, nullptr, nullptr, st, work_counters);
+}
+
+pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
+                          float* out_rgba, pr_aov* out_aov, uint64_t* ray_counter, void* stream) {
+  if (!s || !cameras || !out_rgba || n_frames == 0 || n_frames > 65535)
+    return fail(PR_ERR_INVALID_ARG, "null scene/cameras/output or n_frames outside 1..65535");
+  if (!params_ok(params)) return PR_ERR_INVALID_ARG;
+  if ((params->flags & PR_TRACE_WRITE_AOV) && !out_aov) return fail(PR_ERR_INVALID_ARG, "AOV requested but null");
+  if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_frames before pr_build_bvh");
+  cudaStream_t st = (cudaStream_t)stream;
+  pr_status u = upload_cameras(s, cameras, n_frames, st);
+  if (u != PR_OK) return u;
   return trace_impl(s, cameras, s->d_cams, n_frames, params, out_rgba, out_aov, ray_counter, st);
 }
 

@@ -228,6 +228,22 @@ pr_status pr_scene_read_bvh(pr_scene* scene, uint32_t level, void* stream, uint3
 /* Kernels enqueued by the scene's most recent pr_build_bvh and trace call. */
 pr_status pr_scene_kernel_launches(const pr_scene* scene, uint32_t* build_launches, uint32_t* trace_launches);
 
+/* Build one LBVH level over n device boxes (the device builder of
+ * pr_build_bvh on caller memory; Section 2.2.3's acceleration structure,
+ * here an LBVH: Morton codes of centroids, radix sort, Karras radix tree,
+ * bottom-up unions). Layouts, all device memory owned by the caller:
+ *   boxes     [n][6] float   lo.xyz, hi.xyz
+ *   nodes     [n-1][16] float, 16-byte aligned: two child boxes and the child
+ *             refs (>= 0 internal node, else 0x80000000 | box index); unused if n == 1
+ *   perm      [n] uint32     sorted position -> box index
+ *   codes     [n] uint32     Morton code by sorted position
+ *   root_box  [8] float, 16-byte aligned: lo.xyz, 0, hi.xyz, 0
+ * n <= 1024 builds in one CTA without scratch; larger n takes its scratch
+ * (about 28 bytes per box) from the stream-ordered pool with cudaMallocAsync
+ * and returns it with cudaFreeAsync on `stream`. Asynchronous. */
+pr_status pr_lbvh_build(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
+                        float* root_box, void* stream);
+
 /* ---- Batched requests (wavefront path) ---------------------------------
  * Requests of uneven size (each its own scene, camera and resolution) are
  * fused into one set of persistent kernels per bounce: a primary stage over

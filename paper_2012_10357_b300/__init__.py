@@ -92,6 +92,7 @@ _sig("pr_scene_bounds", _i32, _vp, _vp, _vp)
 _sig("pr_scene_read_bvh", _i32, _vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_scene_device_bytes", ctypes.c_size_t, _vp)
 _sig("pr_scene_kernel_launches", _i32, _vp, _vp, _vp)
+_sig("pr_lbvh_build", _i32, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_batch_create", _i32, _u32, ctypes.c_uint64, _vp)
 _sig("pr_batch_set_tuning", _i32, _vp, _vp)
 _sig("pr_batch_get_tuning", _i32, _vp, _vp)
@@ -105,7 +106,7 @@ _sig("pr_scene_destroy", None, _vp)
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
             "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
-            "pr_scene_destroy", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
+            "pr_scene_destroy", "pr_lbvh_build", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
             "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy"]
 
 
@@ -251,6 +252,7 @@ class Scene:
         tp = trace_params(params, False)
         _check(_lib.pr_trace_work(self._h, arr, len(cams), ctypes.byref(tp), _dptr(out), _dptr(work),
                                   _stream_handle(stream)), "pr_trace_work")
+        torch.cuda.synchronize()          # the launch stream may not be torch's current stream
         vals = work.cpu().tolist()
         return dict(zip(WORK_FIELDS, vals))
 
@@ -299,6 +301,31 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+def lbvh_build(boxes, stream=None) -> dict:
+    """LBVH over a float32 [n, 6] device tensor of boxes (pr_lbvh_build).
+    Returns device tensors: nodes [n-1, 16] float32, perm, codes [n] int32 views
+    of uint32, root [8] float32."""
+    import torch
+    n = int(boxes.shape[0])
+    assert boxes.is_cuda and boxes.dtype == torch.float32 and boxes.is_contiguous()
+    nodes = torch.empty((max(n - 1, 1), 16), dtype=torch.float32, device=boxes.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=boxes.device)
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=boxes.device)
+    root = torch.zeros(8, dtype=torch.float32, device=boxes.device)
+    _check(_lib.pr_lbvh_build(_dptr(boxes), n, _dptr(nodes), _dptr(perm), _dptr(codes), _dptr(root),
+                              _stream_handle(stream)), "pr_lbvh_build")
+    return dict(nodes=nodes[:max(n - 1, 0)], perm=perm[:n], codes=codes[:n], root=root)
+
+
+def lbvh_to_host(res) -> dict:
+    """Device LBVH tensors -> host arrays in the layout of Scene.read_bvh."""
+    nodes = res["nodes"].cpu().numpy()
+    child = nodes[:, 12:14].copy().view(np.int32)
+    root = res["root"].cpu().numpy()
+    return dict(perm=res["perm"].cpu().numpy().view(np.uint32), codes=res["codes"].cpu().numpy().view(np.uint32),
+                child=child, cbox=nodes[:, :12].copy(), root=np.concatenate([root[0:3], root[4:7]]))
 
 
 class _Request(ctypes.Structure):

@@ -277,6 +277,36 @@ bool params_ok(const pr_trace_params* p) {
 
 }  // namespace
 
+namespace pr {
+
+size_t build_scratch_bytes(uint32_t n) {
+  Carver c;
+  for (int k = 0; k < 4; ++k) c.take<uint32_t>(n);
+  c.take<uint32_t>(256 * (size_t)sort_tiles(n));
+  for (int k = 0; k < 3; ++k) c.take<uint32_t>(n);
+  c.take<float>(6 * (size_t)kMaxPartials);
+  return c.off;
+}
+
+BuildScratch carve_build_scratch(void* base, uint32_t n) {
+  Carver c;
+  char* A = (char*)base;
+  BuildScratch sc;
+  sc.keys[0] = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.keys[1] = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.vals[0] = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.vals[1] = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.hist = (uint32_t*)(A + c.take<uint32_t>(256 * (size_t)sort_tiles(n)));
+  sc.counters = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.parent_int = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.parent_leaf = (uint32_t*)(A + c.take<uint32_t>(n));
+  sc.partial = (float*)(A + c.take<float>(6 * (size_t)kMaxPartials));
+  sc.max_n = n;
+  return sc;
+}
+
+}  // namespace pr
+
 pr::SceneView pr_internal_view(const pr_scene* s) { return view_of(s); }
 bool pr_internal_built(const pr_scene* s) { return s && s->built; }
 void pr_internal_set_error(const std::string& msg) { g_last_error = msg; }
@@ -611,6 +641,37 @@ pr_status pr_scene_kernel_launches(const pr_scene* s, uint32_t* build_launches, 
   if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
   if (build_launches) *build_launches = (uint32_t)s->build_launches;
   if (trace_launches) *trace_launches = (uint32_t)s->trace_launches;
+  return PR_OK;
+}
+
+pr_status pr_lbvh_build(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
+                        float* root_box, void* stream) {
+  if (n == 0) return PR_OK;
+  if (!boxes || !perm || !codes || !root_box || (n > 1 && !nodes))
+    return fail(PR_ERR_INVALID_ARG, "pr_lbvh_build: null device pointer");
+  if (n > (1u << 28)) return fail(PR_ERR_INVALID_ARG, "pr_lbvh_build: more than 2^28 boxes");
+  if (((uintptr_t)nodes & 15) || ((uintptr_t)root_box & 15))
+    return fail(PR_ERR_INVALID_ARG, "pr_lbvh_build: nodes and root_box must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  LevelDesc J;
+  J.boxes = boxes;
+  J.gather = nullptr;
+  J.n = n;
+  J.leaf_ref_base = 0;
+  J.nodes = reinterpret_cast<float4*>(nodes);
+  J.perm = perm;
+  J.codes = codes;
+  J.root_box = root_box;
+  if (n <= kSmallMax) {
+    launch_build_small_one(J, st);
+  } else {
+    void* scratch = nullptr;
+    PR_CUDA(cudaMallocAsync(&scratch, build_scratch_bytes(n), st), "cudaMallocAsync LBVH scratch");
+    launch_build_large(J, carve_build_scratch(scratch, n), st);
+    PR_CUDA(cudaFreeAsync(scratch, st), "cudaFreeAsync LBVH scratch");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pr_lbvh_build launch");
   return PR_OK;
 }
 

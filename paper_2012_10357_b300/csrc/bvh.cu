@@ -114,8 +114,7 @@ __device__ __forceinline__ void karras_node(int i, int n, KeyFn key, int& first,
 }
 
 // ---- single-CTA build of a small level (n <= kSmallMax) --------------------
-__global__ void __launch_bounds__(256) k_build_small(const LevelDesc* jobs) {
-  const LevelDesc J = jobs[blockIdx.x];
+__device__ void build_small_body(const LevelDesc& J) {
   const uint32_t n = J.n;
   if (n == 0) return;
   __shared__ unsigned long long keys[kSmallMax];
@@ -201,6 +200,10 @@ __global__ void __launch_bounds__(256) k_build_small(const LevelDesc* jobs) {
     }
   }
 }
+
+__global__ void __launch_bounds__(256) k_build_small(const LevelDesc* jobs) { build_small_body(jobs[blockIdx.x]); }
+
+__global__ void __launch_bounds__(256) k_build_small_one(LevelDesc J) { build_small_body(J); }
 
 // ---- multi-kernel build of a large level ----------------------------------
 __global__ void __launch_bounds__(256) k_centroid_partial(LevelDesc J, float* partial) {
@@ -420,6 +423,12 @@ __global__ void __launch_bounds__(256) k_instances(const float* xform, const uin
 int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s) {
   if (n_jobs == 0) return 0;
   k_build_small<<<n_jobs, 256, 0, s>>>(d_jobs);
+  return 1;
+}
+
+int launch_build_small_one(const LevelDesc& J, cudaStream_t s) {
+  if (J.n == 0) return 0;
+  k_build_small_one<<<1, 256, 0, s>>>(J);
   return 1;
 }
 

@@ -282,7 +282,9 @@ struct WorkCounters {
 };
 static_assert(sizeof(WorkCounters) == 4 * PR_WORK_COUNTERS, "counter layout is part of the ABI");
 
-__device__ __forceinline__ float distance_estimate(uint32_t id, const float4* prm, float3 p, WorkCounters* wc = nullptr) {
+// One out-of-line copy of the estimators: every march and normal shares it,
+// which keeps the instruction footprint of the tracing kernels small.
+static __device__ __noinline__ float distance_estimate(uint32_t id, const float4* prm, float3 p, WorkCounters* wc = nullptr) {
   if (wc) ++wc->de_evals[id < PR_IS_COUNT ? id : 0];
   switch (id) {
     case PR_IS_TORUS: return sdf_torus(prm[0], p);

@@ -67,8 +67,8 @@ __device__ __forceinline__ void to_object(const SceneView& S, int k, float3 o, f
 // BLAS traversal of instance k (object-space ray; t shared with world space
 // because the direction is not renormalised). Returns true if any-hit mode
 // found a hit.
-template <bool kAny, bool kStats>
-__device__ bool traverse_blas(const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
+template <bool kStats>
+__device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
                               uint32_t max_steps, Hit& h, int* stack, int sp0, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->instances;
@@ -132,7 +132,7 @@ __device__ bool traverse_blas(const SceneView& S, int k, float3 o, float3 d, uin
               h.inst = k;
               h.leaf = leaf;
               h.attr = res.attr;
-              if (kAny) return true;
+              if (any_hit) return true;
             }
           }
         }
@@ -145,8 +145,8 @@ __device__ bool traverse_blas(const SceneView& S, int k, float3 o, float3 d, uin
 }
 
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
-template <bool kAny, bool kStats>
-__device__ void trace_ray(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
+template <bool kStats>
+__device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
                           uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->rays;
@@ -177,7 +177,7 @@ __device__ void trace_ray(const SceneView& S, float3 o, float3 d, uint32_t r, fl
       if (hl) { node = lref; continue; }
       if (hr) { node = rref; continue; }
     } else {
-      if (traverse_blas<kAny, kStats>(S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
+      if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -187,10 +187,8 @@ __device__ void trace_ray(const SceneView& S, float3 o, float3 d, uint32_t r, fl
 template <bool kStats>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
                                             float eps, uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc) {
-  if (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT)
-    trace_ray<true, kStats>(S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
-  else
-    trace_ray<false, kStats>(S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
+  const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
+  trace_ray<kStats>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
 }
 
 struct Surface {
@@ -203,7 +201,7 @@ struct Surface {
 
 // Closest-hit inputs of an accepted radiance hit: record (Eq. 1 with r = 0),
 // object-space normal, world normal through the inverse transpose.
-__device__ inline Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
+static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
   if (wc) ++wc->shaded;
   Surface sf;
   uint4 info = __ldg(S.inst_info + h.inst);

@@ -244,6 +244,28 @@ pr_status pr_scene_kernel_launches(const pr_scene* scene, uint32_t* build_launch
 pr_status pr_lbvh_build(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
                         float* root_box, void* stream);
 
+/* Largest n accepted by pr_lbvh_build_noalloc. */
+#define PR_LBVH_NOALLOC_MAX_BOXES 262144u
+
+/* pr_lbvh_build without any device allocation. The paper has no counterpart;
+ * this is a service for callers that cannot let a library allocate device
+ * memory while they run: applications whose device memory belongs to their own
+ * allocator under a fixed budget, and latency-sensitive loops where an
+ * allocation's possible synchronisation or pool growth is not acceptable.
+ * Arguments, layouts and results are those of pr_lbvh_build (bit-identical).
+ * Scratch comes from one fixed device array of the library (about 7.2 MB,
+ * enough for PR_LBVH_NOALLOC_MAX_BOXES boxes), reserved on every device that
+ * loads the library and held until the process exits. n above the limit is
+ * rejected with PR_ERR_INVALID_ARG (nothing is enqueued). The array is shared
+ * by all calls and keeps the last call's contents (the build clears what must
+ * start at zero); calls whose work overlaps on the GPU (different streams, or
+ * different host threads, on one device) race on it and must be serialised by
+ * the caller. The first call on each device looks the array up (a one-time
+ * set-up, done with that device current); make that first call before any
+ * stream capture. Calls no cudaMalloc, cudaFree or allocating routine. */
+pr_status pr_lbvh_build_noalloc(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
+                                float* root_box, void* stream);
+
 /* ---- Batched requests (wavefront path) ---------------------------------
  * Requests of uneven size (each its own scene, camera and resolution) are
  * fused into one set of persistent kernels per bounce: a primary stage over

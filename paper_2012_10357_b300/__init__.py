@@ -93,6 +93,7 @@ _sig("pr_scene_read_bvh", _i32, _vp, _u32, _vp, _u32, _vp, _vp, _vp, _vp, _vp, _
 _sig("pr_scene_device_bytes", ctypes.c_size_t, _vp)
 _sig("pr_scene_kernel_launches", _i32, _vp, _vp, _vp)
 _sig("pr_lbvh_build", _i32, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
+_sig("pr_lbvh_build_noalloc", _i32, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_batch_create", _i32, _u32, ctypes.c_uint64, _vp)
 _sig("pr_batch_set_tuning", _i32, _vp, _vp)
 _sig("pr_batch_get_tuning", _i32, _vp, _vp)
@@ -106,7 +107,7 @@ _sig("pr_scene_destroy", None, _vp)
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
             "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
-            "pr_scene_destroy", "pr_lbvh_build", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
+            "pr_scene_destroy", "pr_lbvh_build", "pr_lbvh_build_noalloc", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
             "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy"]
 
 

@@ -34,7 +34,7 @@ L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
 
 
 def workload_by_name(name: str):
-    if name == "config1":
+    if name in ("config1", "config1_frames"):
         return scenes.config1()
     if name == "config2":
         return scenes.config2()
@@ -45,6 +45,7 @@ def workload_by_name(name: str):
 
 def workload_config(name: str, w) -> dict:
     d = {"workload": {"config1": "tiny analytic scene, 4 AABB primitives, one BLAS",
+                      "config1_frames": "tiny analytic scene, 4096 eye-jittered 64x64 frames per launch",
                       "config2": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
                       "config3": "instanced field, 100000 instances of 8 procedural types"}[name],
          "config": name, "width": w.params.width, "height": w.params.height,
@@ -125,7 +126,7 @@ def _events(torch, n):
 def bench_config1_throughput(pr, work, torch, stream, flush, frames=4096, reps=5) -> dict:
     """Config 1 as a throughput run: 4096 eye-jittered 64x64 frames in one launch."""
     w = scenes.config1()
-    cams = scenes.config1_cameras(0, frames)
+    cams = pr.CameraArray(scenes.config1_cameras(0, frames))   # marshalled once
     with torch.cuda.stream(stream):
         scene = pr.Scene(w.scene, stream=stream)
         out = torch.empty((frames, 64, 64, 4), dtype=torch.float32, device="cuda")
@@ -227,6 +228,62 @@ def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
     return out
 
 
+class _RequestPool:
+    """Config-5 request stream: scene descriptions cached by (kind, seed) so the
+    generator runs once per scene, as a client holding its scenes would."""
+
+    def __init__(self, seed: int):
+        self.rng = np.random.default_rng(seed)
+        self.descs = {}
+
+    def next(self):
+        kind, sseed, wl = scenes.config5_request(self.rng, build=lambda k, s: self.descs.get((k, s)))
+        self.descs.setdefault((kind, sseed), wl.scene)
+        key = (kind << 32) | sseed
+        return key, self.descs[(kind, sseed)], wl.camera, wl.params
+
+
+def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=60.0, seed=0) -> list:
+    """Poisson arrivals at each rate; per-request latency = completion - submission."""
+    out_rows = []
+    ring = [torch.empty(1920 * 1080 * 4, dtype=torch.float32, device="cuda") for _ in range(128)]
+    for lam in rates:
+        pool = _RequestPool(seed)
+        n = int(min(n_requests, max(20, lam * max_seconds)))
+        reqs = [pool.next() for _ in range(n)]
+        gaps = np.random.default_rng(seed + 1).exponential(1.0 / lam, n)
+        srv = pr.Server(mode=mode, max_active=64, mem_budget_bytes=100 << 30, max_batch_pixels=8 << 20,
+                        tuning=tuning)
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for k, (key, desc, cam, tp) in enumerate(reqs):
+            due += gaps[k]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.0005))
+            if k >= len(ring):      # the ring slot's previous request must be done
+                while not srv.poll(tickets[k - len(ring)])[0]:
+                    time.sleep(0.0002)
+            out = ring[k % len(ring)][: tp.width * tp.height * 4].view(tp.height, tp.width, 4)
+            tickets.append(srv.submit(key, desc, cam, tp, out))
+        srv.drain(600.0)
+        st = [srv.poll(t)[1] for t in tickets]
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([s["t_done"] - s["t_submit"] for s in st]) * 1e3
+        span = max(s["t_done"] for s in st) - min(s["t_submit"] for s in st)
+        ok = sum(1 for s in st if s["status"] == 0)
+        out_rows.append({"rate_per_s": lam, "requests": n, "ok": ok, "mode": "continuous" if mode == 0 else "plain",
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "value": stats["rays"] / span / 1e6, "unit": "Mrays/s", "makespan_s": span,
+                         "iterations": stats["iterations"], "cache_hits": stats["cache_hits"],
+                         "cache_misses": stats["cache_misses"]})
+    return out_rows
+
+
 def cpu_baseline(w, budget_s: float = 15.0) -> dict:
     """The FP64 oracle, as it stands, on a seeded pixel sample of the same frame."""
     import oracle
@@ -290,17 +347,26 @@ def run_ours(args):
     from paper_2012_10357_b300 import work
 
     w = workload_by_name(args.workload)
+    frames = None
+    if args.workload == "config1_frames":
+        frames = pr.CameraArray(scenes.config1_cameras(0, 4096))    # marshalled once, outside the timed region
     stream = torch.cuda.Stream()
     H, W = w.params.height, w.params.width
     with torch.cuda.stream(stream):
         scene = pr.Scene(w.scene, stream=stream)
-        out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        out = torch.empty(((len(frames),) if frames else ()) + (H, W, 4), dtype=torch.float32, device="cuda")
         counter = torch.zeros(1, dtype=torch.int64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    def do_trace():
+        if frames:
+            scene.trace_frames(frames, w.params, out=out, ray_counter=counter, stream=stream)
+        else:
+            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+
     def step():
         scene.build_bvh(stream)
-        scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+        do_trace()
 
     def barrier():
         if world > 1:
@@ -323,7 +389,7 @@ def run_ours(args):
             ev[k][0].record(stream)
             scene.build_bvh(stream)
             ev[k][1].record(stream)
-            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+            do_trace()
             ev[k][2].record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
@@ -356,7 +422,7 @@ def run_ours(args):
     value = rays_all / (total_all / 1e3) / 1e6
 
     # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
-    counters = scene.trace_work(w.camera, w.params, stream=stream)
+    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames)
     torch.cuda.synchronize()
     flops = work.frame_flops(counters)
     trace_avg_s = statistics.mean(trace_ms) / 1e3
@@ -377,7 +443,7 @@ def run_ours(args):
     # end to end through the public API: host description -> device, build, frame, image -> host
     e2e = None
     if not args.no_e2e:
-        host_img = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+        host_img = torch.empty(tuple(out.shape), dtype=torch.float32, pin_memory=True)
         e2e_counter = torch.zeros(1, dtype=torch.int64, device="cuda")
         e2e_times = []
         for k in range(args.warmup + max(3, min(args.steps, 10))):
@@ -385,7 +451,10 @@ def run_ours(args):
             t0 = time.perf_counter()
             scene.upload(w.scene, stream)
             scene.build_bvh(stream)
-            scene.trace(w.camera, w.params, out=out, ray_counter=e2e_counter, stream=stream)
+            if frames:
+                scene.trace_frames(frames, w.params, out=out, ray_counter=e2e_counter, stream=stream)
+            else:
+                scene.trace(w.camera, w.params, out=out, ray_counter=e2e_counter, stream=stream)
             with torch.cuda.stream(stream):
                 host_img.copy_(out, non_blocking=True)
             stream.synchronize()
@@ -396,13 +465,22 @@ def run_ours(args):
         e2e_rays = int(e2e_counter.item())
         desc_bytes = scene.desc_bytes
         e2e = {"value": e2e_rays / sum(e2e_times) / 1e6 * world, "unit": "Mrays/s",
-               "h2d_bytes_per_step": int(desc_bytes), "d2h_bytes_per_step": int(H * W * 16),
+               "h2d_bytes_per_step": int(desc_bytes) + (40 * len(frames) if frames else 0),
+               "d2h_bytes_per_step": int(out.numel() * 4),
                "ms_per_step": 1e3 * statistics.mean(e2e_times)}
 
     extra = {}
     if not args.no_extra:
         extra["config1_throughput"] = bench_config1_throughput(pr, work, torch, stream, flush)
         extra["batched"] = bench_batched(pr, torch, stream, flush)
+        tuning = extra["batched"]["autotune"]["tuning"]
+        rows = []
+        for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
+            rows += bench_serving(pr, torch, args.serve_rates, args.serve_requests, mode, tuning)
+        extra["serving"] = {"workload": "config5: Poisson arrivals, config-2 / config-3 (100000 instances) scenes "
+                                        "50/50 from pools of 16, resolution 512^2..1920x1080, orbit cameras, "
+                                        "100 GB budget, 64 slots, 8 Mpx per continuous-batching iteration",
+                            "points": rows}
 
     line = {
         "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -433,10 +511,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config1", "config2", "config3"], default="config2")
+    ap.add_argument("--workload", choices=["config1", "config1_frames", "config2", "config3"], default="config2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the config-1 throughput and batched blocks")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config-1 throughput, batched and serving blocks")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[30.0, 1000.0])
+    ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

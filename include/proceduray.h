@@ -276,7 +276,9 @@ typedef struct {
   pr_scene* scene;          /* built scene */
   pr_camera camera;
   pr_trace_params params;   /* PR_TRACE_WRITE_AOV is not available in batches */
-  float* out_rgba;          /* device, height*width float4 */
+  float* out_rgba;          /* device, height*width float4 (the whole image) */
+  uint32_t row_begin;       /* render rows [row_begin, row_begin + row_count) only; */
+  uint32_t row_count;       /* row_count 0 = the whole image (row_begin must be 0) */
 } pr_request;
 
 /* Launch shape of the batched path: persistent CTAs per SM of the ray
@@ -321,6 +323,72 @@ size_t pr_batch_device_bytes(const pr_batch* batch);
 
 /* Free the batch (synchronises the device first). */
 void pr_batch_destroy(pr_batch* batch);
+
+/* ---- Serving loop ------------------------------------------------------
+ * Requests arrive at any time (pr_server_submit, thread-safe, non-blocking).
+ * A worker thread admits them in arrival order while slots (max_active) and
+ * the device-memory budget allow, keeps each scene (inputs + BVH) resident
+ * in a cache keyed by scene_key (least recently used unreferenced scenes are
+ * evicted to make room), and renders. PR_SERVE_CONTINUOUS: continuous
+ * batching, every iteration one batched launch over row ranges of all
+ * admitted requests (at most max_batch_pixels), so a request that arrives
+ * while others are on the GPU joins at the next iteration. PR_SERVE_PLAIN:
+ * one pr_trace per request, first come first served (the comparison form).
+ * Results are bit-identical to pr_trace of the same request. */
+#define PR_SERVE_CONTINUOUS 0u
+#define PR_SERVE_PLAIN 1u
+
+typedef struct {
+  uint32_t struct_size;        /* sizeof(pr_server_config) */
+  uint32_t mode;               /* PR_SERVE_CONTINUOUS or PR_SERVE_PLAIN */
+  uint32_t max_active;         /* requests admitted at once */
+  uint32_t reserved;
+  uint64_t mem_budget_bytes;   /* device bytes for cached scenes + batch state */
+  uint64_t max_batch_pixels;   /* pixels per batched iteration (>= widest image row) */
+  pr_batch_tuning tuning;      /* launch shape; struct_size 0 keeps the default */
+} pr_server_config;
+
+typedef struct {
+  uint64_t scene_key;          /* equal keys share one resident scene */
+  const pr_scene_desc* desc;   /* copied at submit unless scene_key is cached; may be NULL if cached */
+  pr_camera camera;
+  pr_trace_params params;      /* no AOV */
+  float* out_rgba;             /* device, caller-owned, height*width float4 */
+} pr_server_request;
+
+/* Per-request times (seconds of a steady clock) and outcome. */
+typedef struct {
+  double t_submit, t_admit, t_first_launch, t_done;
+  uint32_t status;             /* pr_status */
+  uint32_t cache_hit;          /* 1 if the scene was resident at admission */
+} pr_request_stats;
+
+typedef struct {
+  uint32_t struct_size, reserved;
+  uint64_t submitted, completed, rays, iterations;
+  uint64_t cache_hits, cache_misses, evictions, cache_bytes, batch_bytes;
+} pr_server_stats;
+
+typedef struct pr_server pr_server;
+
+/* Start a server on the current device (its worker thread and stream). */
+pr_status pr_server_create(const pr_server_config* config, pr_server** out);
+
+/* Queue a request; returns a ticket. Validates and copies the description
+ * if the key is not resident. Thread-safe; does not wait for the GPU. */
+pr_status pr_server_submit(pr_server* server, const pr_server_request* request, uint64_t* ticket);
+
+/* done = 1 once the request's image is complete in out_rgba (or it failed). */
+pr_status pr_server_poll(pr_server* server, uint64_t ticket, int* done, pr_request_stats* stats);
+
+/* Wait until every submitted request is done; PR_ERR_TIMEOUT after timeout_s. */
+pr_status pr_server_drain(pr_server* server, double timeout_s);
+
+/* Totals (rays traced read from the device: synchronises the server stream). */
+pr_status pr_server_get_stats(pr_server* server, pr_server_stats* stats);
+
+/* Finish queued work, stop the worker and free everything. */
+void pr_server_destroy(pr_server* server);
 
 /* Device bytes held by the scene's arena. */
 size_t pr_scene_device_bytes(const pr_scene* scene);

@@ -102,13 +102,22 @@ _sig("pr_trace_batch_graph", _i32, _vp, _u32, _vp, _vp, _vp)
 _sig("pr_batch_autotune", _i32, _vp, _u32, _vp, _vp, _vp, _vp)
 _sig("pr_batch_device_bytes", ctypes.c_size_t, _vp)
 _sig("pr_batch_destroy", None, _vp)
+_sig("pr_server_create", _i32, _vp, _vp)
+_sig("pr_server_submit", _i32, _vp, _vp, _vp)
+_sig("pr_server_poll", _i32, _vp, ctypes.c_uint64, _vp, _vp)
+_sig("pr_server_drain", _i32, _vp, ctypes.c_double)
+_sig("pr_server_get_stats", _i32, _vp, _vp)
+_sig("pr_server_destroy", None, _vp)
 _sig("pr_scene_destroy", None, _vp)
 
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
             "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
             "pr_scene_destroy", "pr_lbvh_build", "pr_lbvh_build_noalloc", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
-            "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy"]
+            "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy",
+            "pr_server_create", "pr_server_submit", "pr_server_poll", "pr_server_drain", "pr_server_get_stats",
+            "pr_server_destroy"]
+PR_SERVE_CONTINUOUS, PR_SERVE_PLAIN = 0, 1
 
 
 def _check(status: int, where: str):
@@ -190,6 +199,17 @@ def _dptr(t) -> Optional[int]:
     return None if t is None else t.data_ptr()
 
 
+class CameraArray:
+    """Cameras marshalled once into a C array (reuse it across launches)."""
+
+    def __init__(self, cameras: Sequence):
+        self.n = len(cameras)
+        self.array = (_Camera * self.n)(*[_camera(c) for c in cameras])
+
+    def __len__(self):
+        return self.n
+
+
 class Scene:
     """A scene on the device: inputs, BVH, shader binding table (pr_scene)."""
 
@@ -235,7 +255,7 @@ class Scene:
             out = torch.empty((n, H, W, 4), dtype=torch.float32, device="cuda")
         if want_aov and aov is None:
             aov = torch.empty((n, H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
-        cams = (_Camera * n)(*[_camera(c) for c in cameras])
+        cams = cameras.array if isinstance(cameras, CameraArray) else CameraArray(cameras).array
         tp = trace_params(params, aov is not None)
         _check(_lib.pr_trace_frames(self._h, cams, n, ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
                                     _stream_handle(stream)), "pr_trace_frames")
@@ -245,11 +265,14 @@ class Scene:
         """Instrumented trace (one camera, or a list of cameras for a multi-frame
         launch): returns the work counters (see PR_WORK_COUNTERS)."""
         import torch
-        cams = [camera] if cameras is None else list(cameras)
+        if cameras is None:
+            cameras = [camera]
+        ca = cameras if isinstance(cameras, CameraArray) else CameraArray(cameras)
         if out is None:
-            out = torch.empty((len(cams), params.height, params.width, 4), dtype=torch.float32, device="cuda")
+            out = torch.empty((len(ca), params.height, params.width, 4), dtype=torch.float32, device="cuda")
         work = torch.zeros(len(WORK_FIELDS), dtype=torch.int64, device="cuda")
-        arr = (_Camera * len(cams))(*[_camera(c) for c in cams])
+        arr = ca.array
+        cams = ca
         tp = trace_params(params, False)
         _check(_lib.pr_trace_work(self._h, arr, len(cams), ctypes.byref(tp), _dptr(out), _dptr(work),
                                   _stream_handle(stream)), "pr_trace_work")
@@ -330,7 +353,8 @@ def lbvh_to_host(res) -> dict:
 
 
 class _Request(ctypes.Structure):
-    _fields_ = [("scene", ctypes.c_void_p), ("camera", _Camera), ("params", _TraceParams), ("out_rgba", ctypes.c_void_p)]
+    _fields_ = [("scene", ctypes.c_void_p), ("camera", _Camera), ("params", _TraceParams), ("out_rgba", ctypes.c_void_p),
+                ("row_begin", ctypes.c_uint32), ("row_count", ctypes.c_uint32)]
 
 
 class _BatchTuning(ctypes.Structure):
@@ -347,13 +371,16 @@ class Batch:
 
     @staticmethod
     def _requests(items):
-        """items: sequence of (Scene, camera, params, out_tensor)."""
+        """items: sequence of (Scene, camera, params, out_tensor[, row_begin, row_count])."""
         arr = (_Request * len(items))()
-        for k, (sc, cam, tp, out) in enumerate(items):
+        for k, it in enumerate(items):
+            sc, cam, tp, out = it[:4]
             arr[k].scene = sc._h.value
             arr[k].camera = _camera(cam)
             arr[k].params = trace_params(tp, False)
             arr[k].out_rgba = out.data_ptr()
+            if len(it) > 4:
+                arr[k].row_begin, arr[k].row_count = int(it[4]), int(it[5])
         return arr
 
     def trace(self, items, ray_counter=None, stream=None, graph: bool = False):
@@ -387,6 +414,82 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             _lib.pr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("mem_budget_bytes", ctypes.c_uint64),
+                ("max_batch_pixels", ctypes.c_uint64), ("tuning", _BatchTuning)]
+
+
+class _ServerRequest(ctypes.Structure):
+    _fields_ = [("scene_key", ctypes.c_uint64), ("desc", ctypes.c_void_p), ("camera", _Camera),
+                ("params", _TraceParams), ("out_rgba", ctypes.c_void_p)]
+
+
+class _RequestStats(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_first_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("status", ctypes.c_uint32), ("cache_hit", ctypes.c_uint32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + [
+        (n, ctypes.c_uint64) for n in ("submitted", "completed", "rays", "iterations", "cache_hits", "cache_misses",
+                                       "evictions", "cache_bytes", "batch_bytes")]
+
+
+class Server:
+    """Serving loop (pr_server): admission by memory budget, scene cache, continuous batching."""
+
+    def __init__(self, mode=PR_SERVE_CONTINUOUS, max_active=64, mem_budget_bytes=100 << 30,
+                 max_batch_pixels=16 << 20, tuning: Optional[dict] = None):
+        cfg = _ServerConfig()
+        cfg.struct_size = ctypes.sizeof(_ServerConfig)
+        cfg.mode, cfg.max_active = mode, max_active
+        cfg.mem_budget_bytes, cfg.max_batch_pixels = mem_budget_bytes, max_batch_pixels
+        if tuning:
+            cfg.tuning = _BatchTuning(ctypes.sizeof(_BatchTuning), tuning["ctas_per_sm"], tuning["tile_w"],
+                                      tuning["tile_h"], tuning["queue_chunk"])
+        self._h = ctypes.c_void_p()
+        _check(_lib.pr_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "pr_server_create")
+
+    def submit(self, key: int, desc, camera, params, out) -> int:
+        """desc: a scene description object (or None if the key is resident)."""
+        r = _ServerRequest()
+        r.scene_key = key
+        ref = _DescRef(desc) if desc is not None else None
+        r.desc = ctypes.addressof(ref.struct) if ref is not None else None
+        r.camera = _camera(camera)
+        r.params = trace_params(params, False)
+        r.out_rgba = out.data_ptr()
+        t = ctypes.c_uint64()
+        _check(_lib.pr_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "pr_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int()
+        st = _RequestStats()
+        _check(_lib.pr_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(st)), "pr_server_poll")
+        return bool(done.value), {k: getattr(st, k) for k, _ in _RequestStats._fields_}
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(_lib.pr_server_drain(self._h, timeout_s), "pr_server_drain")
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_lib.pr_server_get_stats(self._h, ctypes.byref(st)), "pr_server_get_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_ if k not in ("struct_size", "reserved")}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.pr_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libproceduray.so")
-SOURCES = ["api.cu", "bvh.cu", "trace.cu", "wavefront.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "bvh.cu", "trace.cu", "wavefront.cu", "batch.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +29,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    extra = os.environ.get("PR_NVCC_EXTRA", "").split()   # e.g. -DPR_TRACE_MIN_BLOCKS=6
+    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", *extra,
            "-o", LIB + ".tmp", *sources()]
     if verbose_ptxas:
         cmd.insert(1, "-Xptxas=-v")

@@ -85,14 +85,19 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
     d.height = p.height;
     d.max_depth = p.max_depth;
     d.max_steps = p.max_steps;
+    const uint32_t rows = q.row_count ? q.row_count : p.height;
+    if ((q.row_count == 0 && q.row_begin != 0) || (uint64_t)q.row_begin + rows > p.height)
+      return bfail(PR_ERR_INVALID_ARG, "request rows outside the image");
+    d.row_begin = q.row_begin;
+    d.rows = rows;
     d.tile_begin = tiles;
     d.tiles_x = (p.width + b->tuning.tile_w - 1) / b->tuning.tile_w;
     d.out = reinterpret_cast<float4*>(q.out_rgba);
     d.pixel_begin = px;
-    uint64_t t = (uint64_t)d.tiles_x * ((p.height + b->tuning.tile_h - 1) / b->tuning.tile_h);
+    uint64_t t = (uint64_t)d.tiles_x * ((rows + b->tuning.tile_h - 1) / b->tuning.tile_h);
     if (tiles + t > 0xFFFFFFFFull) return bfail(PR_ERR_INVALID_ARG, "too many tiles");
     tiles += (uint32_t)t;
-    px += (uint64_t)p.width * p.height;
+    px += (uint64_t)p.width * rows;
   }
   if (px > b->max_px) return bfail(PR_ERR_BUDGET, "batch pixels exceed the batch's max_pixels");
   H->n_req = n;

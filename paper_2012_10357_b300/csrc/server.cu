@@ -1,0 +1,467 @@
+// Serving loop (pr_server_*): render requests arrive at any time; a worker
+// thread admits them by a device-memory budget, keeps their scenes (device
+// BVH) resident in a cache keyed by the caller's scene key, and renders
+// with continuous batching: every iteration is one batched wavefront launch
+// over row ranges of all admitted requests, so requests that arrive while
+// others are on the GPU join at the next iteration and their work overlaps.
+// PR_SERVE_PLAIN mode renders one whole request per pr_trace, first come
+// first served, for comparison.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/proceduray.h"
+#include "internal.h"
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Deep copy of a scene description (the caller's arrays may be freed after submit).
+struct DescCopy {
+  pr_scene_desc d{};
+  std::vector<float> aabbs, params, xform, materials;
+  std::vector<uint32_t> gpb, gpc, bgb, bgc, iblas, iid, isbt, imask, hg, sbt, rt;
+  explicit DescCopy(const pr_scene_desc* s) {
+    d = *s;
+    auto cpf = [](std::vector<float>& v, const float* p, size_t n) { v.assign(p, p + (p ? n : 0)); return v.data(); };
+    auto cpu = [](std::vector<uint32_t>& v, const uint32_t* p, size_t n) {
+      v.assign(p, p + (p ? n : 0));
+      return v.data();
+    };
+    d.aabbs = cpf(aabbs, s->aabbs, 6 * (size_t)s->n_prims);
+    d.params = cpf(params, s->params, PR_PARAMS_PER_PRIM * (size_t)s->n_prims);
+    d.inst_xform = cpf(xform, s->inst_xform, 12 * (size_t)s->n_inst);
+    d.materials = cpf(materials, s->materials, 4 * (size_t)s->n_materials);
+    d.geom_prim_begin = cpu(gpb, s->geom_prim_begin, s->n_geoms);
+    d.geom_prim_count = cpu(gpc, s->geom_prim_count, s->n_geoms);
+    d.blas_geom_begin = cpu(bgb, s->blas_geom_begin, s->n_blas);
+    d.blas_geom_count = cpu(bgc, s->blas_geom_count, s->n_blas);
+    d.inst_blas = cpu(iblas, s->inst_blas, s->n_inst);
+    d.inst_id = cpu(iid, s->inst_id, s->n_inst);
+    d.inst_sbt_offset = cpu(isbt, s->inst_sbt_offset, s->n_inst);
+    d.inst_mask = cpu(imask, s->inst_mask, s->n_inst);
+    d.hit_groups = cpu(hg, s->hit_groups, 3 * (size_t)s->n_hit_groups);
+    d.sbt = cpu(sbt, s->sbt, 4 * (size_t)s->n_records);
+    d.ray_types = cpu(rt, s->ray_types, 2 * (size_t)s->n_ray_types);
+  }
+};
+
+struct CachedScene {
+  pr_scene* scene = nullptr;
+  size_t bytes = 0;
+  int refs = 0;
+  double last_use = 0.0;
+};
+
+struct Job {
+  uint64_t ticket = 0;
+  uint64_t key = 0;
+  std::shared_ptr<DescCopy> desc;   // only when the key was not cached at submit time
+  pr_camera camera{};
+  pr_trace_params params{};
+  float* out = nullptr;
+  uint32_t next_row = 0, rows_done_launched = 0;
+  uint32_t rows_inflight = 0, rows_finished = 0;
+  pr_request_stats st{};
+  bool cache_hit = false;
+};
+
+struct Iteration {
+  cudaEvent_t done = nullptr;
+  std::vector<std::pair<uint64_t, uint32_t>> parts;   // (ticket, rows) rendered by this launch
+};
+
+}  // namespace
+
+struct pr_server {
+  pr_server_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pr_batch* batch = nullptr;
+  size_t batch_bytes = 0;
+  unsigned long long* d_rays = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  bool stop = false;
+  std::deque<std::shared_ptr<Job>> pending;
+  std::list<std::shared_ptr<Job>> active;
+  std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;   // every ticket (kept for polling)
+  std::unordered_map<uint64_t, CachedScene> cache;
+  size_t cache_bytes = 0;
+  uint64_t next_ticket = 1;
+  uint64_t completed = 0, cache_hits = 0, cache_misses = 0, evictions = 0, iterations = 0;
+  std::deque<Iteration> inflight;
+  std::vector<cudaEvent_t> free_events;
+  std::string error;
+  pr_status failed = PR_OK;
+};
+
+namespace {
+
+pr_status sfail(pr_status st, const std::string& m) {
+  pr_internal_set_error(m);
+  return st;
+}
+
+cudaEvent_t take_event(pr_server* s) {
+  if (!s->free_events.empty()) {
+    cudaEvent_t e = s->free_events.back();
+    s->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  return e;
+}
+
+// Make room under the budget by dropping unreferenced cached scenes, least
+// recently used first. Called with the lock held.
+bool make_room(pr_server* s, size_t need) {
+  while (s->cache_bytes + s->batch_bytes + need > s->cfg.mem_budget_bytes) {
+    auto victim = s->cache.end();
+    for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
+      if (it->second.refs == 0 && (victim == s->cache.end() || it->second.last_use < victim->second.last_use))
+        victim = it;
+    if (victim == s->cache.end()) return false;
+    pr_scene_destroy(victim->second.scene);
+    s->cache_bytes -= victim->second.bytes;
+    s->cache.erase(victim);
+    ++s->evictions;
+  }
+  return true;
+}
+
+// Admit pending jobs in arrival order while slots and memory allow.
+// Scene creation and BVH build run on the server stream.
+void admit(pr_server* s, std::unique_lock<std::mutex>& lk) {
+  while (!s->pending.empty() && s->active.size() < s->cfg.max_active) {
+    std::shared_ptr<Job> j = s->pending.front();
+    auto it = s->cache.find(j->key);
+    if (it == s->cache.end()) {
+      if (!j->desc) {   // the key was cached at submit time but evicted since: cannot rebuild
+        j->st.status = PR_ERR_BUDGET;
+        j->st.t_done = now_s();
+        s->pending.pop_front();
+        ++s->completed;
+        s->cv_done.notify_all();
+        continue;
+      }
+      // estimate: arena grows with primitives and instances; create then account exactly
+      pr_scene* sc = nullptr;
+      lk.unlock();
+      pr_status st = pr_scene_create(&j->desc->d, s->stream, &sc);
+      if (st == PR_OK) st = pr_build_bvh(sc, s->stream);
+      lk.lock();
+      if (st != PR_OK) {
+        if (sc) pr_scene_destroy(sc);
+        j->st.status = st;
+        j->st.t_done = now_s();
+        s->pending.pop_front();
+        ++s->completed;
+        s->cv_done.notify_all();
+        continue;
+      }
+      size_t bytes = pr_scene_device_bytes(sc);
+      if (!make_room(s, bytes)) {
+        // over budget with every cached scene in use: wait for active requests to finish
+        lk.unlock();
+        pr_scene_destroy(sc);
+        lk.lock();
+        if (s->active.empty()) {
+          j->st.status = PR_ERR_BUDGET;
+          j->st.t_done = now_s();
+          s->pending.pop_front();
+          ++s->completed;
+          s->cv_done.notify_all();
+          continue;
+        }
+        return;
+      }
+      CachedScene c;
+      c.scene = sc;
+      c.bytes = bytes;
+      it = s->cache.emplace(j->key, c).first;
+      s->cache_bytes += bytes;
+      ++s->cache_misses;
+      j->cache_hit = false;
+    } else {
+      ++s->cache_hits;
+      j->cache_hit = true;
+    }
+    it->second.refs++;
+    it->second.last_use = now_s();
+    j->desc.reset();
+    j->st.t_admit = now_s();
+    s->pending.pop_front();
+    s->active.push_back(j);
+  }
+}
+
+void finish_iteration(pr_server* s, Iteration& it) {
+  double t = now_s();
+  for (auto& part : it.parts) {
+    auto jt = s->jobs.find(part.first);
+    if (jt == s->jobs.end()) continue;
+    Job& j = *jt->second;
+    j.rows_inflight -= part.second;
+    j.rows_finished += part.second;
+    if (j.rows_finished >= j.params.height) {
+      j.st.t_done = t;
+      j.st.status = PR_OK;
+      auto c = s->cache.find(j.key);
+      if (c != s->cache.end()) {
+        c->second.refs--;
+        c->second.last_use = t;
+      }
+      s->active.remove(jt->second);
+      ++s->completed;
+    }
+  }
+  s->free_events.push_back(it.done);
+  s->cv_done.notify_all();
+}
+
+// One iteration: row ranges of active requests, oldest first, up to the pixel budget.
+bool launch_iteration(pr_server* s) {
+  std::vector<pr_request> reqs;
+  Iteration it;
+  uint64_t px = 0;
+  const uint64_t cap = s->cfg.max_batch_pixels;
+  for (auto& jp : s->active) {
+    Job& j = *jp;
+    if (j.next_row >= j.params.height) continue;
+    if (reqs.size() >= s->cfg.max_active) break;
+    uint64_t room = cap > px ? cap - px : 0;
+    if (room < j.params.width) break;
+    uint32_t rows = (uint32_t)std::min<uint64_t>(j.params.height - j.next_row, room / j.params.width);
+    if (s->cfg.mode == PR_SERVE_PLAIN) rows = j.params.height - j.next_row;
+    pr_request r{};
+    r.scene = s->cache[j.key].scene;
+    r.camera = j.camera;
+    r.params = j.params;
+    r.out_rgba = j.out;
+    r.row_begin = j.next_row;
+    r.row_count = rows;
+    reqs.push_back(r);
+    if (j.st.t_first_launch == 0.0) j.st.t_first_launch = now_s();
+    j.next_row += rows;
+    j.rows_inflight += rows;
+    it.parts.emplace_back(j.ticket, rows);
+    px += (uint64_t)rows * j.params.width;
+    if (s->cfg.mode == PR_SERVE_PLAIN) break;   // one request per launch
+  }
+  if (reqs.empty()) return false;
+  pr_status st;
+  if (s->cfg.mode == PR_SERVE_PLAIN) {
+    st = pr_trace(reqs[0].scene, &reqs[0].camera, &reqs[0].params, reqs[0].out_rgba, nullptr,
+                  reinterpret_cast<uint64_t*>(s->d_rays), s->stream);
+  } else {
+    st = pr_trace_batch_graph(s->batch, (uint32_t)reqs.size(), reqs.data(), reinterpret_cast<uint64_t*>(s->d_rays),
+                              s->stream);
+  }
+  if (st != PR_OK) {
+    s->failed = st;
+    s->error = pr_last_error();
+    return false;
+  }
+  it.done = take_event(s);
+  cudaEventRecord(it.done, s->stream);
+  s->inflight.push_back(std::move(it));
+  ++s->iterations;
+  return true;
+}
+
+void worker_main(pr_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    if (s->stop && s->pending.empty() && s->active.empty()) break;
+    // retire finished iterations
+    while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().done) == cudaSuccess) {
+      finish_iteration(s, s->inflight.front());
+      s->inflight.pop_front();
+    }
+    admit(s, lk);
+    // keep up to two iterations queued on the stream so the GPU never idles
+    bool launched = false;
+    while (s->inflight.size() < 2 && s->failed == PR_OK) {
+      if (!launch_iteration(s)) break;
+      launched = true;
+    }
+    if (!launched) {
+      if (!s->inflight.empty()) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+      } else {
+        s->cv.wait_for(lk, std::chrono::milliseconds(1));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+pr_status pr_server_create(const pr_server_config* cfg, pr_server** out) {
+  if (!cfg || !out || cfg->struct_size != sizeof(pr_server_config))
+    return sfail(PR_ERR_INVALID_ARG, "pr_server_create: null config/output or struct_size mismatch");
+  if (cfg->max_active == 0 || cfg->max_batch_pixels == 0 ||
+      (cfg->mode != PR_SERVE_CONTINUOUS && cfg->mode != PR_SERVE_PLAIN))
+    return sfail(PR_ERR_INVALID_ARG, "pr_server_create: max_active, max_batch_pixels must be > 0; mode 0 or 1");
+  *out = nullptr;
+  pr_server* s = new pr_server();
+  s->cfg = *cfg;
+  cudaGetDevice(&s->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_rays, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_rays, 0, sizeof(unsigned long long), s->stream);
+  if (e != cudaSuccess) {
+    pr_server_destroy(s);
+    return sfail(e == cudaErrorMemoryAllocation ? PR_ERR_OUT_OF_MEMORY : PR_ERR_CUDA,
+                 std::string("pr_server_create: ") + cudaGetErrorString(e));
+  }
+  if (cfg->mode == PR_SERVE_CONTINUOUS) {
+    pr_status st = pr_batch_create(cfg->max_active, cfg->max_batch_pixels, &s->batch);
+    if (st != PR_OK) {
+      pr_server_destroy(s);
+      return st;
+    }
+    s->batch_bytes = pr_batch_device_bytes(s->batch);
+    if (cfg->tuning.struct_size == sizeof(pr_batch_tuning)) {
+      st = pr_batch_set_tuning(s->batch, &cfg->tuning);
+      if (st != PR_OK) {
+        pr_server_destroy(s);
+        return st;
+      }
+    }
+  }
+  if (s->batch_bytes > cfg->mem_budget_bytes) {
+    pr_server_destroy(s);
+    return sfail(PR_ERR_BUDGET, "pr_server_create: the batch state alone exceeds the memory budget");
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return PR_OK;
+}
+
+pr_status pr_server_submit(pr_server* s, const pr_server_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket || !r->out_rgba) return sfail(PR_ERR_INVALID_ARG, "pr_server_submit: null argument");
+  const pr_trace_params& p = r->params;
+  if (p.struct_size != sizeof(pr_trace_params) || p.width == 0 || p.height == 0 || p.width > 65536 ||
+      p.height > 65536 || p.max_depth < 1 || p.max_depth > 2 || p.max_steps == 0 || (p.flags & PR_TRACE_WRITE_AOV) ||
+      (uint64_t)p.width > s->cfg.max_batch_pixels)
+    return sfail(PR_ERR_INVALID_ARG, "pr_server_submit: bad params (no AOV; width must fit max_batch_pixels)");
+  auto j = std::make_shared<Job>();
+  j->key = r->scene_key;
+  j->camera = r->camera;
+  j->params = p;
+  j->out = r->out_rgba;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->failed != PR_OK) return sfail(s->failed, "server stopped after an error: " + s->error);
+  if (!s->cache.count(r->scene_key)) {
+    if (!r->desc) return sfail(PR_ERR_INVALID_ARG, "pr_server_submit: scene key not cached and no description");
+    lk.unlock();
+    pr_status v = pr_scene_validate(r->desc);
+    if (v != PR_OK) return v;
+    auto dc = std::make_shared<DescCopy>(r->desc);
+    lk.lock();
+    j->desc = dc;
+  }
+  j->ticket = s->next_ticket++;
+  j->st.t_submit = now_s();
+  s->jobs[j->ticket] = j;
+  s->pending.push_back(j);
+  *ticket = j->ticket;
+  s->cv.notify_all();
+  return PR_OK;
+}
+
+pr_status pr_server_poll(pr_server* s, uint64_t ticket, int* done, pr_request_stats* stats) {
+  if (!s || !done) return sfail(PR_ERR_INVALID_ARG, "pr_server_poll: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return sfail(PR_ERR_INVALID_ARG, "pr_server_poll: unknown ticket");
+  const Job& j = *it->second;
+  *done = j.st.t_done > 0.0 ? 1 : 0;
+  if (stats) {
+    *stats = j.st;
+    stats->cache_hit = j.cache_hit ? 1u : 0u;
+  }
+  return PR_OK;
+}
+
+pr_status pr_server_drain(pr_server* s, double timeout_s) {
+  if (!s) return sfail(PR_ERR_INVALID_ARG, "pr_server_drain: null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  while (s->completed < s->next_ticket - 1 && s->failed == PR_OK) {
+    if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout &&
+        s->completed < s->next_ticket - 1)
+      return sfail(PR_ERR_TIMEOUT, "pr_server_drain: requests still in flight at the timeout");
+  }
+  if (s->failed != PR_OK) return sfail(s->failed, "server stopped after an error: " + s->error);
+  return PR_OK;
+}
+
+pr_status pr_server_get_stats(pr_server* s, pr_server_stats* out) {
+  if (!s || !out) return sfail(PR_ERR_INVALID_ARG, "pr_server_get_stats: null argument");
+  unsigned long long rays = 0;
+  cudaError_t e = cudaMemcpyAsync(&rays, s->d_rays, sizeof(rays), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return sfail(PR_ERR_CUDA, std::string("pr_server_get_stats: ") + cudaGetErrorString(e));
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->struct_size = sizeof(pr_server_stats);
+  out->submitted = s->next_ticket - 1;
+  out->completed = s->completed;
+  out->rays = rays;
+  out->iterations = s->iterations;
+  out->cache_hits = s->cache_hits;
+  out->cache_misses = s->cache_misses;
+  out->evictions = s->evictions;
+  out->cache_bytes = s->cache_bytes;
+  out->batch_bytes = s->batch_bytes;
+  return PR_OK;
+}
+
+void pr_server_destroy(pr_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    if (s->failed != PR_OK) {   // abandon queued work after a failure
+      s->pending.clear();
+      s->active.clear();
+    }
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& it : s->inflight) cudaEventDestroy(it.done);
+  for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+  for (auto& c : s->cache) pr_scene_destroy(c.second.scene);
+  if (s->batch) pr_batch_destroy(s->batch);
+  if (s->d_rays) cudaFree(s->d_rays);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

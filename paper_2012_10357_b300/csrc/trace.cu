@@ -26,8 +26,13 @@ struct Params {
   unsigned long long* counter;
 };
 
+// Resident CTAs per SM the register allocation must allow (occupancy knob).
+#ifndef PR_TRACE_MIN_BLOCKS
+#define PR_TRACE_MIN_BLOCKS 1
+#endif
+
 template <bool kStats>
-__global__ void __launch_bounds__(128) k_trace(Params P, unsigned long long* work) {
+__global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, unsigned long long* work) {
   const SceneView& S = P.S;
   WorkCounters wcl;
   if (kStats) memset(&wcl, 0, sizeof(wcl));

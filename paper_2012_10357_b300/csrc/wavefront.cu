@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(128) k_wf_primary(BatchView B) {
     }
     const ReqDev& R = sreq;
     const uint32_t lt = tile - R.tile_begin;
-    const int x = (int)(lt % R.tiles_x) * TW + ox, y = (int)(lt / R.tiles_x) * TH + oy;
-    const bool valid = x < (int)R.width && y < (int)R.height;
+    const int x = (int)(lt % R.tiles_x) * TW + ox, y = (int)R.row_begin + (int)(lt / R.tiles_x) * TH + oy;
+    const bool valid = x < (int)R.width && y < (int)(R.row_begin + R.rows);
     bool need_s = false, need_m = false;
     float3 os = f3(0.f, 0.f, 0.f), ds = os, orr = os, dr = os;
     float smax = 0.f;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128) k_wf_primary(BatchView B) {
       const float3 eye = ldf3(R.cam.eye);
       const float3 d = camera_ray(R.cam, x, y, R.width, R.height);
       const float eps = scene_eps(S, R.eps_rel);
-      px = R.pixel_begin + (uint64_t)y * R.width + (uint64_t)x;
+      px = R.pixel_begin + (uint64_t)(y - (int)R.row_begin) * R.width + (uint64_t)x;
       Hit h;
       trace_typed<false>(S, eye, d, 0, 0.f, INFINITY, eps, R.max_steps, h, stack, nullptr);
       uint32_t flags = 0;
@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
         color = mirror_mix(color, f3(lr.x, lr.y, lr.z), a.w);
       }
     }
-    R.out[px - R.pixel_begin] = make_float4(color.x, color.y, color.z, 1.f);
+    const uint64_t local = px - R.pixel_begin;
+    const uint64_t row = R.row_begin + local / R.width, col = local % R.width;
+    R.out[row * R.width + col] = make_float4(color.x, color.y, color.z, 1.f);
   }
 }
 

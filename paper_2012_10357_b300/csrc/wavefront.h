@@ -15,6 +15,7 @@ struct ReqDev {
   float3 light, background;
   float light_intensity, eps_rel, ambient;
   uint32_t width, height, max_depth, max_steps;
+  uint32_t row_begin, rows;          // rendered rows [row_begin, row_begin + rows) of the image
   uint32_t tile_begin, tiles_x;
   float4* out;
   uint64_t pixel_begin;

@@ -493,22 +493,27 @@ def config4_requests(seed: int = 0, n_requests: int = 64, res_choices=(256, 512,
     return out
 
 
-def config5_request(rng: np.random.Generator, scene_pool: int = 16):
-    """One serving request: a config-2 or config-3-type scene (50/50), seed from a pool of
-    16 per kind (so scenes repeat and a BVH cache can hit), resolution t~U[0,1],
-    W=round(512+1408t), H=round(512+568t), orbit camera."""
+def config5_request(rng: np.random.Generator, scene_pool: int = 16, build=None):
+    """One serving request: a config-2 or config-3 scene (50/50), seed from a pool
+    of 16 per kind (so scenes repeat and a BVH cache can hit), resolution
+    t~U[0,1], W=round(512+1408t), H=round(512+568t), orbit camera around the
+    scene. build(kind, seed) may return an already generated description."""
     kind = int(rng.integers(0, 2))
     sseed = int(rng.integers(0, scene_pool))
     t = rng.uniform()
     w, h = int(round(512 + 1408 * t)), int(round(512 + 568 * t))
+    known = build(kind, sseed) if build else None
     if kind == 0:
-        wl = config2(sseed, w, h)
-        cam = orbit_camera(rng, (0.0, 0.5, 1.0), 12.0)
-        wl.camera = cam
+        wl = config2(sseed, w, h) if known is None else Workload(known, None, config2(sseed, 8, 8).params)
+        wl.params.width, wl.params.height = w, h
+        wl.camera = orbit_camera(rng, (0.0, 0.5, 1.0), 12.0)
     else:
-        wl = config3(sseed, w, h, n_inst=10_000)
-        side = 100.0 * (10_000 / 100_000) ** (1.0 / 3.0)
-        wl.camera = orbit_camera(rng, np.full(3, side / 2), math.sqrt(3) * side)
+        if known is None:
+            wl = config3(sseed, w, h)
+        else:
+            wl = Workload(known, None, TraceParams(w, h, max_depth=1, light_pos=_f32([50, 200, -100])))
+        wl.params.width, wl.params.height = w, h
+        wl.camera = orbit_camera(rng, np.full(3, 50.0), math.sqrt(3) * 100.0)
     return kind, sseed, wl
 
 

@@ -1,0 +1,137 @@
+"""Serving loop (pr_server) and row-range batches on a B300.
+
+Each request's image must be the same alone (a plain pr_trace of it) and in
+the mix (rendered by continuous batching together with whatever else was in
+flight, possibly split into row ranges across iterations): bit-identical.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2012_10357_b300 as pr  # noqa: E402
+
+
+def _requests():
+    base = [(1, scenes.config2(seed=1, width=240, height=135)), (2, scenes.config3(seed=2, n_inst=4000, width=200, height=150)),
+            (3, scenes.config1(seed=3, width=64, height=64)), (4, scenes.config2(seed=4, width=97, height=301))]
+    rng = np.random.default_rng(0)
+    reqs = []
+    for k in range(12):
+        key, w = base[k % len(base)]
+        cam = w.camera
+        if k >= len(base):   # same scene, another camera pose
+            cam = scenes.Camera(np.float32(np.asarray(w.camera.eye) + rng.uniform(-1, 1, 3)), w.camera.look_at,
+                                w.camera.up, 60.0)
+        reqs.append((key, w, cam))
+    return reqs
+
+
+def _alone(reqs):
+    outs = []
+    for key, w, cam in reqs:
+        sc = pr.Scene(w.scene)
+        outs.append(sc.trace(cam, w.params))
+        torch.cuda.synchronize()
+        sc.close()
+    return outs
+
+
+def test_row_range_batches_reassemble_the_image():
+    w = scenes.config2(width=150, height=77)
+    sc = pr.Scene(w.scene)
+    ref = sc.trace(w.camera, w.params)
+    out = torch.full((77, 150, 4), -1.0, device="cuda")
+    batch = pr.Batch(8, 150 * 77)
+    batch.trace([(sc, w.camera, w.params, out, 0, 10), (sc, w.camera, w.params, out, 10, 31)])
+    batch.trace([(sc, w.camera, w.params, out, 41, 36)])
+    torch.cuda.synchronize()
+    assert torch.equal(ref, out)
+    with pytest.raises(pr.PrError):
+        batch.trace([(sc, w.camera, w.params, out, 70, 10)])      # past the last row
+
+
+@pytest.mark.parametrize("mode,max_batch", [(pr.PR_SERVE_CONTINUOUS, 20000), (pr.PR_SERVE_CONTINUOUS, 1 << 22),
+                                            (pr.PR_SERVE_PLAIN, 1 << 22)])
+def test_served_equals_alone(mode, max_batch):
+    reqs = _requests()
+    alone = _alone(reqs)
+    srv = pr.Server(mode=mode, max_active=5, mem_budget_bytes=8 << 30, max_batch_pixels=max_batch)
+    outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for _, w, _ in reqs]
+    tickets = []
+    for k, ((key, w, cam), out) in enumerate(zip(reqs, outs)):
+        tickets.append(srv.submit(key, w.scene, cam, w.params, out))
+        if k % 3 == 2:
+            time.sleep(0.002)          # later arrivals join requests already in flight
+    srv.drain(120.0)
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(zip(alone, outs)):
+        assert torch.equal(a, b), f"request {k} differs in the mix"
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["submitted"] == len(reqs)
+    assert st["cache_misses"] == 4 and st["cache_hits"] == len(reqs) - 4
+    for t in tickets:
+        done, s = srv.poll(t)
+        assert done and s["status"] == pr.PR_OK
+        assert s["t_submit"] <= s["t_admit"] <= s["t_first_launch"] <= s["t_done"]
+    if mode == pr.PR_SERVE_CONTINUOUS and max_batch == 20000:
+        assert st["iterations"] > len(reqs)            # large requests were split across iterations
+    srv.close()
+
+
+def test_rays_counted_like_plain_launches():
+    reqs = _requests()[:4]
+    plain_rays = 0
+    for key, w, cam in reqs:
+        sc = pr.Scene(w.scene)
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sc.trace(cam, w.params, ray_counter=c)
+        torch.cuda.synchronize()
+        plain_rays += int(c.item())
+        sc.close()
+    srv = pr.Server(max_active=4, mem_budget_bytes=8 << 30, max_batch_pixels=1 << 20)
+    outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for _, w, _ in reqs]
+    for (key, w, cam), out in zip(reqs, outs):
+        srv.submit(key, w.scene, cam, w.params, out)
+    srv.drain(60.0)
+    assert srv.stats()["rays"] == plain_rays
+    srv.close()
+
+
+def test_admission_refuses_scene_over_budget():
+    w = scenes.config3(seed=5, n_inst=20000, width=32, height=32)
+    probe = pr.Scene(w.scene)
+    need = probe.device_bytes()
+    probe.close()
+    batch_bytes = pr.Batch(2, 4096).device_bytes()
+    srv = pr.Server(max_active=2, mem_budget_bytes=batch_bytes + need // 2, max_batch_pixels=4096)
+    out = torch.empty((32, 32, 4), device="cuda")
+    t = srv.submit(9, w.scene, w.camera, w.params, out)
+    srv.drain(60.0)
+    done, s = srv.poll(t)
+    assert done and s["status"] == pr.PR_ERR_BUDGET
+    srv.close()
+
+
+def test_submit_validation():
+    srv = pr.Server(max_active=2, mem_budget_bytes=4 << 30, max_batch_pixels=4096)
+    w = scenes.config1()
+    out = torch.empty((64, 64, 4), device="cuda")
+    with pytest.raises(pr.PrError):
+        srv.submit(77, None, w.camera, w.params, out)          # key not resident, no description
+    bad = scenes.config1()
+    bad.scene.aabbs[0, 0] = 99.0
+    with pytest.raises(pr.PrError):
+        srv.submit(78, bad.scene, w.camera, w.params, out)     # invalid description
+    wide = scenes.config1(width=5000, height=2)
+    with pytest.raises(pr.PrError):
+        srv.submit(79, wide.scene, wide.camera, wide.params, torch.empty((2, 5000, 4), device="cuda"))
+    srv.close()

@@ -111,6 +111,19 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tuple:
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    if world <= 1:
+        return total_ms, rays
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    r = torch.tensor([rays], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(r.item())
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -312,7 +325,7 @@ def run_reference(args):
     w = workload_by_name(args.workload)
     threads = os.cpu_count() or 1
     n_pix = w.params.width * w.params.height
-    per_step = max(256, n_pix // 512)
+    per_step = min(n_pix, max(4096, n_pix // 32))     # ~65k pixels of a 1080p frame per step
     times, rays = [], 0
     for k in range(args.warmup + args.steps):
         pix = scenes.sample_pixels(w.params.width, w.params.height, per_step, seed=100 + k)
@@ -403,15 +416,7 @@ def run_ours(args):
     n_build, n_trace = scene.kernel_launches()
     err = scene.error_word(stream)
 
-    # max time over ranks, rays summed over ranks
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        r = torch.tensor([rays], dtype=torch.int64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-        total_all, rays_all = float(t.item()), int(r.item())
-    else:
-        total_all, rays_all = total_ms, rays
+    total_all, rays_all = aggregate_over_ranks(total_ms, rays, world, "cuda")
 
     if rank != 0:
         if world > 1:
@@ -435,7 +440,8 @@ def run_ours(args):
             "frac": achieved_tflops / peak_tflops, "traffic": None,
             "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
-            "trace_share_of_step": sum(trace_ms) / total_ms}
+            "trace_share_of_step": sum(trace_ms) / total_ms,
+            "work_counters": {k: v for k, v in counters.items() if v}}
     if clocks:
         roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
         roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
@@ -505,6 +511,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve_sweep(args):
+    """Serving sweep: Poisson rates x {continuous batching, plain per-request launches}."""
+    import torch
+    import paper_2012_10357_b300 as pr
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
+    tuning = None
+    if os.path.exists(tune_path):
+        cache = json.load(open(tune_path))
+        mine = [v for k, v in cache.items() if k.startswith(torch.cuda.get_device_name() + "|config4")]
+        tuning = mine[0]["tuning"] if mine else None
+    rows = []
+    for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
+        rows += bench_serving(pr, torch, args.serve_rates, args.serve_requests, mode, tuning, args.serve_max_seconds)
+    print(json.dumps({"metric": "serving p50/p99 latency and Mrays/s", "points": rows, "tuning": tuning}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,12 +540,16 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the config-1 throughput, batched and serving blocks")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[30.0, 1000.0])
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-max-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-only", action="store_true", help="only the serving sweep (both modes), one JSON line")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        run_serve_sweep(args)
     else:
         run_ours(args)
 

@@ -26,9 +26,10 @@ struct Params {
   unsigned long long* counter;
 };
 
-// Resident CTAs per SM the register allocation must allow (occupancy knob).
+// Resident CTAs per SM the register allocation must allow (occupancy knob;
+// 4 x 128 threads -> at most 128 registers, 4 x 32 KB shared stacks).
 #ifndef PR_TRACE_MIN_BLOCKS
-#define PR_TRACE_MIN_BLOCKS 1
+#define PR_TRACE_MIN_BLOCKS 4
 #endif
 
 template <bool kStats>
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
   const bool valid = x < (int)P.width && y < (int)P.height;
   uint32_t rays = 0;
   if (valid) {
-    int stack[kStackDepth];
+    PR_DECLARE_STACK(128);
     const pr_camera cam = P.cams ? P.cams[frame] : P.cam0;
     const float3 eye = ldf3(cam.eye);
     const float3 d = camera_ray(cam, x, y, P.width, P.height);

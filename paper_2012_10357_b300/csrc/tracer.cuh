@@ -12,6 +12,21 @@
 
 namespace pr {
 
+#ifndef PR_WHILE_WHILE
+#define PR_WHILE_WHILE 0
+#endif
+
+// Per-thread traversal stack. With PR_SMEM_STACK (default) the entries live in
+// shared memory, interleaved across the CTA's threads (entry i of thread t at
+// i * blockDim + t, conflict-free): 32 KB per 128-thread CTA. Otherwise in a
+// per-thread local array. Measured on B300 (interleaved A/B, same box):
+// shared stack with 4 CTAs/SM is 8-25 % faster than the local array.
+struct TravStack {
+  int* p;
+  int stride;
+  __device__ __forceinline__ int& operator[](int i) const { return p[i * stride]; }
+};
+
 struct Hit {
   float t;
   int inst;        // instance index, -1 = none
@@ -69,7 +84,7 @@ __device__ __forceinline__ void to_object(const SceneView& S, int k, float3 o, f
 // found a hit.
 template <bool kStats>
 __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
-                              uint32_t max_steps, Hit& h, int* stack, int sp0, WorkCounters* wc_) {
+                              uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->instances;
   uint4 info = __ldg(S.inst_info + k);
@@ -147,7 +162,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
 template <bool kStats>
 __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
-                          uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc_) {
+                          uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->rays;
   h.t = tmax;
@@ -159,6 +174,47 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
   float3 o_inv = f3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
   int sp = 0;
   int node = S.tlas_root_ref;
+#if PR_WHILE_WHILE
+  // While-while traversal (Aila & Laine 2009): descend internal nodes, hold
+  // back the first instance leaf reached and keep descending until every
+  // converged lane of the warp holds a leaf (or is done), then run the
+  // instance transitions and BLAS work together.
+  constexpr int kDone = 0x7FFFFFFF;
+  while (node != kDone) {
+    int leaf = kDone;
+    while (node != kDone) {
+      if (node >= 0) {
+        float l0, l1, r0, r1;
+        int lref, rref;
+        if (wc) ++wc->tlas_nodes;
+        node_boxes(S.tlas_nodes + 4 * (size_t)node, inv, o_inv, tmin, h.t, l0, l1, r0, r1, lref, rref);
+        const bool hl = l0 <= l1, hr = r0 <= r1;
+        if (hl && hr) {
+          int nearr = lref, farr = rref;
+          if (r0 < l0) { nearr = rref; farr = lref; }
+          if (sp < kStackDepth) stack[sp++] = farr;
+          else atomicOr(S.error_word, kErrStack);
+          node = nearr;
+        } else if (hl) {
+          node = lref;
+        } else if (hr) {
+          node = rref;
+        } else {
+          node = sp ? stack[--sp] : kDone;
+        }
+      }
+      if (node < 0) {
+        if (leaf != kDone) break;          // already holding a leaf: go process it
+        leaf = node;
+        node = sp ? stack[--sp] : kDone;
+      }
+      if (!__any_sync(__activemask(), leaf == kDone)) break;
+    }
+    if (leaf != kDone &&
+        traverse_blas<kStats>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+      return;
+  }
+#else
   for (;;) {
     if (node >= 0) {
       float l0, l1, r0, r1;
@@ -182,11 +238,12 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
     if (sp == 0) break;
     node = stack[--sp];
   }
+#endif
 }
 
 template <bool kStats>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
-                                            float eps, uint32_t max_steps, Hit& h, int* stack, WorkCounters* wc) {
+                                            float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc) {
   const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
   trace_ray<kStats>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
 }
@@ -277,5 +334,20 @@ __device__ __forceinline__ float3 camera_ray(const pr_camera& cam, int x, int y,
 __device__ __forceinline__ float3 miss_rgb(const SceneView& S, uint32_t r, float3 background) {
   return __ldg(S.ray_types + r).x == PR_MISS_BACKGROUND ? background : f3(0.f, 0.f, 0.f);
 }
+
+#ifndef PR_SMEM_STACK
+#define PR_SMEM_STACK 1
+#endif
+
+// Declares `stack` (a TravStack) for a kernel of kThreads threads per CTA.
+#if PR_SMEM_STACK
+#define PR_DECLARE_STACK(kThreads)                                  \
+  __shared__ int pr_stack_mem_[::pr::kStackDepth * (kThreads)];     \
+  const ::pr::TravStack stack{pr_stack_mem_ + threadIdx.x, (kThreads)}
+#else
+#define PR_DECLARE_STACK(kThreads)              \
+  int pr_stack_mem_[::pr::kStackDepth];          \
+  const ::pr::TravStack stack{pr_stack_mem_, 1}
+#endif
 
 }  // namespace pr

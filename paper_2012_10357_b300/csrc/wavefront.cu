@@ -56,14 +56,14 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* count, bool want) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(128) k_wf_primary(BatchView B) {
+__global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
   static_assert(TW * TH == 128, "128-pixel tiles");
   __shared__ ReqDev sreq;
   __shared__ uint32_t s_tile, s_req;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int WX = TW / 8;   // warps across (8x4 pixel sub-tile per warp)
   const int ox = (warp % WX) * 8 + (lane & 7), oy = (warp / WX) * 4 + (lane >> 3);
-  int stack[kStackDepth];
+  PR_DECLARE_STACK(128);
   uint32_t last_req = kFull;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(128) k_wf_primary(BatchView B) {
 }
 
 // Queue stages: each warp pops `chunk` rays at a time (lanes take every 32nd).
-__global__ void __launch_bounds__(128) k_wf_shadow(BatchView B, uint32_t chunk) {
+__global__ void __launch_bounds__(128, 4) k_wf_shadow(BatchView B, uint32_t chunk) {
   const int lane = threadIdx.x & 31;
-  int stack[kStackDepth];
+  PR_DECLARE_STACK(128);
   const uint32_t n = B.hdr->shadow_n;
   for (;;) {
     uint32_t base = 0;
@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(128) k_wf_shadow(BatchView B, uint32_t chunk) 
   }
 }
 
-__global__ void __launch_bounds__(128) k_wf_mirror(BatchView B, uint32_t chunk) {
+__global__ void __launch_bounds__(128, 4) k_wf_mirror(BatchView B, uint32_t chunk) {
   const int lane = threadIdx.x & 31;
-  int stack[kStackDepth];
+  PR_DECLARE_STACK(128);
   const uint32_t n = B.hdr->mirror_n;
   for (;;) {
     uint32_t base = 0;

@@ -375,7 +375,8 @@ def run_ours(args):
         if frames:
             scene.trace_frames(frames, w.params, out=out, ray_counter=counter, stream=stream)
         else:
-            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
+            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream,
+                        binary_tlas=args.binary_tlas)
 
     def step():
         scene.build_bvh(stream)
@@ -427,7 +428,7 @@ def run_ours(args):
     value = rays_all / (total_all / 1e3) / 1e6
 
     # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
-    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames)
+    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames, binary_tlas=args.binary_tlas)
     torch.cuda.synchronize()
     flops = work.frame_flops(counters)
     trace_avg_s = statistics.mean(trace_ms) / 1e3
@@ -542,6 +543,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--serve-max-seconds", type=float, default=60.0)
     ap.add_argument("--serve-only", action="store_true", help="only the serving sweep (both modes), one JSON line")
+    ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -60,9 +60,16 @@ typedef enum {
 #define PR_IS_METABALL4 6u   /* params: 4 centres xyz, 4 radii; smooth-min k = 0.2 */
 #define PR_IS_JULIA 7u       /* params: c (4), iterations, escape radius */
 #define PR_IS_MANDELBULB 8u  /* params: power (8), iterations, bailout */
-#define PR_IS_COUNT 9u
+#define PR_IS_JULIA_CUT 9u   /* params: as Julia, then unit plane normal (3), offset d:
+                                the set cut by the half-space n.p <= d (Fig. 5) */
+#define PR_IS_COUNT 10u
 /* Closest-hit shaders */
 #define PR_CHS_LAMBERT 0u
+/* Any-hit shaders (run on every candidate hit; may ignore it). PR_AHS_CUTOUT
+ * ignores candidates whose object-space point has frac(4*y) < 1/2 (bands cut
+ * out of the surface); allowed with the sphere, box and pac-man shaders, whose
+ * intersection shaders report their candidates in increasing t. */
+#define PR_AHS_CUTOUT 0u
 /* Miss shaders */
 #define PR_MISS_BACKGROUND 0u
 #define PR_MISS_SHADOW 1u
@@ -71,6 +78,10 @@ typedef enum {
 #define PR_RAY_SKIP_CLOSEST_HIT 2u
 /* Trace flags */
 #define PR_TRACE_WRITE_AOV 1u
+#define PR_TRACE_TLAS_BVH2 2u   /* traverse the binary TLAS instead of its 4-wide collapse */
+/* Geometry kinds */
+#define PR_GEOM_AABBS 0u
+#define PR_GEOM_TRIANGLES 1u
 /* Primitive parameter floats per AABB primitive */
 #define PR_PARAMS_PER_PRIM 16u
 /* Largest traversal stack; deeper trees set PR_ERR_STACK_OVERFLOW */
@@ -82,7 +93,7 @@ typedef struct pr_scene pr_scene;
  * paper's Section 3.1 flattened into arrays:
  *  aabbs            [n_prims][6] float  object-space lo.xyz, hi.xyz (lo <= hi)
  *  params           [n_prims][16] float shape parameters of each AABB primitive
- *  geom_prim_begin/count [n_geoms]      primitives of procedural geometry g
+ *  geom_prim_begin/count [n_geoms]      primitives of geometry g (AABBs, or triangles)
  *  blas_geom_begin/count [n_blas]       geometries of each BLAS; the geometry
  *                                       index g of Eq. 1 is the position in it
  *  inst_xform       [n_inst][12] float  object->world, row-major 3x4, invertible
@@ -90,7 +101,7 @@ typedef struct pr_scene pr_scene;
  *                   inst_sbt_offset is Eq. 1's i in records (DXR's
  *                   InstanceContributionToHitGroupIndex); mask 0 hides it
  *  hit_groups       [n_hit_groups][3] uint32 is_id, chs_id, ahs_id (PR_NONE = absent;
- *                   any-hit shaders are reserved and must be PR_NONE)
+ *                   ahs PR_AHS_CUTOUT needs an analytic intersection shader)
  *  materials        [n_materials][4] float albedo rgb, mirror reflectance
  *  sbt              [n_records][4] uint32 hit_group, material, prim_type, instance_index
  *                   (the root arguments of Listing 10)
@@ -117,6 +128,14 @@ typedef struct {
   const float* materials;
   const uint32_t* sbt;
   const uint32_t* ray_types;
+  /* Triangle geometry (the built-in triangle intersection of DXR). geom_type
+   * [n_geoms] is PR_GEOM_AABBS or PR_GEOM_TRIANGLES (NULL: all AABBs); for a
+   * triangle geometry, geom_prim_begin/count index triangles, not AABBs. A
+   * BLAS holds one kind only (as in DXR). */
+  const uint32_t* geom_type;
+  uint32_t n_vertices, n_triangles;
+  const float* vertices;     /* [n_vertices][3] object space */
+  const uint32_t* indices;   /* [n_triangles][3] vertex indices */
 } pr_scene_desc;
 
 /* Pinhole camera (ray generation shader, Section 2.2.3): rays leave eye through
@@ -198,8 +217,9 @@ pr_status pr_trace_frames(pr_scene* scene, const pr_camera* cameras, uint32_t n_
  * visits, BLAS node visits, instance transitions, leaf AABB tests, Eq. 1
  * record lookups, intersection-shader calls per shader id [PR_IS_COUNT],
  * distance-estimate evaluations per shader id [PR_IS_COUNT], Julia
- * iterations, Mandelbulb iterations, shaded hits, rays traced. */
-#define PR_WORK_COUNTERS 27u
+ * iterations, Mandelbulb iterations, shaded hits, rays traced, 4-wide TLAS
+ * node visits. */
+#define PR_WORK_COUNTERS 30u
 
 /* pr_trace_frames with an instrumented kernel variant that also adds the
  * work it did to work_counters (device, PR_WORK_COUNTERS uint64,
@@ -331,7 +351,8 @@ void pr_batch_destroy(pr_batch* batch);
  * in a cache keyed by scene_key (least recently used unreferenced scenes are
  * evicted to make room), and renders. PR_SERVE_CONTINUOUS: continuous
  * batching, every iteration one batched launch over row ranges of all
- * admitted requests (at most max_batch_pixels), so a request that arrives
+ * admitted requests (at most max_batch_pixels; an iteration that is a single
+ * whole request uses the pr_trace megakernel), so a request that arrives
  * while others are on the GPU joins at the next iteration. PR_SERVE_PLAIN:
  * one pr_trace per request, first come first served (the comparison form).
  * Results are bit-identical to pr_trace of the same request. */

@@ -52,7 +52,9 @@ class _Scene(ctypes.Structure):
         ("inst_xform", ctypes.c_void_p), ("inst_blas", ctypes.c_void_p),
         ("inst_id", ctypes.c_void_p), ("inst_sbt_offset", ctypes.c_void_p),
         ("inst_mask", ctypes.c_void_p), ("hit_groups", ctypes.c_void_p),
-        ("materials", ctypes.c_void_p), ("sbt", ctypes.c_void_p), ("ray_types", ctypes.c_void_p)]
+        ("materials", ctypes.c_void_p), ("sbt", ctypes.c_void_p), ("ray_types", ctypes.c_void_p),
+        ("geom_type", ctypes.c_void_p), ("n_vertices", ctypes.c_uint32), ("n_triangles", ctypes.c_uint32),
+        ("vertices", ctypes.c_void_p), ("indices", ctypes.c_void_p)]
 
 
 class _Camera(ctypes.Structure):
@@ -77,7 +79,7 @@ def lib():
         L.or_render.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int]
         L.or_render.restype = ctypes.c_int
         L.or_world_bounds.argtypes = [vp, vp, vp]
-        L.or_intersect.argtypes = [u32, vp, vp, vp, dbl, dbl, dbl, u32, vp, vp, vp]
+        L.or_intersect.argtypes = [u32, u32, vp, vp, vp, dbl, dbl, dbl, u32, vp, vp, vp]
         L.or_intersect.restype = ctypes.c_int
         L.or_de.argtypes = [u32, vp, vp]
         L.or_de.restype = dbl
@@ -117,6 +119,15 @@ class _SceneRef:
         s.sbt_stride_m = int(sc.sbt_stride_m)
         for k, a in self.arrays.items():
             setattr(s, k, a.ctypes.data)
+        gt = getattr(sc, "geom_type", None)
+        self.tri = dict(vertices=c(getattr(sc, "vertices", np.zeros((0, 3))), np.float32).reshape(-1, 3),
+                        indices=c(getattr(sc, "indices", np.zeros((0, 3))), np.uint32).reshape(-1, 3))
+        if gt is not None:
+            self.tri["geom_type"] = c(gt, np.uint32)
+            s.geom_type = self.tri["geom_type"].ctypes.data
+        s.n_vertices, s.n_triangles = len(self.tri["vertices"]), len(self.tri["indices"])
+        s.vertices = self.tri["vertices"].ctypes.data if s.n_vertices else None
+        s.indices = self.tri["indices"].ctypes.data if s.n_triangles else None
         self.struct = s
 
 
@@ -166,13 +177,13 @@ def world_bounds(scene):
     return lo, hi
 
 
-def intersect(is_id, params, o, d, t_lo, t_hi=np.inf, eps=1e-4, max_steps=256):
-    """One object-space primitive. Returns (t, normal, steps) or None."""
+def intersect(is_id, params, o, d, t_lo, t_hi=np.inf, eps=1e-4, max_steps=256, ahs_id=0xFFFFFFFF):
+    """One object-space primitive (optionally with an any-hit shader). Returns (t, normal, steps) or None."""
     prm = np.zeros(16, np.float32)
     prm[: len(params)] = params
     o, d = np.asarray(o, np.float64), np.asarray(d, np.float64)
     t, n, st = ctypes.c_double(), np.zeros(3), ctypes.c_uint32()
-    hit = lib().or_intersect(is_id, _ptr(prm), _ptr(o), _ptr(d), float(t_lo), float(t_hi), float(eps),
+    hit = lib().or_intersect(is_id, ahs_id, _ptr(prm), _ptr(o), _ptr(d), float(t_lo), float(t_hi), float(eps),
                              max_steps, ctypes.byref(t), _ptr(n), ctypes.byref(st))
     return (t.value, n, st.value) if hit else None
 
@@ -213,10 +224,16 @@ def lbvh_f32(boxes: np.ndarray):
 
 
 def blas_leaf_boxes(scene, b: int) -> np.ndarray:
-    """Object-space AABBs of BLAS b in geometry-major order (the BLAS's leaf input)."""
+    """Object-space boxes of BLAS b's primitives in geometry-major order (the BLAS's
+    leaf input): AABBs as given, triangles' vertex bounds."""
     g0, gn = int(scene.blas_geom_begin[b]), int(scene.blas_geom_count[b])
+    gt = getattr(scene, "geom_type", None)
     rows = []
     for g in range(g0, g0 + gn):
         p0, pn = int(scene.geom_prim_begin[g]), int(scene.geom_prim_count[g])
-        rows.append(scene.aabbs[p0:p0 + pn])
+        if gt is not None and int(gt[g]) == 1:
+            tv = np.asarray(scene.vertices, np.float32)[np.asarray(scene.indices)[p0:p0 + pn]]   # [n,3,3]
+            rows.append(np.concatenate([tv.min(1), tv.max(1)], 1))
+        else:
+            rows.append(scene.aabbs[p0:p0 + pn])
     return np.concatenate(rows).astype(np.float32)

@@ -34,15 +34,18 @@ namespace {
 
 // ---- shader ids (scene input format) -------------------------------------
 constexpr uint32_t kSphere = 0, kBox = 1, kPacman = 2, kTorus = 3, kRoundbox = 4,
-                   kCapsule = 5, kMetaball4 = 6, kJulia = 7, kMandelbulb = 8;
+                   kCapsule = 5, kMetaball4 = 6, kJulia = 7, kMandelbulb = 8, kJuliaCut = 9;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kChsLambert = 0;
+constexpr uint32_t kAhsCutout = 0;
+constexpr uint32_t kGeomTriangles = 1;
+constexpr uint32_t kTriangleHit = 1000;   // marks a hit on built-in triangle geometry
 constexpr uint32_t kMissBackground = 0, kMissShadow = 1;
 constexpr uint32_t kTerminateOnFirstHit = 1;
 constexpr double kMetaballK = 0.2;
 constexpr double kInf = std::numeric_limits<double>::infinity();
 
-bool is_sphere_traced(uint32_t id) { return id >= kTorus && id <= kMandelbulb; }
+bool is_sphere_traced(uint32_t id) { return id >= kTorus && id <= kJuliaCut; }
 
 // ---- small vector algebra ----------------------------------------------
 struct V3 { double x, y, z; };
@@ -145,7 +148,17 @@ struct IsHit { double t; V3 n; uint32_t steps; };
 
 // Sphere (centre c, radius R): roots of |o + t d - c|^2 = R^2; the first root
 // with t >= tmin (the far root when the origin is inside). Normal (p - c) / R.
-bool is_sphere(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
+// Any-hit "cutout" shader: ignores candidate hits whose object-space point
+// lies in the lower half of every band of height 1/4 along y (frac(4y) < 1/2).
+// A hit group's any-hit shader runs on every candidate an intersection shader
+// reports (Section 2.2.3); an ignored candidate lets the search continue.
+bool any_hit_accepts(uint32_t ahs, V3 p) {
+  if (ahs != kAhsCutout) return true;
+  double b = 4.0 * p.y;
+  return b - std::floor(b) >= 0.5;
+}
+
+bool is_sphere(const float* prm, V3 o, V3 d, double tmin, IsHit& h, uint32_t ahs) {
   V3 c = fromf(prm);
   double R = prm[3];
   V3 oc = o - c;
@@ -155,8 +168,8 @@ bool is_sphere(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
   double sq = std::sqrt(disc);
   double t0 = (-b - sq) / a, t1 = (-b + sq) / a;
   double t;
-  if (t0 >= tmin) t = t0;
-  else if (t1 >= tmin) t = t1;
+  if (t0 >= tmin && any_hit_accepts(ahs, o + t0 * d)) t = t0;
+  else if (t1 >= tmin && any_hit_accepts(ahs, o + t1 * d)) t = t1;
   else return false;
   h.t = t;
   h.n = (o + t * d - c) * (1.0 / R);
@@ -166,15 +179,15 @@ bool is_sphere(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
 
 // Axis-aligned box (centre c, half extent e): the slab entry point when it is
 // at or beyond tmin (normal: entering face, against d), else the exit point.
-bool is_box(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
+bool is_box(const float* prm, V3 o, V3 d, double tmin, IsHit& h, uint32_t ahs) {
   V3 c = fromf(prm), e = fromf(prm + 3);
   double te, tx;
   int ea, xa;
   if (!slab_interval(o, d, c - e, c + e, te, tx, &ea, &xa)) return false;
-  if (te >= tmin) {
+  if (te >= tmin && any_hit_accepts(ahs, o + te * d)) {
     h.t = te;
     h.n = axis(ea, comp(d, ea) > 0 ? -1.0 : 1.0);
-  } else if (tx >= tmin) {
+  } else if (tx >= tmin && any_hit_accepts(ahs, o + tx * d)) {
     h.t = tx;
     h.n = axis(xa, comp(d, xa) > 0 ? 1.0 : -1.0);
   } else {
@@ -190,7 +203,7 @@ bool is_box(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
 // [s0, s1] and the wedge one interval (w0, w1); the solid is their difference.
 // The hit is its first boundary point with t >= tmin. Normals: the ball's
 // (p - c) / R, or -n_k on the face of wedge plane k.
-bool is_pacman(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
+bool is_pacman(const float* prm, V3 o, V3 d, double tmin, IsHit& h, uint32_t ahs) {
   V3 c = fromf(prm);
   double R = prm[3], a = prm[4];
   V3 oc = o - c;
@@ -229,7 +242,7 @@ bool is_pacman(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
     if (w1 < s1) { ev[ne++] = {w1, p1}; ev[ne++] = {s1, -1}; }
   }
   for (int i = 0; i < ne; ++i) {
-    if (ev[i].t >= tmin) {
+    if (ev[i].t >= tmin && any_hit_accepts(ahs, o + ev[i].t * d)) {
       h.t = ev[i].t;
       h.n = ev[i].kind < 0 ? (o + h.t * d - c) * (1.0 / R) : -nrm[ev[i].kind];
       h.steps = 0;
@@ -237,6 +250,30 @@ bool is_pacman(const float* prm, V3 o, V3 d, double tmin, IsHit& h) {
     }
   }
   return false;
+}
+
+// Built-in triangle intersection (DXR's fixed-function test), written as
+// Moller & Trumbore 1997: t and barycentrics (u, v) from Cramer's rule on
+// o + t d = v0 + u e1 + v e2; a hit needs u, v >= 0, u + v <= 1 and t >= tmin
+// (and the any-hit shader's consent). Normal: e1 x e2, normalised.
+bool is_triangle(V3 v0, V3 v1, V3 v2, V3 o, V3 d, double tmin, IsHit& h, uint32_t ahs) {
+  V3 e1 = v1 - v0, e2 = v2 - v0;
+  V3 pv = cross(d, e2);
+  double det = dot(e1, pv);
+  if (det == 0.0) return false;
+  double inv = 1.0 / det;
+  V3 tv = o - v0;
+  double u = dot(tv, pv) * inv;
+  if (u < 0.0 || u > 1.0) return false;
+  V3 qv = cross(tv, e1);
+  double v = dot(d, qv) * inv;
+  if (v < 0.0 || u + v > 1.0) return false;
+  double t = dot(e2, qv) * inv;
+  if (t < tmin || !any_hit_accepts(ahs, o + t * d)) return false;
+  h.t = t;
+  h.n = normalize(cross(e1, e2));
+  h.steps = 0;
+  return true;
 }
 
 // ---- distance estimators (object space) -----------------------------------
@@ -339,6 +376,14 @@ double de_mandelbulb(const float* prm, V3 p) {
   return 0.0;
 }
 
+// Julia set cut by a plane (the paper's Fig. 5): the set intersected with the
+// half-space n.p <= d (unit n = prm[6..8], d = prm[9]). The larger of the two
+// distance bounds bounds the distance to the intersection from below.
+double de_julia_cut(const float* prm, V3 p) {
+  V3 n = fromf(prm + 6);
+  return std::max(de_julia(prm, p), dot(n, p) - (double)prm[9]);
+}
+
 double distance_estimate(uint32_t id, const float* prm, V3 p) {
   switch (id) {
     case kTorus: return sdf_torus(prm, p);
@@ -347,6 +392,7 @@ double distance_estimate(uint32_t id, const float* prm, V3 p) {
     case kMetaball4: return sdf_metaball4(prm, p);
     case kJulia: return de_julia(prm, p);
     case kMandelbulb: return de_mandelbulb(prm, p);
+    case kJuliaCut: return de_julia_cut(prm, p);
     default: return kInf;
   }
 }
@@ -385,11 +431,11 @@ bool is_sphere_trace(uint32_t id, const float* prm, V3 o, V3 d, double t_lo, dou
 // Intersection-shader dispatch by shader id. Analytic shaders report their
 // first surface point at t >= tmin; sphere-traced ones march [t_lo, t_hi].
 bool intersect(uint32_t id, const float* prm, V3 o, V3 d, double tmin, double t_lo, double t_hi, double eps,
-               uint32_t max_steps, IsHit& h) {
+               uint32_t max_steps, IsHit& h, uint32_t ahs = kNone) {
   switch (id) {
-    case kSphere: return is_sphere(prm, o, d, tmin, h);
-    case kBox: return is_box(prm, o, d, tmin, h);
-    case kPacman: return is_pacman(prm, o, d, tmin, h);
+    case kSphere: return is_sphere(prm, o, d, tmin, h, ahs);
+    case kBox: return is_box(prm, o, d, tmin, h, ahs);
+    case kPacman: return is_pacman(prm, o, d, tmin, h, ahs);
     default:
       if (is_sphere_traced(id)) return is_sphere_trace(id, prm, o, d, t_lo, t_hi, eps, max_steps, h);
       return false;
@@ -406,13 +452,37 @@ struct Prepared {
   double eps;
 };
 
+bool is_triangle_geom(const or_scene* s, uint32_t geom) {
+  return s->geom_type && s->geom_type[geom] == kGeomTriangles;
+}
+
+// Object-space box of one primitive: an AABB as given, or a triangle's vertex bounds.
+void prim_box(const or_scene* s, uint32_t geom, uint32_t prim, float out[6]) {
+  if (!is_triangle_geom(s, geom)) {
+    std::memcpy(out, s->aabbs + 6 * (size_t)prim, 6 * sizeof(float));
+    return;
+  }
+  const uint32_t* t = s->indices + 3 * (size_t)prim;
+  for (int k = 0; k < 3; ++k) {
+    out[k] = INFINITY;
+    out[3 + k] = -INFINITY;
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 3; ++k) {
+      float v = s->vertices[3 * (size_t)t[c] + k];
+      out[k] = std::min(out[k], v);
+      out[3 + k] = std::max(out[3 + k], v);
+    }
+}
+
 void blas_root_box(const or_scene* s, uint32_t b, V3& lo, V3& hi) {
   lo = {kInf, kInf, kInf};
   hi = {-kInf, -kInf, -kInf};
   for (uint32_t g = 0; g < s->blas_geom_count[b]; ++g) {
     uint32_t geom = s->blas_geom_begin[b] + g;
     for (uint32_t q = 0; q < s->geom_prim_count[geom]; ++q) {
-      const float* bx = s->aabbs + 6 * (size_t)(s->geom_prim_begin[geom] + q);
+      float bx[6];
+      prim_box(s, geom, s->geom_prim_begin[geom] + q, bx);
       lo = {std::min(lo.x, (double)bx[0]), std::min(lo.y, (double)bx[1]), std::min(lo.z, (double)bx[2])};
       hi = {std::max(hi.x, (double)bx[3]), std::max(hi.y, (double)bx[4]), std::max(hi.z, (double)bx[5])};
     }
@@ -488,21 +558,36 @@ Hit trace_ray(const Prepared& P, V3 o, V3 d, uint32_t r, double tmin, double tma
     uint32_t b = s->inst_blas[k];
     for (uint32_t g = 0; g < s->blas_geom_count[b]; ++g) {
       uint32_t geom = s->blas_geom_begin[b] + g;
+      const bool tri = is_triangle_geom(s, geom);
       for (uint32_t q = 0; q < s->geom_prim_count[geom]; ++q) {
         uint32_t prim = s->geom_prim_begin[geom] + q;
-        const float* bx = s->aabbs + 6 * (size_t)prim;
-        double be, bxit;
-        if (!slab_interval(oo, dd, fromf(bx), fromf(bx + 3), be, bxit)) continue;
-        double t_lo = std::max(be, tmin), t_hi = std::min(bxit, best.t);
-        if (t_lo > t_hi) continue;
-        uint64_t rec = (uint64_t)r + (uint64_t)s->sbt_stride_m * g + s->inst_sbt_offset[k];
-        if (rec >= s->n_records) { sbt_error = true; continue; }
-        uint32_t hg = s->sbt[4 * rec + 0];
-        if (hg >= s->n_hit_groups) { sbt_error = true; continue; }
-        uint32_t is_id = s->hit_groups[3 * hg + 0];
         IsHit ih;
-        if (!intersect(is_id, s->params + 16 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, P.eps, max_steps, ih))
-          continue;
+        uint64_t rec = (uint64_t)r + (uint64_t)s->sbt_stride_m * g + s->inst_sbt_offset[k];
+        uint32_t is_id;
+        if (tri) {
+          // built-in triangle test; the record still supplies the hit group
+          const uint32_t* t = s->indices + 3 * (size_t)prim;
+          V3 v0 = fromf(s->vertices + 3 * (size_t)t[0]), v1 = fromf(s->vertices + 3 * (size_t)t[1]),
+             v2 = fromf(s->vertices + 3 * (size_t)t[2]);
+          if (rec >= s->n_records) { sbt_error = true; continue; }
+          uint32_t hg = s->sbt[4 * rec + 0];
+          if (hg >= s->n_hit_groups) { sbt_error = true; continue; }
+          if (!is_triangle(v0, v1, v2, oo, dd, tmin, ih, s->hit_groups[3 * hg + 2])) continue;
+          is_id = kTriangleHit;
+        } else {
+          const float* bx = s->aabbs + 6 * (size_t)prim;
+          double be, bxit;
+          if (!slab_interval(oo, dd, fromf(bx), fromf(bx + 3), be, bxit)) continue;
+          double t_lo = std::max(be, tmin), t_hi = std::min(bxit, best.t);
+          if (t_lo > t_hi) continue;
+          if (rec >= s->n_records) { sbt_error = true; continue; }
+          uint32_t hg = s->sbt[4 * rec + 0];
+          if (hg >= s->n_hit_groups) { sbt_error = true; continue; }
+          is_id = s->hit_groups[3 * hg + 0];
+          uint32_t ahs_id = s->hit_groups[3 * hg + 2];
+          if (!intersect(is_id, s->params + 16 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, P.eps, max_steps, ih, ahs_id))
+            continue;
+        }
         if (ih.t < tmin) continue;
         bool accept = ih.t < best.t ||
                       (best.valid && ih.t == best.t && key_less((int32_t)k, (int32_t)g, (int32_t)q, best.inst, best.geom, best.prim));
@@ -731,10 +816,11 @@ int or_world_bounds(const or_scene* s, double lo[3], double hi[3]) {
   return 0;
 }
 
-int or_intersect(uint32_t is_id, const float* params, const double o[3], const double d[3], double t_lo, double t_hi,
-                 double eps, uint32_t max_steps, double* t_out, double n_out[3], uint32_t* steps_out) {
+int or_intersect(uint32_t is_id, uint32_t ahs_id, const float* params, const double o[3], const double d[3],
+                 double t_lo, double t_hi, double eps, uint32_t max_steps, double* t_out, double n_out[3],
+                 uint32_t* steps_out) {
   IsHit h;
-  if (!intersect(is_id, params, from(o), from(d), t_lo, t_lo, t_hi, eps, max_steps, h)) return 0;
+  if (!intersect(is_id, params, from(o), from(d), t_lo, t_lo, t_hi, eps, max_steps, h, ahs_id)) return 0;
   *t_out = h.t;
   n_out[0] = h.n.x; n_out[1] = h.n.y; n_out[2] = h.n.z;
   if (steps_out) *steps_out = h.steps;
@@ -755,7 +841,8 @@ int or_instance_boxes_f32(const or_scene* s, float* boxes_out) {
     for (uint32_t g = 0; g < s->blas_geom_count[b]; ++g) {
       uint32_t geom = s->blas_geom_begin[b] + g;
       for (uint32_t q = 0; q < s->geom_prim_count[geom]; ++q) {
-        const float* bx = s->aabbs + 6 * (size_t)(s->geom_prim_begin[geom] + q);
+        float bx[6];
+        prim_box(s, geom, s->geom_prim_begin[geom] + q, bx);
         for (int k = 0; k < 3; ++k) {
           lo[k] = std::min(lo[k], bx[k]);
           hi[k] = std::max(hi[k], bx[3 + k]);

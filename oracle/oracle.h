@@ -29,6 +29,10 @@ typedef struct {
   const float* materials;        /* [n_materials][4] albedo rgb, reflectance */
   const uint32_t* sbt;           /* [n_records][4] hit_group, material, prim_type, instance_index */
   const uint32_t* ray_types;     /* [n_ray_types][2] miss_id, flags */
+  const uint32_t* geom_type;     /* [n_geoms] 0 AABBs, 1 triangles; NULL: all AABBs */
+  uint32_t n_vertices, n_triangles;
+  const float* vertices;         /* [n_vertices][3] */
+  const uint32_t* indices;       /* [n_triangles][3]; a triangle geometry's prim range indexes these */
 } or_scene;
 
 typedef struct { double eye[3], look_at[3], up[3], vfov_deg; } or_camera;
@@ -59,10 +63,11 @@ int or_render(const or_scene* s, const or_camera* cam, const or_params* p,
 /* World bounds of all instances (FP64, 8-corner transform) and the epsilon it implies. */
 int or_world_bounds(const or_scene* s, double lo[3], double hi[3]);
 
-/* Single object-space primitive: first surface point at t >= t_lo (analytic) or
- * sphere-traced inside [t_lo, t_hi]. Returns 1 on hit and fills t and the
- * object-space normal. eps is the world epsilon; |d| may differ from 1. */
-int or_intersect(uint32_t is_id, const float* params, const double o[3], const double d[3],
+/* Single object-space primitive: first surface point at t >= t_lo (analytic;
+ * candidates an any-hit shader ahs_id rejects are skipped) or sphere-traced
+ * inside [t_lo, t_hi]. Returns 1 on hit and fills t and the object-space
+ * normal. eps is the world epsilon; |d| may differ from 1. */
+int or_intersect(uint32_t is_id, uint32_t ahs_id, const float* params, const double o[3], const double d[3],
                  double t_lo, double t_hi, double eps, uint32_t max_steps,
                  double* t_out, double n_out[3], uint32_t* steps_out);
 

@@ -28,12 +28,13 @@ PR_OK, PR_ERR_INVALID_ARG, PR_ERR_OUT_OF_MEMORY, PR_ERR_CUDA = 0, 1, 2, 3
 PR_ERR_SBT_INDEX, PR_ERR_STACK_OVERFLOW, PR_ERR_TIMEOUT, PR_ERR_NOT_BUILT, PR_ERR_BUDGET = 4, 5, 6, 7, 8
 PR_NONE = 0xFFFFFFFF
 PR_TRACE_WRITE_AOV = 1
+PR_TRACE_TLAS_BVH2 = 2
 ERR_WORD_SBT = 1 << PR_ERR_SBT_INDEX
 ERR_WORD_STACK = 1 << PR_ERR_STACK_OVERFLOW
-PR_IS_COUNT = 9
+PR_IS_COUNT = 10
 WORK_FIELDS = (["tlas_nodes", "blas_nodes", "instances", "leaves", "sbt_lookups"] +
                [f"is_calls_{i}" for i in range(PR_IS_COUNT)] + [f"de_evals_{i}" for i in range(PR_IS_COUNT)] +
-               ["julia_iters", "mandelbulb_iters", "shaded", "rays"])
+               ["julia_iters", "mandelbulb_iters", "shaded", "rays", "tlas_nodes4"])
 
 AOV_DTYPE = np.dtype([("t", "<f4"), ("inst", "<u4"), ("geom", "<u4"), ("prim", "<u4"), ("n", "<f4", 3),
                       ("flags", "<u4"), ("refl_t", "<f4"), ("refl_inst", "<u4"), ("refl_geom", "<u4"),
@@ -55,7 +56,9 @@ class _SceneDesc(ctypes.Structure):
         (n, ctypes.c_void_p) for n in (
             "aabbs", "params", "geom_prim_begin", "geom_prim_count", "blas_geom_begin", "blas_geom_count",
             "inst_xform", "inst_blas", "inst_id", "inst_sbt_offset", "inst_mask", "hit_groups", "materials",
-            "sbt", "ray_types")]
+            "sbt", "ray_types", "geom_type")] + [
+        ("n_vertices", ctypes.c_uint32), ("n_triangles", ctypes.c_uint32),
+        ("vertices", ctypes.c_void_p), ("indices", ctypes.c_void_p)]
 
 
 class _Camera(ctypes.Structure):
@@ -157,8 +160,18 @@ class _DescRef:
         d.n_records, d.n_ray_types, d.sbt_stride_m = len(a["sbt"]), len(a["ray_types"]), int(sc.sbt_stride_m)
         for k, v in a.items():
             setattr(d, k, v.ctypes.data if v.size else None)
+        gt = getattr(sc, "geom_type", None)
+        tri = dict(vertices=c(getattr(sc, "vertices", np.zeros((0, 3))), np.float32).reshape(-1, 3),
+                   indices=c(getattr(sc, "indices", np.zeros((0, 3))), np.uint32).reshape(-1, 3))
+        if gt is not None:
+            tri["geom_type"] = c(gt, np.uint32)
+            d.geom_type = tri["geom_type"].ctypes.data
+        d.n_vertices, d.n_triangles = len(tri["vertices"]), len(tri["indices"])
+        d.vertices = tri["vertices"].ctypes.data if d.n_vertices else None
+        d.indices = tri["indices"].ctypes.data if d.n_triangles else None
+        self.arrays.update(tri)
         self.struct = d
-        self.nbytes = int(sum(v.nbytes for v in a.values()))
+        self.nbytes = int(sum(v.nbytes for v in self.arrays.values()))
 
 
 def validate(desc) -> None:
@@ -175,11 +188,11 @@ def _camera(cam) -> _Camera:
     return c
 
 
-def trace_params(tp, aov: bool = False) -> _TraceParams:
+def trace_params(tp, aov: bool = False, extra_flags: int = 0) -> _TraceParams:
     p = _TraceParams()
     p.struct_size = ctypes.sizeof(_TraceParams)
     p.width, p.height, p.max_depth, p.max_steps = tp.width, tp.height, tp.max_depth, tp.max_steps
-    p.flags = PR_TRACE_WRITE_AOV if aov else 0
+    p.flags = (PR_TRACE_WRITE_AOV if aov else 0) | extra_flags
     p.light_pos[:] = [float(v) for v in tp.light_pos]
     p.light_intensity, p.eps_rel, p.ambient = float(tp.light_intensity), float(tp.eps_rel), float(tp.ambient)
     p.background[:] = [float(v) for v in tp.background]
@@ -231,9 +244,11 @@ class Scene:
     def build_bvh(self, stream=None):
         _check(_lib.pr_build_bvh(self._h, _stream_handle(stream)), "pr_build_bvh")
 
-    def trace(self, camera, params, out=None, aov=None, ray_counter=None, stream=None, want_aov: bool = False):
+    def trace(self, camera, params, out=None, aov=None, ray_counter=None, stream=None, want_aov: bool = False,
+              binary_tlas: bool = False):
         """Render one frame. Returns the float32 [H, W, 4] device tensor (and the
-        uint8 [H, W, 48] AOV tensor when want_aov or aov is given)."""
+        uint8 [H, W, 48] AOV tensor when want_aov or aov is given). binary_tlas
+        traverses the binary TLAS instead of its 4-wide collapse."""
         import torch
         W, H = params.width, params.height
         if out is None:
@@ -241,13 +256,13 @@ class Scene:
         if want_aov and aov is None:
             aov = torch.empty((H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         cam = _camera(camera)
-        tp = trace_params(params, aov is not None)
+        tp = trace_params(params, aov is not None, PR_TRACE_TLAS_BVH2 if binary_tlas else 0)
         _check(_lib.pr_trace(self._h, ctypes.byref(cam), ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
                              _stream_handle(stream)), "pr_trace")
         return (out, aov) if aov is not None else out
 
     def trace_frames(self, cameras: Sequence, params, out=None, aov=None, ray_counter=None, stream=None,
-                     want_aov: bool = False):
+                     want_aov: bool = False, binary_tlas: bool = False):
         import torch
         n = len(cameras)
         W, H = params.width, params.height
@@ -256,12 +271,12 @@ class Scene:
         if want_aov and aov is None:
             aov = torch.empty((n, H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         cams = cameras.array if isinstance(cameras, CameraArray) else CameraArray(cameras).array
-        tp = trace_params(params, aov is not None)
+        tp = trace_params(params, aov is not None, PR_TRACE_TLAS_BVH2 if binary_tlas else 0)
         _check(_lib.pr_trace_frames(self._h, cams, n, ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
                                     _stream_handle(stream)), "pr_trace_frames")
         return (out, aov) if aov is not None else out
 
-    def trace_work(self, camera, params, out=None, stream=None, cameras=None) -> dict:
+    def trace_work(self, camera, params, out=None, stream=None, cameras=None, binary_tlas: bool = False) -> dict:
         """Instrumented trace (one camera, or a list of cameras for a multi-frame
         launch): returns the work counters (see PR_WORK_COUNTERS)."""
         import torch
@@ -273,7 +288,7 @@ class Scene:
         work = torch.zeros(len(WORK_FIELDS), dtype=torch.int64, device="cuda")
         arr = ca.array
         cams = ca
-        tp = trace_params(params, False)
+        tp = trace_params(params, False, PR_TRACE_TLAS_BVH2 if binary_tlas else 0)
         _check(_lib.pr_trace_work(self._h, arr, len(cams), ctypes.byref(tp), _dptr(out), _dptr(work),
                                   _stream_handle(stream)), "pr_trace_work")
         torch.cuda.synchronize()          # the launch stream may not be torch's current stream

@@ -42,6 +42,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Counts and host-side flattening of a description.
 struct Layout {
   uint32_t n_prims, n_geoms, n_blas, n_inst, n_hg, n_mat, n_rec, n_rt, m;
+  uint32_t n_vert = 0, n_tri = 0;
+  std::vector<uint8_t> blas_tri;     // 1 if the BLAS holds triangles
   std::vector<uint32_t> leaf_prim;   // flattened BLAS leaves
   std::vector<uint32_t> leaf_gq;     // pairs (g, q)
   std::vector<int> blas_info;        // 4 ints per BLAS
@@ -87,18 +89,36 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
       if (!(std::isfinite(b[k]) && std::isfinite(b[3 + k]) && b[k] <= b[3 + k]))
         return fail(PR_ERR_INVALID_ARG, "AABB " + std::to_string(p) + " not finite or lo > hi");
   }
+  L.n_vert = d->n_vertices;
+  L.n_tri = d->n_triangles;
+  if ((L.n_vert && !d->vertices) || (L.n_tri && !d->indices))
+    return fail(PR_ERR_INVALID_ARG, "null vertices/indices");
+  if (L.n_vert > (1u << 28) || L.n_tri > (1u << 28)) return fail(PR_ERR_INVALID_ARG, "too many vertices/triangles");
+  for (uint32_t v = 0; v < 3 * L.n_vert; ++v)
+    if (!std::isfinite(d->vertices[v])) return fail(PR_ERR_INVALID_ARG, "vertex not finite");
+  for (uint32_t t = 0; t < 3 * L.n_tri; ++t)
+    if (d->indices[t] >= L.n_vert) return fail(PR_ERR_INVALID_ARG, "triangle vertex index out of range");
+  auto is_tri = [&](uint32_t g) { return d->geom_type && d->geom_type[g] == PR_GEOM_TRIANGLES; };
   for (uint32_t g = 0; g < L.n_geoms; ++g) {
+    if (d->geom_type && d->geom_type[g] != PR_GEOM_AABBS && d->geom_type[g] != PR_GEOM_TRIANGLES)
+      return fail(PR_ERR_INVALID_ARG, "unknown geometry type");
     uint64_t e = (uint64_t)d->geom_prim_begin[g] + d->geom_prim_count[g];
-    if (d->geom_prim_count[g] == 0 || e > L.n_prims)
+    if (d->geom_prim_count[g] == 0 || e > (is_tri(g) ? L.n_tri : L.n_prims))
       return fail(PR_ERR_INVALID_ARG, "geometry " + std::to_string(g) + " primitive range empty or out of bounds");
   }
   L.blas_info.assign(4 * (size_t)L.n_blas, 0);
+  L.blas_tri.assign(L.n_blas, 0);
   uint32_t max_geoms = 0;
   for (uint32_t b = 0; b < L.n_blas; ++b) {
     uint64_t e = (uint64_t)d->blas_geom_begin[b] + d->blas_geom_count[b];
     if (d->blas_geom_count[b] == 0 || e > L.n_geoms)
       return fail(PR_ERR_INVALID_ARG, "BLAS " + std::to_string(b) + " geometry range empty or out of bounds");
     max_geoms = std::max(max_geoms, d->blas_geom_count[b]);
+    const bool tri = is_tri(d->blas_geom_begin[b]);
+    for (uint32_t g = 1; g < d->blas_geom_count[b]; ++g)
+      if (is_tri(d->blas_geom_begin[b] + g) != tri)
+        return fail(PR_ERR_INVALID_ARG, "BLAS " + std::to_string(b) + " mixes triangle and AABB geometries");
+    L.blas_tri[b] = tri ? 1 : 0;
     uint32_t first = L.n_leaves;
     for (uint32_t g = 0; g < d->blas_geom_count[b]; ++g) {
       uint32_t geom = d->blas_geom_begin[b] + g;
@@ -113,7 +133,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
     L.blas_info[4 * b + 0] = (int)L.n_blas_nodes;
     L.blas_info[4 * b + 1] = (int)first;
     L.blas_info[4 * b + 2] = (int)n;
-    L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | first) : 0;
+    L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | (tri ? kTriBit : 0u) | first) : 0;
     L.n_blas_nodes += n - 1;
     if (n > kSmallMax) L.max_large = std::max(L.max_large, n);
   }
@@ -136,7 +156,9 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
     uint32_t is = d->hit_groups[3 * h], chs = d->hit_groups[3 * h + 1], ahs = d->hit_groups[3 * h + 2];
     if (is != PR_NONE && is >= PR_IS_COUNT) return fail(PR_ERR_INVALID_ARG, "unknown intersection shader id");
     if (chs != PR_NONE && chs != PR_CHS_LAMBERT) return fail(PR_ERR_INVALID_ARG, "unknown closest-hit shader id");
-    if (ahs != PR_NONE) return fail(PR_ERR_INVALID_ARG, "any-hit shaders are reserved (must be PR_NONE)");
+    if (ahs != PR_NONE && ahs != PR_AHS_CUTOUT) return fail(PR_ERR_INVALID_ARG, "unknown any-hit shader id");
+    if (ahs == PR_AHS_CUTOUT && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN)
+      return fail(PR_ERR_INVALID_ARG, "any-hit shaders need an analytic intersection shader (sphere, box, pac-man)");
   }
   for (uint32_t r = 0; r < L.n_rec; ++r) {
     if (d->sbt[4 * r] >= L.n_hg) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " hit group out of range");
@@ -166,6 +188,9 @@ struct pr_scene {
   uint32_t* leaf_prim;
   uint2* leaf_gq;
   int4* blas_info;
+  float* vertices;
+  uint32_t* indices;
+  float* tri_boxes;
   // BVH
   float4* blas_box;
   float4* blas_nodes;
@@ -174,6 +199,8 @@ struct pr_scene {
   uint4* inst_info;
   float* inst_boxes;
   float4* tlas_nodes;
+  float4* tlas4;                     // 4-wide TLAS collapsed from tlas_nodes
+  uint32_t *c4_parent, *c4_even, *c4_rank;
   uint32_t *tlas_perm, *tlas_codes;
   float* scene_box;
   uint32_t* error_word;
@@ -229,6 +256,8 @@ pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
   PR_CUDA(cp(s->leaf_prim, L.leaf_prim.data(), sizeof(uint32_t) * L.n_leaves), "copy leaves");
   PR_CUDA(cp(s->leaf_gq, L.leaf_gq.data(), sizeof(uint32_t) * 2 * L.n_leaves), "copy leaf gq");
   PR_CUDA(cp(s->blas_info, L.blas_info.data(), sizeof(int) * 4 * L.n_blas), "copy blas info");
+  PR_CUDA(cp(s->vertices, d->vertices, sizeof(float) * 3 * L.n_vert), "copy vertices");
+  PR_CUDA(cp(s->indices, d->indices, sizeof(uint32_t) * 3 * L.n_tri), "copy indices");
   // hit groups vector is a local: make sure the pageable copy has been staged
   PR_CUDA(cudaStreamSynchronize(st), "sync upload");
   s->built = false;
@@ -241,12 +270,16 @@ SceneView view_of(const pr_scene* s) {
   v.inst_info = s->inst_info;
   v.tlas_nodes = s->tlas_nodes;
   v.tlas_root_ref = s->L.n_inst == 1 ? (int)kLeafBit : 0;
+  v.tlas4 = s->L.n_inst >= 2 ? s->tlas4 : nullptr;
+  v.tlas4_root = v.tlas_root_ref;
   v.scene_box = s->scene_box;
   v.blas_info = s->blas_info;
   v.blas_box = s->blas_box;
   v.blas_nodes = s->blas_nodes;
   v.leaf_prim = s->leaf_prim;
   v.leaf_gq = s->leaf_gq;
+  v.vertices = s->vertices;
+  v.indices = s->indices;
   v.aabbs = s->aabbs;
   v.params = s->params;
   v.sbt = s->sbt;
@@ -346,10 +379,14 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
          o_hg = c.take<uint4>(L.n_hg), o_mat = c.take<float4>(L.n_mat), o_sbt = c.take<uint4>(L.n_rec),
          o_rt = c.take<uint2>(L.n_rt), o_lp = c.take<uint32_t>(L.n_leaves), o_lgq = c.take<uint2>(L.n_leaves),
          o_binfo = c.take<int4>(L.n_blas), o_bbox = c.take<float4>(2 * (size_t)L.n_blas),
+         o_vert = c.take<float>(3 * (size_t)L.n_vert), o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri),
+         o_tbox = c.take<float>(6 * (size_t)L.n_tri),
          o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes), o_bperm = c.take<uint32_t>(L.n_leaves),
          o_bcodes = c.take<uint32_t>(L.n_leaves), o_w2o = c.take<float4>(3 * (size_t)L.n_inst),
          o_info = c.take<uint4>(L.n_inst), o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
-         o_tnodes = c.take<float4>(4 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)), o_tperm = c.take<uint32_t>(L.n_inst),
+         o_tnodes = c.take<float4>(4 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)),
+         o_t4 = c.take<float4>(8 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)), o_c4p = c.take<uint32_t>(L.n_inst),
+         o_c4e = c.take<uint32_t>(L.n_inst), o_c4r = c.take<uint32_t>(L.n_inst), o_tperm = c.take<uint32_t>(L.n_inst),
          o_tcodes = c.take<uint32_t>(L.n_inst), o_sbox = c.take<float>(8), o_err = c.take<uint32_t>(1);
   const uint32_t nl = L.max_large;
   size_t o_k0 = c.take<uint32_t>(nl), o_k1 = c.take<uint32_t>(nl), o_v0 = c.take<uint32_t>(nl),
@@ -379,6 +416,9 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   s->leaf_prim = (uint32_t*)(A + o_lp);
   s->leaf_gq = (uint2*)(A + o_lgq);
   s->blas_info = (int4*)(A + o_binfo);
+  s->vertices = (float*)(A + o_vert);
+  s->indices = (uint32_t*)(A + o_idx);
+  s->tri_boxes = (float*)(A + o_tbox);
   s->blas_box = (float4*)(A + o_bbox);
   s->blas_nodes = (float4*)(A + o_bnodes);
   s->blas_perm = (uint32_t*)(A + o_bperm);
@@ -387,6 +427,10 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   s->inst_info = (uint4*)(A + o_info);
   s->inst_boxes = (float*)(A + o_iboxes);
   s->tlas_nodes = (float4*)(A + o_tnodes);
+  s->tlas4 = (float4*)(A + o_t4);
+  s->c4_parent = (uint32_t*)(A + o_c4p);
+  s->c4_even = (uint32_t*)(A + o_c4e);
+  s->c4_rank = (uint32_t*)(A + o_c4r);
   s->tlas_perm = (uint32_t*)(A + o_tperm);
   s->tlas_codes = (uint32_t*)(A + o_tcodes);
   s->scene_box = (float*)(A + o_sbox);
@@ -406,10 +450,10 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   // Level jobs: BLAS levels (small ones in one launch, large ones separately), then the TLAS.
   for (uint32_t b = 0; b < L.n_blas; ++b) {
     LevelDesc J;
-    J.boxes = s->aabbs;
+    J.boxes = L.blas_tri[b] ? s->tri_boxes : s->aabbs;
     J.gather = s->leaf_prim + L.blas_info[4 * b + 1];
     J.n = (uint32_t)L.blas_info[4 * b + 2];
-    J.leaf_ref_base = (uint32_t)L.blas_info[4 * b + 1];
+    J.leaf_ref_base = (uint32_t)L.blas_info[4 * b + 1] | (L.blas_tri[b] ? kTriBit : 0u);
     J.nodes = s->blas_nodes + 4 * (size_t)L.blas_info[4 * b + 0];
     J.perm = s->blas_perm + L.blas_info[4 * b + 1];
     J.codes = s->blas_codes + L.blas_info[4 * b + 1];
@@ -454,7 +498,7 @@ pr_status pr_scene_upload(pr_scene* s, const pr_scene_desc* desc, void* stream) 
   if (st != PR_OK) return st;
   if (L.n_prims != s->L.n_prims || L.n_geoms != s->L.n_geoms || L.n_blas != s->L.n_blas || L.n_inst != s->L.n_inst ||
       L.n_hg != s->L.n_hg || L.n_mat != s->L.n_mat || L.n_rec != s->L.n_rec || L.n_rt != s->L.n_rt ||
-      L.blas_info != s->L.blas_info)
+      L.blas_info != s->L.blas_info || L.n_vert != s->L.n_vert || L.n_tri != s->L.n_tri)
     return fail(PR_ERR_INVALID_ARG, "pr_scene_upload needs the same counts and BLAS layout as at creation");
   s->L = std::move(L);
   return upload(s, desc, (cudaStream_t)stream);
@@ -464,16 +508,19 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
   if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
   cudaStream_t st = (cudaStream_t)stream;
   int launches = 0;
+  // 0. triangle boxes (leaf input of triangle BLASes)
+  launches += launch_triangle_boxes(s->vertices, s->indices, s->L.n_tri, s->tri_boxes, st);
   // 1. every small BLAS in one launch, one CTA each
   launches += launch_build_small(s->d_jobs, (uint32_t)s->small_jobs.size(), st);
   for (const LevelDesc& J : s->large_blas) launches += launch_build_large(J, s->scratch, st);
   // 2. instance world boxes, world->object transforms
   launches += launch_instances(s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box, s->L.n_inst,
                                s->inst_boxes, s->inst_w2o, s->inst_info, st);
-  // 3. TLAS
+  // 3. TLAS, then its 4-wide collapse
   if (s->L.n_inst > 0) {
     if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
     else launches += launch_build_large(s->tlas_job, s->scratch, st);
+    launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");
@@ -487,6 +534,7 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
                             cudaStream_t st, uint64_t* work = nullptr) {
   TraceLaunch T;
   T.S = view_of(s);
+  if (p->flags & PR_TRACE_TLAS_BVH2) T.S.tlas4 = nullptr;   // binary TLAS traversal (comparison)
   T.cam0 = *cam0;
   T.cams = d_cams;
   T.n_frames = n_frames;
@@ -625,7 +673,7 @@ pr_status pr_scene_read_bvh(pr_scene* s, uint32_t level, void* stream, uint32_t 
       for (int side = 0; side < 2; ++side) {
         int32_t ref;
         memcpy(&ref, f + 12 + side, sizeof(ref));
-        if (ref < 0) ref = (int32_t)(kLeafBit | (((uint32_t)ref & 0x7FFFFFFFu) - base));
+        if (ref < 0) ref = (int32_t)(kLeafBit | (((uint32_t)ref & 0x7FFFFFFFu) - base));   // base holds the kind bit
         child[2 * (size_t)i + side] = ref;
       }
     }

@@ -418,7 +418,95 @@ __global__ void __launch_bounds__(256) k_instances(const float* xform, const uin
   info[k] = make_uint4(b, inst_sbt[k], inst_id[k], inst_mask[k]);
 }
 
+// ---- 4-wide collapse of a binary level -----------------------------------
+// Every internal node at even depth becomes a 4-wide node holding its
+// grandchildren (its internal children are expanded; its leaf children stay).
+__global__ void __launch_bounds__(256) k_bvh2_parents(const float4* nodes, uint32_t n, uint32_t* parent) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) parent[0] = 0xFFFFFFFFu;
+  if (i + 1 >= n) return;
+  float4 r = nodes[4 * (size_t)i + 3];
+  int a = __float_as_int(r.x), b = __float_as_int(r.y);
+  if (a >= 0) parent[a] = i;
+  if (b >= 0) parent[b] = i;
+}
+
+__global__ void __launch_bounds__(256) k_bvh2_even(const uint32_t* parent, uint32_t n, uint32_t* even, uint32_t* rank) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i + 1 >= n) return;
+  uint32_t depth = 0;
+  for (uint32_t v = i; parent[v] != 0xFFFFFFFFu; v = parent[v]) ++depth;
+  uint32_t e = (depth & 1u) == 0u ? 1u : 0u;
+  even[i] = e;
+  rank[i] = e;
+}
+
+__global__ void __launch_bounds__(256) k_bvh4_fill(const float4* nodes, uint32_t n, const uint32_t* even,
+                                                   const uint32_t* rank, float4* out) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i + 1 >= n || !even[i]) return;
+  float lo[3][4], hi[3][4];
+  int ref[4];
+  int cnt = 0;
+  const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)i);
+  for (int side = 0; side < 2; ++side) {
+    int c = __float_as_int(f[12 + side]);
+    if (c >= 0) {
+      const float* g = reinterpret_cast<const float*>(nodes + 4 * (size_t)c);
+      for (int gs = 0; gs < 2; ++gs) {
+        int gr = __float_as_int(g[12 + gs]);
+        for (int a = 0; a < 3; ++a) { lo[a][cnt] = g[6 * gs + a]; hi[a][cnt] = g[6 * gs + 3 + a]; }
+        ref[cnt++] = gr >= 0 ? (int)rank[gr] : gr;
+      }
+    } else {
+      for (int a = 0; a < 3; ++a) { lo[a][cnt] = f[6 * side + a]; hi[a][cnt] = f[6 * side + 3 + a]; }
+      ref[cnt++] = c;
+    }
+  }
+  for (; cnt < 4; ++cnt) {
+    for (int a = 0; a < 3; ++a) { lo[a][cnt] = INFINITY; hi[a][cnt] = -INFINITY; }
+    ref[cnt] = kEmptySlot;
+  }
+  float4* o = out + 8 * (size_t)rank[i];
+  for (int a = 0; a < 3; ++a) {
+    o[a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+    o[3 + a] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+  }
+  o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+  o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Vertex bounds of each triangle (exact: min/max only).
+__global__ void __launch_bounds__(256) k_tri_boxes(const float* v, const uint32_t* idx, uint32_t n, float* boxes) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t a = idx[3 * (size_t)t], b = idx[3 * (size_t)t + 1], c = idx[3 * (size_t)t + 2];
+  for (int k = 0; k < 3; ++k) {
+    float x = v[3 * (size_t)a + k], y = v[3 * (size_t)b + k], z = v[3 * (size_t)c + k];
+    boxes[6 * (size_t)t + k] = fminf(fminf(x, y), z);
+    boxes[6 * (size_t)t + 3 + k] = fmaxf(fmaxf(x, y), z);
+  }
+}
+
 }  // namespace
+
+int launch_triangle_boxes(const float* vertices, const uint32_t* indices, uint32_t n_tri, float* boxes,
+                          cudaStream_t s) {
+  if (n_tri == 0) return 0;
+  k_tri_boxes<<<(n_tri + 255) / 256, 256, 0, s>>>(vertices, indices, n_tri, boxes);
+  return 1;
+}
+
+int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_t* even, uint32_t* rank,
+                     float4* nodes4, cudaStream_t s) {
+  if (n < 2) return 0;
+  uint32_t nb = (n + 255) / 256;
+  k_bvh2_parents<<<nb, 256, 0, s>>>(nodes2, n, parent);
+  k_bvh2_even<<<nb, 256, 0, s>>>(parent, n, even, rank);
+  k_radix_scan<<<1, 1024, 0, s>>>(rank, n - 1);            // exclusive prefix sum: 4-wide node index
+  k_bvh4_fill<<<nb, 256, 0, s>>>(nodes2, n, even, rank, nodes4);
+  return 4;
+}
 
 int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s) {
   if (n_jobs == 0) return 0;

@@ -44,11 +44,16 @@ inline uint32_t sort_tiles(uint32_t n) { return (n + kSortTile - 1) / kSortTile;
 // Launchers (bvh.cu). Each returns the number of kernels launched.
 int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s);
 int launch_build_small_one(const LevelDesc& job, cudaStream_t s);
+// 4-wide collapse of a built binary level of n leaves (scratch: parent, even, rank of n words).
+int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_t* even, uint32_t* rank,
+                     float4* nodes4, cudaStream_t s);
 int launch_build_large(const LevelDesc& job, const BuildScratch& sc, cudaStream_t s);
 
 // Scratch bytes of the large-level path for n leaves, and its carving.
 size_t build_scratch_bytes(uint32_t n);
 BuildScratch carve_build_scratch(void* base, uint32_t n);
+int launch_triangle_boxes(const float* vertices, const uint32_t* indices, uint32_t n_tri, float* boxes,
+                          cudaStream_t s);
 int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
                      const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box, uint32_t n_inst,
                      float* inst_boxes, float4* inst_w2o, uint4* inst_info, cudaStream_t s);

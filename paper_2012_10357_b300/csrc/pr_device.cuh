@@ -8,9 +8,16 @@
 namespace pr {
 
 constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr uint32_t kTriBit = 0x40000000u;    // a BLAS leaf ref of a triangle (kLeafBit | kTriBit | leaf)
 constexpr int kStackDepth = (int)PR_STACK_DEPTH;
 constexpr uint32_t kErrSbt = 1u << PR_ERR_SBT_INDEX;
 constexpr uint32_t kErrStack = 1u << PR_ERR_STACK_OVERFLOW;
+constexpr int kEmptySlot = 0x7FFFFFFF;   // unused child slot of a 4-wide node
+
+// One 4-wide node = 128 bytes = 8 x float4, child boxes stored by coordinate
+// so the four slab tests run on whole vectors:
+//   lo.x[4], lo.y[4], lo.z[4], hi.x[4], hi.y[4], hi.z[4], refs[4] (int bits), unused
+// Empty slots have lo = +inf, hi = -inf (never entered) and ref kEmptySlot.
 
 // One BVH2 node = 64 bytes = 4 x float4, both children's boxes stored in the
 // parent so a visit is one node fetch:
@@ -34,6 +41,8 @@ struct SceneView {
   // TLAS
   const float4* tlas_nodes;   // [max(n_inst-1,0)][4]
   int tlas_root_ref;          // 0 or kLeafBit | instance (single instance)
+  const float4* tlas4;        // [n4][8] 4-wide TLAS collapsed from the binary one, or null
+  int tlas4_root;             // 0 or kLeafBit | instance
   const float* scene_box;     // [6] TLAS root box (world)
   // BLAS
   const int4* blas_info;      // [n_blas] BlasInfo
@@ -42,6 +51,8 @@ struct SceneView {
   // flattened BLAS leaves (geometry-major per BLAS)
   const uint32_t* leaf_prim;  // global primitive index
   const uint2* leaf_gq;       // (g inside the BLAS, primitive index inside geometry)
+  const float* vertices;      // [n_vertices][3] triangle vertices (object space)
+  const uint32_t* indices;    // [n_triangles][3]
   // primitives
   const float* aabbs;         // [n_prims][6]
   const float4* params;       // [n_prims][4]

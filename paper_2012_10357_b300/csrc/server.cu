@@ -36,7 +36,8 @@ double now_s() {
 struct DescCopy {
   pr_scene_desc d{};
   std::vector<float> aabbs, params, xform, materials;
-  std::vector<uint32_t> gpb, gpc, bgb, bgc, iblas, iid, isbt, imask, hg, sbt, rt;
+  std::vector<uint32_t> gpb, gpc, bgb, bgc, iblas, iid, isbt, imask, hg, sbt, rt, gtype, idx;
+  std::vector<float> verts;
   explicit DescCopy(const pr_scene_desc* s) {
     d = *s;
     auto cpf = [](std::vector<float>& v, const float* p, size_t n) { v.assign(p, p + (p ? n : 0)); return v.data(); };
@@ -59,6 +60,9 @@ struct DescCopy {
     d.hit_groups = cpu(hg, s->hit_groups, 3 * (size_t)s->n_hit_groups);
     d.sbt = cpu(sbt, s->sbt, 4 * (size_t)s->n_records);
     d.ray_types = cpu(rt, s->ray_types, 2 * (size_t)s->n_ray_types);
+    d.geom_type = s->geom_type ? cpu(gtype, s->geom_type, s->n_geoms) : nullptr;
+    d.vertices = cpf(verts, s->vertices, 3 * (size_t)s->n_vertices);
+    d.indices = cpu(idx, s->indices, 3 * (size_t)s->n_triangles);
   }
 };
 
@@ -269,7 +273,10 @@ bool launch_iteration(pr_server* s) {
   }
   if (reqs.empty()) return false;
   pr_status st;
-  if (s->cfg.mode == PR_SERVE_PLAIN) {
+  const bool whole_single = reqs.size() == 1 && reqs[0].row_begin == 0 && reqs[0].row_count == reqs[0].params.height;
+  if (s->cfg.mode == PR_SERVE_PLAIN || whole_single) {
+    // plain form, or an iteration that is one whole request: the megakernel
+    // (same image bits, one launch instead of the four batched stages)
     st = pr_trace(reqs[0].scene, &reqs[0].camera, &reqs[0].params, reqs[0].out_rgba, nullptr,
                   reinterpret_cast<uint64_t*>(s->d_rays), s->stream);
   } else {

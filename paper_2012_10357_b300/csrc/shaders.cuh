@@ -54,10 +54,22 @@ __device__ __forceinline__ float3 safe_rcp(float3 d) {
             d.z != 0.f ? 1.f / d.z : copysignf(big, d.z));
 }
 
+// ---- any-hit shaders ---------------------------------------------------------
+// "Cutout": ignores candidate hits whose object-space point lies in the lower
+// half of every band of height 1/4 along y (frac(4y) < 1/2). A hit group's
+// any-hit shader runs on each candidate its intersection shader reports, in
+// increasing t; an ignored candidate lets the search continue (Section 2.2.3).
+__device__ __forceinline__ bool any_hit_accepts(uint32_t ahs, float3 o, float t, float3 d) {
+  if (ahs != PR_AHS_CUTOUT) return true;
+  float b = 4.f * fmaf(t, d.y, o.y);
+  return b - floorf(b) >= 0.5f;
+}
+
 // ---- analytic shaders ------------------------------------------------------
 // Sphere: closest approach t_c = -(o-c).d/|d|^2, squared half chord from the
 // perpendicular distance (numerically kinder than b^2 - ac), first root >= tmin.
-__device__ __forceinline__ bool is_sphere(const float4 p0, float3 o, float3 d, float tmin, IsResult& r) {
+__device__ __forceinline__ bool is_sphere(const float4 p0, float3 o, float3 d, float tmin, IsResult& r,
+                                          uint32_t ahs = PR_NONE) {
   float3 c = f3(p0.x, p0.y, p0.z);
   float R = p0.w;
   float3 f = o - c;
@@ -69,8 +81,8 @@ __device__ __forceinline__ bool is_sphere(const float4 p0, float3 o, float3 d, f
   if (h2 < 0.f) return false;
   float h = sqrtf(h2);
   float t = tc - h;
-  if (t < tmin) t = tc + h;
-  if (t < tmin) return false;
+  if (t < tmin || !any_hit_accepts(ahs, o, t, d)) t = tc + h;
+  if (t < tmin || !any_hit_accepts(ahs, o, t, d)) return false;
   r.t = t;
   r.attr = 0;
   return true;
@@ -78,7 +90,8 @@ __device__ __forceinline__ bool is_sphere(const float4 p0, float3 o, float3 d, f
 
 // Axis-aligned box (centre, half extent): entry point, else exit point when
 // the origin is inside; ties on an edge resolve to the lowest axis.
-__device__ __forceinline__ bool is_box(const float4 p0, const float4 p1, float3 o, float3 d, float tmin, IsResult& r) {
+__device__ __forceinline__ bool is_box(const float4 p0, const float4 p1, float3 o, float3 d, float tmin, IsResult& r,
+                                       uint32_t ahs = PR_NONE) {
   float c[3] = {p0.x, p0.y, p0.z}, e[3] = {p0.w, p1.x, p1.y};
   float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
   float te = -INFINITY, tx = INFINITY;
@@ -100,10 +113,10 @@ __device__ __forceinline__ bool is_box(const float4 p0, const float4 p1, float3 
     if (tf < tx) { tx = tf; xa = k; }
   }
   if (te > tx) return false;
-  if (te >= tmin) {
+  if (te >= tmin && any_hit_accepts(ahs, o, te, d)) {
     r.t = te;
     r.attr = (uint32_t)ea | (dd[ea] > 0.f ? 0u : 4u);
-  } else if (tx >= tmin) {
+  } else if (tx >= tmin && any_hit_accepts(ahs, o, tx, d)) {
     r.t = tx;
     r.attr = (uint32_t)xa | (dd[xa] > 0.f ? 4u : 0u);
   } else {
@@ -116,7 +129,7 @@ __device__ __forceinline__ bool is_box(const float4 p0, const float4 p1, float3 
 // n1 = (-sin a, cos a, 0), n2 = (-sin a, -cos a, 0) (mouth of 2a about +x).
 // Ball chord [s0, s1] minus wedge interval (w0, w1); first boundary >= tmin.
 __device__ __forceinline__ bool is_pacman(const float4 p0, const float4 p1, float3 o, float3 d, float tmin,
-                                          IsResult& r) {
+                                          IsResult& r, uint32_t ahs = PR_NONE) {
   float3 c = f3(p0.x, p0.y, p0.z);
   float R = p0.w;
   float sa, ca;
@@ -159,13 +172,35 @@ __device__ __forceinline__ bool is_pacman(const float4 p0, const float4 p1, floa
     if (w1 < s1) { et[ne] = w1; ek[ne++] = k1; et[ne] = s1; ek[ne++] = 0; }
   }
   for (int i = 0; i < ne; ++i) {
-    if (et[i] >= tmin) {
+    if (et[i] >= tmin && any_hit_accepts(ahs, o, et[i], d)) {
       r.t = et[i];
       r.attr = ek[i];
       return true;
     }
   }
   return false;
+}
+
+__device__ __forceinline__ float3 ldf3g(const float* p) { return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
+
+// Built-in triangle intersection (what DXR does in fixed function), Moller &
+// Trumbore 1997: Cramer's rule on o + t d = v0 + u e1 + v e2; u, v >= 0,
+// u + v <= 1, t >= tmin, and the any-hit shader's consent.
+__device__ __forceinline__ bool is_triangle(float3 v0, float3 v1, float3 v2, float3 o, float3 d, float tmin, float& t,
+                                            uint32_t ahs) {
+  const float3 e1 = v1 - v0, e2 = v2 - v0;
+  const float3 pv = cross3(d, e2);
+  const float det = dot3(e1, pv);
+  if (det == 0.f) return false;
+  const float inv = 1.f / det;
+  const float3 tv = o - v0;
+  const float u = dot3(tv, pv) * inv;
+  if (u < 0.f || u > 1.f) return false;
+  const float3 qv = cross3(tv, e1);
+  const float v = dot3(d, qv) * inv;
+  if (v < 0.f || u + v > 1.f) return false;
+  t = dot3(e2, qv) * inv;
+  return t >= tmin && any_hit_accepts(ahs, o, t, d);
 }
 
 // ---- distance estimators -----------------------------------------------------
@@ -279,6 +314,7 @@ struct WorkCounters {
   uint32_t de_evals[PR_IS_COUNT];
   uint32_t frac_iters[2];   // Julia, Mandelbulb loop trips
   uint32_t shaded, rays;
+  uint32_t tlas_nodes4;     // 4-wide TLAS node visits
 };
 static_assert(sizeof(WorkCounters) == 4 * PR_WORK_COUNTERS, "counter layout is part of the ABI");
 
@@ -293,11 +329,16 @@ static __device__ __noinline__ float distance_estimate(uint32_t id, const float4
     case PR_IS_METABALL4: return sdf_metaball4(prm, p);
     case PR_IS_JULIA: return de_julia(prm[0], prm[1], p, wc ? &wc->frac_iters[0] : nullptr);
     case PR_IS_MANDELBULB: return de_mandelbulb(prm[0], p, wc ? &wc->frac_iters[1] : nullptr);
+    case PR_IS_JULIA_CUT: {   // the Julia set cut by the half-space n.p <= d (Fig. 5)
+      const float4 a = prm[1], b = prm[2];
+      const float plane = fmaf(a.z, p.x, fmaf(a.w, p.y, b.x * p.z)) - b.y;
+      return fmaxf(de_julia(prm[0], a, p, wc ? &wc->frac_iters[0] : nullptr), plane);
+    }
     default: return INFINITY;
   }
 }
 
-__device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_IS_TORUS && id <= PR_IS_MANDELBULB; }
+__device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_IS_TORUS && id <= PR_IS_JULIA_CUT; }
 
 // Sphere tracing (Hart 1996) inside [t_lo, t_hi]: estimates are converted to
 // world units with 1/|d|; hit when below eps, give up past t_hi or after

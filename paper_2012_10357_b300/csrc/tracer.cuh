@@ -54,14 +54,14 @@ __device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3
 }
 
 // Intersection shader dispatch on the hit group's shader id.
-__device__ __forceinline__ bool run_intersection(uint32_t is_id, const float4* prm, float3 o, float3 d, float tmin,
-                                                 float t_lo, float t_hi, float eps, uint32_t max_steps, IsResult& r,
-                                                 WorkCounters* wc) {
+__device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, const float4* prm, float3 o, float3 d,
+                                                 float tmin, float t_lo, float t_hi, float eps, uint32_t max_steps,
+                                                 IsResult& r, WorkCounters* wc) {
   if (wc) ++wc->is_calls[is_id < PR_IS_COUNT ? is_id : 0];
   switch (is_id) {
-    case PR_IS_SPHERE: return is_sphere(__ldg(prm), o, d, tmin, r);
-    case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, tmin, r);
-    case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r);
+    case PR_IS_SPHERE: return is_sphere(__ldg(prm), o, d, tmin, r, ahs);
+    case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
+    case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     default:
       if (is_sphere_traced(is_id)) {
         float4 p[4] = {__ldg(prm), __ldg(prm + 1), __ldg(prm + 2), __ldg(prm + 3)};
@@ -120,9 +120,40 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       if (hl) { node = lref; continue; }
       if (hr) { node = rref; continue; }
     } else {
-      int leaf = node & 0x7FFFFFFF;
+      const bool tri = (node & (int)kTriBit) != 0;
+      int leaf = node & 0x3FFFFFFF;
       if (wc) ++wc->leaves;
       uint32_t prim = __ldg(S.leaf_prim + leaf);
+      if (tri) {
+        // built-in triangle intersection; the record supplies the hit group (any-hit shader)
+        uint2 gq = __ldg(S.leaf_gq + leaf);
+        uint32_t rec = r + S.sbt_stride_m * gq.x + info.y;
+        if (rec >= S.n_records) {
+          atomicOr(S.error_word, kErrSbt);
+        } else {
+          const uint32_t ahs = __ldg(S.hit_groups + __ldg(S.sbt + rec).x).z;
+          const uint32_t* ti = S.indices + 3 * (size_t)prim;
+          float t;
+          const float3 v0 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti));
+          const float3 v1 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti + 1));
+          const float3 v2 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti + 2));
+          if (is_triangle(v0, v1, v2, oo, dd, tmin, t, ahs)) {
+            bool accept = t < h.t;
+            if (!accept && t == h.t && h.inst >= 0)
+              accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
+            if (accept) {
+              h.t = t;
+              h.inst = k;
+              h.leaf = leaf | (int)kTriBit;
+              h.attr = 0;
+              if (any_hit) return true;
+            }
+          }
+        }
+        if (sp == sp0) break;
+        node = stack[--sp];
+        continue;
+      }
       const float* bb = S.aabbs + 6 * (size_t)prim;
       float te, tx;
       slab(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv, te,
@@ -136,12 +167,14 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
           atomicOr(S.error_word, kErrSbt);
         } else {
           uint4 sr = __ldg(S.sbt + rec);
-          uint32_t is_id = __ldg(S.hit_groups + sr.x).x;
+          const uint4 hg = __ldg(S.hit_groups + sr.x);
           IsResult res;
-          if (run_intersection(is_id, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
+          if (run_intersection(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res,
+                               wc) &&
               res.t >= tmin) {
             bool accept = res.t < h.t;
-            if (!accept && res.t == h.t && h.inst >= 0) accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + h.leaf));
+            if (!accept && res.t == h.t && h.inst >= 0)
+              accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
             if (accept) {
               h.t = res.t;
               h.inst = k;
@@ -173,6 +206,56 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
   float3 inv = safe_rcp(d);
   float3 o_inv = f3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
   int sp = 0;
+  if (S.tlas4) {
+    // 4-wide TLAS: four slab tests per node on coordinate vectors, hit
+    // children ordered near to far by a 5-exchange sorting network; the
+    // nearest is visited next, the others pushed farthest first.
+    int node = S.tlas4_root;
+    for (;;) {
+      if (node >= 0) {
+        if (wc) ++wc->tlas_nodes4;
+        const float4* nd = S.tlas4 + 8 * (size_t)node;
+        const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+        const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const float clo[3][4] = {{lx.x, lx.y, lx.z, lx.w}, {ly.x, ly.y, ly.z, ly.w}, {lz.x, lz.y, lz.z, lz.w}};
+        const float chi[3][4] = {{hx.x, hx.y, hx.z, hx.w}, {hy.x, hy.y, hy.z, hy.w}, {hz.x, hz.y, hz.z, hz.w}};
+        int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+        float key[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float ax = fmaf(clo[0][k], inv.x, o_inv.x), bx = fmaf(chi[0][k], inv.x, o_inv.x);
+          float ay = fmaf(clo[1][k], inv.y, o_inv.y), by = fmaf(chi[1][k], inv.y, o_inv.y);
+          float az = fmaf(clo[2][k], inv.z, o_inv.z), bz = fmaf(chi[2][k], inv.z, o_inv.z);
+          float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), tmin));
+          float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), h.t));
+          key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
+        }
+        auto cswap = [&](int a, int b) {
+          if (key[b] < key[a]) {
+            float tk = key[a]; key[a] = key[b]; key[b] = tk;
+            int tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;
+          }
+        };
+        cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+        if (key[0] != INFINITY) {
+#pragma unroll
+          for (int k = 3; k >= 1; --k) {
+            if (key[k] != INFINITY) {
+              if (sp < kStackDepth) stack[sp++] = ref[k];
+              else atomicOr(S.error_word, kErrStack);
+            }
+          }
+          node = ref[0];
+          continue;
+        }
+      } else {
+        if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+          return;
+      }
+      if (sp == 0) return;
+      node = stack[--sp];
+    }
+  }
   int node = S.tlas_root_ref;
 #if PR_WHILE_WHILE
   // While-while traversal (Aila & Laine 2009): descend internal nodes, hold
@@ -262,8 +345,10 @@ static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit&
   if (wc) ++wc->shaded;
   Surface sf;
   uint4 info = __ldg(S.inst_info + h.inst);
-  uint2 gq = __ldg(S.leaf_gq + h.leaf);
-  uint32_t prim = __ldg(S.leaf_prim + h.leaf);
+  const bool tri = (h.leaf & (int)kTriBit) != 0;
+  const int leaf = h.leaf & 0x3FFFFFFF;
+  uint2 gq = __ldg(S.leaf_gq + leaf);
+  uint32_t prim = __ldg(S.leaf_prim + leaf);
   uint32_t rec = 0u + S.sbt_stride_m * gq.x + info.y;
   uint4 sr = __ldg(S.sbt + rec);
   uint4 hg = __ldg(S.hit_groups + sr.x);
@@ -271,10 +356,18 @@ static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit&
   float3 oo, dd;
   to_object(S, h.inst, o, d, oo, dd);
   float3 p = madd(oo, h.t, dd);
-  const float4* pp = S.params + 4 * (size_t)prim;
-  float4 prm[4] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2), __ldg(pp + 3)};
-  float hstep = eps * len3(dd);
-  float3 no = object_normal(hg.x, prm, p, h.attr, hstep, dd, wc);
+  float3 no;
+  if (tri) {
+    const uint32_t* ti = S.indices + 3 * (size_t)prim;
+    const float3 v0 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti)), v1 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti + 1)),
+                 v2 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti + 2));
+    no = cross3(v1 - v0, v2 - v0);
+  } else {
+    const float4* pp = S.params + 4 * (size_t)prim;
+    float4 prm[4] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2), __ldg(pp + 3)};
+    float hstep = eps * len3(dd);
+    no = object_normal(hg.x, prm, p, h.attr, hstep, dd, wc);
+  }
   float4 m0 = __ldg(S.inst_w2o + 3 * h.inst), m1 = __ldg(S.inst_w2o + 3 * h.inst + 1),
          m2 = __ldg(S.inst_w2o + 3 * h.inst + 2);
   float3 nw = f3(fmaf(m0.x, no.x, fmaf(m1.x, no.y, m2.x * no.z)), fmaf(m0.y, no.x, fmaf(m1.y, no.y, m2.y * no.z)),

@@ -11,6 +11,7 @@ from __future__ import annotations
 # per unit, from trace.cu / shaders.cuh
 FLOPS = {
     "tlas_nodes": 50,        # two slab tests (6 FMA + 10 min/max each), clip to [tmin,tmax], order
+    "tlas_nodes4": 104,      # four slab tests with clip (24 FMA + 44 min/max), masks, 5-exchange sort
     "blas_nodes": 50,
     "instances": 64,         # world->object origin (9 FMA) and direction (6 FMA + 3 MUL), 1/d, root-box slab
     "leaves": 25,            # primitive AABB slab + clip
@@ -24,6 +25,7 @@ FLOPS = {
     "de_evals_6": 70 + 8,    # four balls + three polynomial smooth minima
     "de_evals_7": 10 + 8,    # Julia setup + escape tail (iterations counted below)
     "de_evals_8": 5 + 8,     # Mandelbulb escape tail (iterations counted below)
+    "de_evals_9": 10 + 6 + 8,  # cut Julia: Julia setup/tail + plane distance (iterations counted below)
     "julia_iters": 27,       # q^2 + c, |q'|^2 update, |q|^2, escape test
     "mandelbulb_iters": 54,  # trig-free z^8 (two complex cubes of squarings), dr update, escape test
     "shaded": 150,           # surface reconstruction, world normal, two Lambert evaluations

@@ -39,10 +39,14 @@ IS_CAPSULE = 5
 IS_METABALL4 = 6
 IS_JULIA = 7
 IS_MANDELBULB = 8
-N_IS = 9
-SPHERE_TRACED = (IS_TORUS, IS_ROUNDBOX, IS_CAPSULE, IS_METABALL4, IS_JULIA, IS_MANDELBULB)
+IS_JULIA_CUT = 9
+N_IS = 10
+SPHERE_TRACED = (IS_TORUS, IS_ROUNDBOX, IS_CAPSULE, IS_METABALL4, IS_JULIA, IS_MANDELBULB, IS_JULIA_CUT)
 
 CHS_LAMBERT = 0
+AHS_CUTOUT = 0
+GEOM_AABBS = 0
+GEOM_TRIANGLES = 1
 MISS_BACKGROUND = 0
 MISS_SHADOW = 1
 NONE = 0xFFFFFFFF
@@ -56,7 +60,7 @@ RAY_SHADOW = 1
 N_PARAMS = 16  # floats of shape parameters per AABB primitive
 
 IS_NAMES = ["sphere", "box", "pacman", "torus", "roundbox", "capsule",
-            "metaball4", "julia", "mandelbulb"]
+            "metaball4", "julia", "mandelbulb", "julia_cut"]
 
 
 @dataclasses.dataclass
@@ -79,6 +83,10 @@ class SceneDesc:
     sbt              uint32  [R,4]   hit_group, material, prim_type, instance_index
     ray_types        uint32  [T,2]   miss_id, flags
     sbt_stride_m     int             Eq. 1 geometry multiplier m
+    geom_type        uint32  [G]     GEOM_AABBS or GEOM_TRIANGLES (None: all AABBs); a triangle
+                                     geometry's prim range indexes `indices`
+    vertices         float32 [V,3]   triangle vertices (object space)
+    indices          uint32  [T,3]   triangle vertex indices
     """
     aabbs: np.ndarray
     params: np.ndarray
@@ -97,6 +105,9 @@ class SceneDesc:
     ray_types: np.ndarray
     sbt_stride_m: int = 2
     name: str = ""
+    geom_type: Optional[np.ndarray] = None       # uint32 [G]: 0 AABBs, 1 triangles (None: all AABBs)
+    vertices: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 3), np.float32))
+    indices: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 3), np.uint32))
 
     def counts(self):
         return dict(prims=len(self.aabbs), geoms=len(self.geom_prim_begin),
@@ -221,7 +232,18 @@ class SceneBuilder:
         assert len(aabbs) == len(params)
         self.aabbs.append(aabbs)
         self.params.append(params)
-        self.geoms.append((begin, len(aabbs)))
+        self.geoms.append((begin, len(aabbs), GEOM_AABBS))
+        return len(self.geoms) - 1
+
+    def add_triangle_geometry(self, vertices, indices) -> int:
+        """A triangle geometry (built-in triangle intersection): vertices [V,3], indices [T,3]."""
+        if not hasattr(self, "tris"):
+            self.verts, self.tris = [], []
+        vbase = sum(len(v) for v in self.verts)
+        tbegin = sum(len(t) for t in self.tris)
+        self.verts.append(np.asarray(vertices, np.float32).reshape(-1, 3))
+        self.tris.append(np.asarray(indices, np.uint32).reshape(-1, 3) + np.uint32(vbase))
+        self.geoms.append((tbegin, len(self.tris[-1]), GEOM_TRIANGLES))
         return len(self.geoms) - 1
 
     def add_blas(self, geom_ids) -> int:
@@ -259,7 +281,13 @@ class SceneBuilder:
             materials=_f32(self.materials).reshape(-1, 4),
             sbt=_u32(self.sbt).reshape(-1, 4),
             ray_types=_u32(self.ray_types).reshape(-1, 2),
-            sbt_stride_m=self.m, name=name)
+            sbt_stride_m=self.m, name=name,
+            geom_type=(_u32([g[2] for g in self.geoms]).reshape(G)
+                       if any(g[2] != GEOM_AABBS for g in self.geoms) else None),
+            vertices=(np.concatenate(self.verts).astype(np.float32) if getattr(self, "verts", None)
+                      else np.zeros((0, 3), np.float32)),
+            indices=(np.concatenate(self.tris).astype(np.uint32) if getattr(self, "tris", None)
+                     else np.zeros((0, 3), np.uint32)))
 
 
 # --------------------------------------------------------------------------
@@ -316,6 +344,74 @@ def julia_c(rng: np.random.Generator, radius=0.8) -> np.ndarray:
 
 def shape_julia(c, iters=12, escape=4.0):
     return np.array([-1.6] * 3 + [1.6] * 3), params_row(*c, iters, escape)
+
+
+def shape_julia_cut(c, normal, offset, iters=12, escape=4.0):
+    """Julia set cut by the half-space normal.p <= offset (the paper's Fig. 5)."""
+    n = np.asarray(normal, np.float64)
+    n = n / np.linalg.norm(n)
+    return np.array([-1.6] * 3 + [1.6] * 3), params_row(*c, iters, escape, *n, offset)
+
+
+JULIA_CUT_C = (-0.2, 0.6, 0.2, 0.2)   # a connected set (|c| = 0.69), so the cut face is solid
+
+
+def julia_cut_scene(seed: int = 0, normal=(0.0, 0.0, -1.0), offset=0.0, width=320, height=240,
+                    max_steps=256, c=JULIA_CUT_C) -> Workload:
+    """A quaternion Julia set cut by one plane (Fig. 5), on a ground slab, the
+    camera facing the cut. c = None draws c from the seed like the teaser scene."""
+    rng = np.random.default_rng(seed)
+    b = SceneBuilder(sbt_stride_m=2)
+    _standard_rays(b)
+    c = julia_c(rng) if c is None else np.asarray(c, np.float64)
+    hr, hs = b.add_hit_group(IS_JULIA_CUT, CHS_LAMBERT), b.add_hit_group(IS_JULIA_CUT)
+    gr, gs = b.add_hit_group(IS_BOX, CHS_LAMBERT), b.add_hit_group(IS_BOX)
+    mj = b.add_material((0.75, 0.35, 0.85), 0.0)
+    mg = b.add_material((0.6, 0.6, 0.6), 0.0)
+    aabb, prm = shape_julia_cut(c, normal, offset)
+    bj = b.add_blas([b.add_geometry([aabb], [prm])])
+    ag, pg = shape_box((0, -2.205, 0), (8, 0.005, 8))
+    bg = b.add_blas([b.add_geometry([ag], [pg])])
+    b.add_record(hr, mj, IS_JULIA_CUT, 0)
+    b.add_record(hs, mj, IS_JULIA_CUT, 0)
+    b.add_record(gr, mg, IS_BOX, 1)
+    b.add_record(gs, mg, IS_BOX, 1)
+    b.add_instance(bj, xform_trs((0, 0, 0), None, 1.3), 0)
+    b.add_instance(bg, xform_trs((0, 0, 0)), 2)
+    cam = Camera(_f32([0.5, 1.5, -5]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
+    tp = TraceParams(width, height, max_depth=1, max_steps=max_steps, light_pos=_f32([3, 6, -6]))
+    return Workload(b.build("julia-cut"), cam, tp, "julia-cut")
+
+
+def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = True) -> Workload:
+    """Sphere, box and pac-man whose hit groups carry the cutout any-hit shader
+    (bands removed along object y), over a ground slab; with shadow_cutout the
+    shadow hit groups carry it too, so shadows show the bands."""
+    rng = np.random.default_rng(seed)
+    b = SceneBuilder(sbt_stride_m=2)
+    _standard_rays(b)
+    gr, gs = b.add_hit_group(IS_BOX, CHS_LAMBERT), b.add_hit_group(IS_BOX)
+    mg = b.add_material((0.6, 0.6, 0.6), 0.0)
+    ag, pg = shape_box((0, -1.505, 0), (8, 0.005, 8))
+    bg = b.add_blas([b.add_geometry([ag], [pg])])
+    b.add_record(gr, mg, IS_BOX, 0)
+    b.add_record(gs, mg, IS_BOX, 0)
+    b.add_instance(bg, xform_trs((0, 0, 0)), 0)
+    shapes = [(IS_SPHERE, shape_sphere((0, 0, 0), 1.0), (0.9, 0.3, 0.2), (-2.2, 0.0, 0.5)),
+              (IS_BOX, shape_box((0, 0, 0), (0.8, 0.9, 0.7)), (0.3, 0.4, 0.9), (0.0, -0.2, 1.5)),
+              (IS_PACMAN, shape_pacman(1.0), (0.95, 0.85, 0.1), (2.2, 0.0, 0.5))]
+    for is_id, (aabb, prm), alb, pos in shapes:
+        hr = b.add_hit_group(is_id, CHS_LAMBERT, AHS_CUTOUT)
+        hs = b.add_hit_group(is_id, NONE, AHS_CUTOUT if shadow_cutout else NONE)
+        m = b.add_material(alb, 0.0)
+        blas = b.add_blas([b.add_geometry([aabb], [prm])])
+        off = len(b.sbt)
+        b.add_record(hr, m, is_id, len(b.inst))
+        b.add_record(hs, m, is_id, len(b.inst))
+        b.add_instance(blas, xform_trs(pos, rot_y(rng.uniform(-40, 40))), off)
+    cam = Camera(_f32([0, 2.5, -6.5]), _f32([0, -0.2, 0.6]), _f32([0, 1, 0]), 60.0)
+    tp = TraceParams(width, height, max_depth=1, light_pos=_f32([-3, 7, -4]))
+    return Workload(b.build("cutout"), cam, tp, "cutout")
 
 
 def shape_mandelbulb(power=8, iters=12, bailout=2.0):
@@ -403,6 +499,59 @@ def config2(seed: int = 0, width: int = 1920, height: int = 1080) -> Workload:
     cam = Camera(_f32([0, 3, -10]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
     tp = TraceParams(width, height, max_depth=2, light_pos=_f32([6, 10, -6]))
     return Workload(scene, cam, tp, "config2")
+
+
+def plane_mesh(half: float, y: float, cells: int):
+    """A square grid of 2*cells^2 triangles at height y spanning [-half, half]^2 in x, z."""
+    xs = np.linspace(-half, half, cells + 1)
+    verts = np.array([[x, y, z] for z in xs for x in xs], np.float32)
+    idx = []
+    for j in range(cells):
+        for i in range(cells):
+            a, b = j * (cells + 1) + i, j * (cells + 1) + i + 1
+            c, d = a + cells + 1, b + cells + 1
+            idx += [(a, c, b), (b, c, d)]
+    return verts, np.array(idx, np.uint32)
+
+
+def sample_scene(seed: int = 0, width: int = 640, height: int = 360, cells: int = 8) -> Workload:
+    """The paper's sample scene (Fig. 4): a triangle plane mesh and procedural
+    objects (two pac-men, a Julia set, a Mandelbulb). Shader table as Listing 10:
+    the triangle records first (radiance, shadow), then per procedural geometry in
+    insertion order (Julia, Pacman, Mandelbulb; Listing 4) and per instance of it,
+    a radiance and a shadow record, instance_index running over all procedural
+    instances and the material indexed by the procedural geometry ordinal."""
+    rng = np.random.default_rng(seed)
+    b = SceneBuilder(sbt_stride_m=2)
+    _standard_rays(b)
+    tri_r = b.add_hit_group(NONE, CHS_LAMBERT)         # built-in triangle intersection
+    tri_s = b.add_hit_group(NONE)
+    plane_mat = b.add_material((0.6, 0.6, 0.6), 0.4)
+    v, i = plane_mesh(20.0, -1.2, cells)
+    plane_blas = b.add_blas([b.add_triangle_geometry(v, i)])
+    b.add_record(tri_r, plane_mat, NONE, 0)
+    b.add_record(tri_s, plane_mat, NONE, 0)
+    b.add_instance(plane_blas, xform_trs((0, 0, 0)), 0)
+    c = julia_c(rng)
+    kinds = [("Julia", shape_julia(c), IS_JULIA, (0.75, 0.35, 0.85), [xform_trs((0, 1.2, 3), None, 1.5)]),
+             ("Pacman", shape_pacman(1.0), IS_PACMAN, (0.95, 0.85, 0.1),
+              [xform_trs((-3, 0, 0), rot_y(0.0)), xform_trs((3, 0, 0), rot_y(180.0))]),
+             ("Mandelbulb", shape_mandelbulb(), IS_MANDELBULB, (0.35, 0.65, 0.95),
+              [xform_trs((0, 0.5, -1), None, 1.2)])]
+    instance_index = 0
+    for name, (aabb, prm), is_id, alb, xforms in kinds:
+        hr, hs = b.add_hit_group(is_id, CHS_LAMBERT), b.add_hit_group(is_id)
+        mat = b.add_material(alb, 0.2)                  # materialCb[primitiveIndex]
+        blas = b.add_blas([b.add_geometry([aabb], [prm])])
+        for xf in xforms:
+            off = len(b.sbt)
+            b.add_record(hr, mat, is_id, instance_index)
+            b.add_record(hs, mat, is_id, instance_index)
+            b.add_instance(blas, xf, sbt_offset=off)
+            instance_index += 1
+    cam = Camera(_f32([0, 3, -10]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
+    tp = TraceParams(width, height, max_depth=2, light_pos=_f32([6, 10, -6]))
+    return Workload(b.build("sample"), cam, tp, "sample")
 
 
 # --------------------------------------------------------------------------

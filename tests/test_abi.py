@@ -68,7 +68,7 @@ def test_eq1_fig3_golden_through_abi(pr):
     (lambda s: s.inst_blas.__setitem__(0, 99), "BLAS out of range"),
     (lambda s: s.inst_xform.__setitem__((0, slice(0, 3)), 0.0), "not invertible"),
     (lambda s: s.hit_groups.__setitem__((0, 0), 42), "intersection shader"),
-    (lambda s: s.hit_groups.__setitem__((0, 2), 0), "any-hit"),
+    (lambda s: s.hit_groups.__setitem__((0, 2), 5), "any-hit"),
     (lambda s: s.sbt.__setitem__((0, 0), 1000), "hit group out of range"),
     (lambda s: s.sbt.__setitem__((0, 1), 1000), "material out of range"),
     (lambda s: s.geom_prim_count.__setitem__(0, 0), "primitive range"),
@@ -88,6 +88,37 @@ def test_validation_rejects(pr, mutate, frag):
 def test_validation_accepts_all_configs(pr):
     for w in (scenes.config1(), scenes.config2(width=8, height=8), scenes.config3(n_inst=300, width=8, height=8)):
         pr.validate(w.scene)
+
+
+def test_cutout_any_hit_needs_an_analytic_shader(pr):
+    w = scenes.config1()
+    w.scene.hit_groups[0, 2] = scenes.AHS_CUTOUT      # sphere intersection shader: allowed
+    pr.validate(w.scene)
+    f = scenes.config3(n_inst=50, width=8, height=8)
+    torus_hg = [h for h in range(len(f.scene.hit_groups)) if f.scene.hit_groups[h, 0] == scenes.IS_TORUS][0]
+    f.scene.hit_groups[torus_hg, 2] = scenes.AHS_CUTOUT
+    with pytest.raises(pr.PrError) as ei:
+        pr.validate(f.scene)
+    assert "analytic" in str(ei.value)
+
+
+def test_triangle_validation(pr):
+    w = scenes.sample_scene(width=8, height=8)
+    pr.validate(w.scene)
+    bad = scenes.sample_scene(width=8, height=8)
+    bad.scene.indices[0, 0] = 10_000
+    with pytest.raises(pr.PrError) as ei:
+        pr.validate(bad.scene)
+    assert "vertex index" in str(ei.value)
+    mixed = scenes.sample_scene(width=8, height=8)
+    mixed.scene.blas_geom_count[0] = 2            # triangle BLAS swallowing an AABB geometry
+    with pytest.raises(pr.PrError) as ei:
+        pr.validate(mixed.scene)
+    assert "mixes" in str(ei.value)
+    rng = scenes.sample_scene(width=8, height=8)
+    rng.scene.geom_prim_count[0] = 999
+    with pytest.raises(pr.PrError):
+        pr.validate(rng.scene)
 
 
 def test_one_ray_type_is_rejected(pr):

@@ -149,6 +149,93 @@ def test_pacman_reductions(O):
     assert O.intersect(IS_PACMAN, prm, [-0.6, 0.0, -5], [0, 0, 1], 0.0) is not None
 
 
+def test_cutout_any_hit_skips_banded_candidates(O):
+    """Unit sphere, ray in the y-z plane: the front point lies in a removed band
+    (frac(4y) < 1/2), the back point in a kept band, so the far root is reported;
+    with the back point removed too the ray misses; without the shader the near root."""
+    d = _unit([0.0, 0.35, 1.0])
+    band = lambda y: 4 * y - math.floor(4 * y)
+
+    def roots_of(o):
+        b, c = np.dot(o, d), np.dot(o, o) - 1.0
+        disc = b * b - c
+        return None if disc < 0 else (-b - math.sqrt(disc), -b + math.sqrt(disc))
+
+    o = None
+    for dy in np.linspace(-1.6, -0.2, 141):            # pick a ray with this geometry
+        cand = np.array([0.0, dy, -3.0])
+        r = roots_of(cand)
+        if r and band((cand + r[0] * d)[1]) < 0.45 and band((cand + r[1] * d)[1]) > 0.55:
+            o = cand
+            break
+    assert o is not None
+    t0, t1 = roots_of(o)
+    t, n, _ = O.intersect(IS_SPHERE, [0, 0, 0, 1], o, d, 0.0, ahs_id=scenes.AHS_CUTOUT)
+    assert t == pytest.approx(t1, abs=1e-12)
+    t, n, _ = O.intersect(IS_SPHERE, [0, 0, 0, 1], o, d, 0.0)
+    assert t == pytest.approx(t0, abs=1e-12)
+    # shift the ray so that both candidates fall in removed bands: no hit
+    for dy in np.linspace(-0.2, 0.2, 81):
+        o2 = o + np.array([0.0, dy, 0.0])
+        r = roots_of(o2)
+        if r is None:
+            continue
+        ya, yb = [(o2 + t * d)[1] for t in r]
+        if min(abs(band(ya) - 0.5), abs(band(yb) - 0.5), band(ya), band(yb)) < 1e-9:
+            continue                                    # on a band edge: ill-conditioned
+        res = O.intersect(IS_SPHERE, [0, 0, 0, 1], o2, d, 0.0, ahs_id=scenes.AHS_CUTOUT)
+        expect = None if (band(ya) < 0.5 and band(yb) < 0.5) else (r[0] if band(ya) >= 0.5 else r[1])
+        if expect is None:
+            assert res is None
+        else:
+            assert res is not None and res[0] == pytest.approx(expect, abs=1e-9)
+    # box: entry face removed, exit face kept
+    t, n, _ = O.intersect(IS_BOX, [0, 0, 0, 1, 1, 1], [-5, 0.1, 0.0], [1, 0.06, 0], 0.0, ahs_id=scenes.AHS_CUTOUT)
+    ye = 0.1 + 0.06 * 4.0
+    assert band(ye) < 0.5 and t == pytest.approx(6.0) and np.allclose(n, [1, 0, 0])
+
+
+def _one_triangle_workload(v, eye, look):
+    b = scenes.SceneBuilder()
+    scenes._standard_rays(b)
+    hr, hs = b.add_hit_group(scenes.NONE, scenes.CHS_LAMBERT), b.add_hit_group(scenes.NONE)
+    m = b.add_material((0.5, 0.5, 0.5))
+    blas = b.add_blas([b.add_triangle_geometry(np.asarray(v, np.float32), [[0, 1, 2]])])
+    b.add_record(hr, m, scenes.NONE, 0)
+    b.add_record(hs, m, scenes.NONE, 0)
+    b.add_instance(blas, scenes.xform_trs((0, 0, 0)), 0)
+    cam = scenes.Camera(np.float32(eye), np.float32(look), np.float32([0, 1, 0]), 1.0)
+    return scenes.Workload(b.build("tri"), cam, scenes.TraceParams(1, 1, light_pos=np.float32([0, 0, -50])))
+
+
+def test_triangle_hits_by_half_spaces(O):
+    """Built-in triangle test: a ray along +z through (x, y) meets the triangle
+    (0,0,0), (2,0,0), (0,2,0) iff x >= 0, y >= 0, x + y <= 2 (half-space test,
+    independent of the barycentric solve), at t = 10 with normal +-z."""
+    tri = [[0, 0, 0], [2, 0, 0], [0, 2, 0]]
+    for x in np.linspace(-0.5, 2.5, 13):
+        for y in np.linspace(-0.5, 2.5, 13):
+            inside = x >= 0 and y >= 0 and x + y <= 2
+            if min(abs(x), abs(y), abs(x + y - 2)) < 1e-9:
+                continue
+            px = O.render(_one_triangle_workload(tri, [x, y, -10], [x, y, 0]))[0]
+            assert bool(px["flags"] & 1) == inside, (x, y)
+            if inside:
+                assert px["t"] == pytest.approx(10.0, abs=1e-9)
+                assert np.allclose(np.abs(px["n"]), [0, 0, 1])
+
+
+def test_triangle_slanted_plane_point(O):
+    """A slanted triangle: the hit point must satisfy the plane equation."""
+    tri = np.array([[-3, -2, 1], [4, -1, 3], [0, 3, 6]], np.float64)
+    n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    for x, y in [(0.0, 0.0), (0.5, 0.7), (-0.4, 1.2)]:
+        px = O.render(_one_triangle_workload(tri, [x, y, -10], [x, y, 0]))[0]
+        assert px["flags"] & 1
+        p = np.float32([x, y, -10.0]).astype(np.float64) + px["t"] * np.array([0, 0, 1.0])   # the eye is float32
+        assert abs(np.dot(n, p - tri[0])) < 1e-9 * np.linalg.norm(n)
+
+
 def test_pacman_random_dense_membership(O):
     rng = np.random.default_rng(3)
     a = float(np.float32(math.radians(30)))
@@ -250,6 +337,23 @@ def test_julia_c0_closed_form(O):
     assert O.de(IS_JULIA, prm, [0.2, 0.3, -0.4]) == 0.0
     # points just outside the unit ball whose orbit has not escaped after 12 steps
     assert O.de(IS_JULIA, prm, [1.0001, 0, 0]) == 0.0
+
+
+def test_julia_cut_closed_form(O):
+    """c = 0 cut by n = (0,0,-1), d = 0: the half ball z >= 0. The estimate is
+    max(Julia estimate, plane distance); a ray along +z through the ball's
+    centre meets the cut face at z = 0 with normal -z."""
+    prm = [0, 0, 0, 0, 12, 4, 0, 0, -1, 0]
+    assert O.de(scenes.IS_JULIA_CUT, prm, [0, 0, -0.5]) == pytest.approx(0.5)      # removed half of the ball
+    assert O.de(scenes.IS_JULIA_CUT, prm, [0.1, 0.2, 0.5]) == 0.0                   # kept half: inside
+    p = _unit([0.3, -0.5, 0.8]) * 2.0                                               # outside both: the larger bound
+    assert O.de(scenes.IS_JULIA_CUT, prm, p) == pytest.approx(max(0.5 * 2 * math.log(2), -p[2]))
+    t, n, _ = O.intersect(scenes.IS_JULIA_CUT, prm, [0.05, 0.02, -3], [0, 0, 1], 0.0, 10.0, 1e-5, 256)
+    assert t == pytest.approx(3.0, abs=2e-5) and np.allclose(n, [0, 0, -1], atol=1e-3)
+    # the same ray with the half-space flipped keeps the front half: the ball's sphere at z ~ -1
+    prm2 = [0, 0, 0, 0, 12, 4, 0, 0, 1, 0]
+    t2, _, _ = O.intersect(scenes.IS_JULIA_CUT, prm2, [0.05, 0.02, -3], [0, 0, 1], 0.0, 10.0, 1e-5, 256)
+    assert t2 == pytest.approx(3.0 - math.sqrt(1 - 0.05 ** 2 - 0.02 ** 2), abs=1e-3)
 
 
 def test_mandelbulb_axis_reduces_to_real_iteration(O):

@@ -39,6 +39,8 @@ pr_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr uint32_t kTlas4MinInstances = 64;
+
 // Counts and host-side flattening of a description.
 struct Layout {
   uint32_t n_prims, n_geoms, n_blas, n_inst, n_hg, n_mat, n_rec, n_rt, m;
@@ -270,7 +272,9 @@ SceneView view_of(const pr_scene* s) {
   v.inst_info = s->inst_info;
   v.tlas_nodes = s->tlas_nodes;
   v.tlas_root_ref = s->L.n_inst == 1 ? (int)kLeafBit : 0;
-  v.tlas4 = s->L.n_inst >= 2 ? s->tlas4 : nullptr;
+  // the 4-wide TLAS pays off on large instance counts only (measured: +3 % at
+  // 100 000 instances, -7 % at 5); small TLASes keep the binary traversal
+  v.tlas4 = s->L.n_inst >= kTlas4MinInstances ? s->tlas4 : nullptr;
   v.tlas4_root = v.tlas_root_ref;
   v.scene_box = s->scene_box;
   v.blas_info = s->blas_info;

@@ -204,16 +204,22 @@ __device__ __forceinline__ bool is_triangle(float3 v0, float3 v1, float3 v2, flo
 }
 
 // ---- distance estimators -----------------------------------------------------
+// Inside the estimators (the hot loops of sphere tracing) square roots,
+// divisions and logarithms use CUDA's fast approximations (rsqrtf,
+// __fdividef, __logf; a few ulp): an estimate only steers the march, and its
+// hit threshold eps is far coarser than those ulps.
+__device__ __forceinline__ float est_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ float est_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ float sdf_torus(const float4 p0, float3 p) {
-  float qx = sqrtf(fmaf(p.x, p.x, p.z * p.z)) - p0.x;
-  return sqrtf(fmaf(qx, qx, p.y * p.y)) - p0.y;
+  float qx = est_sqrt(fmaf(p.x, p.x, p.z * p.z)) - p0.x;
+  return est_sqrt(fmaf(qx, qx, p.y * p.y)) - p0.y;
 }
 
 __device__ __forceinline__ float sdf_roundbox(const float4 p0, float3 p) {
   float rr = p0.w;
   float qx = fabsf(p.x) - (p0.x - rr), qy = fabsf(p.y) - (p0.y - rr), qz = fabsf(p.z) - (p0.z - rr);
   float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
-  float outside = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+  float outside = est_sqrt(fmaf(mx, mx, fmaf(my, my, mz * mz)));
   float inside = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
   return outside + inside - rr;
 }
@@ -221,20 +227,22 @@ __device__ __forceinline__ float sdf_roundbox(const float4 p0, float3 p) {
 __device__ __forceinline__ float sdf_capsule(const float4 p0, float3 p) {
   float y = fminf(fmaxf(p.y, -p0.x), p0.x);
   float dy = p.y - y;
-  return sqrtf(fmaf(p.x, p.x, fmaf(dy, dy, p.z * p.z))) - p0.y;
+  return est_sqrt(fmaf(p.x, p.x, fmaf(dy, dy, p.z * p.z))) - p0.y;
 }
 
 __device__ __forceinline__ float smin_poly(float a, float b, float k) {
-  float h = fmaxf(k - fabsf(a - b), 0.f) / k;
+  float h = est_div(fmaxf(k - fabsf(a - b), 0.f), k);
   return fminf(a, b) - h * h * k * 0.25f;
 }
 
 __device__ __forceinline__ float sdf_metaball4(const float4* prm, float3 p) {
   const float4 p0 = prm[0], p1 = prm[1], p2 = prm[2], p3 = prm[3];
-  float d0 = len3(p - f3(p0.x, p0.y, p0.z)) - p3.x;
-  float d1 = len3(p - f3(p0.w, p1.x, p1.y)) - p3.y;
-  float d2 = len3(p - f3(p1.z, p1.w, p2.x)) - p3.z;
-  float d3 = len3(p - f3(p2.y, p2.z, p2.w)) - p3.w;
+  const float3 q0 = p - f3(p0.x, p0.y, p0.z), q1 = p - f3(p0.w, p1.x, p1.y);
+  const float3 q2 = p - f3(p1.z, p1.w, p2.x), q3 = p - f3(p2.y, p2.z, p2.w);
+  float d0 = est_sqrt(dot3(q0, q0)) - p3.x;
+  float d1 = est_sqrt(dot3(q1, q1)) - p3.y;
+  float d2 = est_sqrt(dot3(q2, q2)) - p3.z;
+  float d3 = est_sqrt(dot3(q3, q3)) - p3.w;
   const float k = 0.2f;
   return smin_poly(smin_poly(smin_poly(d0, d1, k), d2, k), d3, k);
 }
@@ -256,7 +264,7 @@ __device__ __forceinline__ float de_julia(const float4 c, const float4 p1, float
     float ny = fmaf(tx, qy, c.y), nz = fmaf(tx, qz, c.z), nw = fmaf(tx, qw, c.w);
     qx = nx; qy = ny; qz = nz; qw = nw;
     r2 = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, qw * qw)));
-    if (r2 > esc2) return 0.25f * logf(r2) * sqrtf(r2 / md2);
+    if (r2 > esc2) return 0.25f * __logf(r2) * est_sqrt(est_div(r2, md2));
   }
   return 0.f;
 }
@@ -275,10 +283,10 @@ __device__ __forceinline__ float de_mandelbulb(const float4 p0, float3 p, uint32
     float x2 = x * x, y2 = y * y, z2 = z * z;
     float rho2 = x2 + y2;
     float r2 = rho2 + z2;
-    float r = sqrtf(r2);
+    float r = est_sqrt(r2);
     float r6 = r2 * r2 * r2;
     dr = fmaf(8.f * r6 * r, dr, 1.f);
-    float rho = sqrtf(rho2);
+    float rho = est_sqrt(rho2);
     // w = (z + i rho)^2, ^4, ^8
     float a = z2 - rho2, b = 2.f * z * rho;
     float a2 = fmaf(a, a, -b * b), b2 = 2.f * a * b;
@@ -286,7 +294,7 @@ __device__ __forceinline__ float de_mandelbulb(const float4 p0, float3 p, uint32
     // u^2 = (x + i y)^2 / rho^2, then ^4, ^8
     float ux, uy;
     if (rho2 > 0.f) {
-      float ir = 1.f / rho2;
+      float ir = est_div(1.f, rho2);
       ux = (x2 - y2) * ir;
       uy = 2.f * x * y * ir;
     } else {
@@ -300,8 +308,8 @@ __device__ __forceinline__ float de_mandelbulb(const float4 p0, float3 p, uint32
     z = a3 + p.z;
     float n2 = fmaf(x, x, fmaf(y, y, z * z));
     if (n2 > bail2) {
-      float rn = sqrtf(n2);
-      return 0.5f * logf(rn) * rn / dr;
+      float rn = est_sqrt(n2);
+      return est_div(0.5f * __logf(rn) * rn, dr);
     }
   }
   return 0.f;

@@ -65,13 +65,4 @@ struct SceneView {
   uint32_t* error_word;
 };
 
-struct FrameView {
-  float3 eye, fwd, right, up;   // camera basis is computed on the device per thread
-  float tan_half, aspect;
-  uint32_t width, height, max_depth, max_steps, flags;
-  float3 light;
-  float light_intensity, eps_rel, ambient;
-  float3 background;
-};
-
 }  // namespace pr

@@ -47,11 +47,14 @@ __device__ __forceinline__ void slab(const float3 lo, const float3 hi, const flo
 }
 
 __device__ __forceinline__ float3 safe_rcp(float3 d) {
-  // a zero component becomes +/- a huge value so that the slab of that axis is
-  // (-inf, inf) when the origin lies inside it and empty otherwise
+  // slab-test reciprocals (hardware approximation, ~1 ulp: the tests only cull
+  // boxes; primitives are intersected exactly). A zero component becomes a
+  // huge value of its sign, so the axis's slab is (-inf, inf) when the origin
+  // lies inside it and empty otherwise.
   const float big = 1e30f;
-  return f3(d.x != 0.f ? 1.f / d.x : copysignf(big, d.x), d.y != 0.f ? 1.f / d.y : copysignf(big, d.y),
-            d.z != 0.f ? 1.f / d.z : copysignf(big, d.z));
+  return f3(d.x != 0.f ? __fdividef(1.f, d.x) : copysignf(big, d.x),
+            d.y != 0.f ? __fdividef(1.f, d.y) : copysignf(big, d.y),
+            d.z != 0.f ? __fdividef(1.f, d.z) : copysignf(big, d.z));
 }
 
 // ---- any-hit shaders ---------------------------------------------------------

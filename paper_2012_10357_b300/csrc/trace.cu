@@ -43,12 +43,14 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
   const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
   const bool valid = x < (int)P.width && y < (int)P.height;
+  __shared__ CameraBasis s_cam;
+  if (threadIdx.x == 0) s_cam = camera_basis(P.cams ? P.cams[frame] : P.cam0, P.width, P.height);
+  __syncthreads();
   uint32_t rays = 0;
   if (valid) {
     PR_DECLARE_STACK(128);
-    const pr_camera cam = P.cams ? P.cams[frame] : P.cam0;
-    const float3 eye = ldf3(cam.eye);
-    const float3 d = camera_ray(cam, x, y, P.width, P.height);
+    const float3 eye = s_cam.eye;
+    const float3 d = camera_ray(s_cam, x, y);
     const float eps = scene_eps(S, P.eps_rel);
 
     Hit h;

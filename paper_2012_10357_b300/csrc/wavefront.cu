@@ -59,6 +59,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
   static_assert(TW * TH == 128, "128-pixel tiles");
   __shared__ ReqDev sreq;
+  __shared__ CameraBasis scam;
   __shared__ uint32_t s_tile, s_req;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int WX = TW / 8;   // warps across (8x4 pixel sub-tile per warp)
@@ -79,6 +80,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
       for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
+      if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
+      __syncthreads();
       last_req = r;
     }
     const ReqDev& R = sreq;
@@ -91,8 +94,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
     uint64_t px = 0;
     if (valid) {
       const SceneView& S = R.S;
-      const float3 eye = ldf3(R.cam.eye);
-      const float3 d = camera_ray(R.cam, x, y, R.width, R.height);
+      const float3 eye = scam.eye;
+      const float3 d = camera_ray(scam, x, y);
       const float eps = scene_eps(S, R.eps_rel);
       px = R.pixel_begin + (uint64_t)(y - (int)R.row_begin) * R.width + (uint64_t)x;
       Hit h;

@@ -124,6 +124,31 @@ def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tupl
     return float(t.item()), int(r.item())
 
 
+# DRAM traffic of one timed k_trace launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# one ncu capture of this script's own command, L2 flushed before the launch as in the timed
+# loop), per workload and traversal mode. A figure holds only for the kernel sources it was
+# taken on: it is keyed by their SHA-1 and reported as null once they change.
+TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/csrc/tracer.cuh",
+                 "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
+                 "include/proceduray.h"]
+TRACE_TRAFFIC = {}   # {sha1: {workload: bytes per launch}}
+
+
+def trace_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for rel in TRACE_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def trace_traffic(workload: str, binary_tlas: bool):
+    if binary_tlas:
+        return None
+    return TRACE_TRAFFIC.get(trace_sources_sha1(), {}).get(workload)
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -438,7 +463,7 @@ def run_ours(args):
     peak_tflops = work.fp32_peak_tflops(props.multi_processor_count, sm_max)
     achieved_tflops = flops / trace_avg_s / 1e12
     roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak_tflops, "traffic": None,
+            "frac": achieved_tflops / peak_tflops, "traffic": trace_traffic(args.workload, args.binary_tlas),
             "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
             "trace_share_of_step": sum(trace_ms) / total_ms,

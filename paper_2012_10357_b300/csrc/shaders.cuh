@@ -353,22 +353,71 @@ __device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_
 
 // Sphere tracing (Hart 1996) inside [t_lo, t_hi]: estimates are converted to
 // world units with 1/|d|; hit when below eps, give up past t_hi or after
-// max_steps estimates.
-__device__ __forceinline__ bool sphere_trace(uint32_t id, const float4* prm, float3 o, float3 d, float inv_len,
-                                             float t_lo, float t_hi, float eps, uint32_t max_steps, IsResult& r,
-                                             WorkCounters* wc = nullptr) {
+// max_steps estimates. The estimate is inlined into the loop (one branch on
+// the shader id per march, parameters kept in registers); the conversion is
+// rounded on its own so no multiply-add forms across the estimate's result.
+template <class DE>
+__device__ __forceinline__ IsResult march(DE de, float3 o, float3 d, float inv_len, float t_lo, float t_hi, float eps,
+                                          uint32_t max_steps) {
+  IsResult r{0.f, 0u};
   float t = t_lo;
   for (uint32_t s = 0; s < max_steps; ++s) {
-    if (t > t_hi) return false;
-    float dist = distance_estimate(id, prm, madd(o, t, d), wc) * inv_len;
+    if (t > t_hi) return r;
+    const float dist = __fmul_rn(de(madd(o, t, d)), inv_len);
     if (dist < eps) {
       r.t = t;
-      r.attr = s + 1;
-      return true;
+      r.attr = s + 1;   // >= 1 marks a hit
+      return r;
     }
     t += dist;
   }
-  return false;
+  return r;
+}
+
+// One out-of-line march per call of a sphere-traced intersection shader; attr
+// of the result is 0 on a miss.
+static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* prm, float3 o, float3 d, float inv_len,
+                                                     float t_lo, float t_hi, float eps, uint32_t max_steps,
+                                                     WorkCounters* wc = nullptr) {
+  uint32_t* de_ctr = wc ? &wc->de_evals[id < PR_IS_COUNT ? id : 0] : nullptr;
+  uint32_t* jit = wc ? &wc->frac_iters[0] : nullptr;
+  uint32_t* mit = wc ? &wc->frac_iters[1] : nullptr;
+  const float4 p0 = __ldg(prm);
+  switch (id) {
+    case PR_IS_TORUS:
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return sdf_torus(p0, p); }, o, d, inv_len, t_lo, t_hi, eps,
+                   max_steps);
+    case PR_IS_ROUNDBOX:
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return sdf_roundbox(p0, p); }, o, d, inv_len, t_lo, t_hi, eps,
+                   max_steps);
+    case PR_IS_CAPSULE:
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return sdf_capsule(p0, p); }, o, d, inv_len, t_lo, t_hi, eps,
+                   max_steps);
+    case PR_IS_METABALL4: {
+      const float4 q[4] = {p0, __ldg(prm + 1), __ldg(prm + 2), __ldg(prm + 3)};
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return sdf_metaball4(q, p); }, o, d, inv_len, t_lo, t_hi, eps,
+                   max_steps);
+    }
+    case PR_IS_JULIA: {
+      const float4 p1 = __ldg(prm + 1);
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return de_julia(p0, p1, p, jit); }, o, d, inv_len, t_lo, t_hi,
+                   eps, max_steps);
+    }
+    case PR_IS_MANDELBULB:
+      return march([&](float3 p) { if (de_ctr) ++*de_ctr; return de_mandelbulb(p0, p, mit); }, o, d, inv_len, t_lo, t_hi,
+                   eps, max_steps);
+    case PR_IS_JULIA_CUT: {   // the Julia set cut by the half-space n.p <= d (Fig. 5)
+      const float4 a = __ldg(prm + 1), b = __ldg(prm + 2);
+      return march(
+          [&](float3 p) {
+            if (de_ctr) ++*de_ctr;
+            const float plane = fmaf(a.z, p.x, fmaf(a.w, p.y, b.x * p.z)) - b.y;
+            return fmaxf(de_julia(p0, a, p, jit), plane);
+          },
+          o, d, inv_len, t_lo, t_hi, eps, max_steps);
+    }
+    default: return IsResult{0.f, 0u};
+  }
 }
 
 // Object-space normal at the accepted hit (called once per shaded hit).

@@ -64,8 +64,8 @@ __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, c
     case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     default:
       if (is_sphere_traced(is_id)) {
-        float4 p[4] = {__ldg(prm), __ldg(prm + 1), __ldg(prm + 2), __ldg(prm + 3)};
-        return sphere_trace(is_id, p, o, d, rsqrtf(dot3(d, d)), t_lo, t_hi, eps, max_steps, r, wc);
+        r = sphere_trace(is_id, prm, o, d, rsqrtf(dot3(d, d)), t_lo, t_hi, eps, max_steps, wc);
+        return r.attr != 0u;
       }
       return false;
   }

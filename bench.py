@@ -333,12 +333,19 @@ def cpu_baseline(w, budget_s: float = 15.0) -> dict:
     dt = time.perf_counter() - t0
     n = int(min(n_pix, max(len(probe), len(probe) * budget_s / max(dt, 1e-3) * 0.8)))
     pix = scenes.sample_pixels(w.params.width, w.params.height, n, seed=4)
+    # a frame smaller than the budget is rendered whole, repeatedly, for about 10 s
+    rays, passes = 0, 0
     t0 = time.perf_counter()
-    ref = oracle.render(w, pixels=pix, threads=threads)
-    dt = time.perf_counter() - t0
-    rays = int(ref["rays"].sum())
+    while True:
+        ref = oracle.render(w, pixels=pix, threads=threads)
+        rays += int(ref["rays"].sum())
+        passes += 1
+        dt = time.perf_counter() - t0
+        if n < n_pix or dt >= 0.65 * budget_s or passes >= 10000:
+            break
     return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} of {n_pix} pixels (seeded uniform sample), {rays} rays, {dt:.1f} s, FP64 brute force"}
+            "sample": f"{passes} x {n} of {n_pix} pixels (seeded uniform sample), {rays} rays, {dt:.1f} s, "
+                      f"FP64 brute force"}
 
 
 def run_reference(args):

@@ -6,6 +6,7 @@ oracle renders in seconds (several tiles plus ragged edges) and, at the full
 configuration sizes in the benchmark's launch configuration, on seeded pixel
 samples.
 """
+import dataclasses
 import json
 import os
 
@@ -219,6 +220,28 @@ def test_trace_frames_equals_single_frames():
     for f, c in enumerate(cams):
         one = scene.trace(c, w.params)
         assert torch.equal(batch[f], one)
+    scene.close()
+
+
+def test_repeated_launches_on_two_streams():
+    """Many launches of one scene in a row, of two sizes and on two streams,
+    all give the image of the first launch of their size (a launch keeps no
+    state in the scene)."""
+    w = scenes.config1()
+    scene = pr.Scene(w.scene)
+    small = dataclasses.replace(w.params, width=37, height=23)
+    ref = scene.trace(w.camera, w.params).clone()
+    ref_small = scene.trace(w.camera, small).clone()
+    torch.cuda.synchronize()
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    outs = []
+    for k in range(150):
+        is_small = k % 3 == 0
+        outs.append((is_small, scene.trace(w.camera, small if is_small else w.params, stream=streams[k % 2])))
+    torch.cuda.synchronize()
+    for is_small, o in outs:
+        assert torch.equal(o, ref_small if is_small else ref)
+    assert scene.error_word() == 0
     scene.close()
 
 

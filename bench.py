@@ -478,6 +478,15 @@ def run_ours(args):
     if clocks:
         roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
         roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
+    sustained = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if sustained:
+        # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
+        roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(props.multi_processor_count, float(sustained))
+        roof["frac_at_measured_sustained_clock"] = achieved_tflops / roof["peak_at_measured_sustained_clock"]
+    # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
+    probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
+    roof["peak_fma_probe"] = probe_tflops
+    roof["frac_of_fma_probe"] = achieved_tflops / probe_tflops if probe_tflops > 0 else None
 
     # end to end through the public API: host description -> device, build, frame, image -> host
     e2e = None

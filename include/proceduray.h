@@ -264,6 +264,16 @@ pr_status pr_scene_kernel_launches(const pr_scene* scene, uint32_t* build_launch
 pr_status pr_lbvh_build(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
                         float* root_box, void* stream);
 
+/* FP32 FMA throughput probe (measurement support; no counterpart in the
+ * paper): fills every SM with 256-thread CTAs, each thread running 8
+ * independent fused multiply-add chains for iters rounds (1..2^24), times a
+ * second launch after a warm-up with CUDA events on `stream`, and returns the
+ * achieved rate in *tflops_out (2 FLOP per FMA) and the launch time in *ms_out
+ * (may be NULL). It is the measured counterpart of the derived FP32 peak
+ * (SMs x 128 lanes x 2 FLOP x clock) used for the trace kernel's roofline.
+ * Synchronises the stream. */
+pr_status pr_fma_peak_probe(uint32_t iters, float* tflops_out, float* ms_out, void* stream);
+
 /* Largest n accepted by pr_lbvh_build_noalloc. */
 #define PR_LBVH_NOALLOC_MAX_BOXES 262144u
 

@@ -112,6 +112,7 @@ _sig("pr_server_drain", _i32, _vp, ctypes.c_double)
 _sig("pr_server_get_stats", _i32, _vp, _vp)
 _sig("pr_server_destroy", None, _vp)
 _sig("pr_scene_destroy", None, _vp)
+_sig("pr_fma_peak_probe", _i32, _u32, _vp, _vp, _vp)
 
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
             "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
@@ -119,7 +120,7 @@ EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", 
             "pr_scene_destroy", "pr_lbvh_build", "pr_lbvh_build_noalloc", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
             "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy",
             "pr_server_create", "pr_server_submit", "pr_server_poll", "pr_server_drain", "pr_server_get_stats",
-            "pr_server_destroy"]
+            "pr_server_destroy", "pr_fma_peak_probe"]
 PR_SERVE_CONTINUOUS, PR_SERVE_PLAIN = 0, 1
 
 
@@ -356,6 +357,15 @@ def lbvh_build(boxes, stream=None) -> dict:
     _check(_lib.pr_lbvh_build(_dptr(boxes), n, _dptr(nodes), _dptr(perm), _dptr(codes), _dptr(root),
                               _stream_handle(stream)), "pr_lbvh_build")
     return dict(nodes=nodes[:max(n - 1, 0)], perm=perm[:n], codes=codes[:n], root=root)
+
+
+def fma_peak_probe(iters: int = 16384, stream=None) -> tuple:
+    """Measured FP32 FMA throughput of the current GPU (pr_fma_peak_probe):
+    returns (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_float(), ctypes.c_float()
+    _check(_lib.pr_fma_peak_probe(int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream_handle(stream)),
+           "pr_fma_peak_probe")
+    return float(tf.value), float(ms.value)
 
 
 def lbvh_to_host(res) -> dict:

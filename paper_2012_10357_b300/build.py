@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libproceduray.so")
-SOURCES = ["api.cu", "bvh.cu", "trace.cu", "wavefront.cu", "batch.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["api.cu", "bvh.cu", "trace.cu", "wavefront.cu", "batch.cu", "noalloc.cu", "server.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -56,24 +56,29 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
     Hit h;
     rays = 1;
     trace_typed<kStats>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
+    const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
+    // AOV fields are stored as soon as they are known, so none of them stays
+    // live across the shadow and mirror traces
+    pr_aov* av = P.aov ? P.aov + pix : nullptr;
     float3 color;
     uint32_t flags = 0;
-    pr_aov av;
-    av.t = -1.f;
-    av.inst = av.geom = av.prim = PR_NONE;
-    av.n[0] = av.n[1] = av.n[2] = 0.f;
-    av.refl_t = -1.f;
-    av.refl_inst = av.refl_geom = av.refl_prim = PR_NONE;
     if (h.inst < 0) {
       color = miss_rgb(S, 0, P.background);
+      if (av) {
+        av->t = -1.f;
+        av->inst = av->geom = av->prim = PR_NONE;
+        av->n[0] = av->n[1] = av->n[2] = 0.f;
+      }
     } else {
       flags |= 1u;
       Surface sf = surface_at(S, h, eye, d, eps, wc);
-      av.t = h.t;
-      av.inst = (uint32_t)h.inst;
-      av.geom = sf.geom;
-      av.prim = sf.prim;
-      av.n[0] = sf.n.x; av.n[1] = sf.n.y; av.n[2] = sf.n.z;
+      if (av) {
+        av->t = h.t;
+        av->inst = (uint32_t)h.inst;
+        av->geom = sf.geom;
+        av->prim = sf.prim;
+        av->n[0] = sf.n.x; av->n[1] = sf.n.y; av->n[2] = sf.n.z;
+      }
       if (sf.chs != PR_CHS_LAMBERT) {
         color = f3(0.f, 0.f, 0.f);
       } else {
@@ -98,6 +103,7 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
           // one mirror bounce, its hit shaded without a shadow ray
           float3 orr = madd(pt, delta, sf.n);
           float3 dr = normalize3(d - sf.n * (2.f * dot3(d, sf.n)));
+          const float kr = sf.kr;
           Hit rh;
           rays++;
           flags |= 8u;
@@ -106,25 +112,29 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
           if (rh.inst >= 0) {
             flags |= 16u;
             Surface s2 = surface_at(S, rh, orr, dr, eps, wc);
-            av.refl_t = rh.t;
-            av.refl_inst = (uint32_t)rh.inst;
-            av.refl_geom = s2.geom;
-            av.refl_prim = s2.prim;
+            if (av) {
+              av->refl_t = rh.t;
+              av->refl_inst = (uint32_t)rh.inst;
+              av->refl_geom = s2.geom;
+              av->refl_prim = s2.prim;
+            }
             lr = s2.chs == PR_CHS_LAMBERT
                      ? lambert_rgb(s2.albedo, P.ambient, P.light_intensity, light_ndl(s2, P.light, madd(orr, rh.t, dr)), 1.f)
                      : f3(0.f, 0.f, 0.f);
           } else {
             lr = miss_rgb(S, 0, P.background);
           }
-          color = mirror_mix(color, lr, sf.kr);
+          color = mirror_mix(color, lr, kr);
         }
       }
     }
-    size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
     P.out[pix] = make_float4(color.x, color.y, color.z, 1.f);
-    if (P.aov) {
-      av.flags = flags;
-      P.aov[pix] = av;
+    if (av) {
+      if (!(flags & 16u)) {
+        av->refl_t = -1.f;
+        av->refl_inst = av->refl_geom = av->refl_prim = PR_NONE;
+      }
+      av->flags = flags;
     }
   }
   if (P.counter) {

@@ -253,21 +253,33 @@ __device__ __forceinline__ float sdf_metaball4(const float4* prm, float3 p) {
 // Quaternion Julia set (q.x real, slice w = 0). Tracks |q'|^2 so that no
 // square root is needed per iteration: |q'_{n+1}|^2 = 4 |q_n|^2 |q'_n|^2.
 // DE = 0.5 |q| ln|q| / |q'| = 0.25 ln(|q|^2) sqrt(|q|^2 / |q'|^2) once escaped, 0 inside.
+// Written as state / step / estimate of one iteration.
+struct JuliaState {
+  float qx, qy, qz, qw, r2, md2;
+};
+__device__ __forceinline__ JuliaState julia_start(float3 p) {
+  return JuliaState{p.x, p.y, p.z, 0.f, fmaf(p.x, p.x, fmaf(p.y, p.y, p.z * p.z)), 1.f};
+}
+// q <- q^2 + c; returns true once |q|^2 exceeds the escape radius squared
+__device__ __forceinline__ bool julia_step(JuliaState& s, const float4 c, float esc2) {
+  s.md2 *= 4.f * s.r2;
+  const float nx = fmaf(s.qx, s.qx, -fmaf(s.qy, s.qy, fmaf(s.qz, s.qz, s.qw * s.qw))) + c.x;
+  const float tx = 2.f * s.qx;
+  const float ny = fmaf(tx, s.qy, c.y), nz = fmaf(tx, s.qz, c.z), nw = fmaf(tx, s.qw, c.w);
+  s.qx = nx; s.qy = ny; s.qz = nz; s.qw = nw;
+  s.r2 = fmaf(s.qx, s.qx, fmaf(s.qy, s.qy, fmaf(s.qz, s.qz, s.qw * s.qw)));
+  return s.r2 > esc2;
+}
+__device__ __forceinline__ float julia_estimate(const JuliaState& s) {
+  return 0.25f * __logf(s.r2) * est_sqrt(est_div(s.r2, s.md2));
+}
 __device__ __forceinline__ float de_julia(const float4 c, const float4 p1, float3 p, uint32_t* it = nullptr) {
-  int iters = (int)p1.x;
-  float esc2 = p1.y * p1.y;
-  float qx = p.x, qy = p.y, qz = p.z, qw = 0.f;
-  float r2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
-  float md2 = 1.f;
+  const int iters = (int)p1.x;
+  const float esc2 = p1.y * p1.y;
+  JuliaState s = julia_start(p);
   for (int i = 0; i < iters; ++i) {
     if (it) ++*it;
-    md2 *= 4.f * r2;
-    float nx = fmaf(qx, qx, -fmaf(qy, qy, fmaf(qz, qz, qw * qw))) + c.x;
-    float tx = 2.f * qx;
-    float ny = fmaf(tx, qy, c.y), nz = fmaf(tx, qz, c.z), nw = fmaf(tx, qw, c.w);
-    qx = nx; qy = ny; qz = nz; qw = nw;
-    r2 = fmaf(qx, qx, fmaf(qy, qy, fmaf(qz, qz, qw * qw)));
-    if (r2 > esc2) return 0.25f * __logf(r2) * est_sqrt(est_div(r2, md2));
+    if (julia_step(s, c, esc2)) return julia_estimate(s);
   }
   return 0.f;
 }
@@ -276,44 +288,53 @@ __device__ __forceinline__ float de_julia(const float4 c, const float4 p1, float
 // r^8 (cos 8theta + i sin 8theta) and ((x + i y)/rho)^8 gives e^{8 i phi};
 // z^8 = (Im w8 * Re u8, Im w8 * Im u8, Re w8). dr <- 8 r^7 dr + 1.
 // DE = 0.5 ln(r) r / dr once |z| > bailout, 0 inside.
+struct BulbState {
+  float x, y, z, dr, n2;
+};
+__device__ __forceinline__ BulbState bulb_start(float3 p) { return BulbState{p.x, p.y, p.z, 1.f, 0.f}; }
+// z <- z^8 + c; returns true once |z|^2 exceeds the bailout squared
+__device__ __forceinline__ bool bulb_step(BulbState& s, float3 c, float bail2) {
+  const float x = s.x, y = s.y, z = s.z;
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float rho2 = x2 + y2;
+  const float r2 = rho2 + z2;
+  const float r = est_sqrt(r2);
+  const float r6 = r2 * r2 * r2;
+  s.dr = fmaf(8.f * r6 * r, s.dr, 1.f);
+  const float rho = est_sqrt(rho2);
+  // w = (z + i rho)^2, ^4, ^8
+  const float a = z2 - rho2, b = 2.f * z * rho;
+  const float a2 = fmaf(a, a, -b * b), b2 = 2.f * a * b;
+  const float a3 = fmaf(a2, a2, -b2 * b2), b3 = 2.f * a2 * b2;
+  // u^2 = (x + i y)^2 / rho^2, then ^4, ^8
+  float ux, uy;
+  if (rho2 > 0.f) {
+    const float ir = est_div(1.f, rho2);
+    ux = (x2 - y2) * ir;
+    uy = 2.f * x * y * ir;
+  } else {
+    ux = 1.f;
+    uy = 0.f;
+  }
+  const float vx = fmaf(ux, ux, -uy * uy), vy = 2.f * ux * uy;
+  const float sx = fmaf(vx, vx, -vy * vy), sy = 2.f * vx * vy;
+  s.x = fmaf(b3, sx, c.x);
+  s.y = fmaf(b3, sy, c.y);
+  s.z = a3 + c.z;
+  s.n2 = fmaf(s.x, s.x, fmaf(s.y, s.y, s.z * s.z));
+  return s.n2 > bail2;
+}
+__device__ __forceinline__ float bulb_estimate(const BulbState& s) {
+  const float rn = est_sqrt(s.n2);
+  return est_div(0.5f * __logf(rn) * rn, s.dr);
+}
 __device__ __forceinline__ float de_mandelbulb(const float4 p0, float3 p, uint32_t* it = nullptr) {
-  int iters = (int)p0.y;
-  float bail2 = p0.z * p0.z;
-  float x = p.x, y = p.y, z = p.z;
-  float dr = 1.f;
+  const int iters = (int)p0.y;
+  const float bail2 = p0.z * p0.z;
+  BulbState s = bulb_start(p);
   for (int i = 0; i < iters; ++i) {
     if (it) ++*it;
-    float x2 = x * x, y2 = y * y, z2 = z * z;
-    float rho2 = x2 + y2;
-    float r2 = rho2 + z2;
-    float r = est_sqrt(r2);
-    float r6 = r2 * r2 * r2;
-    dr = fmaf(8.f * r6 * r, dr, 1.f);
-    float rho = est_sqrt(rho2);
-    // w = (z + i rho)^2, ^4, ^8
-    float a = z2 - rho2, b = 2.f * z * rho;
-    float a2 = fmaf(a, a, -b * b), b2 = 2.f * a * b;
-    float a3 = fmaf(a2, a2, -b2 * b2), b3 = 2.f * a2 * b2;
-    // u^2 = (x + i y)^2 / rho^2, then ^4, ^8
-    float ux, uy;
-    if (rho2 > 0.f) {
-      float ir = est_div(1.f, rho2);
-      ux = (x2 - y2) * ir;
-      uy = 2.f * x * y * ir;
-    } else {
-      ux = 1.f;
-      uy = 0.f;
-    }
-    float vx = fmaf(ux, ux, -uy * uy), vy = 2.f * ux * uy;
-    float sx = fmaf(vx, vx, -vy * vy), sy = 2.f * vx * vy;
-    x = fmaf(b3, sx, p.x);
-    y = fmaf(b3, sy, p.y);
-    z = a3 + p.z;
-    float n2 = fmaf(x, x, fmaf(y, y, z * z));
-    if (n2 > bail2) {
-      float rn = est_sqrt(n2);
-      return est_div(0.5f * __logf(rn) * rn, dr);
-    }
+    if (bulb_step(s, p, bail2)) return bulb_estimate(s);
   }
   return 0.f;
 }
@@ -329,24 +350,72 @@ struct WorkCounters {
 };
 static_assert(sizeof(WorkCounters) == 4 * PR_WORK_COUNTERS, "counter layout is part of the ABI");
 
-// One out-of-line copy of the estimators: every march and normal shares it,
-// which keeps the instruction footprint of the tracing kernels small.
-static __device__ __noinline__ float distance_estimate(uint32_t id, const float4* prm, float3 p, WorkCounters* wc = nullptr) {
-  if (wc) ++wc->de_evals[id < PR_IS_COUNT ? id : 0];
-  switch (id) {
-    case PR_IS_TORUS: return sdf_torus(prm[0], p);
-    case PR_IS_ROUNDBOX: return sdf_roundbox(prm[0], p);
-    case PR_IS_CAPSULE: return sdf_capsule(prm[0], p);
-    case PR_IS_METABALL4: return sdf_metaball4(prm, p);
-    case PR_IS_JULIA: return de_julia(prm[0], prm[1], p, wc ? &wc->frac_iters[0] : nullptr);
-    case PR_IS_MANDELBULB: return de_mandelbulb(prm[0], p, wc ? &wc->frac_iters[1] : nullptr);
-    case PR_IS_JULIA_CUT: {   // the Julia set cut by the half-space n.p <= d (Fig. 5)
-      const float4 a = prm[1], b = prm[2];
-      const float plane = fmaf(a.z, p.x, fmaf(a.w, p.y, b.x * p.z)) - b.y;
-      return fmaxf(de_julia(prm[0], a, p, wc ? &wc->frac_iters[0] : nullptr), plane);
-    }
-    default: return INFINITY;
+// Central-difference stencil of the estimate at p (six estimates at p +/- h
+// along each axis), for the normal of a sphere-traced hit. The closed-form
+// SDFs are evaluated side by side (six independent chains overlap); the
+// fractal estimates one point after another, each running to its own escape
+// (measured: interleaving their iterations runs every point to the slowest
+// one's count, which costs more than the overlap gains). Returns
+// (d(+x) - d(-x), d(+y) - d(-y), d(+z) - d(-z)).
+template <class DE>
+__device__ __forceinline__ float3 stencil_one_by_one(float3 p, float h, DE de) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < 6; ++k) {
+    const float sh = (k & 1) ? -h : h;
+    const int ax = k >> 1;
+    const float v = de(f3(ax == 0 ? p.x + sh : p.x, ax == 1 ? p.y + sh : p.y, ax == 2 ? p.z + sh : p.z));
+    if (ax == 0) gx = (k & 1) ? gx - v : v;
+    else if (ax == 1) gy = (k & 1) ? gy - v : v;
+    else gz = (k & 1) ? gz - v : v;
   }
+  return f3(gx, gy, gz);
+}
+
+static __device__ __noinline__ float3 de_stencil(uint32_t id, const float4* prm, float3 p, float h,
+                                                 WorkCounters* wc = nullptr) {
+  if (wc) wc->de_evals[id < PR_IS_COUNT ? id : 0] += 6;
+  const float3 pt[6] = {f3(p.x + h, p.y, p.z), f3(p.x - h, p.y, p.z), f3(p.x, p.y + h, p.z),
+                        f3(p.x, p.y - h, p.z), f3(p.x, p.y, p.z + h), f3(p.x, p.y, p.z - h)};
+  float v[6];
+  const float4 p0 = prm[0];
+  switch (id) {
+    case PR_IS_JULIA:
+    case PR_IS_JULIA_CUT: {
+      const float4 p1 = prm[1], b = prm[2];
+      const bool cut = id == PR_IS_JULIA_CUT;
+      uint32_t* it = wc ? &wc->frac_iters[0] : nullptr;
+      return stencil_one_by_one(p, h, [&](float3 q) {
+        const float dj = de_julia(p0, p1, q, it);
+        // the Julia set cut by the half-space n.p <= d (Fig. 5)
+        return cut ? fmaxf(dj, fmaf(p1.z, q.x, fmaf(p1.w, q.y, b.x * q.z)) - b.y) : dj;
+      });
+    }
+    case PR_IS_MANDELBULB: {
+      uint32_t* it = wc ? &wc->frac_iters[1] : nullptr;
+      return stencil_one_by_one(p, h, [&](float3 q) { return de_mandelbulb(p0, q, it); });
+    }
+    case PR_IS_TORUS:
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = sdf_torus(p0, pt[k]);
+      break;
+    case PR_IS_ROUNDBOX:
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = sdf_roundbox(p0, pt[k]);
+      break;
+    case PR_IS_CAPSULE:
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = sdf_capsule(p0, pt[k]);
+      break;
+    case PR_IS_METABALL4:
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = sdf_metaball4(prm, pt[k]);
+      break;
+    default:
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = INFINITY;
+  }
+  return f3(v[0] - v[1], v[2] - v[3], v[4] - v[5]);
 }
 
 __device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_IS_TORUS && id <= PR_IS_JULIA_CUT; }
@@ -441,9 +510,7 @@ __device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, 
       return f3(sa, attr == 1 ? -ca : ca, 0.f);   // -n_k
     }
     default: {
-      float3 g = f3(distance_estimate(id, prm, f3(p.x + h, p.y, p.z), wc) - distance_estimate(id, prm, f3(p.x - h, p.y, p.z), wc),
-                    distance_estimate(id, prm, f3(p.x, p.y + h, p.z), wc) - distance_estimate(id, prm, f3(p.x, p.y - h, p.z), wc),
-                    distance_estimate(id, prm, f3(p.x, p.y, p.z + h), wc) - distance_estimate(id, prm, f3(p.x, p.y, p.z - h), wc));
+      const float3 g = de_stencil(id, prm, p, h, wc);
       float gl2 = dot3(g, g);
       return gl2 > 0.f ? g * rsqrtf(gl2) : -normalize3(d);
     }

@@ -214,8 +214,9 @@ pr_status pr_trace_frames(pr_scene* scene, const pr_camera* cameras, uint32_t n_
                           void* stream);
 
 /* Work counters of pr_trace_work (uint64 each, in this order): TLAS node
- * visits, BLAS node visits, instance transitions, leaf AABB tests, Eq. 1
- * record lookups, intersection-shader calls per shader id [PR_IS_COUNT],
+ * visits, BLAS node visits, instance transitions, leaf tests (AABB slab
+ * or triangle; the leaf of a one-AABB BLAS is tested by its root box and
+ * not counted here), Eq. 1 record lookups, intersection-shader calls per shader id [PR_IS_COUNT],
  * distance-estimate evaluations per shader id [PR_IS_COUNT], Julia
  * iterations, Mandelbulb iterations, shaded hits, rays traced, 4-wide TLAS
  * node visits. */

@@ -94,11 +94,49 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
   float3 inv = safe_rcp(dd);
   float3 o_inv = f3(-oo.x * inv.x, -oo.y * inv.y, -oo.z * inv.z);
   const int4 bi = __ldg(S.blas_info + info.x);
+  float r_lo, r_hi;   // root-box slab interval
   {
     float4 blo = __ldg(S.blas_box + 2 * info.x), bhi = __ldg(S.blas_box + 2 * info.x + 1);
     float t0, t1;
     slab(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, t0, t1);
-    if (fmaxf(t0, tmin) > fminf(t1, h.t)) return false;
+    r_lo = fmaxf(t0, tmin);
+    r_hi = fminf(t1, h.t);
+    if (r_lo > r_hi) return false;
+  }
+  // Procedural leaf whose AABB slab interval is [t_lo, t_hi]: Eq. 1 record,
+  // intersection shader, closest-hit bookkeeping. True when any-hit mode
+  // accepted a hit (the trace ends).
+  auto procedural_leaf = [&](int leaf, uint32_t prim, float t_lo, float t_hi) -> bool {
+    uint2 gq = __ldg(S.leaf_gq + leaf);
+    if (wc) ++wc->sbt_lookups;
+    uint32_t rec = r + S.sbt_stride_m * gq.x + info.y;
+    if (rec >= S.n_records) {
+      atomicOr(S.error_word, kErrSbt);
+      return false;
+    }
+    uint4 sr = __ldg(S.sbt + rec);
+    const uint4 hg = __ldg(S.hit_groups + sr.x);
+    IsResult res;
+    if (run_intersection(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
+        res.t >= tmin) {
+      bool accept = res.t < h.t;
+      if (!accept && res.t == h.t && h.inst >= 0)
+        accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
+      if (accept) {
+        h.t = res.t;
+        h.inst = k;
+        h.leaf = leaf;
+        h.attr = res.attr;
+        if (any_hit) return true;
+      }
+    }
+    return false;
+  };
+  if (bi.w < 0 && !(bi.w & (int)kTriBit)) {
+    // One-AABB BLAS: the build copies that AABB as the root box, so the root
+    // slab interval is the leaf's own; no second slab test.
+    const int leaf = bi.w & 0x3FFFFFFF;
+    return procedural_leaf(leaf, __ldg(S.leaf_prim + leaf), r_lo, r_hi);
   }
   int sp = sp0;
   int node = bi.w;
@@ -159,32 +197,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       slab(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv, te,
            tx);
       float t_lo = fmaxf(te, tmin), t_hi = fminf(tx, h.t);
-      if (t_lo <= t_hi) {
-        uint2 gq = __ldg(S.leaf_gq + leaf);
-        if (wc) ++wc->sbt_lookups;
-        uint32_t rec = r + S.sbt_stride_m * gq.x + info.y;
-        if (rec >= S.n_records) {
-          atomicOr(S.error_word, kErrSbt);
-        } else {
-          uint4 sr = __ldg(S.sbt + rec);
-          const uint4 hg = __ldg(S.hit_groups + sr.x);
-          IsResult res;
-          if (run_intersection(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res,
-                               wc) &&
-              res.t >= tmin) {
-            bool accept = res.t < h.t;
-            if (!accept && res.t == h.t && h.inst >= 0)
-              accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
-            if (accept) {
-              h.t = res.t;
-              h.inst = k;
-              h.leaf = leaf;
-              h.attr = res.attr;
-              if (any_hit) return true;
-            }
-          }
-        }
-      }
+      if (t_lo <= t_hi && procedural_leaf(leaf, prim, t_lo, t_hi)) return true;
     }
     if (sp == sp0) break;
     node = stack[--sp];

@@ -369,7 +369,9 @@ def test_four_wide_tlas_gives_the_same_image(n_inst):
         k2 = scene.trace_work(w.camera, w.params, binary_tlas=True)
         assert k4["tlas_nodes"] == 0 and k2["tlas_nodes4"] == 0
         assert k4["tlas_nodes4"] < k2["tlas_nodes"]
-        assert k4["leaves"] == k2["leaves"] or True     # visit order may differ; the image may not
+        # the visit order (and so the number of leaves reached before the
+        # closest hit prunes the rest) may differ; the rays cast may not
+        assert k4["rays"] == k2["rays"]
     scene.close()
 
 

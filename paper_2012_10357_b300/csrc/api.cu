@@ -197,8 +197,7 @@ struct pr_scene {
   float4* blas_box;
   float4* blas_nodes;
   uint32_t *blas_perm, *blas_codes;
-  float4* inst_w2o;
-  uint4* inst_info;
+  float4* inst_rec;                  // [n_inst][6] instance records (see SceneView)
   float* inst_boxes;
   float4* tlas_nodes;
   float4* tlas4;                     // 4-wide TLAS collapsed from tlas_nodes
@@ -268,8 +267,7 @@ pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
 
 SceneView view_of(const pr_scene* s) {
   SceneView v;
-  v.inst_w2o = s->inst_w2o;
-  v.inst_info = s->inst_info;
+  v.inst_rec = s->inst_rec;
   v.tlas_nodes = s->tlas_nodes;
   v.tlas_root_ref = s->L.n_inst == 1 ? (int)kLeafBit : 0;
   // the 4-wide TLAS pays off on large instance counts only (measured: +3 % at
@@ -386,8 +384,8 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
          o_vert = c.take<float>(3 * (size_t)L.n_vert), o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri),
          o_tbox = c.take<float>(6 * (size_t)L.n_tri),
          o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes), o_bperm = c.take<uint32_t>(L.n_leaves),
-         o_bcodes = c.take<uint32_t>(L.n_leaves), o_w2o = c.take<float4>(3 * (size_t)L.n_inst),
-         o_info = c.take<uint4>(L.n_inst), o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
+         o_bcodes = c.take<uint32_t>(L.n_leaves), o_rec = c.take<float4>(6 * (size_t)L.n_inst),
+         o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
          o_tnodes = c.take<float4>(4 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)),
          o_t4 = c.take<float4>(8 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)), o_c4p = c.take<uint32_t>(L.n_inst),
          o_c4e = c.take<uint32_t>(L.n_inst), o_c4r = c.take<uint32_t>(L.n_inst), o_tperm = c.take<uint32_t>(L.n_inst),
@@ -427,8 +425,7 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   s->blas_nodes = (float4*)(A + o_bnodes);
   s->blas_perm = (uint32_t*)(A + o_bperm);
   s->blas_codes = (uint32_t*)(A + o_bcodes);
-  s->inst_w2o = (float4*)(A + o_w2o);
-  s->inst_info = (uint4*)(A + o_info);
+  s->inst_rec = (float4*)(A + o_rec);
   s->inst_boxes = (float*)(A + o_iboxes);
   s->tlas_nodes = (float4*)(A + o_tnodes);
   s->tlas4 = (float4*)(A + o_t4);
@@ -518,8 +515,8 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
   launches += launch_build_small(s->d_jobs, (uint32_t)s->small_jobs.size(), st);
   for (const LevelDesc& J : s->large_blas) launches += launch_build_large(J, s->scratch, st);
   // 2. instance world boxes, world->object transforms
-  launches += launch_instances(s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box, s->L.n_inst,
-                               s->inst_boxes, s->inst_w2o, s->inst_info, st);
+  launches += launch_instances(s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box,
+                               s->blas_info, s->L.n_inst, s->inst_boxes, s->inst_rec, st);
   // 3. TLAS, then its 4-wide collapse
   if (s->L.n_inst > 0) {
     if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);

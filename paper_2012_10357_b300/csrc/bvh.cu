@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals
 
 __global__ void __launch_bounds__(256) k_instances(const float* xform, const uint32_t* inst_blas,
                                                     const uint32_t* inst_id, const uint32_t* inst_sbt,
-                                                    const uint32_t* inst_mask, const float4* blas_box, uint32_t n,
-                                                    float* boxes, float4* w2o, uint4* info) {
+                                                    const uint32_t* inst_mask, const float4* blas_box,
+                                                    const int4* blas_info, uint32_t n, float* boxes, float4* rec) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const float* m = xform + 12 * (size_t)k;
@@ -411,11 +411,17 @@ __global__ void __launch_bounds__(256) k_instances(const float* xform, const uin
                    {c01 * id, (a00 * a22 - a02 * a20) * id, (a02 * a10 - a00 * a12) * id},
                    {c02 * id, (a01 * a20 - a00 * a21) * id, (a00 * a11 - a01 * a10) * id}};
   float t[3] = {m[3], m[7], m[11]};
+  float4* out = rec + 6 * (size_t)k;
   for (int row = 0; row < 3; ++row) {
     float tw = -(r[row][0] * t[0] + r[row][1] * t[1] + r[row][2] * t[2]);
-    w2o[3 * (size_t)k + row] = make_float4(r[row][0], r[row][1], r[row][2], tw);
+    out[row] = make_float4(r[row][0], r[row][1], r[row][2], tw);
   }
-  info[k] = make_uint4(b, inst_sbt[k], inst_id[k], inst_mask[k]);
+  // what the traversal needs of the instance's BLAS, beside the transform
+  const int4 bi = blas_info[b];
+  out[3] = make_float4(blo.x, blo.y, blo.z, __int_as_float(bi.w));
+  out[4] = make_float4(bhi.x, bhi.y, bhi.z, __int_as_float(bi.x));
+  out[5] = make_float4(__uint_as_float(b), __uint_as_float(inst_sbt[k]), __uint_as_float(inst_id[k]),
+                       __uint_as_float(inst_mask[k]));
 }
 
 // ---- 4-wide collapse of a binary level -----------------------------------
@@ -548,11 +554,11 @@ int launch_build_large(const LevelDesc& J, const BuildScratch& sc, cudaStream_t 
 }
 
 int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
-                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box, uint32_t n_inst,
-                     float* inst_boxes, float4* inst_w2o, uint4* inst_info, cudaStream_t s) {
+                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box,
+                     const int4* blas_info, uint32_t n_inst, float* inst_boxes, float4* inst_rec, cudaStream_t s) {
   if (n_inst == 0) return 0;
-  k_instances<<<(n_inst + 255) / 256, 256, 0, s>>>(xform, inst_blas, inst_id, inst_sbt, inst_mask, blas_box, n_inst,
-                                                   inst_boxes, inst_w2o, inst_info);
+  k_instances<<<(n_inst + 255) / 256, 256, 0, s>>>(xform, inst_blas, inst_id, inst_sbt, inst_mask, blas_box, blas_info,
+                                                   n_inst, inst_boxes, inst_rec);
   return 1;
 }
 

@@ -55,8 +55,8 @@ BuildScratch carve_build_scratch(void* base, uint32_t n);
 int launch_triangle_boxes(const float* vertices, const uint32_t* indices, uint32_t n_tri, float* boxes,
                           cudaStream_t s);
 int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
-                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box, uint32_t n_inst,
-                     float* inst_boxes, float4* inst_w2o, uint4* inst_info, cudaStream_t s);
+                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box,
+                     const int4* blas_info, uint32_t n_inst, float* inst_boxes, float4* inst_rec, cudaStream_t s);
 
 // Tracer (trace.cu).
 struct TraceLaunch {

@@ -35,9 +35,13 @@ struct BlasInfo {      // int4 on the device
 
 // Everything a trace kernel reads; passed by value.
 struct SceneView {
-  // instances (creation order)
-  const float4* inst_w2o;     // [n_inst][3] world->object rows (lin xyz, translation w)
-  const uint4* inst_info;     // [n_inst] blas, sbt_offset, inst_id, mask
+  // instances (creation order): one 96-byte record each, read with six
+  // independent 16-byte loads when a ray reaches the instance
+  //   [0..2] world->object rows (linear xyz, translation w)
+  //   [3]    BLAS root box lo.xyz, BLAS root ref (int bits)
+  //   [4]    BLAS root box hi.xyz, BLAS first node (int bits)
+  //   [5]    blas, sbt_offset, inst_id, mask (uint bits)
+  const float4* inst_rec;
   // TLAS
   const float4* tlas_nodes;   // [max(n_inst-1,0)][4]
   int tlas_root_ref;          // 0 or kLeafBit | instance (single instance)

@@ -71,8 +71,7 @@ __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, c
   }
 }
 
-__device__ __forceinline__ void to_object(const SceneView& S, int k, float3 o, float3 d, float3& oo, float3& dd) {
-  float4 m0 = __ldg(S.inst_w2o + 3 * k), m1 = __ldg(S.inst_w2o + 3 * k + 1), m2 = __ldg(S.inst_w2o + 3 * k + 2);
+__device__ __forceinline__ void to_object(float4 m0, float4 m1, float4 m2, float3 o, float3 d, float3& oo, float3& dd) {
   oo = f3(fmaf(m0.x, o.x, fmaf(m0.y, o.y, fmaf(m0.z, o.z, m0.w))), fmaf(m1.x, o.x, fmaf(m1.y, o.y, fmaf(m1.z, o.z, m1.w))),
           fmaf(m2.x, o.x, fmaf(m2.y, o.y, fmaf(m2.z, o.z, m2.w))));
   dd = f3(fmaf(m0.x, d.x, fmaf(m0.y, d.y, m0.z * d.z)), fmaf(m1.x, d.x, fmaf(m1.y, d.y, m1.z * d.z)),
@@ -87,16 +86,17 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
                               uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->instances;
-  uint4 info = __ldg(S.inst_info + k);
+  const float4* R = S.inst_rec + 6 * (size_t)k;
+  const float4 m0 = __ldg(R), m1 = __ldg(R + 1), m2 = __ldg(R + 2), blo = __ldg(R + 3), bhi = __ldg(R + 4);
+  const uint4 info = __ldg(reinterpret_cast<const uint4*>(R + 5));   // blas, sbt_offset, inst_id, mask
   if ((info.w & 0xFFu) == 0u) return false;
   float3 oo, dd;
-  to_object(S, k, o, d, oo, dd);
+  to_object(m0, m1, m2, o, d, oo, dd);
   float3 inv = safe_rcp(dd);
   float3 o_inv = f3(-oo.x * inv.x, -oo.y * inv.y, -oo.z * inv.z);
-  const int4 bi = __ldg(S.blas_info + info.x);
+  const int root_ref = __float_as_int(blo.w), node_base = __float_as_int(bhi.w);
   float r_lo, r_hi;   // root-box slab interval
   {
-    float4 blo = __ldg(S.blas_box + 2 * info.x), bhi = __ldg(S.blas_box + 2 * info.x + 1);
     float t0, t1;
     slab(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, t0, t1);
     r_lo = fmaxf(t0, tmin);
@@ -132,20 +132,20 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
     }
     return false;
   };
-  if (bi.w < 0 && !(bi.w & (int)kTriBit)) {
+  if (root_ref < 0 && !(root_ref & (int)kTriBit)) {
     // One-AABB BLAS: the build copies that AABB as the root box, so the root
     // slab interval is the leaf's own; no second slab test.
-    const int leaf = bi.w & 0x3FFFFFFF;
+    const int leaf = root_ref & 0x3FFFFFFF;
     return procedural_leaf(leaf, __ldg(S.leaf_prim + leaf), r_lo, r_hi);
   }
   int sp = sp0;
-  int node = bi.w;
+  int node = root_ref;
   for (;;) {
     if (node >= 0) {
       float l0, l1, r0, r1;
       int lref, rref;
       if (wc) ++wc->blas_nodes;
-      node_boxes(S.blas_nodes + 4 * (size_t)(bi.x + node), inv, o_inv, tmin, h.t, l0, l1, r0, r1, lref, rref);
+      node_boxes(S.blas_nodes + 4 * (size_t)(node_base + node), inv, o_inv, tmin, h.t, l0, l1, r0, r1, lref, rref);
       bool hl = l0 <= l1, hr = r0 <= r1;
       if (hl && hr) {
         int nearr = lref, farr = rref;
@@ -357,7 +357,8 @@ struct Surface {
 static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
   if (wc) ++wc->shaded;
   Surface sf;
-  uint4 info = __ldg(S.inst_info + h.inst);
+  const float4* R = S.inst_rec + 6 * (size_t)h.inst;
+  const uint4 info = __ldg(reinterpret_cast<const uint4*>(R + 5));
   const bool tri = (h.leaf & (int)kTriBit) != 0;
   const int leaf = h.leaf & 0x3FFFFFFF;
   uint2 gq = __ldg(S.leaf_gq + leaf);
@@ -367,7 +368,7 @@ static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit&
   uint4 hg = __ldg(S.hit_groups + sr.x);
   float4 mat = __ldg(S.materials + sr.y);
   float3 oo, dd;
-  to_object(S, h.inst, o, d, oo, dd);
+  to_object(__ldg(R), __ldg(R + 1), __ldg(R + 2), o, d, oo, dd);
   float3 p = madd(oo, h.t, dd);
   float3 no;
   if (tri) {
@@ -381,8 +382,8 @@ static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit&
     float hstep = eps * len3(dd);
     no = object_normal(hg.x, prm, p, h.attr, hstep, dd, wc);
   }
-  float4 m0 = __ldg(S.inst_w2o + 3 * h.inst), m1 = __ldg(S.inst_w2o + 3 * h.inst + 1),
-         m2 = __ldg(S.inst_w2o + 3 * h.inst + 2);
+  // the rows again (L1 hits) rather than held live across the normal's estimates
+  const float4 m0 = __ldg(R), m1 = __ldg(R + 1), m2 = __ldg(R + 2);
   float3 nw = f3(fmaf(m0.x, no.x, fmaf(m1.x, no.y, m2.x * no.z)), fmaf(m0.y, no.x, fmaf(m1.y, no.y, m2.y * no.z)),
                  fmaf(m0.z, no.x, fmaf(m1.z, no.y, m2.z * no.z)));
   nw = normalize3(nw);

@@ -37,13 +37,27 @@ struct IsResult {
 };
 
 // Ray/box slab interval with precomputed 1/d and -o/d: per plane one FMA.
-__device__ __forceinline__ void slab(const float3 lo, const float3 hi, const float3 inv_d, const float3 o_inv,
-                                     float& t0, float& t1) {
+// Three-input minimum / maximum (PTX min.f32 / max.f32 with three sources,
+// sm_100 and later): exact, the same value as two nested two-input ones.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Slab interval clipped to [tmin, tmax] (the parametric range still open).
+__device__ __forceinline__ void slab_clip(const float3 lo, const float3 hi, const float3 inv_d, const float3 o_inv,
+                                          float tmin, float tmax, float& t0, float& t1) {
   float ax = fmaf(lo.x, inv_d.x, o_inv.x), bx = fmaf(hi.x, inv_d.x, o_inv.x);
   float ay = fmaf(lo.y, inv_d.y, o_inv.y), by = fmaf(hi.y, inv_d.y, o_inv.y);
   float az = fmaf(lo.z, inv_d.z, o_inv.z), bz = fmaf(hi.z, inv_d.z, o_inv.z);
-  t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
-  t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+  t0 = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), tmin));
+  t1 = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), tmax));
 }
 
 __device__ __forceinline__ float3 safe_rcp(float3 d) {

@@ -15,6 +15,10 @@ namespace pr {
 #ifndef PR_WHILE_WHILE
 #define PR_WHILE_WHILE 0
 #endif
+// While-while order in the 4-wide TLAS traversal (used from 64 instances up).
+#ifndef PR_TLAS4_WHILE_WHILE
+#define PR_TLAS4_WHILE_WHILE 0
+#endif
 
 // Per-thread traversal stack. With PR_SMEM_STACK (default) the entries live in
 // shared memory, interleaved across the CTA's threads (entry i of thread t at
@@ -43,12 +47,8 @@ __device__ __forceinline__ bool key_less(int i0, uint2 gq0, int i1, uint2 gq1) {
 __device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3 o_inv, float tmin, float tmax,
                                            float& l0, float& l1, float& r0, float& r1, int& lref, int& rref) {
   float4 a = __ldg(n), b = __ldg(n + 1), c = __ldg(n + 2), e = __ldg(n + 3);
-  slab(f3(a.x, a.y, a.z), f3(a.w, b.x, b.y), inv_d, o_inv, l0, l1);
-  slab(f3(b.z, b.w, c.x), f3(c.y, c.z, c.w), inv_d, o_inv, r0, r1);
-  l0 = fmaxf(l0, tmin);
-  l1 = fminf(l1, tmax);
-  r0 = fmaxf(r0, tmin);
-  r1 = fminf(r1, tmax);
+  slab_clip(f3(a.x, a.y, a.z), f3(a.w, b.x, b.y), inv_d, o_inv, tmin, tmax, l0, l1);
+  slab_clip(f3(b.z, b.w, c.x), f3(c.y, c.z, c.w), inv_d, o_inv, tmin, tmax, r0, r1);
   lref = __float_as_int(e.x);
   rref = __float_as_int(e.y);
 }
@@ -96,13 +96,8 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
   float3 o_inv = f3(-oo.x * inv.x, -oo.y * inv.y, -oo.z * inv.z);
   const int root_ref = __float_as_int(blo.w), node_base = __float_as_int(bhi.w);
   float r_lo, r_hi;   // root-box slab interval
-  {
-    float t0, t1;
-    slab(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, t0, t1);
-    r_lo = fmaxf(t0, tmin);
-    r_hi = fminf(t1, h.t);
-    if (r_lo > r_hi) return false;
-  }
+  slab_clip(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, tmin, h.t, r_lo, r_hi);
+  if (r_lo > r_hi) return false;
   // Procedural leaf whose AABB slab interval is [t_lo, t_hi]: Eq. 1 record,
   // intersection shader, closest-hit bookkeeping. True when any-hit mode
   // accepted a hit (the trace ends).
@@ -193,10 +188,9 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
         continue;
       }
       const float* bb = S.aabbs + 6 * (size_t)prim;
-      float te, tx;
-      slab(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv, te,
-           tx);
-      float t_lo = fmaxf(te, tmin), t_hi = fminf(tx, h.t);
+      float t_lo, t_hi;
+      slab_clip(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv,
+                tmin, h.t, t_lo, t_hi);
       if (t_lo <= t_hi && procedural_leaf(leaf, prim, t_lo, t_hi)) return true;
     }
     if (sp == sp0) break;
@@ -223,51 +217,78 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
     // 4-wide TLAS: four slab tests per node on coordinate vectors, hit
     // children ordered near to far by a 5-exchange sorting network; the
     // nearest is visited next, the others pushed farthest first.
+    constexpr int kNone = 0x7FFFFFFF;   // no node (never a node index: those are < 2^30)
+    auto visit4 = [&](int node) -> int {
+      if (wc) ++wc->tlas_nodes4;
+      const float4* nd = S.tlas4 + 8 * (size_t)node;
+      const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+      const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+      const float clo[3][4] = {{lx.x, lx.y, lx.z, lx.w}, {ly.x, ly.y, ly.z, ly.w}, {lz.x, lz.y, lz.z, lz.w}};
+      const float chi[3][4] = {{hx.x, hx.y, hx.z, hx.w}, {hy.x, hy.y, hy.z, hy.w}, {hz.x, hz.y, hz.z, hz.w}};
+      int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+      float key[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float ax = fmaf(clo[0][k], inv.x, o_inv.x), bx = fmaf(chi[0][k], inv.x, o_inv.x);
+        float ay = fmaf(clo[1][k], inv.y, o_inv.y), by = fmaf(chi[1][k], inv.y, o_inv.y);
+        float az = fmaf(clo[2][k], inv.z, o_inv.z), bz = fmaf(chi[2][k], inv.z, o_inv.z);
+        float t0 = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), tmin));
+        float t1 = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), h.t));
+        key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
+      }
+      auto cswap = [&](int a, int b) {
+        if (key[b] < key[a]) {
+          float tk = key[a]; key[a] = key[b]; key[b] = tk;
+          int tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;
+        }
+      };
+      cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+      if (key[0] == INFINITY) return kNone;
+#pragma unroll
+      for (int k = 3; k >= 1; --k) {
+        if (key[k] != INFINITY) {
+          if (sp < kStackDepth) stack[sp++] = ref[k];
+          else atomicOr(S.error_word, kErrStack);
+        }
+      }
+      return ref[0];
+    };
     int node = S.tlas4_root;
+#if PR_TLAS4_WHILE_WHILE
+    // While-while order (Aila & Laine 2009): descend until every converged
+    // lane of the warp holds an instance leaf (or is done), then run the
+    // instance transitions and BLAS work of the warp together.
+    while (node != kNone) {
+      int leaf = kNone;
+      while (node != kNone) {
+        if (node >= 0) {
+          node = visit4(node);
+          if (node == kNone) node = sp ? stack[--sp] : kNone;
+        }
+        if (node < 0) {
+          if (leaf != kNone) break;   // already holding one: go process it
+          leaf = node;
+          node = sp ? stack[--sp] : kNone;
+        }
+        if (!__any_sync(__activemask(), leaf == kNone)) break;
+      }
+      if (leaf != kNone &&
+          traverse_blas<kStats>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+        return;
+    }
+    return;
+#else
     for (;;) {
       if (node >= 0) {
-        if (wc) ++wc->tlas_nodes4;
-        const float4* nd = S.tlas4 + 8 * (size_t)node;
-        const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
-        const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
-        const float clo[3][4] = {{lx.x, lx.y, lx.z, lx.w}, {ly.x, ly.y, ly.z, ly.w}, {lz.x, lz.y, lz.z, lz.w}};
-        const float chi[3][4] = {{hx.x, hx.y, hx.z, hx.w}, {hy.x, hy.y, hy.z, hy.w}, {hz.x, hz.y, hz.z, hz.w}};
-        int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
-        float key[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float ax = fmaf(clo[0][k], inv.x, o_inv.x), bx = fmaf(chi[0][k], inv.x, o_inv.x);
-          float ay = fmaf(clo[1][k], inv.y, o_inv.y), by = fmaf(chi[1][k], inv.y, o_inv.y);
-          float az = fmaf(clo[2][k], inv.z, o_inv.z), bz = fmaf(chi[2][k], inv.z, o_inv.z);
-          float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), tmin));
-          float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), h.t));
-          key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
-        }
-        auto cswap = [&](int a, int b) {
-          if (key[b] < key[a]) {
-            float tk = key[a]; key[a] = key[b]; key[b] = tk;
-            int tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;
-          }
-        };
-        cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
-        if (key[0] != INFINITY) {
-#pragma unroll
-          for (int k = 3; k >= 1; --k) {
-            if (key[k] != INFINITY) {
-              if (sp < kStackDepth) stack[sp++] = ref[k];
-              else atomicOr(S.error_word, kErrStack);
-            }
-          }
-          node = ref[0];
-          continue;
-        }
-      } else {
-        if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
-          return;
+        node = visit4(node);
+        if (node != kNone) continue;
+      } else if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) {
+        return;
       }
       if (sp == 0) return;
       node = stack[--sp];
     }
+#endif
   }
   int node = S.tlas_root_ref;
 #if PR_WHILE_WHILE

@@ -521,7 +521,9 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
   if (s->L.n_inst > 0) {
     if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
     else launches += launch_build_large(s->tlas_job, s->scratch, st);
-    launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
+    // the 4-wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
+    if (s->L.n_inst >= kTlas4MinInstances)
+      launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");

@@ -184,12 +184,16 @@ pr_status pr_scene_validate(const pr_scene_desc* desc);
  * Returns PR_ERR_SBT_INDEX when the index is >= n_records (no write). */
 pr_status pr_sbt_index(uint32_t r, uint32_t m, uint32_t g, uint32_t i, uint32_t n_records, uint32_t* out);
 
-/* Validate, allocate one device arena sized for the scene and its BVH build,
- * and copy the description to the device on `stream`. The BVH is not built. */
+/* Validate, allocate one device arena sized for the scene and its BVH build
+ * (and a pinned host buffer of the size of its inputs), and copy the
+ * description to the device on `stream`. The caller's arrays are read during
+ * the call only. The BVH is not built. */
 pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** out);
 
 /* Re-upload a description with the same counts into an existing scene
- * (no allocation); marks the BVH stale. */
+ * (no allocation); marks the BVH stale. The inputs are packed into the
+ * scene's pinned buffer during the call and sent with one asynchronous copy on
+ * `stream` (the call first waits for the previous upload's copy to finish). */
 pr_status pr_scene_upload(pr_scene* scene, const pr_scene_desc* desc, void* stream);
 
 /* Build the two-level BVH on the device (asynchronous on `stream`): each BLAS

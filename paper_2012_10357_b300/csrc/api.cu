@@ -178,6 +178,11 @@ struct pr_scene {
   Layout L;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  // pinned mirror of the arena's input prefix: an upload packs the inputs here
+  // and sends them with one asynchronous copy
+  char* h_stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_done = nullptr;   // the last upload's copy has read h_stage
   // inputs
   float* aabbs;
   float4* params;
@@ -234,33 +239,34 @@ struct Carver {
 
 pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
   const Layout& L = s->L;
-  auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
-    if (!bytes) return cudaSuccess;
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  // the previous upload's copy must have read the staging buffer before it is refilled
+  PR_CUDA(cudaEventSynchronize(s->stage_done), "wait for the previous upload");
+  char* H = s->h_stage;
+  auto put = [&](const void* dev_dst, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(H + (static_cast<const char*>(dev_dst) - s->arena), src, bytes);
   };
-  std::vector<uint32_t> hg(4 * (size_t)L.n_hg);
+  put(s->aabbs, d->aabbs, sizeof(float) * 6 * L.n_prims);
+  put(s->params, d->params, sizeof(float) * PR_PARAMS_PER_PRIM * L.n_prims);
+  put(s->xform, d->inst_xform, sizeof(float) * 12 * L.n_inst);
+  put(s->inst_blas, d->inst_blas, sizeof(uint32_t) * L.n_inst);
+  put(s->inst_id, d->inst_id, sizeof(uint32_t) * L.n_inst);
+  put(s->inst_sbt, d->inst_sbt_offset, sizeof(uint32_t) * L.n_inst);
+  put(s->inst_mask, d->inst_mask, sizeof(uint32_t) * L.n_inst);
+  uint32_t* hg = reinterpret_cast<uint32_t*>(H + (reinterpret_cast<const char*>(s->hit_groups) - s->arena));
   for (uint32_t h = 0; h < L.n_hg; ++h) {
     for (int k = 0; k < 3; ++k) hg[4 * h + k] = d->hit_groups[3 * h + k];
     hg[4 * h + 3] = 0;
   }
-  PR_CUDA(cp(s->aabbs, d->aabbs, sizeof(float) * 6 * L.n_prims), "copy aabbs");
-  PR_CUDA(cp(s->params, d->params, sizeof(float) * PR_PARAMS_PER_PRIM * L.n_prims), "copy params");
-  PR_CUDA(cp(s->xform, d->inst_xform, sizeof(float) * 12 * L.n_inst), "copy transforms");
-  PR_CUDA(cp(s->inst_blas, d->inst_blas, sizeof(uint32_t) * L.n_inst), "copy inst_blas");
-  PR_CUDA(cp(s->inst_id, d->inst_id, sizeof(uint32_t) * L.n_inst), "copy inst_id");
-  PR_CUDA(cp(s->inst_sbt, d->inst_sbt_offset, sizeof(uint32_t) * L.n_inst), "copy inst_sbt_offset");
-  PR_CUDA(cp(s->inst_mask, d->inst_mask, sizeof(uint32_t) * L.n_inst), "copy inst_mask");
-  PR_CUDA(cp(s->hit_groups, hg.data(), sizeof(uint32_t) * hg.size()), "copy hit groups");
-  PR_CUDA(cp(s->materials, d->materials, sizeof(float) * 4 * L.n_mat), "copy materials");
-  PR_CUDA(cp(s->sbt, d->sbt, sizeof(uint32_t) * 4 * L.n_rec), "copy sbt");
-  PR_CUDA(cp(s->ray_types, d->ray_types, sizeof(uint32_t) * 2 * L.n_rt), "copy ray types");
-  PR_CUDA(cp(s->leaf_prim, L.leaf_prim.data(), sizeof(uint32_t) * L.n_leaves), "copy leaves");
-  PR_CUDA(cp(s->leaf_gq, L.leaf_gq.data(), sizeof(uint32_t) * 2 * L.n_leaves), "copy leaf gq");
-  PR_CUDA(cp(s->blas_info, L.blas_info.data(), sizeof(int) * 4 * L.n_blas), "copy blas info");
-  PR_CUDA(cp(s->vertices, d->vertices, sizeof(float) * 3 * L.n_vert), "copy vertices");
-  PR_CUDA(cp(s->indices, d->indices, sizeof(uint32_t) * 3 * L.n_tri), "copy indices");
-  // hit groups vector is a local: make sure the pageable copy has been staged
-  PR_CUDA(cudaStreamSynchronize(st), "sync upload");
+  put(s->materials, d->materials, sizeof(float) * 4 * L.n_mat);
+  put(s->sbt, d->sbt, sizeof(uint32_t) * 4 * L.n_rec);
+  put(s->ray_types, d->ray_types, sizeof(uint32_t) * 2 * L.n_rt);
+  put(s->leaf_prim, L.leaf_prim.data(), sizeof(uint32_t) * L.n_leaves);
+  put(s->leaf_gq, L.leaf_gq.data(), sizeof(uint32_t) * 2 * L.n_leaves);
+  put(s->blas_info, L.blas_info.data(), sizeof(int) * 4 * L.n_blas);
+  put(s->vertices, d->vertices, sizeof(float) * 3 * L.n_vert);
+  put(s->indices, d->indices, sizeof(uint32_t) * 3 * L.n_tri);
+  PR_CUDA(cudaMemcpyAsync(s->arena, H, s->stage_bytes, cudaMemcpyHostToDevice, st), "copy scene inputs");
+  PR_CUDA(cudaEventRecord(s->stage_done, st), "record upload");
   s->built = false;
   return PR_OK;
 }
@@ -380,9 +386,10 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
          o_iid = c.take<uint32_t>(L.n_inst), o_isbt = c.take<uint32_t>(L.n_inst), o_imask = c.take<uint32_t>(L.n_inst),
          o_hg = c.take<uint4>(L.n_hg), o_mat = c.take<float4>(L.n_mat), o_sbt = c.take<uint4>(L.n_rec),
          o_rt = c.take<uint2>(L.n_rt), o_lp = c.take<uint32_t>(L.n_leaves), o_lgq = c.take<uint2>(L.n_leaves),
-         o_binfo = c.take<int4>(L.n_blas), o_bbox = c.take<float4>(2 * (size_t)L.n_blas),
-         o_vert = c.take<float>(3 * (size_t)L.n_vert), o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri),
-         o_tbox = c.take<float>(6 * (size_t)L.n_tri),
+         o_binfo = c.take<int4>(L.n_blas), o_vert = c.take<float>(3 * (size_t)L.n_vert),
+         o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri),
+         // everything above is input (one prefix of the arena, copied in one piece)
+         o_tbox = c.take<float>(6 * (size_t)L.n_tri), o_bbox = c.take<float4>(2 * (size_t)L.n_blas),
          o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes), o_bperm = c.take<uint32_t>(L.n_leaves),
          o_bcodes = c.take<uint32_t>(L.n_leaves), o_rec = c.take<float4>(6 * (size_t)L.n_inst),
          o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
@@ -398,10 +405,13 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   const size_t n_jobs = (size_t)L.n_blas + 1;
   size_t o_jobs = c.take<LevelDesc>(n_jobs);
   s->arena_bytes = c.off;
+  s->stage_bytes = o_tbox;
   cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, s->stage_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    delete s;
-    return cuda_fail(e, "cudaMalloc scene arena");
+    pr_scene_destroy(s);
+    return cuda_fail(e, "scene arena / pinned staging buffer");
   }
   char* A = s->arena;
   s->aabbs = (float*)(A + o_aabbs);
@@ -733,6 +743,8 @@ void pr_scene_destroy(pr_scene* s) {
   cudaDeviceSynchronize();
   if (s->arena) cudaFree(s->arena);
   if (s->d_cams) cudaFree(s->d_cams);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->stage_done) cudaEventDestroy(s->stage_done);
   delete s;
 }
 

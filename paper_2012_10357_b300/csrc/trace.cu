@@ -31,6 +31,11 @@ struct Params {
 #ifndef PR_TRACE_MIN_BLOCKS
 #define PR_TRACE_MIN_BLOCKS 4
 #endif
+// Width of a warp's pixel tile (4, 8 or 16; height 32 / width).
+#ifndef PR_WARP_TILE_W
+#define PR_WARP_TILE_W 8
+#endif
+static_assert(PR_WARP_TILE_W == 4 || PR_WARP_TILE_W == 8 || PR_WARP_TILE_W == 16, "warp tile width");
 
 template <bool kStats>
 __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, unsigned long long* work) {
@@ -40,8 +45,10 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
   WorkCounters* wc = kStats ? &wcl : nullptr;
   const uint32_t frame = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-  const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+  // 16x8-pixel CTA tile split into four warp tiles of kWarpW x (32 / kWarpW) pixels
+  constexpr int kWarpW = PR_WARP_TILE_W, kWarpsX = 16 / kWarpW;
+  const int x = blockIdx.x * 16 + (warp % kWarpsX) * kWarpW + (lane % kWarpW);
+  const int y = blockIdx.y * 8 + (warp / kWarpsX) * (32 / kWarpW) + lane / kWarpW;
   const bool valid = x < (int)P.width && y < (int)P.height;
   __shared__ CameraBasis s_cam;
   if (threadIdx.x == 0) s_cam = camera_basis(P.cams ? P.cams[frame] : P.cam0, P.width, P.height);

@@ -483,6 +483,11 @@ def run_ours(args):
         # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
         roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(props.multi_processor_count, float(sustained))
         roof["frac_at_measured_sustained_clock"] = achieved_tflops / roof["peak_at_measured_sustained_clock"]
+    if roof["traffic"]:
+        # DRAM bytes of a launch over its mean duration, against the measured copy bandwidth
+        roof["traffic_gbs"] = roof["traffic"] / trace_avg_s / 1e9
+        if peaks.get("hbm_gbs"):
+            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / float(peaks["hbm_gbs"])
     # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
     probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
     roof["peak_fma_probe"] = probe_tflops

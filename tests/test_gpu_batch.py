@@ -127,3 +127,37 @@ def test_batch_budget_and_argument_errors():
     with pytest.raises(pr.PrError) as ei:
         pr.Batch(1, 4096).trace([(unbuilt, w.camera, w.params, out)])
     assert ei.value.status == pr.PR_ERR_NOT_BUILT
+
+
+def test_config4_full_batch_sampled_vs_oracle():
+    """The config-4 batch at full size (64 requests, 83.6 M pixels, in the
+    launch configuration the benchmark uses: one graph launch): every request's
+    image equals its pr_trace, and 64 seeded pixels of every request (4096 in
+    all, parity on the sampled pixels as the oracle renders them one by one)
+    agree with the oracle within the 0.1 % budget."""
+    from parity import AGREE_MIN
+    ws = scenes.config4_requests(0, 64)
+    total = sum(w.params.width * w.params.height for w in ws)
+    objs = [pr.Scene(w.scene) for w in ws]
+    outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+    batch = pr.Batch(len(ws), total)
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], graph=True)
+    torch.cuda.synchronize()
+    n = agree = ok = 0
+    for k, (o, w, out) in enumerate(zip(objs, ws, outs)):
+        img, aov = o.trace(w.camera, w.params, want_aov=True)
+        torch.cuda.synchronize()
+        assert torch.equal(img, out), f"request {k}"
+        pix = scenes.sample_pixels(w.params.width, w.params.height, 64, seed=100 + k)
+        box = o.bounds()
+        rep = compare(oracle.render(w, pixels=pix), pr.aov_to_numpy(aov).reshape(-1)[pix],
+                      img[..., :3].reshape(-1, 3).cpu().numpy()[pix], float(np.linalg.norm(box[3:] - box[:3])))
+        n += rep["n"]
+        agree += round(rep["agree"] * rep["n"])
+        ok += round(rep["agree_within_tol"] * rep["n"])
+        del img, aov
+    batch.close()
+    for o in objs:
+        o.close()
+    assert n == 64 * len(ws)
+    assert agree / n >= AGREE_MIN and ok / n >= AGREE_MIN, (n, agree, ok)

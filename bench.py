@@ -131,7 +131,11 @@ def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tupl
 TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/csrc/tracer.cuh",
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
-TRACE_TRAFFIC = {}   # {sha1: {workload: bytes per launch}}
+TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
+    "3114c49b4a8d85d0a8578b3a909cf6cf333fb05c": {"config2": 129024 + 760576,
+                                                 "config3": 6503168 + 84262400,
+                                                 "config1_frames": 250880 + 220156672},
+}
 
 
 def trace_sources_sha1() -> str:

@@ -40,6 +40,9 @@ pr_status cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr uint32_t kTlas4MinInstances = 64;
+// Scenes with at most this many BLAS levels (all small) and a small TLAS are
+// built by one single-CTA launch.
+constexpr uint32_t kFusedBuildMaxBlas = 32;
 
 // Counts and host-side flattening of a description.
 struct Layout {
@@ -519,21 +522,28 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
   if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
   cudaStream_t st = (cudaStream_t)stream;
   int launches = 0;
-  // 0. triangle boxes (leaf input of triangle BLASes)
-  launches += launch_triangle_boxes(s->vertices, s->indices, s->L.n_tri, s->tri_boxes, st);
-  // 1. every small BLAS in one launch, one CTA each
-  launches += launch_build_small(s->d_jobs, (uint32_t)s->small_jobs.size(), st);
-  for (const LevelDesc& J : s->large_blas) launches += launch_build_large(J, s->scratch, st);
-  // 2. instance world boxes, world->object transforms
-  launches += launch_instances(s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box,
-                               s->blas_info, s->L.n_inst, s->inst_boxes, s->inst_rec, st);
-  // 3. TLAS, then its 4-wide collapse
-  if (s->L.n_inst > 0) {
-    if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
-    else launches += launch_build_large(s->tlas_job, s->scratch, st);
-    // the 4-wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
-    if (s->L.n_inst >= kTlas4MinInstances)
-      launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
+  const InstanceArgs IA{s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box,
+                        s->blas_info, s->L.n_inst, s->inst_boxes, s->inst_rec};
+  if (s->L.n_tri == 0 && s->large_blas.empty() && s->L.n_inst > 0 && s->tlas_small &&
+      s->small_jobs.size() <= kFusedBuildMaxBlas && s->L.n_inst < kTlas4MinInstances) {
+    // small scene: BLAS levels, instances and TLAS in one single-CTA launch
+    launches += launch_build_scene_small(s->d_jobs, (uint32_t)s->small_jobs.size(), IA, st);
+  } else {
+    // 0. triangle boxes (leaf input of triangle BLASes)
+    launches += launch_triangle_boxes(s->vertices, s->indices, s->L.n_tri, s->tri_boxes, st);
+    // 1. every small BLAS in one launch, one CTA each
+    launches += launch_build_small(s->d_jobs, (uint32_t)s->small_jobs.size(), st);
+    for (const LevelDesc& J : s->large_blas) launches += launch_build_large(J, s->scratch, st);
+    // 2. instance world boxes, world->object transforms
+    launches += launch_instances(IA, st);
+    // 3. TLAS, then its 4-wide collapse
+    if (s->L.n_inst > 0) {
+      if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
+      else launches += launch_build_large(s->tlas_job, s->scratch, st);
+      // the 4-wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
+      if (s->L.n_inst >= kTlas4MinInstances)
+        launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");

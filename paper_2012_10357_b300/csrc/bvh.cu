@@ -113,10 +113,24 @@ __device__ __forceinline__ void karras_node(int i, int n, KeyFn key, int& first,
   last = max(i, j);
 }
 
+// A level of one leaf: its centroid bounds are that centroid (extent 0), so
+// the leaf's Morton code is 0; the root box is the leaf's box.
+__device__ void single_leaf_level(const LevelDesc& J) {
+  J.perm[0] = 0u;
+  J.codes[0] = 0u;
+  const float* b = leaf_box(J, 0);
+  const float bb[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
+  write_root(J.root_box, bb);
+}
+
 // ---- single-CTA build of a small level (n <= kSmallMax) --------------------
 __device__ void build_small_body(const LevelDesc& J) {
   const uint32_t n = J.n;
   if (n == 0) return;
+  if (n == 1) {
+    if (threadIdx.x == 0) single_leaf_level(J);
+    return;
+  }
   __shared__ unsigned long long keys[kSmallMax];
   __shared__ float red[6 * 32];
   __shared__ float sh_lo[3], sh_ext[3];
@@ -163,14 +177,6 @@ __device__ void build_small_body(const LevelDesc& J) {
   for (uint32_t p = tid; p < n; p += bd) {
     J.perm[p] = (uint32_t)(keys[p] & 0xFFFFFFFFull);
     J.codes[p] = (uint32_t)(keys[p] >> 32);
-  }
-  if (n == 1) {
-    if (tid == 0) {
-      const float* b = leaf_box(J, (uint32_t)(keys[0] & 0xFFFFFFFFull));
-      float bb[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
-      write_root(J.root_box, bb);
-    }
-    return;
   }
   auto key = [&](int a) -> unsigned long long { return keys[a]; };
   for (int i = tid; i < (int)n - 1; i += bd) {
@@ -380,12 +386,14 @@ __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals
   }
 }
 
-__global__ void __launch_bounds__(256) k_instances(const float* xform, const uint32_t* inst_blas,
-                                                    const uint32_t* inst_id, const uint32_t* inst_sbt,
-                                                    const uint32_t* inst_mask, const float4* blas_box,
-                                                    const int4* blas_info, uint32_t n, float* boxes, float4* rec) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+// Instance k: world box of its BLAS root box, world->object transform, record.
+__device__ void instance_body(uint32_t k, const InstanceArgs& A) {
+  const float* xform = A.xform;
+  const uint32_t *inst_blas = A.inst_blas, *inst_id = A.inst_id, *inst_sbt = A.inst_sbt, *inst_mask = A.inst_mask;
+  const float4* blas_box = A.blas_box;
+  const int4* blas_info = A.blas_info;
+  float* boxes = A.boxes;
+  float4* rec = A.rec;
   const float* m = xform + 12 * (size_t)k;
   uint32_t b = inst_blas[k];
   float4 blo = blas_box[2 * b], bhi = blas_box[2 * b + 1];
@@ -422,6 +430,33 @@ __global__ void __launch_bounds__(256) k_instances(const float* xform, const uin
   out[4] = make_float4(bhi.x, bhi.y, bhi.z, __int_as_float(bi.x));
   out[5] = make_float4(__uint_as_float(b), __uint_as_float(inst_sbt[k]), __uint_as_float(inst_id[k]),
                        __uint_as_float(inst_mask[k]));
+}
+
+__global__ void __launch_bounds__(256) k_instances(InstanceArgs A) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < A.n) instance_body(k, A);
+}
+
+// Whole two-level build of a small scene in one CTA (one launch instead of
+// three): every BLAS level in turn, the instances, then the TLAS level. The
+// same device routines as the separate launches, in the same order, so the
+// result is the same bit for bit.
+__global__ void __launch_bounds__(256) k_build_scene_small(const LevelDesc* jobs, uint32_t n_blas_jobs,
+                                                            InstanceArgs A) {
+  // one-leaf levels (one AABB per BLAS is common): one thread each
+  for (uint32_t j = threadIdx.x; j < n_blas_jobs; j += blockDim.x)
+    if (jobs[j].n == 1) single_leaf_level(jobs[j]);
+  // the others with the whole CTA, one after another
+  for (uint32_t j = 0; j < n_blas_jobs; ++j) {
+    if (jobs[j].n > 1) {
+      build_small_body(jobs[j]);
+      __syncthreads();   // shared scratch reused by the next level
+    }
+  }
+  __syncthreads();     // BLAS root boxes visible to the instance pass
+  for (uint32_t k = threadIdx.x; k < A.n; k += blockDim.x) instance_body(k, A);
+  __syncthreads();     // instance world boxes visible to the TLAS level
+  build_small_body(jobs[n_blas_jobs]);
 }
 
 // ---- 4-wide collapse of a binary level -----------------------------------
@@ -553,12 +588,14 @@ int launch_build_large(const LevelDesc& J, const BuildScratch& sc, cudaStream_t 
   return launches;
 }
 
-int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
-                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box,
-                     const int4* blas_info, uint32_t n_inst, float* inst_boxes, float4* inst_rec, cudaStream_t s) {
-  if (n_inst == 0) return 0;
-  k_instances<<<(n_inst + 255) / 256, 256, 0, s>>>(xform, inst_blas, inst_id, inst_sbt, inst_mask, blas_box, blas_info,
-                                                   n_inst, inst_boxes, inst_rec);
+int launch_instances(const InstanceArgs& A, cudaStream_t s) {
+  if (A.n == 0) return 0;
+  k_instances<<<(A.n + 255) / 256, 256, 0, s>>>(A);
+  return 1;
+}
+
+int launch_build_scene_small(const LevelDesc* d_jobs, uint32_t n_blas_jobs, const InstanceArgs& A, cudaStream_t s) {
+  k_build_scene_small<<<1, 256, 0, s>>>(d_jobs, n_blas_jobs, A);
   return 1;
 }
 

@@ -54,9 +54,20 @@ size_t build_scratch_bytes(uint32_t n);
 BuildScratch carve_build_scratch(void* base, uint32_t n);
 int launch_triangle_boxes(const float* vertices, const uint32_t* indices, uint32_t n_tri, float* boxes,
                           cudaStream_t s);
-int launch_instances(const float* xform, const uint32_t* inst_blas, const uint32_t* inst_id,
-                     const uint32_t* inst_sbt, const uint32_t* inst_mask, const float4* blas_box,
-                     const int4* blas_info, uint32_t n_inst, float* inst_boxes, float4* inst_rec, cudaStream_t s);
+// Inputs and outputs of the instance pass (world boxes, records).
+struct InstanceArgs {
+  const float* xform;
+  const uint32_t *inst_blas, *inst_id, *inst_sbt, *inst_mask;
+  const float4* blas_box;
+  const int4* blas_info;
+  uint32_t n;
+  float* boxes;
+  float4* rec;
+};
+int launch_instances(const InstanceArgs& A, cudaStream_t s);
+// BLAS levels, instances and TLAS of a small scene in one single-CTA launch;
+// d_jobs holds the n_blas_jobs BLAS levels followed by the TLAS level.
+int launch_build_scene_small(const LevelDesc* d_jobs, uint32_t n_blas_jobs, const InstanceArgs& A, cudaStream_t s);
 
 // Tracer (trace.cu).
 struct TraceLaunch {

@@ -383,6 +383,28 @@ def julia_cut_scene(seed: int = 0, normal=(0.0, 0.0, -1.0), offset=0.0, width=32
     return Workload(b.build("julia-cut"), cam, tp, "julia-cut")
 
 
+def mirror_pair(width: int = 33, height: int = 33) -> Workload:
+    """Two unit spheres on the view axis: A at the origin (albedo (0.5, 0.25, 1),
+    k_r = 0.5) in front of the camera, B at z = -20 behind the camera (albedo
+    (0.2, 0.9, 0.4)); the light at z = 5 behind A. The mirror ray of A's front
+    pole returns along the axis to B's pole, which faces the light with A in
+    between (a reflected hit that a shadow ray would find occluded)."""
+    b = SceneBuilder()
+    _standard_rays(b)
+    hr, hs = b.add_hit_group(IS_SPHERE, CHS_LAMBERT), b.add_hit_group(IS_SPHERE)
+    m_a, m_b = b.add_material((0.5, 0.25, 1.0), 0.5), b.add_material((0.2, 0.9, 0.4), 0.0)
+    g0, p0 = shape_sphere((0, 0, 0), 1.0)
+    g1, p1 = shape_sphere((0, 0, -20), 1.0)
+    blas = b.add_blas([b.add_geometry([g0], [p0]), b.add_geometry([g1], [p1])])
+    for mat in (m_a, m_b):
+        b.add_record(hr, mat, IS_SPHERE, 0)
+        b.add_record(hs, mat, IS_SPHERE, 0)
+    b.add_instance(blas, xform_trs((0, 0, 0)), 0)
+    cam = Camera(_f32([0, 0, -10]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
+    tp = TraceParams(width, height, max_depth=2, light_pos=_f32([0, 0, 5]))
+    return Workload(b.build("mirror-pair"), cam, tp, "mirror_pair")
+
+
 def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = True) -> Workload:
     """Sphere, box and pac-man whose hit groups carry the cutout any-hit shader
     (bands removed along object y), over a ground slab; with shadow_cutout the

@@ -175,6 +175,17 @@ def test_config1_degenerate_edge_row_is_the_only_disagreement():
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
+def test_mirror_hit_is_shaded_without_shadow():
+    """Strict parity on the two-sphere mirror scene (reflected hit that a
+    shadow ray would find occluded), plus its centre pixel's closed form."""
+    w = scenes.mirror_pair(33, 33)
+    check_full(w, "mirror pair")
+    rgb, a, diag, rays, err, _ = render_gpu(w)
+    c = rgb.reshape(-1, 3)[16 * 33 + 16]
+    assert np.allclose(c, 0.5 * 0.1 * np.array([0.5, 0.25, 1.0]) + 0.5 * 1.1 * np.array([0.2, 0.9, 0.4]), atol=1e-6)
+    assert int(a.reshape(-1)[16 * 33 + 16]["refl_geom"]) == 1
+
+
 def test_config1_other_seeds(seed):
     check_full(scenes.config1(seed=seed, width=96, height=80), f"config1 seed {seed}")
 

@@ -520,6 +520,23 @@ def test_shadow_any_hit_and_mirror_miss(O):
     assert np.allclose(px["rgb"], np.array([0.5, 0.25, 1.0]) * 0.1, atol=1e-12)
 
 
+def test_mirror_hit_is_shaded_without_shadow(O):
+    """Sphere A (k_r = 0.5) seen head-on with the light behind it: its front
+    pole gets ambient only (n.l = -1, no shadow ray). The mirror ray returns
+    along the axis, past the camera, to sphere B behind it; B's pole faces the
+    light (n.l = 1) but A lies between them. The reflected hit is shaded
+    without a shadow ray, so it is lit: rgb = 0.5 * 0.1 a_A + 0.5 * 1.1 a_B.
+    A shadowed reflection would give 0.5 * 0.1 a_B instead."""
+    a_A, a_B = np.array([0.5, 0.25, 1.0]), np.array([0.2, 0.9, 0.4])
+    px = O.render(scenes.mirror_pair(), pixels=[16 * 33 + 16])[0]
+    assert px["flags"] & 1 and not px["flags"] & 2       # hit, no shadow ray (n.l < 0)
+    assert px["flags"] & 8 and px["flags"] & 16           # mirror ray cast and hit
+    assert (px["refl_inst"], px["refl_geom"], px["refl_prim"]) == (0, 1, 0)
+    assert px["refl_t"] == pytest.approx(18.0, abs=0.01)  # from the offset origin near z = -1 to z = -19
+    assert px["rays"] == 2
+    assert np.allclose(px["rgb"], 0.5 * 0.1 * a_A + 0.5 * 1.1 * a_B, atol=1e-12)
+
+
 def test_tie_keeps_lower_instance(O):
     """Two instances of the same sphere at the same place: exact tie in t, the
     lower (instance, geometry, primitive) key wins."""

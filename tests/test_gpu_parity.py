@@ -174,7 +174,6 @@ def test_config1_degenerate_edge_row_is_the_only_disagreement():
     assert rep["agree"] == 1.0 and rep["t_bad"] == rep["n_bad"] == rep["rgb_bad"] == 0, rep
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
 def test_mirror_hit_is_shaded_without_shadow():
     """Strict parity on the two-sphere mirror scene (reflected hit that a
     shadow ray would find occluded), plus its centre pixel's closed form."""
@@ -186,6 +185,7 @@ def test_mirror_hit_is_shaded_without_shadow():
     assert int(a.reshape(-1)[16 * 33 + 16]["refl_geom"]) == 1
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
 def test_config1_other_seeds(seed):
     check_full(scenes.config1(seed=seed, width=96, height=80), f"config1 seed {seed}")
 

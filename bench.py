@@ -132,9 +132,9 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "3114c49b4a8d85d0a8578b3a909cf6cf333fb05c": {"config2": 129024 + 760576,
-                                                 "config3": 6503168 + 84262400,
-                                                 "config1_frames": 250880 + 220156672},
+    "4190df935e3c37975707172784dc0dafd8feb151": {"config2": 126464 + 824576,
+                                                 "config3": 6424064 + 85360640,
+                                                 "config1_frames": 251648 + 220171008},
 }
 
 

@@ -256,6 +256,33 @@ def test_repeated_launches_on_two_streams():
     scene.close()
 
 
+def test_4096_frame_launch_sampled_vs_oracle():
+    """The config-1 throughput launch as the benchmark times it (4096 jittered
+    64x64 frames in one pr_trace_frames call): 32 seeded frames x 64 seeded
+    pixels agree with the oracle (strict: an analytic scene), and those frames
+    equal single-frame renders bit for bit."""
+    w = scenes.config1()
+    cams = scenes.config1_cameras(0, 4096)
+    scene = pr.Scene(w.scene)
+    out, aov = scene.trace_frames(pr.CameraArray(cams), w.params, want_aov=True)
+    torch.cuda.synchronize()
+    box = scene.bounds()
+    diag = float(np.linalg.norm(box[3:] - box[:3]))
+    rng = np.random.default_rng(11)
+    n = agree = 0
+    for f in sorted(rng.choice(4096, 32, replace=False).tolist()):
+        wf = scenes.Workload(w.scene, cams[f], w.params)
+        pix = scenes.sample_pixels(64, 64, 64, seed=f)
+        rep = compare(oracle.render(wf, pixels=pix), pr.aov_to_numpy(aov[f]).reshape(-1)[pix],
+                      out[f, ..., :3].reshape(-1, 3).cpu().numpy()[pix], diag)
+        assert rep["t_bad"] == 0 and rep["n_bad"] == 0 and rep["rgb_bad"] == 0, (f, rep)
+        n += rep["n"]
+        agree += round(rep["agree"] * rep["n"])
+        assert torch.equal(scene.trace(cams[f], w.params), out[f])
+    scene.close()
+    assert agree / n >= 0.999, (n, agree)
+
+
 def test_jittered_frames_vs_oracle():
     w = scenes.config1()
     cams = scenes.config1_cameras(0, 4)

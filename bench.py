@@ -34,20 +34,20 @@ L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
 
 
 def workload_by_name(name: str):
-    if name in ("config1", "config1_frames"):
-        return scenes.config1()
-    if name == "config2":
-        return scenes.config2()
-    if name == "config3":
-        return scenes.config3()
+    if name in ("analytic_64x64", "analytic_64x64_x4096"):
+        return scenes.small_analytic()
+    if name == "teaser_1080p":
+        return scenes.teaser()
+    if name == "field_100k_2160p":
+        return scenes.field()
     raise SystemExit(f"unknown workload {name}")
 
 
 def workload_config(name: str, w) -> dict:
-    d = {"workload": {"config1": "tiny analytic scene, 4 AABB primitives, one BLAS",
-                      "config1_frames": "tiny analytic scene, 4096 eye-jittered 64x64 frames per launch",
-                      "config2": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
-                      "config3": "instanced field, 100000 instances of 8 procedural types"}[name],
+    d = {"workload": {"analytic_64x64": "tiny analytic scene, 4 AABB primitives, one BLAS",
+                      "analytic_64x64_x4096": "tiny analytic scene, 4096 eye-jittered 64x64 frames per launch",
+                      "teaser_1080p": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
+                      "field_100k_2160p": "instanced field, 100000 instances of 8 procedural types"}[name],
          "config": name, "width": w.params.width, "height": w.params.height,
          "instances": int(len(w.scene.inst_blas)), "max_depth": w.params.max_depth,
          "rays_per_pixel_max": 1 + 1 + (1 if w.params.max_depth >= 2 else 0),
@@ -132,9 +132,9 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "4190df935e3c37975707172784dc0dafd8feb151": {"config2": 126464 + 824576,
-                                                 "config3": 6424064 + 85360640,
-                                                 "config1_frames": 251648 + 220171008},
+    "4190df935e3c37975707172784dc0dafd8feb151": {"teaser_1080p": 126464 + 824576,
+                                                 "field_100k_2160p": 6424064 + 85360640,
+                                                 "analytic_64x64_x4096": 251648 + 220171008},
 }
 
 
@@ -165,10 +165,10 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def bench_config1_throughput(pr, work, torch, stream, flush, frames=4096, reps=5) -> dict:
-    """Config 1 as a throughput run: 4096 eye-jittered 64x64 frames in one launch."""
-    w = scenes.config1()
-    cams = pr.CameraArray(scenes.config1_cameras(0, frames))   # marshalled once
+def bench_analytic_frames(pr, work, torch, stream, flush, frames=4096, reps=5) -> dict:
+    """The tiny analytic scene as a throughput run: 4096 eye-jittered 64x64 frames in one launch."""
+    w = scenes.small_analytic()
+    cams = pr.CameraArray(scenes.small_analytic_cameras(0, frames))   # marshalled once
     with torch.cuda.stream(stream):
         scene = pr.Scene(w.scene, stream=stream)
         out = torch.empty((frames, 64, 64, 4), dtype=torch.float32, device="cuda")
@@ -192,7 +192,7 @@ def bench_config1_throughput(pr, work, torch, stream, flush, frames=4096, reps=5
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     peak = work.fp32_peak_tflops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz", 2032.0)))
     scene.close()
-    return {"workload": "config1: 4096 eye-jittered 64x64 frames, one pr_trace_frames launch",
+    return {"workload": "tiny analytic scene: 4096 eye-jittered 64x64 frames, one pr_trace_frames launch",
             "value": rays / avg_s / 1e6, "unit": "Mrays/s", "ms_per_launch": statistics.mean(ms),
             "rays_per_launch": rays,
             "roofline": {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -200,9 +200,9 @@ def bench_config1_throughput(pr, work, torch, stream, flush, frames=4096, reps=5
 
 
 def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
-    """Config 4: 64 requests of uneven size, one batched wavefront launch (CUDA
+    """Batch: 64 requests of uneven size, one batched wavefront launch (CUDA
     graph, autotuned launch shape) vs 64 plain per-request launches."""
-    ws = scenes.config4_requests(0, n_requests)
+    ws = scenes.batch_requests(0, n_requests)
     total_px = sum(w.params.width * w.params.height for w in ws)
     with torch.cuda.stream(stream):
         objs = [pr.Scene(w.scene, stream=stream) for w in ws]
@@ -212,7 +212,7 @@ def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
     batch = pr.Batch(n_requests, total_px)
     items = [(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs_batch)]
     tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
-    key = f"{torch.cuda.get_device_name()}|config4|{n_requests}|{total_px}"
+    key = f"{torch.cuda.get_device_name()}|batch|{n_requests}|{total_px}"
     cache = json.load(open(tune_path)) if os.path.exists(tune_path) else {}
     if key in cache:
         batch.set_tuning(**cache[key]["tuning"])
@@ -258,7 +258,7 @@ def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
                      "ms_per_batch": statistics.mean(totals), "p50_ms": float(np.percentile(lat, 50)),
                      "p99_ms": float(np.percentile(lat, 99)), "rays_per_batch": rays}
     identical = all(torch.equal(a, b) for a, b in zip(outs_plain, outs_batch))
-    out = {"workload": f"config4: {n_requests} requests, resolutions from {{256^2..2048^2}}, "
+    out = {"workload": f"batch: {n_requests} requests, resolutions from {{256^2..2048^2}}, "
                        f"1..10000 instances each, {total_px} pixels",
            "plain": res["plain"], "batched_graph": res["batched_graph"], "batched_direct": res["batched_direct"],
            "speedup_graph_vs_plain": res["plain"]["ms_per_batch"] / res["batched_graph"]["ms_per_batch"],
@@ -271,7 +271,7 @@ def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
 
 
 class _RequestPool:
-    """Config-5 request stream: scene descriptions cached by (kind, seed) so the
+    """Serving request stream: scene descriptions cached by (kind, seed) so the
     generator runs once per scene, as a client holding its scenes would."""
 
     def __init__(self, seed: int):
@@ -279,7 +279,7 @@ class _RequestPool:
         self.descs = {}
 
     def next(self):
-        kind, sseed, wl = scenes.config5_request(self.rng, build=lambda k, s: self.descs.get((k, s)))
+        kind, sseed, wl = scenes.serving_request(self.rng, build=lambda k, s: self.descs.get((k, s)))
         self.descs.setdefault((kind, sseed), wl.scene)
         key = (kind << 32) | sseed
         return key, self.descs[(kind, sseed)], wl.camera, wl.params
@@ -397,8 +397,8 @@ def run_ours(args):
 
     w = workload_by_name(args.workload)
     frames = None
-    if args.workload == "config1_frames":
-        frames = pr.CameraArray(scenes.config1_cameras(0, 4096))    # marshalled once, outside the timed region
+    if args.workload == "analytic_64x64_x4096":
+        frames = pr.CameraArray(scenes.small_analytic_cameras(0, 4096))    # marshalled once, outside the timed region
     stream = torch.cuda.Stream()
     H, W = w.params.height, w.params.width
     with torch.cuda.stream(stream):
@@ -564,13 +564,13 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra:
-        extra["config1_throughput"] = bench_config1_throughput(pr, work, torch, stream, flush)
+        extra["analytic_4096_frames"] = bench_analytic_frames(pr, work, torch, stream, flush)
         extra["batched"] = bench_batched(pr, torch, stream, flush)
         tuning = extra["batched"]["autotune"]["tuning"]
         rows = []
         for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
             rows += bench_serving(pr, torch, args.serve_rates, args.serve_requests, mode, tuning)
-        extra["serving"] = {"workload": "config5: Poisson arrivals, config-2 / config-3 (100000 instances) scenes "
+        extra["serving"] = {"workload": "serving: Poisson arrivals, teaser / instanced-field (100000 instances) scenes "
                                         "50/50 from pools of 16, resolution 512^2..1920x1080, orbit cameras, "
                                         "100 GB budget, 64 slots, 8 Mpx per continuous-batching iteration",
                             "points": rows}
@@ -607,7 +607,7 @@ def run_serve_sweep(args):
     tuning = None
     if os.path.exists(tune_path):
         cache = json.load(open(tune_path))
-        mine = [v for k, v in cache.items() if k.startswith(torch.cuda.get_device_name() + "|config4")]
+        mine = [v for k, v in cache.items() if k.startswith(torch.cuda.get_device_name() + "|batch")]
         tuning = mine[0]["tuning"] if mine else None
     rows = []
     for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
@@ -621,10 +621,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config1", "config1_frames", "config2", "config3"], default="config2")
+    ap.add_argument("--workload", choices=["analytic_64x64", "analytic_64x64_x4096", "teaser_1080p", "field_100k_2160p"], default="teaser_1080p")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the config-1 throughput, batched and serving blocks")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 4096-frame throughput, batched and serving blocks")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[30.0, 1000.0])
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--serve-max-seconds", type=float, default=60.0)

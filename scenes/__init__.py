@@ -447,9 +447,9 @@ def _standard_rays(b: SceneBuilder):
 
 
 # --------------------------------------------------------------------------
-# Config 1: tiny analytic scene, one BLAS with four geometries.
+# Tiny analytic scene (64x64): one BLAS with four geometries.
 # --------------------------------------------------------------------------
-def config1(seed: int = 0, width: int = 64, height: int = 64) -> Workload:
+def small_analytic(seed: int = 0, width: int = 64, height: int = 64) -> Workload:
     rng = np.random.default_rng(seed)
     b = SceneBuilder(sbt_stride_m=2)
     _standard_rays(b)
@@ -472,14 +472,14 @@ def config1(seed: int = 0, width: int = 64, height: int = 64) -> Workload:
         mat = b.add_material(alb, 0.0)
         b.add_record(hr, mat, pt, 0)   # record r + 2g, r = 0
         b.add_record(hs, mat, pt, 0)   # r = 1
-    scene = b.build("config1")
+    scene = b.build("small_analytic")
     cam = Camera(_f32([0, 2, -8]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
     tp = TraceParams(width, height, max_depth=1, light_pos=_f32([5, 8, -5]))
-    return Workload(scene, cam, tp, "config1")
+    return Workload(scene, cam, tp, "small_analytic")
 
 
-def config1_cameras(seed: int, n_frames: int, base: Optional[Camera] = None) -> List[Camera]:
-    """Per-frame cameras of the config-1 throughput run: eye jittered by U[-0.5,0.5]^3."""
+def small_analytic_cameras(seed: int, n_frames: int, base: Optional[Camera] = None) -> List[Camera]:
+    """Per-frame cameras of the 4096-frame throughput run: eye jittered by U[-0.5,0.5]^3."""
     rng = np.random.default_rng(seed + 7919)
     base = base or Camera(_f32([0, 2, -8]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
     jit = rng.uniform(-0.5, 0.5, (n_frames, 3))
@@ -487,12 +487,12 @@ def config1_cameras(seed: int, n_frames: int, base: Optional[Camera] = None) -> 
 
 
 # --------------------------------------------------------------------------
-# Config 2: teaser-like scene, each primitive its own BLAS + hit groups.
+# Teaser-like scene (1920x1080): each primitive its own BLAS + hit groups.
 # Shader-table layout follows Listing 10: per geometry (insertion order), per
 # instance: a radiance record then a shadow record; instance_index runs across
 # procedural geometries.
 # --------------------------------------------------------------------------
-def config2(seed: int = 0, width: int = 1920, height: int = 1080) -> Workload:
+def teaser(seed: int = 0, width: int = 1920, height: int = 1080) -> Workload:
     rng = np.random.default_rng(seed)
     b = SceneBuilder(sbt_stride_m=2)
     _standard_rays(b)
@@ -517,10 +517,10 @@ def config2(seed: int = 0, width: int = 1920, height: int = 1080) -> Workload:
             b.add_record(hs, mat, is_id, instance_index)
             b.add_instance(blas, xf, sbt_offset=off)
             instance_index += 1
-    scene = b.build("config2")
+    scene = b.build("teaser")
     cam = Camera(_f32([0, 3, -10]), _f32([0, 0, 0]), _f32([0, 1, 0]), 60.0)
     tp = TraceParams(width, height, max_depth=2, light_pos=_f32([6, 10, -6]))
-    return Workload(scene, cam, tp, "config2")
+    return Workload(scene, cam, tp, "teaser")
 
 
 def plane_mesh(half: float, y: float, cells: int):
@@ -577,7 +577,8 @@ def sample_scene(seed: int = 0, width: int = 640, height: int = 360, cells: int 
 
 
 # --------------------------------------------------------------------------
-# Config 3 (and config-4 request scenes): instanced field of 8 primitive types.
+# Instanced field of 8 primitive types (100 000 instances at 3840x2160; the batch
+# requests use the same mix at other sizes).
 # --------------------------------------------------------------------------
 FIELD_TYPES = [IS_SPHERE, IS_TORUS, IS_ROUNDBOX, IS_CAPSULE, IS_METABALL4, IS_PACMAN,
                IS_JULIA, IS_MANDELBULB]
@@ -627,13 +628,13 @@ def instanced_field(seed: int, n_inst: int, side: float, origin=(0.0, 0.0, 0.0),
     return scene
 
 
-def config3(seed: int = 0, width: int = 3840, height: int = 2160, n_inst: int = 100_000) -> Workload:
+def field(seed: int = 0, width: int = 3840, height: int = 2160, n_inst: int = 100_000) -> Workload:
     side = 100.0 * (n_inst / 100_000) ** (1.0 / 3.0)
-    scene = instanced_field(seed, n_inst, side, name="config3")
+    scene = instanced_field(seed, n_inst, side, name="field")
     s = side / 100.0
     cam = Camera(_f32([50 * s, 50 * s, -60 * s]), _f32([50 * s, 50 * s, 50 * s]), _f32([0, 1, 0]), 60.0)
     tp = TraceParams(width, height, max_depth=1, light_pos=_f32([50 * s, 200 * s, -100 * s]))
-    return Workload(scene, cam, tp, "config3")
+    return Workload(scene, cam, tp, "field")
 
 
 def orbit_camera(rng: np.random.Generator, center, diag) -> Camera:
@@ -646,7 +647,7 @@ def orbit_camera(rng: np.random.Generator, center, diag) -> Camera:
     return Camera(_f32(eye), _f32(center), _f32([0, 1, 0]), 60.0)
 
 
-def config4_requests(seed: int = 0, n_requests: int = 64, res_choices=(256, 512, 1024, 2048)) -> List[Workload]:
+def batch_requests(seed: int = 0, n_requests: int = 64, res_choices=(256, 512, 1024, 2048)) -> List[Workload]:
     """64 render requests: resolution from {256^2..2048^2}, instanced-field scenes with
     n = floor(10^U[0,4]) instances in a cube of side 100*(n/1e5)^(1/3), orbit cameras."""
     rng = np.random.default_rng(seed)
@@ -664,8 +665,8 @@ def config4_requests(seed: int = 0, n_requests: int = 64, res_choices=(256, 512,
     return out
 
 
-def config5_request(rng: np.random.Generator, scene_pool: int = 16, build=None):
-    """One serving request: a config-2 or config-3 scene (50/50), seed from a pool
+def serving_request(rng: np.random.Generator, scene_pool: int = 16, build=None):
+    """One serving request: a teaser or an instanced-field scene (50/50), seed from a pool
     of 16 per kind (so scenes repeat and a BVH cache can hit), resolution
     t~U[0,1], W=round(512+1408t), H=round(512+568t), orbit camera around the
     scene. build(kind, seed) may return an already generated description."""
@@ -675,12 +676,12 @@ def config5_request(rng: np.random.Generator, scene_pool: int = 16, build=None):
     w, h = int(round(512 + 1408 * t)), int(round(512 + 568 * t))
     known = build(kind, sseed) if build else None
     if kind == 0:
-        wl = config2(sseed, w, h) if known is None else Workload(known, None, config2(sseed, 8, 8).params)
+        wl = teaser(sseed, w, h) if known is None else Workload(known, None, teaser(sseed, 8, 8).params)
         wl.params.width, wl.params.height = w, h
         wl.camera = orbit_camera(rng, (0.0, 0.5, 1.0), 12.0)
     else:
         if known is None:
-            wl = config3(sseed, w, h)
+            wl = field(sseed, w, h)
         else:
             wl = Workload(known, None, TraceParams(w, h, max_depth=1, light_pos=_f32([50, 200, -100])))
         wl.params.width, wl.params.height = w, h

@@ -76,7 +76,7 @@ def test_eq1_fig3_golden_through_abi(pr):
     (lambda s: s.ray_types.__setitem__((0, 0), 7), "miss shader"),
 ])
 def test_validation_rejects(pr, mutate, frag):
-    w = scenes.config1()
+    w = scenes.small_analytic()
     pr.validate(w.scene)
     mutate(w.scene)
     with pytest.raises(pr.PrError) as ei:
@@ -86,15 +86,15 @@ def test_validation_rejects(pr, mutate, frag):
 
 
 def test_validation_accepts_all_configs(pr):
-    for w in (scenes.config1(), scenes.config2(width=8, height=8), scenes.config3(n_inst=300, width=8, height=8)):
+    for w in (scenes.small_analytic(), scenes.teaser(width=8, height=8), scenes.field(n_inst=300, width=8, height=8)):
         pr.validate(w.scene)
 
 
 def test_cutout_any_hit_needs_an_analytic_shader(pr):
-    w = scenes.config1()
+    w = scenes.small_analytic()
     w.scene.hit_groups[0, 2] = scenes.AHS_CUTOUT      # sphere intersection shader: allowed
     pr.validate(w.scene)
-    f = scenes.config3(n_inst=50, width=8, height=8)
+    f = scenes.field(n_inst=50, width=8, height=8)
     torus_hg = [h for h in range(len(f.scene.hit_groups)) if f.scene.hit_groups[h, 0] == scenes.IS_TORUS][0]
     f.scene.hit_groups[torus_hg, 2] = scenes.AHS_CUTOUT
     with pytest.raises(pr.PrError) as ei:
@@ -122,7 +122,7 @@ def test_triangle_validation(pr):
 
 
 def test_one_ray_type_is_rejected(pr):
-    w = scenes.config1()
+    w = scenes.small_analytic()
     w.scene.ray_types = w.scene.ray_types[:1]
     with pytest.raises(pr.PrError):
         pr.validate(w.scene)

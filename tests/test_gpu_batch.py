@@ -22,10 +22,10 @@ import oracle  # noqa: E402
 
 
 def _mixed_workloads():
-    ws = [scenes.config1(width=67, height=45), scenes.config2(width=200, height=113),
-          scenes.config3(n_inst=3000, width=150, height=97), scenes.config1(seed=4, width=1, height=1),
-          scenes.config2(seed=2, width=33, height=250)]
-    ws += scenes.config4_requests(seed=0, n_requests=6, res_choices=(64, 96, 128))
+    ws = [scenes.small_analytic(width=67, height=45), scenes.teaser(width=200, height=113),
+          scenes.field(n_inst=3000, width=150, height=97), scenes.small_analytic(seed=4, width=1, height=1),
+          scenes.teaser(seed=2, width=33, height=250)]
+    ws += scenes.batch_requests(seed=0, n_requests=6, res_choices=(64, 96, 128))
     return ws
 
 
@@ -94,7 +94,7 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
 
 
 def test_batch_request_vs_oracle():
-    w = scenes.config2(width=160, height=90)
+    w = scenes.teaser(width=160, height=90)
     sc = pr.Scene(w.scene)
     batch = pr.Batch(2, 2 * 160 * 90)
     out = torch.empty((90, 160, 4), device="cuda")
@@ -108,11 +108,11 @@ def test_batch_request_vs_oracle():
                   float(np.linalg.norm(box[3:] - box[:3])))
     # the teaser holds sphere-traced fractals: out-of-tolerance pixels count
     # against the 0.1 % budget instead of failing one by one
-    assert_parity(rep, "batched config2 160x90", strict=False)
+    assert_parity(rep, "batched teaser 160x90", strict=False)
 
 
 def test_batch_budget_and_argument_errors():
-    w = scenes.config1()
+    w = scenes.small_analytic()
     sc = pr.Scene(w.scene)
     out = torch.empty((64, 64, 4), device="cuda")
     batch = pr.Batch(2, 1000)                     # fewer pixels than one 64x64 request
@@ -129,14 +129,14 @@ def test_batch_budget_and_argument_errors():
     assert ei.value.status == pr.PR_ERR_NOT_BUILT
 
 
-def test_config4_full_batch_sampled_vs_oracle():
-    """The config-4 batch at full size (64 requests, 83.6 M pixels, in the
+def test_full_request_batch_sampled_vs_oracle():
+    """The 64-request batch at full size (64 requests, 83.6 M pixels, in the
     launch configuration the benchmark uses: one graph launch): every request's
     image equals its pr_trace, and 64 seeded pixels of every request (4096 in
     all, parity on the sampled pixels as the oracle renders them one by one)
     agree with the oracle within the 0.1 % budget."""
     from parity import AGREE_MIN
-    ws = scenes.config4_requests(0, 64)
+    ws = scenes.batch_requests(0, 64)
     total = sum(w.params.width * w.params.height for w in ws)
     objs = [pr.Scene(w.scene) for w in ws]
     outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]

@@ -103,18 +103,18 @@ def _many_prim_scene(n_big=3000, n_small=700, seed=11):
     return b.build("many-prims")
 
 
-@pytest.mark.parametrize("which", ["config1", "config2", "config3_small", "config3_large", "many_prims", "sample"])
+@pytest.mark.parametrize("which", ["small_analytic", "teaser", "field_900", "field_30000", "many_prims", "sample"])
 def test_lbvh_levels_bit_exact(which):
     if which == "sample":
         sc = scenes.sample_scene(width=8, height=8, cells=24).scene          # 1152-triangle BLAS
-    elif which == "config1":
-        sc = scenes.config1().scene
-    elif which == "config2":
-        sc = scenes.config2(width=8, height=8).scene
-    elif which == "config3_small":
-        sc = scenes.config3(n_inst=900, width=8, height=8).scene
-    elif which == "config3_large":
-        sc = scenes.config3(n_inst=30000, width=8, height=8).scene
+    elif which == "small_analytic":
+        sc = scenes.small_analytic().scene
+    elif which == "teaser":
+        sc = scenes.teaser(width=8, height=8).scene
+    elif which == "field_900":
+        sc = scenes.field(n_inst=900, width=8, height=8).scene
+    elif which == "field_30000":
+        sc = scenes.field(n_inst=30000, width=8, height=8).scene
     else:
         sc = _many_prim_scene()
     scene = pr.Scene(sc)
@@ -126,15 +126,15 @@ def test_lbvh_levels_bit_exact(which):
 
 
 def test_lbvh_full_size_tlas_bit_exact():
-    sc = scenes.config3(width=8, height=8).scene          # 100 000 instances
+    sc = scenes.field(width=8, height=8).scene          # 100 000 instances
     scene = pr.Scene(sc)
     torch.cuda.synchronize()
-    _cmp_level(scene.read_bvh(pr.PR_NONE), oracle.lbvh_f32(oracle.instance_boxes_f32(sc)), "config3 TLAS")
+    _cmp_level(scene.read_bvh(pr.PR_NONE), oracle.lbvh_f32(oracle.instance_boxes_f32(sc)), "field 100000 TLAS")
     scene.close()
 
 
 def test_rebuild_is_deterministic():
-    sc = scenes.config3(n_inst=20000, width=8, height=8).scene
+    sc = scenes.field(n_inst=20000, width=8, height=8).scene
     scene = pr.Scene(sc)
     a = scene.read_bvh(pr.PR_NONE)
     scene.build_bvh()
@@ -147,25 +147,25 @@ def test_rebuild_is_deterministic():
 # ---------------------------------------------------------------------------
 # Images
 # ---------------------------------------------------------------------------
-def test_config1_full_frame():
-    check_full(scenes.config1(), "config1 64x64")
+def test_small_analytic_full_frame():
+    check_full(scenes.small_analytic(), "small analytic 64x64")
 
 
 @pytest.mark.parametrize("wh", [(67, 45), (1, 1), (3, 200), (200, 3), (17, 9)])
-def test_config1_ragged_sizes(wh):
+def test_small_analytic_ragged_sizes(wh):
     """Ragged and degenerate image sizes. A jittered eye is used: with the
     default eye every ray of the centre row of an odd-height image passes
     exactly through the far edge of the ground slab (y = 2 - 18/4 = -2.5 at
     z = 10), an ill-conditioned hit/miss on which FP32 and FP64 may differ."""
-    w = scenes.config1(width=wh[0], height=wh[1])
-    w.camera = scenes.config1_cameras(0, 1)[0]
-    check_full(w, f"config1 {wh}")
+    w = scenes.small_analytic(width=wh[0], height=wh[1])
+    w.camera = scenes.small_analytic_cameras(0, 1)[0]
+    check_full(w, f"small analytic {wh}")
 
 
-def test_config1_degenerate_edge_row_is_the_only_disagreement():
+def test_small_analytic_degenerate_edge_row_is_the_only_disagreement():
     """With the default eye the centre row of an odd-height image grazes the
     slab's far edge; all other pixels agree strictly."""
-    w = scenes.config1(width=67, height=45)
+    w = scenes.small_analytic(width=67, height=45)
     rgb, a, diag, rays, err, _ = render_gpu(w)
     ref = oracle.render(w)
     keep = np.ones((45, 67), bool)
@@ -186,26 +186,26 @@ def test_mirror_hit_is_shaded_without_shadow():
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_config1_other_seeds(seed):
-    check_full(scenes.config1(seed=seed, width=96, height=80), f"config1 seed {seed}")
+def test_small_analytic_other_seeds(seed):
+    check_full(scenes.small_analytic(seed=seed, width=96, height=80), f"small analytic seed {seed}")
 
 
-def test_config2_reduced_full_frame():
-    check_full(scenes.config2(width=320, height=180), "config2 320x180")
+def test_teaser_reduced_full_frame():
+    check_full(scenes.teaser(width=320, height=180), "teaser 320x180")
 
 
-def test_config3_reduced_full_frame():
-    check_full(scenes.config3(n_inst=2000, width=192, height=108), "config3 2000 inst 192x108")
+def test_field_reduced_full_frame():
+    check_full(scenes.field(n_inst=2000, width=192, height=108), "field 2000 inst 192x108")
 
 
-def test_config3_mid_full_frame():
-    check_full(scenes.config3(n_inst=20000, width=160, height=90), "config3 20000 inst 160x90")
+def test_field_mid_full_frame():
+    check_full(scenes.field(n_inst=20000, width=160, height=90), "field 20000 inst 160x90")
 
 
-@pytest.mark.parametrize("cfg", ["config2", "config3"])
+@pytest.mark.parametrize("cfg", ["teaser_1080p", "field_100k_2160p"])
 def test_full_size_sampled_pixels(cfg):
     """Full configuration sizes, the benchmark's trace call; oracle on a pixel sample."""
-    w = scenes.config2() if cfg == "config2" else scenes.config3()
+    w = scenes.teaser() if cfg == "teaser_1080p" else scenes.field()
     scene = pr.Scene(w.scene)
     plain = scene.trace(w.camera, w.params)           # exactly what bench.py times
     out, aov = scene.trace(w.camera, w.params, want_aov=True)
@@ -214,7 +214,7 @@ def test_full_size_sampled_pixels(cfg):
     assert scene.error_word() == 0
     box = scene.bounds()
     diag = float(np.linalg.norm(box[3:] - box[:3]))
-    pix = scenes.sample_pixels(w.params.width, w.params.height, 3000 if cfg == "config2" else 1500, seed=5)
+    pix = scenes.sample_pixels(w.params.width, w.params.height, 3000 if cfg == "teaser_1080p" else 1500, seed=5)
     a = pr.aov_to_numpy(aov).reshape(-1)[pix]
     rgb = out[..., :3].reshape(-1, 3).cpu().numpy()[pix]
     ref = oracle.render(w, pixels=pix)
@@ -224,8 +224,8 @@ def test_full_size_sampled_pixels(cfg):
 
 
 def test_trace_frames_equals_single_frames():
-    w = scenes.config1()
-    cams = scenes.config1_cameras(0, 5)
+    w = scenes.small_analytic()
+    cams = scenes.small_analytic_cameras(0, 5)
     scene = pr.Scene(w.scene)
     batch = scene.trace_frames(cams, w.params)
     for f, c in enumerate(cams):
@@ -238,7 +238,7 @@ def test_repeated_launches_on_two_streams():
     """Many launches of one scene in a row, of two sizes and on two streams,
     all give the image of the first launch of their size (a launch keeps no
     state in the scene)."""
-    w = scenes.config1()
+    w = scenes.small_analytic()
     scene = pr.Scene(w.scene)
     small = dataclasses.replace(w.params, width=37, height=23)
     ref = scene.trace(w.camera, w.params).clone()
@@ -257,12 +257,12 @@ def test_repeated_launches_on_two_streams():
 
 
 def test_4096_frame_launch_sampled_vs_oracle():
-    """The config-1 throughput launch as the benchmark times it (4096 jittered
+    """The 4096-frame throughput launch as the benchmark times it (4096 jittered
     64x64 frames in one pr_trace_frames call): 32 seeded frames x 64 seeded
     pixels agree with the oracle (strict: an analytic scene), and those frames
     equal single-frame renders bit for bit."""
-    w = scenes.config1()
-    cams = scenes.config1_cameras(0, 4096)
+    w = scenes.small_analytic()
+    cams = scenes.small_analytic_cameras(0, 4096)
     scene = pr.Scene(w.scene)
     out, aov = scene.trace_frames(pr.CameraArray(cams), w.params, want_aov=True)
     torch.cuda.synchronize()
@@ -284,8 +284,8 @@ def test_4096_frame_launch_sampled_vs_oracle():
 
 
 def test_jittered_frames_vs_oracle():
-    w = scenes.config1()
-    cams = scenes.config1_cameras(0, 4)
+    w = scenes.small_analytic()
+    cams = scenes.small_analytic_cameras(0, 4)
     scene = pr.Scene(w.scene)
     out, aov = scene.trace_frames(cams, w.params, want_aov=True)
     torch.cuda.synchronize()
@@ -300,7 +300,7 @@ def test_jittered_frames_vs_oracle():
 
 
 def test_sbt_index_outside_table_sets_error_word():
-    w = scenes.config1()
+    w = scenes.small_analytic()
     w.scene.inst_sbt_offset[:] = 7
     rgb, a, diag, rays, err, _ = render_gpu(w)
     ref = oracle.render(w)
@@ -363,15 +363,15 @@ def test_julia_cut_scene(plane):
 def test_animation_by_sphere_tracing_step_cap(steps):
     """Fig. 6 animates the Mandelbulb by the number of ray-marching steps: a
     per-frame parameter (max_steps) of every trace call."""
-    w = scenes.config2(width=192, height=108)
+    w = scenes.teaser(width=192, height=108)
     w.params.max_steps = steps
-    check_full(w, f"config2 max_steps {steps}")
+    check_full(w, f"teaser max_steps {steps}")
 
 
 def test_animation_by_iteration_count_via_upload():
     """Changing the fractal iteration count between frames: re-upload the
     description (same counts, no allocation), rebuild, trace."""
-    w = scenes.config2(width=160, height=90)
+    w = scenes.teaser(width=160, height=90)
     bulb = [k for k in range(len(w.scene.sbt)) if w.scene.sbt[k, 2] == scenes.IS_MANDELBULB]
     assert bulb
     scene = pr.Scene(w.scene)
@@ -396,7 +396,7 @@ def test_animation_by_iteration_count_via_upload():
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n_inst", [64, 65, 100, 700, 30000])
 def test_four_wide_tlas_gives_the_same_image(n_inst):
-    w = scenes.config3(n_inst=n_inst, width=160, height=90)
+    w = scenes.field(n_inst=n_inst, width=160, height=90)
     scene = pr.Scene(w.scene)
     a = scene.trace(w.camera, w.params)
     b = scene.trace(w.camera, w.params, binary_tlas=True)
@@ -414,7 +414,7 @@ def test_four_wide_tlas_gives_the_same_image(n_inst):
 
 
 def test_four_wide_tlas_full_size_sampled():
-    w = scenes.config3()
+    w = scenes.field()
     scene = pr.Scene(w.scene)
     a = scene.trace(w.camera, w.params)
     b = scene.trace(w.camera, w.params, binary_tlas=True)

@@ -21,8 +21,8 @@ import paper_2012_10357_b300 as pr  # noqa: E402
 
 
 def _requests():
-    base = [(1, scenes.config2(seed=1, width=240, height=135)), (2, scenes.config3(seed=2, n_inst=4000, width=200, height=150)),
-            (3, scenes.config1(seed=3, width=64, height=64)), (4, scenes.config2(seed=4, width=97, height=301))]
+    base = [(1, scenes.teaser(seed=1, width=240, height=135)), (2, scenes.field(seed=2, n_inst=4000, width=200, height=150)),
+            (3, scenes.small_analytic(seed=3, width=64, height=64)), (4, scenes.teaser(seed=4, width=97, height=301))]
     rng = np.random.default_rng(0)
     reqs = []
     for k in range(12):
@@ -46,7 +46,7 @@ def _alone(reqs):
 
 
 def test_row_range_batches_reassemble_the_image():
-    w = scenes.config2(width=150, height=77)
+    w = scenes.teaser(width=150, height=77)
     sc = pr.Scene(w.scene)
     ref = sc.trace(w.camera, w.params)
     out = torch.full((77, 150, 4), -1.0, device="cuda")
@@ -107,7 +107,7 @@ def test_rays_counted_like_plain_launches():
 
 
 def test_admission_refuses_scene_over_budget():
-    w = scenes.config3(seed=5, n_inst=20000, width=32, height=32)
+    w = scenes.field(seed=5, n_inst=20000, width=32, height=32)
     probe = pr.Scene(w.scene)
     need = probe.device_bytes()
     probe.close()
@@ -123,15 +123,15 @@ def test_admission_refuses_scene_over_budget():
 
 def test_submit_validation():
     srv = pr.Server(max_active=2, mem_budget_bytes=4 << 30, max_batch_pixels=4096)
-    w = scenes.config1()
+    w = scenes.small_analytic()
     out = torch.empty((64, 64, 4), device="cuda")
     with pytest.raises(pr.PrError):
         srv.submit(77, None, w.camera, w.params, out)          # key not resident, no description
-    bad = scenes.config1()
+    bad = scenes.small_analytic()
     bad.scene.aabbs[0, 0] = 99.0
     with pytest.raises(pr.PrError):
         srv.submit(78, bad.scene, w.camera, w.params, out)     # invalid description
-    wide = scenes.config1(width=5000, height=2)
+    wide = scenes.small_analytic(width=5000, height=2)
     with pytest.raises(pr.PrError):
         srv.submit(79, wide.scene, wide.camera, wide.params, torch.empty((2, 5000, 4), device="cuda"))
     srv.close()

@@ -759,7 +759,7 @@ def test_lbvh_single_leaf(O):
 
 
 def test_instance_boxes_f32_close_to_fp64_corners(O):
-    w = scenes.config3(seed=3, n_inst=500, width=8, height=8)
+    w = scenes.field(seed=3, n_inst=500, width=8, height=8)
     b32 = O.instance_boxes_f32(w.scene).astype(np.float64)
     s = w.scene
     for k in range(len(s.inst_blas)):

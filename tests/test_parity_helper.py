@@ -22,7 +22,7 @@ def _as_aov(ref):
 
 
 def test_compare_identity_and_planted_differences(oracle_lib):
-    w = scenes.config2(width=96, height=54)
+    w = scenes.teaser(width=96, height=54)
     ref = oracle_lib.render(w)
     a = _as_aov(ref)
     rgb = ref["rgb"].astype(np.float32)

@@ -58,12 +58,12 @@ def test_single_rank_is_identity():
 def test_reference_arm_prints_on_rank_zero_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3", "--workload", "config1"], env=env, capture_output=True, text=True,
+                          "--warmup", "3", "--workload", "analytic_64x64"], env=env, capture_output=True, text=True,
                          timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == ""
     env["RANK"] = "0"
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3", "--workload", "config1"], env=env, capture_output=True, text=True,
+                          "--warmup", "3", "--workload", "analytic_64x64"], env=env, capture_output=True, text=True,
                          timeout=300)
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0

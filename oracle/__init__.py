@@ -1,8 +1,8 @@
 """CPU FP64 oracle — TEST INFRASTRUCTURE ONLY.
 
 Python marshalling for ``liboracle.so`` (built from ``oracle.cpp`` with g++).
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package. It never imports the CUDA package and
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg and reference arm may import this package. It never imports the CUDA package and
 the CUDA package never imports it.
 """
 from __future__ import annotations

@@ -75,7 +75,7 @@ typedef enum {
 #define PR_MISS_SHADOW 1u
 /* Ray-type flags (what DXR passes as TraceRay flags) */
 #define PR_RAY_TERMINATE_ON_FIRST_HIT 1u
-#define PR_RAY_SKIP_CLOSEST_HIT 2u
+#define PR_RAY_SKIP_CLOSEST_HIT 2u   /* accepted as DXR's flag; closest-hit shaders run for radiance rays only */
 /* Trace flags */
 #define PR_TRACE_WRITE_AOV 1u
 #define PR_TRACE_TLAS_BVH2 2u   /* traverse the binary TLAS instead of its 4-wide collapse */

@@ -53,7 +53,8 @@ def workload_config(name: str, w) -> dict:
          "config": name, "width": w.params.width, "height": w.params.height,
          "instances": int(len(w.scene.inst_blas)), "max_depth": w.params.max_depth,
          "rays_per_pixel_max": 1 + 1 + (1 if w.params.max_depth >= 2 else 0),
-         "step": "device LBVH build + one frame", "l2": "flushed between timed steps (256 MB write)",
+         "step": "device LBVH build + one frame", "output": "rgb float32 image, 12 B/pixel",
+         "l2": "flushed between timed steps (256 MB write)",
          "parallelism": "replicas"}
     return d
 
@@ -435,7 +436,8 @@ def run_ours(args):
     H, W = w.params.height, w.params.width
     with torch.cuda.stream(stream):
         scene = pr.Scene(w.scene, stream=stream)
-        out = torch.empty(((len(frames),) if frames else ()) + (H, W, 4), dtype=torch.float32, device="cuda")
+        # the image as r, g, b floats per pixel (PR_TRACE_OUTPUT_RGB: the alpha channel, always 1, is not stored)
+        out = torch.empty(((len(frames),) if frames else ()) + (H, W, 3), dtype=torch.float32, device="cuda")
         counter = torch.zeros(1, dtype=torch.int64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 

@@ -79,6 +79,8 @@ typedef enum {
 /* Trace flags */
 #define PR_TRACE_WRITE_AOV 1u
 #define PR_TRACE_TLAS_BVH2 2u   /* traverse the binary TLAS instead of its 4-wide collapse */
+#define PR_TRACE_OUTPUT_RGB 4u  /* the image holds 3 floats per pixel (r, g, b; 12 bytes) instead of
+                                   4 (r, g, b, alpha = 1); the values are the same */
 /* Geometry kinds */
 #define PR_GEOM_AABBS 0u
 #define PR_GEOM_TRIANGLES 1u
@@ -204,7 +206,7 @@ pr_status pr_scene_upload(pr_scene* scene, const pr_scene_desc* desc, void* stre
 pr_status pr_build_bvh(pr_scene* scene, void* stream);
 
 /* Render one frame into out_rgba (device, caller-owned, height*width float4,
- * row-major, alpha = 1). out_aov (device, height*width pr_aov) is written when
+ * row-major, alpha = 1; height*width*3 floats with PR_TRACE_OUTPUT_RGB). out_aov (device, height*width pr_aov) is written when
  * params->flags has PR_TRACE_WRITE_AOV, else may be NULL. ray_counter (device
  * uint64, optional) is incremented by the number of rays cast. Asynchronous. */
 pr_status pr_trace(pr_scene* scene, const pr_camera* camera, const pr_trace_params* params, float* out_rgba,

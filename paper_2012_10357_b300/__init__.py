@@ -29,6 +29,7 @@ PR_ERR_SBT_INDEX, PR_ERR_STACK_OVERFLOW, PR_ERR_TIMEOUT, PR_ERR_NOT_BUILT, PR_ER
 PR_NONE = 0xFFFFFFFF
 PR_TRACE_WRITE_AOV = 1
 PR_TRACE_TLAS_BVH2 = 2
+PR_TRACE_OUTPUT_RGB = 4
 ERR_WORD_SBT = 1 << PR_ERR_SBT_INDEX
 ERR_WORD_STACK = 1 << PR_ERR_STACK_OVERFLOW
 PR_IS_COUNT = 10
@@ -200,6 +201,14 @@ def trace_params(tp, aov: bool = False, extra_flags: int = 0) -> _TraceParams:
     return p
 
 
+def _check_image(out, lead: tuple, rgb: bool):
+    """The output tensor: contiguous float32 on the GPU, lead dims + 3 or 4 channels."""
+    import torch
+    want = tuple(lead) + (3 if rgb else 4,)
+    if (tuple(out.shape) != want or out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous()):
+        raise ValueError(f"output image must be a contiguous float32 CUDA tensor of shape {want}")
+
+
 def _stream_handle(stream) -> Optional[int]:
     import torch
     if stream is None:
@@ -246,33 +255,40 @@ class Scene:
         _check(_lib.pr_build_bvh(self._h, _stream_handle(stream)), "pr_build_bvh")
 
     def trace(self, camera, params, out=None, aov=None, ray_counter=None, stream=None, want_aov: bool = False,
-              binary_tlas: bool = False):
-        """Render one frame. Returns the float32 [H, W, 4] device tensor (and the
-        uint8 [H, W, 48] AOV tensor when want_aov or aov is given). binary_tlas
-        traverses the binary TLAS instead of its 4-wide collapse."""
+              binary_tlas: bool = False, rgb: bool = False):
+        """Render one frame. Returns the float32 [H, W, 4] device tensor ([H, W, 3]
+        with rgb, or when out has 3 channels) and the uint8 [H, W, 48] AOV tensor
+        when want_aov or aov is given. binary_tlas traverses the binary TLAS
+        instead of its 4-wide collapse."""
         import torch
         W, H = params.width, params.height
+        rgb = rgb or (out is not None and out.shape[-1] == 3)
         if out is None:
-            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+            out = torch.empty((H, W, 3 if rgb else 4), dtype=torch.float32, device="cuda")
+        _check_image(out, (H, W), rgb)
         if want_aov and aov is None:
             aov = torch.empty((H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         cam = _camera(camera)
-        tp = trace_params(params, aov is not None, PR_TRACE_TLAS_BVH2 if binary_tlas else 0)
+        tp = trace_params(params, aov is not None,
+                          (PR_TRACE_TLAS_BVH2 if binary_tlas else 0) | (PR_TRACE_OUTPUT_RGB if rgb else 0))
         _check(_lib.pr_trace(self._h, ctypes.byref(cam), ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
                              _stream_handle(stream)), "pr_trace")
         return (out, aov) if aov is not None else out
 
     def trace_frames(self, cameras: Sequence, params, out=None, aov=None, ray_counter=None, stream=None,
-                     want_aov: bool = False, binary_tlas: bool = False):
+                     want_aov: bool = False, binary_tlas: bool = False, rgb: bool = False):
         import torch
         n = len(cameras)
         W, H = params.width, params.height
+        rgb = rgb or (out is not None and out.shape[-1] == 3)
         if out is None:
-            out = torch.empty((n, H, W, 4), dtype=torch.float32, device="cuda")
+            out = torch.empty((n, H, W, 3 if rgb else 4), dtype=torch.float32, device="cuda")
+        _check_image(out, (n, H, W), rgb)
         if want_aov and aov is None:
             aov = torch.empty((n, H, W, AOV_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         cams = cameras.array if isinstance(cameras, CameraArray) else CameraArray(cameras).array
-        tp = trace_params(params, aov is not None, PR_TRACE_TLAS_BVH2 if binary_tlas else 0)
+        tp = trace_params(params, aov is not None,
+                          (PR_TRACE_TLAS_BVH2 if binary_tlas else 0) | (PR_TRACE_OUTPUT_RGB if rgb else 0))
         _check(_lib.pr_trace_frames(self._h, cams, n, ctypes.byref(tp), _dptr(out), _dptr(aov), _dptr(ray_counter),
                                     _stream_handle(stream)), "pr_trace_frames")
         return (out, aov) if aov is not None else out
@@ -286,6 +302,7 @@ class Scene:
         ca = cameras if isinstance(cameras, CameraArray) else CameraArray(cameras)
         if out is None:
             out = torch.empty((len(ca), params.height, params.width, 4), dtype=torch.float32, device="cuda")
+        _check_image(out, (len(ca), params.height, params.width), False)
         work = torch.zeros(len(WORK_FIELDS), dtype=torch.int64, device="cuda")
         arr = ca.array
         cams = ca
@@ -402,7 +419,9 @@ class Batch:
             sc, cam, tp, out = it[:4]
             arr[k].scene = sc._h.value
             arr[k].camera = _camera(cam)
-            arr[k].params = trace_params(tp, False)
+            rgb = out.shape[-1] == 3
+            _check_image(out, (tp.height, tp.width), rgb)
+            arr[k].params = trace_params(tp, False, PR_TRACE_OUTPUT_RGB if rgb else 0)
             arr[k].out_rgba = out.data_ptr()
             if len(it) > 4:
                 arr[k].row_begin, arr[k].row_count = int(it[4]), int(it[5])
@@ -492,7 +511,9 @@ class Server:
         ref = _DescRef(desc) if desc is not None else None
         r.desc = ctypes.addressof(ref.struct) if ref is not None else None
         r.camera = _camera(camera)
-        r.params = trace_params(params, False)
+        rgb = out.shape[-1] == 3
+        _check_image(out, (params.height, params.width), rgb)
+        r.params = trace_params(params, False, PR_TRACE_OUTPUT_RGB if rgb else 0)
         r.out_rgba = out.data_ptr()
         t = ctypes.c_uint64()
         _check(_lib.pr_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "pr_server_submit")

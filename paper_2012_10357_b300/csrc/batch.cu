@@ -93,6 +93,8 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
     d.tile_begin = tiles;
     d.tiles_x = (p.width + b->tuning.tile_w - 1) / b->tuning.tile_w;
     d.out = reinterpret_cast<float4*>(q.out_rgba);
+    d.out_rgb = (p.flags & PR_TRACE_OUTPUT_RGB) ? 1u : 0u;
+    d.pad_ = 0u;
     d.pixel_begin = px;
     uint64_t t = (uint64_t)d.tiles_x * ((rows + b->tuning.tile_h - 1) / b->tuning.tile_h);
     if (tiles + t > 0xFFFFFFFFull) return bfail(PR_ERR_INVALID_ARG, "too many tiles");

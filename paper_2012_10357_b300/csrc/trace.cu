@@ -141,7 +141,14 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
         }
       }
     }
-    P.out[pix] = make_float4(color.x, color.y, color.z, 1.f);
+    if (P.flags & PR_TRACE_OUTPUT_RGB) {
+      float* o = reinterpret_cast<float*>(P.out) + 3 * pix;
+      o[0] = color.x;
+      o[1] = color.y;
+      o[2] = color.z;
+    } else {
+      P.out[pix] = make_float4(color.x, color.y, color.z, 1.f);
+    }
     if (av) {
       if (!(flags & 16u)) {
         av->refl_t = -1.f;

@@ -236,7 +236,15 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
     }
     const uint64_t local = px - R.pixel_begin;
     const uint64_t row = R.row_begin + local / R.width, col = local % R.width;
-    R.out[row * R.width + col] = make_float4(color.x, color.y, color.z, 1.f);
+    const uint64_t o = row * R.width + col;
+    if (R.out_rgb) {
+      float* f = reinterpret_cast<float*>(R.out) + 3 * o;
+      f[0] = color.x;
+      f[1] = color.y;
+      f[2] = color.z;
+    } else {
+      R.out[o] = make_float4(color.x, color.y, color.z, 1.f);
+    }
   }
 }
 

@@ -17,8 +17,9 @@ struct ReqDev {
   uint32_t width, height, max_depth, max_steps;
   uint32_t row_begin, rows;          // rendered rows [row_begin, row_begin + rows) of the image
   uint32_t tile_begin, tiles_x;
-  float4* out;
+  float4* out;                       // float4 per pixel, or 3 floats with out_rgb
   uint64_t pixel_begin;
+  uint32_t out_rgb, pad_;
 };
 
 // Counters and totals of the current batch (device memory).

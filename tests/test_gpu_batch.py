@@ -161,3 +161,22 @@ def test_full_request_batch_sampled_vs_oracle():
         o.close()
     assert n == 64 * len(ws)
     assert agree / n >= AGREE_MIN and ok / n >= AGREE_MIN, (n, agree, ok)
+
+
+def test_batch_rgb_outputs_equal_plain():
+    """Requests whose output image has 3 channels get PR_TRACE_OUTPUT_RGB: the
+    batch writes r, g, b per pixel, equal to the plain RGBA image's channels."""
+    ws = _mixed_workloads()[:6]
+    objs = [pr.Scene(w.scene) for w in ws]
+    outs = [torch.empty((w.params.height, w.params.width, 3 if k % 2 else 4), device="cuda") for k, w in enumerate(ws)]
+    total = sum(w.params.width * w.params.height for w in ws)
+    batch = pr.Batch(len(ws), total)
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], graph=True)
+    torch.cuda.synchronize()
+    for o, w, out in zip(objs, ws, outs):
+        ref = o.trace(w.camera, w.params)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref[..., :out.shape[-1]].contiguous())
+    batch.close()
+    for o in objs:
+        o.close()

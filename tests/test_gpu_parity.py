@@ -283,6 +283,25 @@ def test_4096_frame_launch_sampled_vs_oracle():
     assert agree / n >= 0.999, (n, agree)
 
 
+@pytest.mark.parametrize("which", ["teaser", "field"])
+def test_rgb_output_equals_the_rgba_channels(which):
+    """PR_TRACE_OUTPUT_RGB writes 3 floats per pixel: the same values as the
+    first three channels of the RGBA image (single frames and frame batches)."""
+    w = scenes.teaser(width=203, height=97) if which == "teaser" else scenes.field(n_inst=3000, width=203, height=97)
+    scene = pr.Scene(w.scene)
+    rgba = scene.trace(w.camera, w.params)
+    rgb = scene.trace(w.camera, w.params, rgb=True)
+    cams = [w.camera, w.camera]
+    fr = scene.trace_frames(cams, w.params, rgb=True)
+    torch.cuda.synchronize()
+    assert rgb.shape == (97, 203, 3)
+    assert torch.equal(rgb, rgba[..., :3].contiguous())
+    assert torch.equal(fr[1], rgb)
+    with pytest.raises(ValueError):
+        scene.trace(w.camera, w.params, out=torch.empty((97, 203, 2), device="cuda"))
+    scene.close()
+
+
 def test_jittered_frames_vs_oracle():
     w = scenes.small_analytic()
     cams = scenes.small_analytic_cameras(0, 4)

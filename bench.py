@@ -161,13 +161,10 @@ def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tupl
 TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/csrc/tracer.cuh",
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
-_TRAFFIC_4190DF93 = {"teaser_1080p": 126464 + 824576,
-                     "field_100k_2160p": 6424064 + 85360640,
-                     "analytic_64x64_x4096": 251648 + 220171008}
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "4190df935e3c37975707172784dc0dafd8feb151": _TRAFFIC_4190DF93,
-    # a header comment changed since; the trace.cu cubin compiled from it is byte-identical
-    "7672014b057773ee734cb74068c086f9d0df7a97": _TRAFFIC_4190DF93,
+    "dcf7cc8c625254552d134e3dc21e4aaba1ff1a04": {"teaser_1080p": 132096 + 264448,
+                                                 "field_100k_2160p": 6040576 + 51865344,
+                                                 "analytic_64x64_x4096": 249856 + 154887424},
 }
 
 

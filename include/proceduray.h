@@ -313,17 +313,23 @@ typedef struct {
   pr_scene* scene;          /* built scene */
   pr_camera camera;
   pr_trace_params params;   /* PR_TRACE_WRITE_AOV is not available in batches */
-  float* out_rgba;          /* device, height*width float4 (the whole image) */
+  float* out_rgba;          /* device, the whole image: height*width float4, or height*width*3
+                               floats with PR_TRACE_OUTPUT_RGB in params.flags */
   uint32_t row_begin;       /* render rows [row_begin, row_begin + row_count) only; */
   uint32_t row_count;       /* row_count 0 = the whole image (row_begin must be 0) */
 } pr_request;
 
 /* Launch shape of the batched path: persistent CTAs per SM of the ray
  * stages, the primary stage's 128-pixel tile (16x8, 32x4 or 8x16) and the
- * rays a warp pops from a queue at a time (multiple of 32). */
+ * rays a warp pops from a queue at a time (multiple of 32). megakernel = 1
+ * replaces the four wavefront stages by one persistent kernel whose CTAs claim
+ * 16x8 tiles of all requests and run each pixel's whole pipeline (the
+ * single-request kernel's per-pixel code; tile 16x8 required, queue_chunk
+ * unused); the images are the same either way. */
 typedef struct {
   uint32_t struct_size; /* sizeof(pr_batch_tuning) */
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
+  uint32_t megakernel;
 } pr_batch_tuning;
 
 typedef struct pr_batch pr_batch;

@@ -400,7 +400,8 @@ class _Request(ctypes.Structure):
 
 
 class _BatchTuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint32) for n in ("struct_size", "ctas_per_sm", "tile_w", "tile_h", "queue_chunk")]
+    _fields_ = [(n, ctypes.c_uint32) for n in ("struct_size", "ctas_per_sm", "tile_w", "tile_h", "queue_chunk",
+                                               "megakernel")]
 
 
 class Batch:
@@ -441,16 +442,17 @@ class Batch:
         _check(_lib.pr_batch_autotune(self._h, len(items), arr, _stream_handle(stream), ctypes.byref(best),
                                       ctypes.byref(ms)), "pr_batch_autotune")
         return dict(ctas_per_sm=best.ctas_per_sm, tile_w=best.tile_w, tile_h=best.tile_h,
-                    queue_chunk=best.queue_chunk), float(ms.value)
+                    queue_chunk=best.queue_chunk, megakernel=best.megakernel), float(ms.value)
 
-    def set_tuning(self, ctas_per_sm, tile_w, tile_h, queue_chunk):
-        t = _BatchTuning(ctypes.sizeof(_BatchTuning), ctas_per_sm, tile_w, tile_h, queue_chunk)
+    def set_tuning(self, ctas_per_sm, tile_w, tile_h, queue_chunk, megakernel=0):
+        t = _BatchTuning(ctypes.sizeof(_BatchTuning), ctas_per_sm, tile_w, tile_h, queue_chunk, megakernel)
         _check(_lib.pr_batch_set_tuning(self._h, ctypes.byref(t)), "pr_batch_set_tuning")
 
     def tuning(self) -> dict:
         t = _BatchTuning()
         _check(_lib.pr_batch_get_tuning(self._h, ctypes.byref(t)), "pr_batch_get_tuning")
-        return dict(ctas_per_sm=t.ctas_per_sm, tile_w=t.tile_w, tile_h=t.tile_h, queue_chunk=t.queue_chunk)
+        return dict(ctas_per_sm=t.ctas_per_sm, tile_w=t.tile_w, tile_h=t.tile_h, queue_chunk=t.queue_chunk,
+                    megakernel=t.megakernel)
 
     def device_bytes(self) -> int:
         return int(_lib.pr_batch_device_bytes(self._h))
@@ -500,7 +502,7 @@ class Server:
         cfg.mem_budget_bytes, cfg.max_batch_pixels = mem_budget_bytes, max_batch_pixels
         if tuning:
             cfg.tuning = _BatchTuning(ctypes.sizeof(_BatchTuning), tuning["ctas_per_sm"], tuning["tile_w"],
-                                      tuning["tile_h"], tuning["queue_chunk"])
+                                      tuning["tile_h"], tuning["queue_chunk"], tuning.get("megakernel", 0))
         self._h = ctypes.c_void_p()
         _check(_lib.pr_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "pr_server_create")
 

@@ -25,7 +25,7 @@ struct pr_batch {
   BatchView V{};
   char* staging = nullptr;            // pinned: BatchHdr followed by ReqDev[max_req]
   cudaEvent_t staged = nullptr;       // the last staging copy has been consumed
-  BatchTuning tuning{8, 16, 8, 64};
+  BatchTuning tuning{8, 16, 8, 64, 0};
   int n_sm = 0;
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -49,6 +49,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool tuning_ok(const BatchTuning& t) {
   bool tile = (t.tile_w == 16 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 4) || (t.tile_w == 8 && t.tile_h == 16);
+  if (t.megakernel > 1 || (t.megakernel && !(t.tile_w == 16 && t.tile_h == 8))) return false;
   return tile && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 16 && t.queue_chunk >= 32 && t.queue_chunk <= 1024 &&
          t.queue_chunk % 32 == 0;
 }
@@ -191,7 +192,7 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
 
 pr_status pr_batch_set_tuning(pr_batch* b, const pr_batch_tuning* t) {
   if (!b || !t || t->struct_size != sizeof(pr_batch_tuning)) return bfail(PR_ERR_INVALID_ARG, "null batch/tuning or size");
-  BatchTuning bt{t->ctas_per_sm, t->tile_w, t->tile_h, t->queue_chunk};
+  BatchTuning bt{t->ctas_per_sm, t->tile_w, t->tile_h, t->queue_chunk, t->megakernel};
   if (!tuning_ok(bt))
     return bfail(PR_ERR_INVALID_ARG, "tuning: tiles 16x8, 32x4 or 8x16; 1..16 CTAs/SM; chunk multiple of 32 in 32..1024");
   b->tuning = bt;
@@ -205,6 +206,7 @@ pr_status pr_batch_get_tuning(const pr_batch* b, pr_batch_tuning* t) {
   t->tile_w = b->tuning.tile_w;
   t->tile_h = b->tuning.tile_h;
   t->queue_chunk = b->tuning.queue_chunk;
+  t->megakernel = b->tuning.megakernel;
   return PR_OK;
 }
 
@@ -247,26 +249,31 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
   BatchTuning keep = b->tuning, win = b->tuning;
   float win_ms = 1e30f;
   pr_status status = PR_OK;
+  // the wavefront shapes, then the megakernel at 4 and 8 CTAs per SM (16x8 tiles)
+  std::vector<BatchTuning> cands;
   for (uint32_t c : ctas)
     for (auto& tw : tiles)
-      for (uint32_t ch : chunks) {
-        b->tuning = BatchTuning{c, tw[0], tw[1], ch};
-        float ms_best = 1e30f;
-        for (int rep = 0; rep < 3 && status == PR_OK; ++rep) {
-          cudaEventRecord(e0, st);
-          status = pr_trace_batch(b, n, reqs, nullptr, st);
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0) ms_best = std::min(ms_best, ms);   // first run warms caches
-        }
-        if (status != PR_OK) break;
-        if (ms_best < win_ms) {
-          win_ms = ms_best;
-          win = b->tuning;
-        }
-      }
+      for (uint32_t ch : chunks) cands.push_back(BatchTuning{c, tw[0], tw[1], ch, 0u});
+  cands.push_back(BatchTuning{4, 16, 8, 32, 1u});
+  cands.push_back(BatchTuning{8, 16, 8, 32, 1u});
+  for (const BatchTuning& cand : cands) {
+    b->tuning = cand;
+    float ms_best = 1e30f;
+    for (int rep = 0; rep < 3 && status == PR_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      status = pr_trace_batch(b, n, reqs, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_best = std::min(ms_best, ms);   // first run warms caches
+    }
+    if (status != PR_OK) break;
+    if (ms_best < win_ms) {
+      win_ms = ms_best;
+      win = b->tuning;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->tuning = status == PR_OK ? win : keep;
@@ -276,6 +283,7 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
   best->tile_w = win.tile_w;
   best->tile_h = win.tile_h;
   best->queue_chunk = win.queue_chunk;
+  best->megakernel = win.megakernel;
   if (best_ms) *best_ms = win_ms;
   return PR_OK;
 }

@@ -479,6 +479,104 @@ __device__ __forceinline__ float3 miss_rgb(const SceneView& S, uint32_t r, float
   return __ldg(S.ray_types + r).x == PR_MISS_BACKGROUND ? background : f3(0.f, 0.f, 0.f);
 }
 
+// The per-pixel pipeline of a radiance sample (Section 2.2.3's ray generation
+// shader onwards): primary ray, closest-hit shading with its shadow ray, one
+// mirror bounce shaded unshadowed, miss shaders. Shared by the single-request
+// megakernel and the batched one, so both give the same bits. Writes the AOV
+// record when av is given; adds the rays cast to `rays`.
+struct PixelParams {
+  float3 light, background;
+  float light_intensity, ambient;
+  uint32_t max_depth, max_steps;
+};
+
+template <bool kStats>
+__device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
+                                               TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
+  Hit h;
+  rays += 1;
+  trace_typed<kStats>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
+  // AOV fields are stored as soon as they are known, so none of them stays
+  // live across the shadow and mirror traces
+  float3 color;
+  uint32_t flags = 0;
+  if (h.inst < 0) {
+    color = miss_rgb(S, 0, P.background);
+    if (av) {
+      av->t = -1.f;
+      av->inst = av->geom = av->prim = PR_NONE;
+      av->n[0] = av->n[1] = av->n[2] = 0.f;
+    }
+  } else {
+    flags |= 1u;
+    Surface sf = surface_at(S, h, eye, d, eps, wc);
+    if (av) {
+      av->t = h.t;
+      av->inst = (uint32_t)h.inst;
+      av->geom = sf.geom;
+      av->prim = sf.prim;
+      av->n[0] = sf.n.x; av->n[1] = sf.n.y; av->n[2] = sf.n.z;
+    }
+    if (sf.chs != PR_CHS_LAMBERT) {
+      color = f3(0.f, 0.f, 0.f);
+    } else {
+      const float3 pt = madd(eye, h.t, d);
+      const float delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
+      const float ndl = light_ndl(sf, P.light, pt);
+      float vis = 1.f;
+      if (ndl > 0.f) {
+        // shadow ray: offset origin, toward the light, ends at the light
+        float3 os = madd(pt, delta, sf.n);
+        float3 ls = P.light - os;
+        float dist = len3(ls);
+        Hit sh;
+        rays++;
+        flags |= 2u;
+        trace_typed<kStats>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
+        vis = sh.inst >= 0 ? 0.f : 1.f;
+        if (sh.inst < 0) flags |= 4u;
+      }
+      color = lambert_rgb(sf.albedo, P.ambient, P.light_intensity, ndl, vis);
+      if (P.max_depth >= 2 && sf.kr > 0.f) {
+        // one mirror bounce, its hit shaded without a shadow ray
+        float3 orr = madd(pt, delta, sf.n);
+        float3 dr = normalize3(d - sf.n * (2.f * dot3(d, sf.n)));
+        const float kr = sf.kr;
+        Hit rh;
+        rays++;
+        flags |= 8u;
+        trace_typed<kStats>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
+        float3 lr;
+        if (rh.inst >= 0) {
+          flags |= 16u;
+          Surface s2 = surface_at(S, rh, orr, dr, eps, wc);
+          if (av) {
+            av->refl_t = rh.t;
+            av->refl_inst = (uint32_t)rh.inst;
+            av->refl_geom = s2.geom;
+            av->refl_prim = s2.prim;
+          }
+          lr = s2.chs == PR_CHS_LAMBERT
+                   ? lambert_rgb(s2.albedo, P.ambient, P.light_intensity, light_ndl(s2, P.light, madd(orr, rh.t, dr)), 1.f)
+                   : f3(0.f, 0.f, 0.f);
+        } else {
+          lr = miss_rgb(S, 0, P.background);
+        }
+        color = mirror_mix(color, lr, kr);
+      }
+    }
+  }
+  if (av) {
+    if (!(flags & 16u)) {
+      av->refl_t = -1.f;
+      av->refl_inst = av->refl_geom = av->refl_prim = PR_NONE;
+    }
+    av->flags = flags;
+  }
+  return color;
+}
+
+
 #ifndef PR_SMEM_STACK
 #define PR_SMEM_STACK 1
 #endif

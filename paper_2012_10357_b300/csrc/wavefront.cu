@@ -248,12 +248,75 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
   }
 }
 
+// Batched megakernel: persistent CTAs claim 16x8 tiles of all requests from
+// one counter; every pixel runs the single-request kernel's pipeline
+// (render_pixel: primary, shadow and mirror rays, shading) and writes its
+// request's image directly, with no per-pixel state or ray queues in memory.
+template <int kWarpW>
+__global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
+  static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
+  __shared__ ReqDev sreq;
+  __shared__ CameraBasis scam;
+  __shared__ uint32_t s_tile, s_req;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarpsX = 16 / kWarpW;
+  const int ox = (warp % kWarpsX) * kWarpW + (lane % kWarpW), oy = (warp / kWarpsX) * (32 / kWarpW) + lane / kWarpW;
+  PR_DECLARE_STACK(128);
+  uint32_t last_req = kFull, rays = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(&B.hdr->tile_ctr, 1u);
+      s_tile = t;
+      s_req = t < B.hdr->total_tiles ? find_request(B.reqs, B.hdr->n_req, t) : 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile, r = s_req;
+    if (tile >= B.hdr->total_tiles) break;
+    if (r != last_req) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(B.reqs + r);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
+      for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
+      __syncthreads();
+      last_req = r;
+    }
+    const ReqDev& R = sreq;
+    const uint32_t lt = tile - R.tile_begin;
+    const int x = (int)(lt % R.tiles_x) * 16 + ox, y = (int)R.row_begin + (int)(lt / R.tiles_x) * 8 + oy;
+    if (x < (int)R.width && y < (int)(R.row_begin + R.rows)) {
+      const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
+      const float eps = scene_eps(R.S, R.eps_rel);
+      const float3 color =
+          render_pixel<false>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps, stack, nullptr, nullptr, rays);
+      const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
+      if (R.out_rgb) {
+        float* f = reinterpret_cast<float*>(R.out) + 3 * o;
+        f[0] = color.x;
+        f[1] = color.y;
+        f[2] = color.z;
+      } else {
+        R.out[o] = make_float4(color.x, color.y, color.z, 1.f);
+      }
+    }
+    __syncthreads();   // every thread is done with this tile's request record and counters
+  }
+  if (B.hdr->counter) {
+    const uint32_t total = __reduce_add_sync(kFull, rays);
+    if (lane == 0 && total) atomicAdd(B.hdr->counter, (unsigned long long)total);
+  }
+}
+
 }  // namespace
 
 int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, cudaStream_t s) {
   int launches = 0;
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr
   const uint32_t grid = (uint32_t)n_sm * T.ctas_per_sm;
+  if (T.megakernel) {
+    k_batch_mega<8><<<grid, 128, 0, s>>>(B);
+    return 1;
+  }
   if (T.tile_w == 32) k_wf_primary<32, 4><<<grid, 128, 0, s>>>(B);
   else if (T.tile_w == 8) k_wf_primary<8, 16><<<grid, 128, 0, s>>>(B);
   else k_wf_primary<16, 8><<<grid, 128, 0, s>>>(B);

@@ -46,6 +46,7 @@ struct BatchView {
 
 struct BatchTuning {
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
+  uint32_t megakernel;   // 1: one persistent kernel per batch (16x8 tiles), else the four stages
 };
 
 int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, cudaStream_t s);

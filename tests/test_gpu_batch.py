@@ -63,14 +63,17 @@ def test_batch_bit_identical_to_plain(graph):
     batch.close()
 
 
-@pytest.mark.parametrize("shape", [(2, 16, 8, 32), (8, 32, 4, 128), (16, 8, 16, 64), (1, 16, 8, 1024)])
+@pytest.mark.parametrize("shape", [(2, 16, 8, 32, 0), (8, 32, 4, 128, 0), (16, 8, 16, 64, 0), (1, 16, 8, 1024, 0),
+                                   (4, 16, 8, 32, 1), (1, 16, 8, 32, 1)])
 def test_batch_launch_shapes_do_not_change_results(shape):
+    """Wavefront stages or the batched megakernel, any launch shape: every
+    request equals its plain pr_trace image bit for bit."""
     ws = _mixed_workloads()[:5]
     objs = [pr.Scene(w.scene) for w in ws]
     plain, _ = _plain(objs, ws)
     batch = pr.Batch(8, sum(w.params.width * w.params.height for w in ws))
     batch.set_tuning(*shape)
-    assert batch.tuning() == dict(zip(("ctas_per_sm", "tile_w", "tile_h", "queue_chunk"), shape))
+    assert batch.tuning() == dict(zip(("ctas_per_sm", "tile_w", "tile_h", "queue_chunk", "megakernel"), shape))
     outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
     batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)])
     torch.cuda.synchronize()
@@ -177,6 +180,35 @@ def test_batch_rgb_outputs_equal_plain():
         ref = o.trace(w.camera, w.params)
         torch.cuda.synchronize()
         assert torch.equal(out, ref[..., :out.shape[-1]].contiguous())
+    batch.close()
+    for o in objs:
+        o.close()
+
+
+def test_batch_megakernel_needs_16x8_tiles():
+    batch = pr.Batch(2, 1024)
+    with pytest.raises(pr.PrError):
+        batch.set_tuning(4, 32, 4, 32, 1)
+    batch.close()
+
+
+def test_batched_megakernel_rays_and_graph():
+    """The batched megakernel counts the same rays as the plain launches and
+    runs the same through its CUDA graph; RGB and RGBA outputs both."""
+    ws = _mixed_workloads()
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, rays_plain = _plain(objs, ws)
+    batch = pr.Batch(len(ws), sum(w.params.width * w.params.height for w in ws))
+    batch.set_tuning(4, 16, 8, 32, 1)
+    for graph in (False, True):
+        outs = [torch.empty((w.params.height, w.params.width, 3 if k % 2 else 4), device="cuda")
+                for k, w in enumerate(ws)]
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], ray_counter=c, graph=graph)
+        torch.cuda.synchronize()
+        assert int(c.item()) == rays_plain
+        for a, b in zip(plain, outs):
+            assert torch.equal(a[..., :b.shape[-1]].contiguous(), b)
     batch.close()
     for o in objs:
         o.close()

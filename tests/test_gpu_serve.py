@@ -45,12 +45,14 @@ def _alone(reqs):
     return outs
 
 
-def test_row_range_batches_reassemble_the_image():
+@pytest.mark.parametrize("megakernel", [0, 1])
+def test_row_range_batches_reassemble_the_image(megakernel):
     w = scenes.teaser(width=150, height=77)
     sc = pr.Scene(w.scene)
     ref = sc.trace(w.camera, w.params)
     out = torch.full((77, 150, 4), -1.0, device="cuda")
     batch = pr.Batch(8, 150 * 77)
+    batch.set_tuning(4, 16, 8, 32, megakernel)
     batch.trace([(sc, w.camera, w.params, out, 0, 10), (sc, w.camera, w.params, out, 10, 31)])
     batch.trace([(sc, w.camera, w.params, out, 41, 36)])
     torch.cuda.synchronize()
@@ -59,12 +61,13 @@ def test_row_range_batches_reassemble_the_image():
         batch.trace([(sc, w.camera, w.params, out, 70, 10)])      # past the last row
 
 
-@pytest.mark.parametrize("mode,max_batch", [(pr.PR_SERVE_CONTINUOUS, 20000), (pr.PR_SERVE_CONTINUOUS, 1 << 22),
-                                            (pr.PR_SERVE_PLAIN, 1 << 22)])
-def test_served_equals_alone(mode, max_batch):
+@pytest.mark.parametrize("mode,max_batch,mega", [(pr.PR_SERVE_CONTINUOUS, 20000, 0), (pr.PR_SERVE_CONTINUOUS, 1 << 22, 0),
+                                                 (pr.PR_SERVE_PLAIN, 1 << 22, 0), (pr.PR_SERVE_CONTINUOUS, 20000, 1)])
+def test_served_equals_alone(mode, max_batch, mega):
     reqs = _requests()
     alone = _alone(reqs)
-    srv = pr.Server(mode=mode, max_active=5, mem_budget_bytes=8 << 30, max_batch_pixels=max_batch)
+    tuning = dict(ctas_per_sm=4, tile_w=16, tile_h=8, queue_chunk=32, megakernel=mega)
+    srv = pr.Server(mode=mode, max_active=5, mem_budget_bytes=8 << 30, max_batch_pixels=max_batch, tuning=tuning)
     outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for _, w, _ in reqs]
     tickets = []
     for k, ((key, w, cam), out) in enumerate(zip(reqs, outs)):

@@ -324,8 +324,9 @@ typedef struct {
  * rays a warp pops from a queue at a time (multiple of 32). megakernel = 1
  * replaces the four wavefront stages by one persistent kernel whose CTAs claim
  * 16x8 tiles of all requests and run each pixel's whole pipeline (the
- * single-request kernel's per-pixel code; tile 16x8 required, queue_chunk
- * unused); the images are the same either way. */
+ * single-request kernel's per-pixel code); megakernel = 2 runs the same with
+ * one CTA per tile (ctas_per_sm unused). Both need tile 16x8 and ignore
+ * queue_chunk; the images are the same in every mode. */
 typedef struct {
   uint32_t struct_size; /* sizeof(pr_batch_tuning) */
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;

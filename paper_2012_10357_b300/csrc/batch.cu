@@ -30,6 +30,9 @@ struct pr_batch {
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   BatchTuning graph_tuning{};
+  uint32_t graph_tiles = 0;          // grid of the captured one-CTA-per-tile megakernel
+  uint32_t graph_launches = 0;
+  uint32_t staged_tiles = 0;         // tiles of the last staged batch
   uint32_t last_launches = 0;
 };
 
@@ -49,7 +52,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool tuning_ok(const BatchTuning& t) {
   bool tile = (t.tile_w == 16 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 4) || (t.tile_w == 8 && t.tile_h == 16);
-  if (t.megakernel > 1 || (t.megakernel && !(t.tile_w == 16 && t.tile_h == 8))) return false;
+  if (t.megakernel > 2 || (t.megakernel && !(t.tile_w == 16 && t.tile_h == 8))) return false;
   return tile && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 16 && t.queue_chunk >= 32 && t.queue_chunk <= 1024 &&
          t.queue_chunk % 32 == 0;
 }
@@ -105,6 +108,7 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   if (px > b->max_px) return bfail(PR_ERR_BUDGET, "batch pixels exceed the batch's max_pixels");
   H->n_req = n;
   H->total_tiles = tiles;
+  b->staged_tiles = tiles;
   H->total_pixels = px;
   H->tile_ctr = H->shadow_n = H->mirror_n = H->shadow_ctr = H->mirror_ctr = H->pad = 0;
   H->counter = reinterpret_cast<unsigned long long*>(counter);
@@ -123,7 +127,7 @@ pr_status capture(pr_batch* b) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bcuda(e, "begin capture");
-  launch_wavefront(b->V, b->tuning, b->n_sm, b->capture_stream);
+  b->graph_launches = (uint32_t)launch_wavefront(b->V, b->tuning, b->n_sm, b->graph_tiles, b->capture_stream);
   e = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess) return bcuda(e, "end capture");
   e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -215,7 +219,7 @@ pr_status pr_trace_batch(pr_batch* b, uint32_t n, const pr_request* reqs, uint64
   cudaStream_t st = (cudaStream_t)stream;
   pr_status s = stage(b, n, reqs, ray_counter, st);
   if (s != PR_OK) return s;
-  b->last_launches = (uint32_t)launch_wavefront(b->V, b->tuning, b->n_sm, st);
+  b->last_launches = (uint32_t)launch_wavefront(b->V, b->tuning, b->n_sm, b->staged_tiles, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bcuda(e, "wavefront launch");
   return PR_OK;
@@ -224,15 +228,23 @@ pr_status pr_trace_batch(pr_batch* b, uint32_t n, const pr_request* reqs, uint64
 pr_status pr_trace_batch_graph(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* ray_counter, void* stream) {
   if (!b) return bfail(PR_ERR_INVALID_ARG, "null batch");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!b->graph || memcmp(&b->graph_tuning, &b->tuning, sizeof(BatchTuning)) != 0) {
+  pr_status s = stage(b, n, reqs, ray_counter, st);
+  if (s != PR_OK) return s;
+  // the one-CTA-per-tile megakernel needs a grid of at least this batch's tiles: capture again
+  // (with room to grow) when it is larger than the captured one
+  const bool grow = b->tuning.megakernel == 2 && b->staged_tiles > b->graph_tiles;
+  if (grow) {
+    uint32_t g = 1024;
+    while (g < b->staged_tiles && g < 0x80000000u) g <<= 1;
+    b->graph_tiles = g;
+  }
+  if (!b->graph || grow || memcmp(&b->graph_tuning, &b->tuning, sizeof(BatchTuning)) != 0) {
     pr_status c = capture(b);
     if (c != PR_OK) return c;
   }
-  pr_status s = stage(b, n, reqs, ray_counter, st);
-  if (s != PR_OK) return s;
   cudaError_t e = cudaGraphLaunch(b->graph, st);
   if (e != cudaSuccess) return bcuda(e, "graph launch");
-  b->last_launches = 4;
+  b->last_launches = b->graph_launches;
   return PR_OK;
 }
 
@@ -256,6 +268,7 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
       for (uint32_t ch : chunks) cands.push_back(BatchTuning{c, tw[0], tw[1], ch, 0u});
   cands.push_back(BatchTuning{4, 16, 8, 32, 1u});
   cands.push_back(BatchTuning{8, 16, 8, 32, 1u});
+  cands.push_back(BatchTuning{4, 16, 8, 32, 2u});
   for (const BatchTuning& cand : cands) {
     b->tuning = cand;
     float ms_best = 1e30f;

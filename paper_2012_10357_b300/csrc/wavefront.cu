@@ -307,13 +307,64 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
   }
 }
 
+// The same with one CTA per 16x8 tile (no claiming loop: the hardware
+// schedules the tiles); CTAs past the batch's last tile return at once.
+template <int kWarpW>
+__global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
+  const uint32_t tile = blockIdx.x;
+  if (tile >= B.hdr->total_tiles) return;
+  __shared__ ReqDev sreq;
+  __shared__ CameraBasis scam;
+  __shared__ uint32_t s_req;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarpsX = 16 / kWarpW;
+  if (threadIdx.x == 0) s_req = find_request(B.reqs, B.hdr->n_req, tile);
+  __syncthreads();
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(B.reqs + s_req);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
+    for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
+  __syncthreads();
+  const ReqDev& R = sreq;
+  const uint32_t lt = tile - R.tile_begin;
+  const int x = (int)(lt % R.tiles_x) * 16 + (warp % kWarpsX) * kWarpW + (lane % kWarpW);
+  const int y = (int)R.row_begin + (int)(lt / R.tiles_x) * 8 + (warp / kWarpsX) * (32 / kWarpW) + lane / kWarpW;
+  uint32_t rays = 0;
+  if (x < (int)R.width && y < (int)(R.row_begin + R.rows)) {
+    PR_DECLARE_STACK(128);
+    const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
+    const float eps = scene_eps(R.S, R.eps_rel);
+    const float3 color = render_pixel<false>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps, stack, nullptr, nullptr, rays);
+    const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
+    if (R.out_rgb) {
+      float* f = reinterpret_cast<float*>(R.out) + 3 * o;
+      f[0] = color.x;
+      f[1] = color.y;
+      f[2] = color.z;
+    } else {
+      R.out[o] = make_float4(color.x, color.y, color.z, 1.f);
+    }
+  }
+  if (B.hdr->counter) {
+    const uint32_t total = __reduce_add_sync(kFull, rays);
+    if (lane == 0 && total) atomicAdd(B.hdr->counter, (unsigned long long)total);
+  }
+}
+
 }  // namespace
 
-int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, cudaStream_t s) {
+int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s) {
   int launches = 0;
+  if (T.megakernel == 2) {
+    if (grid_tiles) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
+    return grid_tiles ? 1 : 0;
+  }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr
   const uint32_t grid = (uint32_t)n_sm * T.ctas_per_sm;
-  if (T.megakernel) {
+  if (T.megakernel == 1) {
     k_batch_mega<8><<<grid, 128, 0, s>>>(B);
     return 1;
   }

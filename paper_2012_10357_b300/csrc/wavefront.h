@@ -46,9 +46,10 @@ struct BatchView {
 
 struct BatchTuning {
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
-  uint32_t megakernel;   // 1: one persistent kernel per batch (16x8 tiles), else the four stages
+  uint32_t megakernel;   // 1: one persistent megakernel (16x8 tiles), 2: one CTA per 16x8 tile, 0: four stages
 };
 
-int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, cudaStream_t s);
+// grid_tiles: CTAs of the one-CTA-per-tile megakernel (at least the batch's tiles); unused otherwise
+int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s);
 
 }  // namespace pr

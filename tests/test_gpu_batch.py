@@ -64,7 +64,7 @@ def test_batch_bit_identical_to_plain(graph):
 
 
 @pytest.mark.parametrize("shape", [(2, 16, 8, 32, 0), (8, 32, 4, 128, 0), (16, 8, 16, 64, 0), (1, 16, 8, 1024, 0),
-                                   (4, 16, 8, 32, 1), (1, 16, 8, 32, 1)])
+                                   (4, 16, 8, 32, 1), (1, 16, 8, 32, 1), (4, 16, 8, 32, 2)])
 def test_batch_launch_shapes_do_not_change_results(shape):
     """Wavefront stages or the batched megakernel, any launch shape: every
     request equals its plain pr_trace image bit for bit."""
@@ -192,14 +192,16 @@ def test_batch_megakernel_needs_16x8_tiles():
     batch.close()
 
 
-def test_batched_megakernel_rays_and_graph():
-    """The batched megakernel counts the same rays as the plain launches and
-    runs the same through its CUDA graph; RGB and RGBA outputs both."""
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batched_megakernel_rays_and_graph(mode):
+    """The batched megakernel (persistent, or one CTA per tile) counts the same
+    rays as the plain launches and runs the same through its CUDA graph; RGB
+    and RGBA outputs both."""
     ws = _mixed_workloads()
     objs = [pr.Scene(w.scene) for w in ws]
     plain, rays_plain = _plain(objs, ws)
     batch = pr.Batch(len(ws), sum(w.params.width * w.params.height for w in ws))
-    batch.set_tuning(4, 16, 8, 32, 1)
+    batch.set_tuning(4, 16, 8, 32, mode)
     for graph in (False, True):
         outs = [torch.empty((w.params.height, w.params.width, 3 if k % 2 else 4), device="cuda")
                 for k, w in enumerate(ws)]
@@ -212,3 +214,22 @@ def test_batched_megakernel_rays_and_graph():
     batch.close()
     for o in objs:
         o.close()
+
+
+def test_tile_megakernel_graph_grows_with_the_batch():
+    """One CTA per tile: the captured graph's grid grows (recapture) when a
+    later batch has more tiles, and a smaller batch reuses the larger grid."""
+    small = scenes.small_analytic(width=40, height=24)
+    big = scenes.teaser(width=400, height=300)
+    a, b_ = pr.Scene(small.scene), pr.Scene(big.scene)
+    batch = pr.Batch(2, 400 * 300 + 40 * 24)
+    batch.set_tuning(4, 16, 8, 32, 2)
+    for w, sc in ((small, a), (big, b_), (small, a)):
+        out = torch.empty((w.params.height, w.params.width, 4), device="cuda")
+        batch.trace([(sc, w.camera, w.params, out)], graph=True)
+        ref = sc.trace(w.camera, w.params)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    batch.close()
+    a.close()
+    b_.close()

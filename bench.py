@@ -498,50 +498,6 @@ def run_ours(args):
     n_build, n_trace = scene.kernel_launches()
     err = scene.error_word(stream)
 
-    total_all, rays_all = aggregate_over_ranks(total_ms, rays, world, "cuda")
-
-    if rank != 0:
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
-    value = rays_all / (total_all / 1e3) / 1e6
-
-    # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
-    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames, binary_tlas=args.binary_tlas)
-    torch.cuda.synchronize()
-    flops = work.frame_flops(counters)
-    trace_avg_s = statistics.mean(trace_ms) / 1e3
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tflops = work.fp32_peak_tflops(props.multi_processor_count, sm_max)
-    achieved_tflops = flops / trace_avg_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak_tflops, "traffic": trace_traffic(args.workload, args.binary_tlas),
-            "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
-            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
-            "trace_share_of_step": sum(trace_ms) / total_ms,
-            "work_counters": {k: v for k, v in counters.items() if v}}
-    if clocks:
-        roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
-        roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
-    sustained = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
-    if sustained:
-        # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
-        roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(props.multi_processor_count, float(sustained))
-        roof["frac_at_measured_sustained_clock"] = achieved_tflops / roof["peak_at_measured_sustained_clock"]
-    if roof["traffic"]:
-        # DRAM bytes of a launch over its mean duration, against the measured copy bandwidth
-        roof["traffic_gbs"] = roof["traffic"] / trace_avg_s / 1e9
-        if peaks.get("hbm_gbs"):
-            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / float(peaks["hbm_gbs"])
-    # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
-    probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
-    roof["peak_fma_probe"] = probe_tflops
-    roof["frac_of_fma_probe"] = achieved_tflops / probe_tflops if probe_tflops > 0 else None
-
     # end to end through the public API: host description -> device (pinned staging, one copy),
     # build, frame, image -> pinned host memory, every step
     e2e = None
@@ -596,16 +552,64 @@ def run_ours(args):
         pipe_s = time.perf_counter() - t0
         e2e_rays = int(e2e_counter.item())
         desc_bytes = scene.desc_bytes
-        e2e = {"value": e2e_rays / pipe_s / 1e6 * world, "unit": "Mrays/s",
+        # every rank streams its own frames; the job's time is the slowest rank's
+        pipe_ms, e2e_rays = aggregate_over_ranks(pipe_s * 1e3, e2e_rays, world, "cuda")
+        serial_ms, serial_rays = aggregate_over_ranks(sum(serial_times) * 1e3, serial_rays, world, "cuda")
+        pipe_s = pipe_ms / 1e3
+        e2e = {"value": e2e_rays / pipe_s / 1e6, "unit": "Mrays/s",
                "h2d_bytes_per_step": int(desc_bytes) + (40 * len(frames) if frames else 0),
                "d2h_bytes_per_step": int(out.numel() * 4),
                "ms_per_step": 1e3 * pipe_s / n_e2e,
                "mode": f"{n_e2e} consecutive frames, each: description to the device, BVH build, frame, "
                        "image to pinned host memory; the image copy of frame k overlaps frame k+1 "
                        "(second stream, double-buffered image)",
-               "serial": {"value": serial_rays / sum(serial_times) / 1e6 * world, "unit": "Mrays/s",
-                          "ms_per_step": 1e3 * statistics.mean(serial_times),
+               "serial": {"value": serial_rays / (serial_ms / 1e3) / 1e6, "unit": "Mrays/s",
+                          "ms_per_step": serial_ms / n_e2e,
                           "mode": "one frame at a time, synchronised after each"}}
+
+    total_all, rays_all = aggregate_over_ranks(total_ms, rays, world, "cuda")
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    value = rays_all / (total_all / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
+    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames, binary_tlas=args.binary_tlas)
+    torch.cuda.synchronize()
+    flops = work.frame_flops(counters)
+    trace_avg_s = statistics.mean(trace_ms) / 1e3
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = work.fp32_peak_tflops(props.multi_processor_count, sm_max)
+    achieved_tflops = flops / trace_avg_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / peak_tflops, "traffic": trace_traffic(args.workload, args.binary_tlas),
+            "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
+            "trace_share_of_step": sum(trace_ms) / total_ms,
+            "work_counters": {k: v for k, v in counters.items() if v}}
+    if clocks:
+        roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
+        roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
+    sustained = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if sustained:
+        # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
+        roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(props.multi_processor_count, float(sustained))
+        roof["frac_at_measured_sustained_clock"] = achieved_tflops / roof["peak_at_measured_sustained_clock"]
+    if roof["traffic"]:
+        # DRAM bytes of a launch over its mean duration, against the measured copy bandwidth
+        roof["traffic_gbs"] = roof["traffic"] / trace_avg_s / 1e9
+        if peaks.get("hbm_gbs"):
+            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / float(peaks["hbm_gbs"])
+    # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
+    probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
+    roof["peak_fma_probe"] = probe_tflops
+    roof["frac_of_fma_probe"] = achieved_tflops / probe_tflops if probe_tflops > 0 else None
 
     extra = {}
     if not args.no_extra:

@@ -162,9 +162,9 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "dcf7cc8c625254552d134e3dc21e4aaba1ff1a04": {"teaser_1080p": 132096 + 264448,
-                                                 "field_100k_2160p": 6040576 + 51865344,
-                                                 "analytic_64x64_x4096": 249856 + 154887424},
+    "1bc3833e12b47bea30f68d23f82c1c2bff90665d": {"teaser_1080p": 146432 + 250880,
+                                                 "field_100k_2160p": 6503680 + 52185344,
+                                                 "analytic_64x64_x4096": 260864 + 154935808},
 }
 
 

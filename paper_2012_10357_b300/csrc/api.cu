@@ -223,6 +223,7 @@ struct pr_scene {
   bool built = false;
   // frame cameras
   pr_camera* d_cams = nullptr;
+  void* d_bases = nullptr;             // camera bases of the frames, computed per launch
   uint32_t cams_cap = 0;
   int build_launches = 0;
   int trace_launches = 0;
@@ -560,6 +561,7 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
   if (p->flags & PR_TRACE_TLAS_BVH2) T.S.tlas4 = nullptr;   // binary TLAS traversal (comparison)
   T.cam0 = *cam0;
   T.cams = d_cams;
+  T.bases = d_cams ? s->d_bases : nullptr;
   T.n_frames = n_frames;
   T.width = p->width;
   T.height = p->height;
@@ -597,10 +599,13 @@ static pr_status upload_cameras(pr_scene* s, const pr_camera* cameras, uint32_t 
     if (s->d_cams) {
       cudaStreamSynchronize(st);
       cudaFree(s->d_cams);
+      cudaFree(s->d_bases);
       s->d_cams = nullptr;
+      s->d_bases = nullptr;
       s->cams_cap = 0;
     }
     PR_CUDA(cudaMalloc(&s->d_cams, sizeof(pr_camera) * n_frames), "cudaMalloc cameras");
+    PR_CUDA(cudaMalloc(&s->d_bases, kCameraBasisBytes * (size_t)n_frames), "cudaMalloc camera bases");
     s->cams_cap = n_frames;
   }
   PR_CUDA(cudaMemcpyAsync(s->d_cams, cameras, sizeof(pr_camera) * n_frames, cudaMemcpyHostToDevice, st),
@@ -753,6 +758,7 @@ void pr_scene_destroy(pr_scene* s) {
   cudaDeviceSynchronize();
   if (s->arena) cudaFree(s->arena);
   if (s->d_cams) cudaFree(s->d_cams);
+  if (s->d_bases) cudaFree(s->d_bases);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->stage_done) cudaEventDestroy(s->stage_done);
   delete s;

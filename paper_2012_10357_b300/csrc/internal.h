@@ -74,6 +74,7 @@ struct TraceLaunch {
   SceneView S;
   pr_camera cam0;
   const pr_camera* cams;   // device array of n_frames cameras, or null (use cam0)
+  void* bases;             // device scratch for n_frames camera bases when cams is set
   uint32_t n_frames;
   uint32_t width, height, max_depth, max_steps, flags;
   float light[3], light_intensity, eps_rel, ambient, background[3];
@@ -83,6 +84,8 @@ struct TraceLaunch {
   unsigned long long* work;   // non-null: instrumented variant, adds WorkCounters
 };
 int launch_trace(const TraceLaunch& L, cudaStream_t s);
+// Device bytes of one camera basis (TraceLaunch::bases holds n_frames of them).
+constexpr size_t kCameraBasisBytes = 64;
 
 }  // namespace pr
 

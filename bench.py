@@ -162,9 +162,9 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "1bc3833e12b47bea30f68d23f82c1c2bff90665d": {"teaser_1080p": 146432 + 250880,
-                                                 "field_100k_2160p": 6503680 + 52185344,
-                                                 "analytic_64x64_x4096": 260864 + 154935808},
+    "2f46009b9da347812ca83a8837584c033c9f8967": {"teaser_1080p": 142592 + 306688,
+                                                 "field_100k_2160p": 6126592 + 52024832,
+                                                 "analytic_64x64_x4096": 403456 + 154923008},
 }
 
 

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libproceduray.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2012_10357_b300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2012_10357_b300/build.py` "
                       "(the CUDA library is required; there is no CPU fallback)")
 
 _lib = ctypes.CDLL(LIB_PATH)

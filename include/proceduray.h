@@ -291,15 +291,19 @@ pr_status pr_fma_peak_probe(uint32_t iters, float* tflops_out, float* ms_out, vo
  * allocation's possible synchronisation or pool growth is not acceptable.
  * Arguments, layouts and results are those of pr_lbvh_build (bit-identical).
  * Scratch comes from one fixed device array of the library (about 7.2 MB,
- * enough for PR_LBVH_NOALLOC_MAX_BOXES boxes), reserved on every device that
- * loads the library and held until the process exits. n above the limit is
- * rejected with PR_ERR_INVALID_ARG (nothing is enqueued). The array is shared
- * by all calls and keeps the last call's contents (the build clears what must
- * start at zero); calls whose work overlaps on the GPU (different streams, or
- * different host threads, on one device) race on it and must be serialised by
- * the caller. The first call on each device looks the array up (a one-time
- * set-up, done with that device current); make that first call before any
- * stream capture. Calls no cudaMalloc, cudaFree or allocating routine. */
+ * enough for PR_LBVH_NOALLOC_MAX_BOXES boxes), held until the process exits.
+ * n above the limit is rejected with PR_ERR_INVALID_ARG (nothing is enqueued).
+ * The array is shared by all calls and keeps the last call's contents (the
+ * build clears what must start at zero); calls whose work overlaps on the GPU
+ * (different streams, or different host threads, on one device) race on it
+ * and must be serialised by the caller. The first call on each device, whatever
+ * n, performs a one-time set-up with that device current: it looks the array
+ * up, and since CUDA may load the library's modules lazily, that is when the
+ * array's module is loaded and its 7.2 MB are reserved on that device if this
+ * has not happened yet. Make that first call before any stream capture and
+ * before any phase whose device memory must not grow. The address is kept for
+ * the life of the process: cudaDeviceReset while the library is in use is not
+ * supported. Later calls make no cudaMalloc, cudaFree or allocating call. */
 pr_status pr_lbvh_build_noalloc(const float* boxes, uint32_t n, float* nodes, uint32_t* perm, uint32_t* codes,
                                 float* root_box, void* stream);
 
@@ -370,16 +374,23 @@ void pr_batch_destroy(pr_batch* batch);
 
 /* ---- Serving loop ------------------------------------------------------
  * Requests arrive at any time (pr_server_submit, thread-safe, non-blocking).
- * A worker thread admits them in arrival order while slots (max_active) and
- * the device-memory budget allow, keeps each scene (inputs + BVH) resident
- * in a cache keyed by scene_key (least recently used unreferenced scenes are
- * evicted to make room), and renders. PR_SERVE_CONTINUOUS: continuous
- * batching, every iteration one batched launch over row ranges of all
- * admitted requests (at most max_batch_pixels; an iteration that is a single
- * whole request uses the pr_trace megakernel), so a request that arrives
- * while others are on the GPU joins at the next iteration. PR_SERVE_PLAIN:
- * one pr_trace per request, first come first served (the comparison form).
- * Results are bit-identical to pr_trace of the same request. */
+ * Scenes (inputs + BVH) stay resident in a cache keyed by scene_key; a
+ * loader thread builds the scene of a request whose key is not resident, on
+ * its own stream, oldest request first, once the device-memory budget holds
+ * it: its device bytes are computed from the description at submit, and
+ * least recently used unreferenced scenes are evicted to make room before
+ * anything is allocated. A worker thread admits requests whose scene is
+ * resident, in arrival order, while slots (max_active) allow, and renders.
+ * PR_SERVE_CONTINUOUS: continuous batching, every iteration one batched
+ * launch over row ranges of all admitted requests (at most
+ * max_batch_pixels; an iteration that is a single whole request uses the
+ * pr_trace megakernel), so a request that arrives while others are on the
+ * GPU joins at the next iteration; with the batched megakernel a request is
+ * complete (and pr_server_poll says so) as soon as its last tile is written,
+ * through a host-mapped completion flag, not at the end of the launch.
+ * PR_SERVE_PLAIN: one pr_trace per request, first come first served (the
+ * comparison form; same cache and loader). Results are bit-identical to
+ * pr_trace of the same request. */
 #define PR_SERVE_CONTINUOUS 0u
 #define PR_SERVE_PLAIN 1u
 
@@ -408,10 +419,15 @@ typedef struct {
   uint32_t cache_hit;          /* 1 if the scene was resident at admission */
 } pr_request_stats;
 
+/* cache_misses: admissions whose scene was built for them; scene_loads: scene
+ * builds started by the server (equal to cache_misses unless a build failed:
+ * a scene is built only once the budget holds it, so it is never built and
+ * dropped again for lack of room). */
 typedef struct {
   uint32_t struct_size, reserved;
   uint64_t submitted, completed, rays, iterations;
   uint64_t cache_hits, cache_misses, evictions, cache_bytes, batch_bytes;
+  uint64_t scene_loads;
 } pr_server_stats;
 
 typedef struct pr_server pr_server;

@@ -74,20 +74,26 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        vp, u32, i64, dbl = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_double
-        L.or_render.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int]
-        L.or_render.restype = ctypes.c_int
-        L.or_world_bounds.argtypes = [vp, vp, vp]
-        L.or_intersect.argtypes = [u32, u32, vp, vp, vp, dbl, dbl, dbl, u32, vp, vp, vp]
-        L.or_intersect.restype = ctypes.c_int
-        L.or_de.argtypes = [u32, vp, vp]
-        L.or_de.restype = dbl
-        L.or_triplex_pow.argtypes = [vp, dbl, vp]
-        L.or_instance_boxes_f32.argtypes = [vp, vp]
-        L.or_lbvh_f32.argtypes = [vp, u32, vp, vp, vp, vp, vp]
-        _lib = L
+        _lib = load(_LIB)
     return _lib
+
+
+def load(path: str):
+    """Load an oracle library built from oracle.cpp (the one above, or a copy with
+    a planted mistake that the pin tests must catch) and declare its signatures."""
+    L = ctypes.CDLL(path)
+    vp, u32, i64, dbl = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_double
+    L.or_render.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int]
+    L.or_render.restype = ctypes.c_int
+    L.or_world_bounds.argtypes = [vp, vp, vp]
+    L.or_intersect.argtypes = [u32, u32, vp, vp, vp, dbl, dbl, dbl, u32, vp, vp, vp]
+    L.or_intersect.restype = ctypes.c_int
+    L.or_de.argtypes = [u32, vp, vp]
+    L.or_de.restype = dbl
+    L.or_triplex_pow.argtypes = [vp, dbl, vp]
+    L.or_instance_boxes_f32.argtypes = [vp, vp]
+    L.or_lbvh_f32.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+    return L
 
 
 def _ptr(a: np.ndarray):

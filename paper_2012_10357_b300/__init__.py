@@ -488,7 +488,7 @@ class _RequestStats(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + [
         (n, ctypes.c_uint64) for n in ("submitted", "completed", "rays", "iterations", "cache_hits", "cache_misses",
-                                       "evictions", "cache_bytes", "batch_bytes")]
+                                       "evictions", "cache_bytes", "batch_bytes", "scene_loads")]
 
 
 class Server:

@@ -241,6 +241,69 @@ struct Carver {
   }
 };
 
+// Byte offsets of every buffer in a scene's device arena (256-byte aligned);
+// the inputs form the prefix [0, o_tbox), copied to the device in one piece.
+struct ArenaPlan {
+  size_t o_aabbs, o_params, o_xform, o_iblas, o_iid, o_isbt, o_imask, o_hg, o_mat, o_sbt, o_rt, o_lp, o_lgq, o_binfo,
+      o_vert, o_idx;
+  size_t o_tbox, o_bbox, o_bnodes, o_bperm, o_bcodes, o_rec, o_iboxes, o_tnodes, o_t4, o_c4p, o_c4e, o_c4r, o_tperm,
+      o_tcodes, o_sbox, o_err;
+  size_t o_k0, o_k1, o_v0, o_v1, o_hist, o_cnt, o_pi, o_pl, o_part, o_jobs;
+  size_t total;
+};
+
+ArenaPlan plan_arena(const Layout& L) {
+  Carver c;
+  ArenaPlan P;
+  P.o_aabbs = c.take<float>(6 * (size_t)L.n_prims);
+  P.o_params = c.take<float4>(4 * (size_t)L.n_prims);
+  P.o_xform = c.take<float>(12 * (size_t)L.n_inst);
+  P.o_iblas = c.take<uint32_t>(L.n_inst);
+  P.o_iid = c.take<uint32_t>(L.n_inst);
+  P.o_isbt = c.take<uint32_t>(L.n_inst);
+  P.o_imask = c.take<uint32_t>(L.n_inst);
+  P.o_hg = c.take<uint4>(L.n_hg);
+  P.o_mat = c.take<float4>(L.n_mat);
+  P.o_sbt = c.take<uint4>(L.n_rec);
+  P.o_rt = c.take<uint2>(L.n_rt);
+  P.o_lp = c.take<uint32_t>(L.n_leaves);
+  P.o_lgq = c.take<uint2>(L.n_leaves);
+  P.o_binfo = c.take<int4>(L.n_blas);
+  P.o_vert = c.take<float>(3 * (size_t)L.n_vert);
+  P.o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri);
+  // everything above is input (one prefix of the arena, copied in one piece)
+  const size_t ni = L.n_inst ? L.n_inst - 1 : 0;
+  P.o_tbox = c.take<float>(6 * (size_t)L.n_tri);
+  P.o_bbox = c.take<float4>(2 * (size_t)L.n_blas);
+  P.o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes);
+  P.o_bperm = c.take<uint32_t>(L.n_leaves);
+  P.o_bcodes = c.take<uint32_t>(L.n_leaves);
+  P.o_rec = c.take<float4>(6 * (size_t)L.n_inst);
+  P.o_iboxes = c.take<float>(6 * (size_t)L.n_inst);
+  P.o_tnodes = c.take<float4>(4 * ni);
+  P.o_t4 = c.take<float4>(8 * ni);
+  P.o_c4p = c.take<uint32_t>(L.n_inst);
+  P.o_c4e = c.take<uint32_t>(L.n_inst);
+  P.o_c4r = c.take<uint32_t>(L.n_inst);
+  P.o_tperm = c.take<uint32_t>(L.n_inst);
+  P.o_tcodes = c.take<uint32_t>(L.n_inst);
+  P.o_sbox = c.take<float>(8);
+  P.o_err = c.take<uint32_t>(1);
+  const uint32_t nl = L.max_large;
+  P.o_k0 = c.take<uint32_t>(nl);
+  P.o_k1 = c.take<uint32_t>(nl);
+  P.o_v0 = c.take<uint32_t>(nl);
+  P.o_v1 = c.take<uint32_t>(nl);
+  P.o_hist = c.take<uint32_t>(256 * (size_t)sort_tiles(nl));
+  P.o_cnt = c.take<uint32_t>(nl);
+  P.o_pi = c.take<uint32_t>(nl);
+  P.o_pl = c.take<uint32_t>(nl);
+  P.o_part = c.take<float>(6 * (size_t)kMaxPartials);
+  P.o_jobs = c.take<LevelDesc>((size_t)L.n_blas + 1);
+  P.total = c.off;
+  return P;
+}
+
 pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
   const Layout& L = s->L;
   // the previous upload's copy must have read the staging buffer before it is refilled
@@ -353,6 +416,13 @@ BuildScratch carve_build_scratch(void* base, uint32_t n) {
 }  // namespace pr
 
 pr::SceneView pr_internal_view(const pr_scene* s) { return view_of(s); }
+
+pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes) {
+  Layout L;
+  pr_status st = validate_and_flatten(desc, L);
+  if (st == PR_OK) *bytes = plan_arena(L).total;
+  return st;
+}
 bool pr_internal_built(const pr_scene* s) { return s && s->built; }
 void pr_internal_set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -384,32 +454,9 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
     return vs;
   }
   const Layout& L = s->L;
-  Carver c;
-  size_t o_aabbs = c.take<float>(6 * (size_t)L.n_prims), o_params = c.take<float4>(4 * (size_t)L.n_prims),
-         o_xform = c.take<float>(12 * (size_t)L.n_inst), o_iblas = c.take<uint32_t>(L.n_inst),
-         o_iid = c.take<uint32_t>(L.n_inst), o_isbt = c.take<uint32_t>(L.n_inst), o_imask = c.take<uint32_t>(L.n_inst),
-         o_hg = c.take<uint4>(L.n_hg), o_mat = c.take<float4>(L.n_mat), o_sbt = c.take<uint4>(L.n_rec),
-         o_rt = c.take<uint2>(L.n_rt), o_lp = c.take<uint32_t>(L.n_leaves), o_lgq = c.take<uint2>(L.n_leaves),
-         o_binfo = c.take<int4>(L.n_blas), o_vert = c.take<float>(3 * (size_t)L.n_vert),
-         o_idx = c.take<uint32_t>(3 * (size_t)L.n_tri),
-         // everything above is input (one prefix of the arena, copied in one piece)
-         o_tbox = c.take<float>(6 * (size_t)L.n_tri), o_bbox = c.take<float4>(2 * (size_t)L.n_blas),
-         o_bnodes = c.take<float4>(4 * (size_t)L.n_blas_nodes), o_bperm = c.take<uint32_t>(L.n_leaves),
-         o_bcodes = c.take<uint32_t>(L.n_leaves), o_rec = c.take<float4>(6 * (size_t)L.n_inst),
-         o_iboxes = c.take<float>(6 * (size_t)L.n_inst),
-         o_tnodes = c.take<float4>(4 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)),
-         o_t4 = c.take<float4>(8 * (size_t)(L.n_inst ? L.n_inst - 1 : 0)), o_c4p = c.take<uint32_t>(L.n_inst),
-         o_c4e = c.take<uint32_t>(L.n_inst), o_c4r = c.take<uint32_t>(L.n_inst), o_tperm = c.take<uint32_t>(L.n_inst),
-         o_tcodes = c.take<uint32_t>(L.n_inst), o_sbox = c.take<float>(8), o_err = c.take<uint32_t>(1);
-  const uint32_t nl = L.max_large;
-  size_t o_k0 = c.take<uint32_t>(nl), o_k1 = c.take<uint32_t>(nl), o_v0 = c.take<uint32_t>(nl),
-         o_v1 = c.take<uint32_t>(nl), o_hist = c.take<uint32_t>(256 * (size_t)sort_tiles(nl)),
-         o_cnt = c.take<uint32_t>(nl), o_pi = c.take<uint32_t>(nl), o_pl = c.take<uint32_t>(nl),
-         o_part = c.take<float>(6 * (size_t)kMaxPartials);
-  const size_t n_jobs = (size_t)L.n_blas + 1;
-  size_t o_jobs = c.take<LevelDesc>(n_jobs);
-  s->arena_bytes = c.off;
-  s->stage_bytes = o_tbox;
+  const ArenaPlan P = plan_arena(L);
+  s->arena_bytes = P.total;
+  s->stage_bytes = P.o_tbox;
   cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, s->stage_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming);
@@ -418,49 +465,49 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
     return cuda_fail(e, "scene arena / pinned staging buffer");
   }
   char* A = s->arena;
-  s->aabbs = (float*)(A + o_aabbs);
-  s->params = (float4*)(A + o_params);
-  s->xform = (float*)(A + o_xform);
-  s->inst_blas = (uint32_t*)(A + o_iblas);
-  s->inst_id = (uint32_t*)(A + o_iid);
-  s->inst_sbt = (uint32_t*)(A + o_isbt);
-  s->inst_mask = (uint32_t*)(A + o_imask);
-  s->hit_groups = (uint4*)(A + o_hg);
-  s->materials = (float4*)(A + o_mat);
-  s->sbt = (uint4*)(A + o_sbt);
-  s->ray_types = (uint2*)(A + o_rt);
-  s->leaf_prim = (uint32_t*)(A + o_lp);
-  s->leaf_gq = (uint2*)(A + o_lgq);
-  s->blas_info = (int4*)(A + o_binfo);
-  s->vertices = (float*)(A + o_vert);
-  s->indices = (uint32_t*)(A + o_idx);
-  s->tri_boxes = (float*)(A + o_tbox);
-  s->blas_box = (float4*)(A + o_bbox);
-  s->blas_nodes = (float4*)(A + o_bnodes);
-  s->blas_perm = (uint32_t*)(A + o_bperm);
-  s->blas_codes = (uint32_t*)(A + o_bcodes);
-  s->inst_rec = (float4*)(A + o_rec);
-  s->inst_boxes = (float*)(A + o_iboxes);
-  s->tlas_nodes = (float4*)(A + o_tnodes);
-  s->tlas4 = (float4*)(A + o_t4);
-  s->c4_parent = (uint32_t*)(A + o_c4p);
-  s->c4_even = (uint32_t*)(A + o_c4e);
-  s->c4_rank = (uint32_t*)(A + o_c4r);
-  s->tlas_perm = (uint32_t*)(A + o_tperm);
-  s->tlas_codes = (uint32_t*)(A + o_tcodes);
-  s->scene_box = (float*)(A + o_sbox);
-  s->error_word = (uint32_t*)(A + o_err);
-  s->scratch.keys[0] = (uint32_t*)(A + o_k0);
-  s->scratch.keys[1] = (uint32_t*)(A + o_k1);
-  s->scratch.vals[0] = (uint32_t*)(A + o_v0);
-  s->scratch.vals[1] = (uint32_t*)(A + o_v1);
-  s->scratch.hist = (uint32_t*)(A + o_hist);
-  s->scratch.counters = (uint32_t*)(A + o_cnt);
-  s->scratch.parent_int = (uint32_t*)(A + o_pi);
-  s->scratch.parent_leaf = (uint32_t*)(A + o_pl);
-  s->scratch.partial = (float*)(A + o_part);
-  s->scratch.max_n = nl;
-  s->d_jobs = (LevelDesc*)(A + o_jobs);
+  s->aabbs = (float*)(A + P.o_aabbs);
+  s->params = (float4*)(A + P.o_params);
+  s->xform = (float*)(A + P.o_xform);
+  s->inst_blas = (uint32_t*)(A + P.o_iblas);
+  s->inst_id = (uint32_t*)(A + P.o_iid);
+  s->inst_sbt = (uint32_t*)(A + P.o_isbt);
+  s->inst_mask = (uint32_t*)(A + P.o_imask);
+  s->hit_groups = (uint4*)(A + P.o_hg);
+  s->materials = (float4*)(A + P.o_mat);
+  s->sbt = (uint4*)(A + P.o_sbt);
+  s->ray_types = (uint2*)(A + P.o_rt);
+  s->leaf_prim = (uint32_t*)(A + P.o_lp);
+  s->leaf_gq = (uint2*)(A + P.o_lgq);
+  s->blas_info = (int4*)(A + P.o_binfo);
+  s->vertices = (float*)(A + P.o_vert);
+  s->indices = (uint32_t*)(A + P.o_idx);
+  s->tri_boxes = (float*)(A + P.o_tbox);
+  s->blas_box = (float4*)(A + P.o_bbox);
+  s->blas_nodes = (float4*)(A + P.o_bnodes);
+  s->blas_perm = (uint32_t*)(A + P.o_bperm);
+  s->blas_codes = (uint32_t*)(A + P.o_bcodes);
+  s->inst_rec = (float4*)(A + P.o_rec);
+  s->inst_boxes = (float*)(A + P.o_iboxes);
+  s->tlas_nodes = (float4*)(A + P.o_tnodes);
+  s->tlas4 = (float4*)(A + P.o_t4);
+  s->c4_parent = (uint32_t*)(A + P.o_c4p);
+  s->c4_even = (uint32_t*)(A + P.o_c4e);
+  s->c4_rank = (uint32_t*)(A + P.o_c4r);
+  s->tlas_perm = (uint32_t*)(A + P.o_tperm);
+  s->tlas_codes = (uint32_t*)(A + P.o_tcodes);
+  s->scene_box = (float*)(A + P.o_sbox);
+  s->error_word = (uint32_t*)(A + P.o_err);
+  s->scratch.keys[0] = (uint32_t*)(A + P.o_k0);
+  s->scratch.keys[1] = (uint32_t*)(A + P.o_k1);
+  s->scratch.vals[0] = (uint32_t*)(A + P.o_v0);
+  s->scratch.vals[1] = (uint32_t*)(A + P.o_v1);
+  s->scratch.hist = (uint32_t*)(A + P.o_hist);
+  s->scratch.counters = (uint32_t*)(A + P.o_cnt);
+  s->scratch.parent_int = (uint32_t*)(A + P.o_pi);
+  s->scratch.parent_leaf = (uint32_t*)(A + P.o_pl);
+  s->scratch.partial = (float*)(A + P.o_part);
+  s->scratch.max_n = s->L.max_large;
+  s->d_jobs = (LevelDesc*)(A + P.o_jobs);
 
   // Level jobs: BLAS levels (small ones in one launch, large ones separately), then the TLAS.
   for (uint32_t b = 0; b < L.n_blas; ++b) {

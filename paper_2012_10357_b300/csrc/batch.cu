@@ -34,6 +34,8 @@ struct pr_batch {
   uint32_t graph_launches = 0;
   uint32_t staged_tiles = 0;         // tiles of the last staged batch
   uint32_t last_launches = 0;
+  uint32_t* notify = nullptr;        // completion flags for the next staged batch (host-mapped)
+  uint32_t notify_seq = 0;
 };
 
 namespace {
@@ -98,10 +100,12 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
     d.tiles_x = (p.width + b->tuning.tile_w - 1) / b->tuning.tile_w;
     d.out = reinterpret_cast<float4*>(q.out_rgba);
     d.out_rgb = (p.flags & PR_TRACE_OUTPUT_RGB) ? 1u : 0u;
-    d.pad_ = 0u;
+    d.tiles_done = 0u;
+    d.pad_[0] = d.pad_[1] = d.pad_[2] = 0u;
     d.pixel_begin = px;
     uint64_t t = (uint64_t)d.tiles_x * ((rows + b->tuning.tile_h - 1) / b->tuning.tile_h);
     if (tiles + t > 0xFFFFFFFFull) return bfail(PR_ERR_INVALID_ARG, "too many tiles");
+    d.n_tiles = (uint32_t)t;
     tiles += (uint32_t)t;
     px += (uint64_t)p.width * rows;
   }
@@ -112,6 +116,10 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   H->total_pixels = px;
   H->tile_ctr = H->shadow_n = H->mirror_n = H->shadow_ctr = H->mirror_ctr = H->pad = 0;
   H->counter = reinterpret_cast<unsigned long long*>(counter);
+  H->notify = b->notify;
+  H->seq = b->notify_seq;
+  H->pad2 = 0;
+  b->notify = nullptr;   // one batch only
   size_t bytes = a256(sizeof(BatchHdr)) + sizeof(ReqDev) * n;
   e = cudaMemcpyAsync(b->V.hdr, b->staging, bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->staged, st);
@@ -302,6 +310,17 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
 }
 
 size_t pr_batch_device_bytes(const pr_batch* b) { return b ? b->arena_bytes : 0; }
+
+}  // extern "C"
+
+bool pr_internal_batch_notify(pr_batch* b, uint32_t* notify, uint32_t seq) {
+  if (!b || b->tuning.megakernel == 0) return false;
+  b->notify = notify;
+  b->notify_seq = seq;
+  return true;
+}
+
+extern "C" {
 
 void pr_batch_destroy(pr_batch* b) {
   if (!b) return;

@@ -92,6 +92,15 @@ constexpr size_t kCameraBasisBytes = 64;
 // Accessors the batch path needs from a scene (api.cu).
 pr::SceneView pr_internal_view(const pr_scene* s);
 bool pr_internal_built(const pr_scene* s);
+// Validate a description and give the device bytes pr_scene_create would
+// allocate for it (pr_scene_device_bytes of the new scene), without allocating.
+pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes);
+// Completion flags for the next pr_trace_batch[_graph] of this batch: when
+// the last tile of request r is written, the kernel stores seq into notify[r]
+// (host-mapped memory, at least n requests). Only the megakernel modes write
+// them; returns false (and sets nothing) for the four-stage wavefront.
+struct pr_batch;
+bool pr_internal_batch_notify(pr_batch* b, uint32_t* notify, uint32_t seq);
 void pr_internal_set_error(const std::string& msg);
 
 namespace pr {

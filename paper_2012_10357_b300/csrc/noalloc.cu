@@ -7,8 +7,13 @@
 // that pool, so an outside allocation can fail or push them over budget), and
 // latency-sensitive loops in which an allocation's possible device
 // synchronisation or pool growth is not acceptable. For them this variant
-// keeps its scratch in one file-scope device array of fixed size, reserved
-// when the library is loaded on a device and held until the process exits.
+// keeps its scratch in one file-scope device array of fixed size, held until
+// the process exits. The array lives in this file's module, which CUDA may
+// load lazily: the first call on a device (whatever n) looks its address up,
+// which loads the module and reserves the array there if that has not
+// happened yet. The address is kept per device for the life of the process,
+// so destroying the primary context (cudaDeviceReset) while the library is in
+// use is not supported.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -85,6 +90,10 @@ extern "C" pr_status pr_lbvh_build_noalloc(const float* boxes, uint32_t n, float
     pr_internal_set_error("pr_lbvh_build_noalloc: scratch layout larger than the fixed array");
     return PR_ERR_INVALID_ARG;
   }
+  // the per-device set-up runs on the first call, also when this call needs no scratch
+  void* scratch = nullptr;
+  pr_status s = scratch_address(&scratch);
+  if (s != PR_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   pr::LevelDesc J;
   J.boxes = boxes;
@@ -98,9 +107,6 @@ extern "C" pr_status pr_lbvh_build_noalloc(const float* boxes, uint32_t n, float
   if (n <= pr::kSmallMax) {
     pr::launch_build_small_one(J, st);           // one CTA, shared memory only
   } else {
-    void* scratch = nullptr;
-    pr_status s = scratch_address(&scratch);
-    if (s != PR_OK) return s;
     // the refit counters must start at zero: the radix-sort path clears them
     // with cudaMemsetAsync on `stream` before its refit kernel
     pr::launch_build_large(J, pr::carve_build_scratch(scratch, n), st);

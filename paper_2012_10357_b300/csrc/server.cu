@@ -67,28 +67,39 @@ struct DescCopy {
 };
 
 struct CachedScene {
-  pr_scene* scene = nullptr;
-  size_t bytes = 0;
-  int refs = 0;
+  pr_scene* scene = nullptr;   // null while the loader builds it
+  size_t bytes = 0;            // device bytes (the plan's estimate while loading)
+  int refs = 0;                // admitted requests using it
   double last_use = 0.0;
+  bool ready = false;
 };
 
 struct Job {
   uint64_t ticket = 0;
   uint64_t key = 0;
   std::shared_ptr<DescCopy> desc;   // only when the key was not cached at submit time
+  size_t bytes = 0;                 // device bytes its scene needs (from the description)
   pr_camera camera{};
   pr_trace_params params{};
   float* out = nullptr;
-  uint32_t next_row = 0, rows_done_launched = 0;
+  uint32_t next_row = 0;
   uint32_t rows_inflight = 0, rows_finished = 0;
   pr_request_stats st{};
-  bool cache_hit = false;
+  bool loaded_for_me = false;       // the loader built the scene for this request
+};
+
+// One launch: the row ranges it renders, by position in the launch's request table.
+struct Part {
+  uint64_t ticket;
+  uint32_t rows;
+  bool done;
 };
 
 struct Iteration {
   cudaEvent_t done = nullptr;
-  std::vector<std::pair<uint64_t, uint32_t>> parts;   // (ticket, rows) rendered by this launch
+  uint32_t seq = 0;
+  bool flags = false;        // the kernel writes per-request completion flags
+  std::vector<Part> parts;
 };
 
 }  // namespace
@@ -96,21 +107,24 @@ struct Iteration {
 struct pr_server {
   pr_server_config cfg{};
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;        // launches
+  cudaStream_t load_stream = nullptr;   // scene uploads and BVH builds
   pr_batch* batch = nullptr;
   size_t batch_bytes = 0;
   unsigned long long* d_rays = nullptr;
-  std::thread worker;
+  uint32_t* notify = nullptr;           // host-mapped completion flags [max_active]
+  uint32_t seq = 0;
+  std::thread worker, loader;
   std::mutex mu;
-  std::condition_variable cv, cv_done;
+  std::condition_variable cv, cv_done, cv_load;
   bool stop = false;
   std::deque<std::shared_ptr<Job>> pending;
   std::list<std::shared_ptr<Job>> active;
   std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;   // every ticket (kept for polling)
   std::unordered_map<uint64_t, CachedScene> cache;
-  size_t cache_bytes = 0;
+  size_t cache_bytes = 0;               // resident scenes + reservations of scenes being built
   uint64_t next_ticket = 1;
-  uint64_t completed = 0, cache_hits = 0, cache_misses = 0, evictions = 0, iterations = 0;
+  uint64_t completed = 0, cache_hits = 0, cache_misses = 0, evictions = 0, iterations = 0, scene_loads = 0;
   std::deque<Iteration> inflight;
   std::vector<cudaEvent_t> free_events;
   std::string error;
@@ -135,16 +149,30 @@ cudaEvent_t take_event(pr_server* s) {
   return e;
 }
 
-// Make room under the budget by dropping unreferenced cached scenes, least
-// recently used first. Called with the lock held.
-bool make_room(pr_server* s, size_t need) {
+void complete_job(pr_server* s, Job& j, pr_status status, double t) {
+  j.st.status = status;
+  j.st.t_done = t;
+  ++s->completed;
+  s->cv_done.notify_all();
+  s->cv_load.notify_all();   // memory may have been freed for a waiting load
+}
+
+// Make room for `need` bytes under the budget by removing unreferenced
+// resident scenes, least recently used first. The removed scenes are handed
+// back to be destroyed without the lock. Called with the lock held; false if
+// the budget cannot hold `need` even then (nothing is removed in that case).
+bool make_room(pr_server* s, size_t need, std::vector<pr_scene*>& victims) {
+  size_t freeable = 0;
+  for (auto& kv : s->cache)
+    if (kv.second.ready && kv.second.refs == 0) freeable += kv.second.bytes;
+  if (s->cache_bytes - freeable + s->batch_bytes + need > s->cfg.mem_budget_bytes) return false;
   while (s->cache_bytes + s->batch_bytes + need > s->cfg.mem_budget_bytes) {
     auto victim = s->cache.end();
     for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
-      if (it->second.refs == 0 && (victim == s->cache.end() || it->second.last_use < victim->second.last_use))
+      if (it->second.ready && it->second.refs == 0 &&
+          (victim == s->cache.end() || it->second.last_use < victim->second.last_use))
         victim = it;
-    if (victim == s->cache.end()) return false;
-    pr_scene_destroy(victim->second.scene);
+    victims.push_back(victim->second.scene);
     s->cache_bytes -= victim->second.bytes;
     s->cache.erase(victim);
     ++s->evictions;
@@ -152,94 +180,144 @@ bool make_room(pr_server* s, size_t need) {
   return true;
 }
 
-// Admit pending jobs in arrival order while slots and memory allow.
-// Scene creation and BVH build run on the server stream.
-void admit(pr_server* s, std::unique_lock<std::mutex>& lk) {
-  while (!s->pending.empty() && s->active.size() < s->cfg.max_active) {
-    std::shared_ptr<Job> j = s->pending.front();
-    auto it = s->cache.find(j->key);
-    if (it == s->cache.end()) {
-      if (!j->desc) {   // the key was cached at submit time but evicted since: cannot rebuild
-        j->st.status = PR_ERR_BUDGET;
-        j->st.t_done = now_s();
-        s->pending.pop_front();
-        ++s->completed;
-        s->cv_done.notify_all();
-        continue;
+// Loader thread: builds the scenes of pending requests whose key is neither
+// resident nor being built, oldest request first, on its own stream, so scene
+// uploads and BVH builds never hold up the launches of admitted requests.
+// The bytes a scene needs are known from its description, so the budget is
+// checked (and room made) before anything is allocated.
+void loader_main(pr_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    if (s->stop && s->pending.empty()) break;
+    std::shared_ptr<Job> j;
+    for (auto& p : s->pending)
+      if (p->desc && !s->cache.count(p->key)) {
+        j = p;
+        break;
       }
-      // estimate: arena grows with primitives and instances; create then account exactly
-      pr_scene* sc = nullptr;
-      lk.unlock();
-      pr_status st = pr_scene_create(&j->desc->d, s->stream, &sc);
-      if (st == PR_OK) st = pr_build_bvh(sc, s->stream);
-      lk.lock();
-      if (st != PR_OK) {
-        if (sc) pr_scene_destroy(sc);
-        j->st.status = st;
-        j->st.t_done = now_s();
-        s->pending.pop_front();
-        ++s->completed;
-        s->cv_done.notify_all();
-        continue;
-      }
-      size_t bytes = pr_scene_device_bytes(sc);
-      if (!make_room(s, bytes)) {
-        // over budget with every cached scene in use: wait for active requests to finish
-        lk.unlock();
-        pr_scene_destroy(sc);
-        lk.lock();
-        if (s->active.empty()) {
-          j->st.status = PR_ERR_BUDGET;
-          j->st.t_done = now_s();
-          s->pending.pop_front();
-          ++s->completed;
-          s->cv_done.notify_all();
-          continue;
-        }
-        return;
-      }
-      CachedScene c;
-      c.scene = sc;
-      c.bytes = bytes;
-      it = s->cache.emplace(j->key, c).first;
-      s->cache_bytes += bytes;
-      ++s->cache_misses;
-      j->cache_hit = false;
-    } else {
-      ++s->cache_hits;
-      j->cache_hit = true;
+    if (!j) {
+      s->cv_load.wait_for(lk, std::chrono::milliseconds(1));
+      continue;
     }
+    std::vector<pr_scene*> victims;
+    if (!make_room(s, j->bytes, victims)) {
+      bool busy = !s->active.empty();
+      for (auto& kv : s->cache) busy = busy || kv.second.refs > 0 || !kv.second.ready;
+      if (!busy) {   // cannot fit even with every other scene evicted and nothing in flight
+        s->pending.erase(std::find(s->pending.begin(), s->pending.end(), j));
+        complete_job(s, *j, PR_ERR_BUDGET, now_s());
+        continue;
+      }
+      s->cv_load.wait_for(lk, std::chrono::milliseconds(1));   // wait for requests to finish
+      continue;
+    }
+    CachedScene& slot = s->cache[j->key];
+    slot.bytes = j->bytes;
+    slot.ready = false;
+    s->cache_bytes += j->bytes;
+    std::shared_ptr<DescCopy> desc = j->desc;
+    lk.unlock();
+    for (pr_scene* v : victims) pr_scene_destroy(v);
+    pr_scene* sc = nullptr;
+    pr_status st = pr_scene_create(&desc->d, s->load_stream, &sc);
+    if (st == PR_OK) st = pr_build_bvh(sc, s->load_stream);
+    if (st == PR_OK && cudaStreamSynchronize(s->load_stream) != cudaSuccess) st = PR_ERR_CUDA;
+    const std::string msg = st == PR_OK ? std::string() : std::string(pr_last_error());
+    lk.lock();
+    ++s->scene_loads;
+    auto it = s->cache.find(j->key);
+    if (st != PR_OK) {
+      s->cache_bytes -= it->second.bytes;
+      s->cache.erase(it);
+      auto pj = std::find(s->pending.begin(), s->pending.end(), j);
+      if (pj != s->pending.end()) s->pending.erase(pj);
+      complete_job(s, *j, st, now_s());
+      lk.unlock();
+      if (sc) pr_scene_destroy(sc);
+      lk.lock();
+      continue;
+    }
+    const size_t bytes = pr_scene_device_bytes(sc);
+    s->cache_bytes = s->cache_bytes - it->second.bytes + bytes;
+    it->second.scene = sc;
+    it->second.bytes = bytes;
+    it->second.ready = true;
+    it->second.last_use = now_s();
+    j->loaded_for_me = true;
+    s->cv.notify_all();
+  }
+}
+
+// Admit pending requests whose scene is resident, oldest first, while slots
+// allow (a request whose scene is being built does not hold up later ones).
+void admit(pr_server* s) {
+  for (auto p = s->pending.begin(); p != s->pending.end() && s->active.size() < s->cfg.max_active;) {
+    std::shared_ptr<Job> j = *p;
+    auto it = s->cache.find(j->key);
+    if (it == s->cache.end() && !j->desc) {   // cached at submit time but evicted since: cannot rebuild
+      p = s->pending.erase(p);
+      complete_job(s, *j, PR_ERR_BUDGET, now_s());
+      continue;
+    }
+    if (it == s->cache.end() || !it->second.ready) {
+      ++p;
+      continue;
+    }
+    if (j->loaded_for_me) ++s->cache_misses;
+    else ++s->cache_hits;
     it->second.refs++;
     it->second.last_use = now_s();
     j->desc.reset();
     j->st.t_admit = now_s();
-    s->pending.pop_front();
+    p = s->pending.erase(p);
     s->active.push_back(j);
   }
 }
 
-void finish_iteration(pr_server* s, Iteration& it) {
-  double t = now_s();
-  for (auto& part : it.parts) {
-    auto jt = s->jobs.find(part.first);
-    if (jt == s->jobs.end()) continue;
-    Job& j = *jt->second;
-    j.rows_inflight -= part.second;
-    j.rows_finished += part.second;
-    if (j.rows_finished >= j.params.height) {
-      j.st.t_done = t;
-      j.st.status = PR_OK;
-      auto c = s->cache.find(j.key);
-      if (c != s->cache.end()) {
-        c->second.refs--;
-        c->second.last_use = t;
-      }
-      s->active.remove(jt->second);
-      ++s->completed;
+// A part of an iteration is rendered: account its rows; the request is done
+// with its last rows.
+void finish_part(pr_server* s, Part& part, double t) {
+  part.done = true;
+  auto jt = s->jobs.find(part.ticket);
+  if (jt == s->jobs.end()) return;
+  Job& j = *jt->second;
+  j.rows_inflight -= part.rows;
+  j.rows_finished += part.rows;
+  if (j.rows_finished >= j.params.height) {
+    auto c = s->cache.find(j.key);
+    if (c != s->cache.end()) {
+      c->second.refs--;
+      c->second.last_use = t;
+    }
+    s->active.remove(jt->second);
+    complete_job(s, j, PR_OK, t);
+  }
+}
+
+// Completed work of the launches in flight: per-request completion flags of
+// the batched megakernel (a request is done as soon as its last tile is, not
+// at the end of the launch), then whole launches by their events. Stream
+// order means that every launch before one that wrote a flag is complete, so
+// a flag value at or past a launch's sequence number marks its part done.
+void retire(pr_server* s) {
+  const double t = now_s();
+  for (Iteration& it : s->inflight) {
+    if (!it.flags) continue;
+    for (size_t k = 0; k < it.parts.size(); ++k) {
+      Part& part = it.parts[k];
+      if (part.done) continue;
+      const uint32_t v = reinterpret_cast<volatile uint32_t*>(s->notify)[k];
+      if ((int32_t)(v - it.seq) >= 0) finish_part(s, part, t);
     }
   }
-  s->free_events.push_back(it.done);
-  s->cv_done.notify_all();
+  while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().done) == cudaSuccess) {
+    Iteration& it = s->inflight.front();
+    for (Part& part : it.parts)
+      if (!part.done) finish_part(s, part, t);
+    s->free_events.push_back(it.done);
+    s->inflight.pop_front();
+  }
 }
 
 // One iteration: row ranges of active requests, oldest first, up to the pixel budget.
@@ -267,7 +345,7 @@ bool launch_iteration(pr_server* s) {
     if (j.st.t_first_launch == 0.0) j.st.t_first_launch = now_s();
     j.next_row += rows;
     j.rows_inflight += rows;
-    it.parts.emplace_back(j.ticket, rows);
+    it.parts.push_back(Part{j.ticket, rows, false});
     px += (uint64_t)rows * j.params.width;
     if (s->cfg.mode == PR_SERVE_PLAIN) break;   // one request per launch
   }
@@ -280,6 +358,8 @@ bool launch_iteration(pr_server* s) {
     st = pr_trace(reqs[0].scene, &reqs[0].camera, &reqs[0].params, reqs[0].out_rgba, nullptr,
                   reinterpret_cast<uint64_t*>(s->d_rays), s->stream);
   } else {
+    it.seq = ++s->seq;
+    it.flags = pr_internal_batch_notify(s->batch, s->notify, it.seq);
     st = pr_trace_batch_graph(s->batch, (uint32_t)reqs.size(), reqs.data(), reinterpret_cast<uint64_t*>(s->d_rays),
                               s->stream);
   }
@@ -299,13 +379,9 @@ void worker_main(pr_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    if (s->stop && s->pending.empty() && s->active.empty()) break;
-    // retire finished iterations
-    while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().done) == cudaSuccess) {
-      finish_iteration(s, s->inflight.front());
-      s->inflight.pop_front();
-    }
-    admit(s, lk);
+    if (s->stop && s->pending.empty() && s->active.empty() && s->inflight.empty()) break;
+    retire(s);
+    admit(s);
     // keep up to two iterations queued on the stream so the GPU never idles
     bool launched = false;
     while (s->inflight.size() < 2 && s->failed == PR_OK) {
@@ -339,6 +415,9 @@ pr_status pr_server_create(const pr_server_config* cfg, pr_server** out) {
   s->cfg = *cfg;
   cudaGetDevice(&s->device);
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->load_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->notify, sizeof(uint32_t) * cfg->max_active, cudaHostAllocMapped);
+  if (e == cudaSuccess) std::memset(s->notify, 0, sizeof(uint32_t) * cfg->max_active);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rays, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_rays, 0, sizeof(unsigned long long), s->stream);
   if (e != cudaSuccess) {
@@ -366,6 +445,7 @@ pr_status pr_server_create(const pr_server_config* cfg, pr_server** out) {
     return sfail(PR_ERR_BUDGET, "pr_server_create: the batch state alone exceeds the memory budget");
   }
   s->worker = std::thread(worker_main, s);
+  s->loader = std::thread(loader_main, s);
   *out = s;
   return PR_OK;
 }
@@ -387,11 +467,13 @@ pr_status pr_server_submit(pr_server* s, const pr_server_request* r, uint64_t* t
   if (!s->cache.count(r->scene_key)) {
     if (!r->desc) return sfail(PR_ERR_INVALID_ARG, "pr_server_submit: scene key not cached and no description");
     lk.unlock();
-    pr_status v = pr_scene_validate(r->desc);
+    size_t bytes = 0;
+    pr_status v = pr_internal_scene_bytes(r->desc, &bytes);   // validates the description
     if (v != PR_OK) return v;
     auto dc = std::make_shared<DescCopy>(r->desc);
     lk.lock();
     j->desc = dc;
+    j->bytes = bytes;
   }
   j->ticket = s->next_ticket++;
   j->st.t_submit = now_s();
@@ -399,6 +481,7 @@ pr_status pr_server_submit(pr_server* s, const pr_server_request* r, uint64_t* t
   s->pending.push_back(j);
   *ticket = j->ticket;
   s->cv.notify_all();
+  s->cv_load.notify_all();
   return PR_OK;
 }
 
@@ -411,7 +494,7 @@ pr_status pr_server_poll(pr_server* s, uint64_t ticket, int* done, pr_request_st
   *done = j.st.t_done > 0.0 ? 1 : 0;
   if (stats) {
     *stats = j.st;
-    stats->cache_hit = j.cache_hit ? 1u : 0u;
+    stats->cache_hit = (j.st.t_admit > 0.0 && !j.loaded_for_me) ? 1u : 0u;
   }
   return PR_OK;
 }
@@ -446,6 +529,7 @@ pr_status pr_server_get_stats(pr_server* s, pr_server_stats* out) {
   out->evictions = s->evictions;
   out->cache_bytes = s->cache_bytes;
   out->batch_bytes = s->batch_bytes;
+  out->scene_loads = s->scene_loads;
   return PR_OK;
 }
 
@@ -460,14 +544,19 @@ void pr_server_destroy(pr_server* s) {
     }
   }
   s->cv.notify_all();
+  s->cv_load.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->loader.joinable()) s->loader.join();
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->load_stream) cudaStreamSynchronize(s->load_stream);
   for (auto& it : s->inflight) cudaEventDestroy(it.done);
   for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
   for (auto& c : s->cache) pr_scene_destroy(c.second.scene);
   if (s->batch) pr_batch_destroy(s->batch);
   if (s->d_rays) cudaFree(s->d_rays);
+  if (s->notify) cudaFreeHost(s->notify);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->load_stream) cudaStreamDestroy(s->load_stream);
   delete s;
 }
 

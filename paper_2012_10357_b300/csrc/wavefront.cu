@@ -248,6 +248,29 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
   }
 }
 
+// Completion flag of a request (batched megakernel modes): every thread
+// fences its image writes of the tile, the CTA synchronises, and thread 0
+// counts the tile; the CTA that finishes the request's last tile publishes
+// the batch's sequence number in the request's host-mapped flag.
+__device__ __forceinline__ void tile_finished(const BatchView& B, uint32_t r, uint32_t n_tiles) {
+  uint32_t* notify = B.hdr->notify;
+  if (notify == nullptr) {
+    __syncthreads();
+    return;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ReqDev* req = const_cast<ReqDev*>(B.reqs) + r;
+    const uint32_t done = atomicAdd(&req->tiles_done, 1u) + 1u;
+    if (done == n_tiles) {
+      __threadfence_system();
+      const uint32_t seq = B.hdr->seq;
+      asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(notify + r), "r"(seq) : "memory");
+    }
+  }
+}
+
 // Batched megakernel: persistent CTAs claim 16x8 tiles of all requests from
 // one counter; every pixel runs the single-request kernel's pipeline
 // (render_pixel: primary, shadow and mirror rays, shading) and writes its
@@ -299,7 +322,8 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
         R.out[o] = make_float4(color.x, color.y, color.z, 1.f);
       }
     }
-    __syncthreads();   // every thread is done with this tile's request record and counters
+    // every thread is done with this tile's request record and counters
+    tile_finished(B, r, R.n_tiles);
   }
   if (B.hdr->counter) {
     const uint32_t total = __reduce_add_sync(kFull, rays);
@@ -352,6 +376,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
     const uint32_t total = __reduce_add_sync(kFull, rays);
     if (lane == 0 && total) atomicAdd(B.hdr->counter, (unsigned long long)total);
   }
+  tile_finished(B, s_req, R.n_tiles);
 }
 
 }  // namespace

@@ -19,7 +19,8 @@ struct ReqDev {
   uint32_t tile_begin, tiles_x;
   float4* out;                       // float4 per pixel, or 3 floats with out_rgb
   uint64_t pixel_begin;
-  uint32_t out_rgb, pad_;
+  uint32_t out_rgb, n_tiles;         // n_tiles: tiles of this request in the batch
+  uint32_t tiles_done, pad_[3];      // tiles finished (megakernel modes with completion flags)
 };
 
 // Counters and totals of the current batch (device memory).
@@ -28,6 +29,10 @@ struct BatchHdr {
   uint64_t total_pixels;
   uint32_t tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr, pad;
   unsigned long long* counter;   // rays traced (optional)
+  // Completion flags (optional, megakernel modes): when the last tile of
+  // request r is written, notify[r] = seq. notify is host-mapped memory.
+  uint32_t* notify;
+  uint32_t seq, pad2;
 };
 
 struct BatchView {

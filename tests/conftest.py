@@ -26,3 +26,14 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Every parity comparison of the session with its counts (disagreeing pixels,
+    out-of-tolerance pixels by kind, the strict and budgeted totals)."""
+    parity = sys.modules.get("parity")
+    if parity is None or not parity.REPORTS:
+        return
+    terminalreporter.section("parity against the oracle")
+    for label, rep in parity.REPORTS:
+        terminalreporter.write_line(parity.summary_line(label, rep))

@@ -7,12 +7,16 @@ whether the mirror ray hit and what. On the pixels that agree, the primary hit
 distance is within 1e-3 x scene diagonal, the shading normal within 1e-2 rad
 and the radiance within 1e-3 (max norm).
 
-Reading for sphere-traced surfaces: a fractal's surface point and normal are
-ill-conditioned between FP32 and FP64 (a hit a few epsilons away has an
-unrelated normal, and a mirror ray from it lands elsewhere on the fractal), so
-there a pixel whose continuous values exceed the tolerances counts as one that
-does not agree, inside the same 0.1 % budget. Scenes made only of analytic
-primitives are held to the strict form: every agreeing pixel within tolerance.
+Reading for fractals and any-hit shaders (the only exception): the surface
+point and normal of a quaternion Julia set or a Mandelbulb are ill-conditioned
+between FP32 and FP64 (a hit a few epsilons away has an unrelated normal, and a
+mirror ray from it lands elsewhere on the fractal), and an any-hit shader's
+band test is a discontinuous decision on the candidate point. A pixel whose
+primary or mirror hit (on either side) is on such a primitive may therefore
+exceed the continuous tolerances; it then counts as a disagreeing pixel, inside
+the same 0.1 % budget. Every other agreeing pixel, including hits on the
+sphere-traced exact SDFs (torus, rounded box, capsule, metaballs), must be
+within tolerance.
 """
 from __future__ import annotations
 
@@ -26,9 +30,37 @@ N_RAD = 1e-2
 RGB_ABS = 1e-3
 AGREE_MIN = 0.999
 
+IS_JULIA, IS_MANDELBULB, IS_JULIA_CUT = 7, 8, 9
+ILL_CONDITIONED_IS = (IS_JULIA, IS_MANDELBULB, IS_JULIA_CUT)
 
-def compare(ref: np.ndarray, aov: np.ndarray, rgb: np.ndarray, diag: float) -> dict:
-    """ref: oracle pixels; aov: AOV structured array; rgb: [N,3] float32 radiance."""
+# (label, report) of every assert_parity call of this process, printed at the
+# end of the test session
+REPORTS = []
+
+
+def ill_conditioned_hits(scene, inst: np.ndarray, geom: np.ndarray) -> np.ndarray:
+    """True where (instance, geometry) is a radiance hit on a fractal primitive or
+    on one whose hit group has an any-hit shader (Eq. 1 record with r = 0)."""
+    inst = inst.astype(np.int64)
+    geom = geom.astype(np.int64)
+    hit = (inst >= 0) & (inst < len(scene.inst_sbt_offset)) & (geom >= 0)
+    out = np.zeros(len(inst), bool)
+    if not hit.any():
+        return out
+    rec = int(scene.sbt_stride_m) * geom[hit] + np.asarray(scene.inst_sbt_offset, np.int64)[inst[hit]]
+    ok = rec < len(scene.sbt)
+    hg = np.asarray(scene.sbt, np.int64)[np.where(ok, rec, 0), 0]
+    groups = np.asarray(scene.hit_groups, np.int64)
+    is_id, ahs = groups[hg, 0], groups[hg, 2]
+    bad = ok & (np.isin(is_id, ILL_CONDITIONED_IS) | (ahs != NONE))
+    out[np.nonzero(hit)[0]] = bad
+    return out
+
+
+def compare(ref: np.ndarray, aov: np.ndarray, rgb: np.ndarray, diag: float, scene=None) -> dict:
+    """ref: oracle pixels; aov: AOV structured array; rgb: [N,3] float32 radiance.
+    scene: the description, to find the pixels of the fractal / any-hit reading
+    (without it every pixel is held to the strict form)."""
     ref = ref.reshape(-1)
     aov = aov.reshape(-1)
     rgb = rgb.reshape(-1, 3).astype(np.float64)
@@ -52,7 +84,18 @@ def compare(ref: np.ndarray, aov: np.ndarray, rgb: np.ndarray, diag: float) -> d
     t_bad = hit & (dt > T_REL * diag)
     n_bad = hit & (ang > N_RAD)
     rgb_bad = agree & (drgb > RGB_ABS)
-    ok = agree & ~t_bad & ~n_bad & ~rgb_bad
+    out_of_tol = t_bad | n_bad | rgb_bad
+    ill = np.zeros(n, bool)
+    if scene is not None:
+        signed = lambda a: np.where(a.astype(np.int64) == NONE, -1, a.astype(np.int64))
+        ill = (ill_conditioned_hits(scene, ref["inst"], ref["geom"]) |
+               ill_conditioned_hits(scene, signed(aov["inst"]), signed(aov["geom"])) |
+               ill_conditioned_hits(scene, ref["refl_inst"], ref["refl_geom"]) |
+               ill_conditioned_hits(scene, signed(aov["refl_inst"]), signed(aov["refl_geom"])))
+    strict_bad = agree & ~ill & out_of_tol
+    budget_bad = ~agree | (agree & ill & out_of_tol)
+    ok = agree & ~out_of_tol
+    strict_hit = hit & ~ill
     return dict(
         n=n,
         agree_within_tol=float(ok.mean()) if n else 1.0,
@@ -60,25 +103,50 @@ def compare(ref: np.ndarray, aov: np.ndarray, rgb: np.ndarray, diag: float) -> d
         agree=float(agree.mean()) if n else 1.0,
         n_disagree=int((~agree).sum()),
         t_bad=int(t_bad.sum()), n_bad=int(n_bad.sum()), rgb_bad=int(rgb_bad.sum()),
+        n_ill=int(ill.sum()), strict_bad=int(strict_bad.sum()), budget_bad=int(budget_bad.sum()),
         max_dt=float(dt[hit].max()) if hit.any() else 0.0,
         max_ang=float(ang[hit].max()) if hit.any() else 0.0,
         max_drgb=float(drgb[agree].max()) if agree.any() else 0.0,
+        strict_max_dt_rel=float(dt[strict_hit].max() / diag) if strict_hit.any() else 0.0,
+        strict_max_ang=float(ang[strict_hit].max()) if strict_hit.any() else 0.0,
+        strict_max_drgb=float(drgb[agree & ~ill].max()) if (agree & ~ill).any() else 0.0,
         hits=int(hit.sum()), sbt_err_ref=int(((r_flags & F_SBT) != 0).sum()),
         sbt_err_gpu=int(((g_flags & F_SBT) != 0).sum()),
         rays_ref=int(ref["rays"].sum()),
     )
 
 
-def assert_parity(rep: dict, label: str = "", strict: bool = True):
-    """strict: analytic scenes (every agreeing pixel within tolerance);
-    otherwise out-of-tolerance pixels count against the 0.1 % budget."""
+def assert_parity(rep: dict, label: str = ""):
+    """>= 99.9 % of pixels agree on every ray's discrete outcome; every agreeing
+    pixel outside the fractal / any-hit reading is within tolerance; pixels that
+    disagree plus out-of-tolerance pixels of that reading stay within 0.1 %."""
+    REPORTS.append((label, rep))
     msg = f"{label}: {rep}"
     assert rep["primary_agree"] >= AGREE_MIN, msg
     assert rep["agree"] >= AGREE_MIN, msg
-    if strict:
-        assert rep["t_bad"] == 0 and rep["n_bad"] == 0 and rep["rgb_bad"] == 0, msg
-    else:
-        assert rep["agree_within_tol"] >= AGREE_MIN, msg
+    assert rep["strict_bad"] == 0, msg
+    assert rep["budget_bad"] <= (1.0 - AGREE_MIN) * rep["n"] + 1e-9, msg
+
+
+def merge_reports(reps) -> dict:
+    """One report over several comparisons (e.g. the sampled pixels of many requests)."""
+    n = sum(r["n"] for r in reps)
+    out = {"n": n}
+    for k in ("n_disagree", "t_bad", "n_bad", "rgb_bad", "n_ill", "strict_bad", "budget_bad", "hits", "sbt_err_ref",
+              "sbt_err_gpu", "rays_ref"):
+        out[k] = sum(r[k] for r in reps)
+    for k in ("agree_within_tol", "primary_agree", "agree"):
+        out[k] = sum(r[k] * r["n"] for r in reps) / n if n else 1.0
+    for k in ("max_dt", "max_ang", "max_drgb", "strict_max_dt_rel", "strict_max_ang", "strict_max_drgb"):
+        out[k] = max((r[k] for r in reps), default=0.0)
+    return out
+
+
+def summary_line(label: str, rep: dict) -> str:
+    return (f"{label}: n={rep['n']} disagree={rep['n_disagree']} fractal/any-hit px={rep['n_ill']} "
+            f"t_bad={rep['t_bad']} n_bad={rep['n_bad']} rgb_bad={rep['rgb_bad']} strict_bad={rep['strict_bad']} "
+            f"budget_used={rep['budget_bad']}/{rep['n']} strict max |dt|/diag={rep['strict_max_dt_rel']:.2e} "
+            f"angle={rep['strict_max_ang']:.2e} rad |drgb|={rep['strict_max_drgb']:.2e}")
 
 
 def gpu_rays_from_flags(aov: np.ndarray) -> np.ndarray:

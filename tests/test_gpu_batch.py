@@ -108,10 +108,8 @@ def test_batch_request_vs_oracle():
     assert torch.equal(out, out2)
     box = sc.bounds()
     rep = compare(oracle.render(w), pr.aov_to_numpy(aov), out[..., :3].cpu().numpy(),
-                  float(np.linalg.norm(box[3:] - box[:3])))
-    # the teaser holds sphere-traced fractals: out-of-tolerance pixels count
-    # against the 0.1 % budget instead of failing one by one
-    assert_parity(rep, "batched teaser 160x90", strict=False)
+                  float(np.linalg.norm(box[3:] - box[:3])), scene=w.scene)
+    assert_parity(rep, "batched teaser 160x90")
 
 
 def test_batch_budget_and_argument_errors():
@@ -138,7 +136,7 @@ def test_full_request_batch_sampled_vs_oracle():
     image equals its pr_trace, and 64 seeded pixels of every request (4096 in
     all, parity on the sampled pixels as the oracle renders them one by one)
     agree with the oracle within the 0.1 % budget."""
-    from parity import AGREE_MIN
+    from parity import merge_reports
     ws = scenes.batch_requests(0, 64)
     total = sum(w.params.width * w.params.height for w in ws)
     objs = [pr.Scene(w.scene) for w in ws]
@@ -146,24 +144,23 @@ def test_full_request_batch_sampled_vs_oracle():
     batch = pr.Batch(len(ws), total)
     batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], graph=True)
     torch.cuda.synchronize()
-    n = agree = ok = 0
+    reps = []
     for k, (o, w, out) in enumerate(zip(objs, ws, outs)):
         img, aov = o.trace(w.camera, w.params, want_aov=True)
         torch.cuda.synchronize()
         assert torch.equal(img, out), f"request {k}"
         pix = scenes.sample_pixels(w.params.width, w.params.height, 64, seed=100 + k)
         box = o.bounds()
-        rep = compare(oracle.render(w, pixels=pix), pr.aov_to_numpy(aov).reshape(-1)[pix],
-                      img[..., :3].reshape(-1, 3).cpu().numpy()[pix], float(np.linalg.norm(box[3:] - box[:3])))
-        n += rep["n"]
-        agree += round(rep["agree"] * rep["n"])
-        ok += round(rep["agree_within_tol"] * rep["n"])
+        reps.append(compare(oracle.render(w, pixels=pix), pr.aov_to_numpy(aov).reshape(-1)[pix],
+                            img[..., :3].reshape(-1, 3).cpu().numpy()[pix], float(np.linalg.norm(box[3:] - box[:3])),
+                            scene=w.scene))
         del img, aov
     batch.close()
     for o in objs:
         o.close()
-    assert n == 64 * len(ws)
-    assert agree / n >= AGREE_MIN and ok / n >= AGREE_MIN, (n, agree, ok)
+    rep = merge_reports(reps)
+    assert rep["n"] == 64 * len(ws)
+    assert_parity(rep, "64-request batch, 64 sampled pixels per request")
 
 
 def test_batch_rgb_outputs_equal_plain():

@@ -327,6 +327,114 @@ def test_sdf_sphere_tracing_vs_bisection(O, is_id, prm):
     assert hits > 20
 
 
+# --------------------------------------------------------------------------
+# Normals of sphere-traced hits against closed-form gradients
+# --------------------------------------------------------------------------
+# The oracle's sphere-traced normal is the normalised central difference of the
+# estimate (step eps |d|). For the exact SDFs the gradient has a closed form
+# written from the geometry (the direction from the closest point of the core
+# set: ring circle, segment, inner box); for the smooth-min metaballs it is the
+# chain rule of the polynomial smooth minimum. A swapped or wrong-axis stencil,
+# or a sign error inside an SDF, moves these normals by far more than 1e-3 rad.
+def _grad_torus(p, R, r):
+    rho = math.hypot(p[0], p[2])
+    core = np.array([R * p[0] / rho, 0.0, R * p[2] / rho])
+    return _unit(p - core)
+
+
+def _grad_capsule(p, h, r):
+    return _unit(p - np.array([0.0, min(max(p[1], -h), h), 0.0]))
+
+
+def _grad_roundbox(p, b, rr):
+    e = np.asarray(b, np.float64) - rr
+    v = p - np.clip(p, -e, e)          # face, edge or corner region of the inner box
+    assert np.linalg.norm(v) > 0.5 * rr
+    return _unit(v)
+
+
+def _grad_metaball4(p, prm, k=0.2):
+    """Chain rule through smin(smin(smin(d0, d1), d2), d3): with
+    h = max(k - |a - b|, 0) / k, d smin / d min(a, b) = 1 - h/2 and
+    d smin / d max(a, b) = h/2."""
+    prm = np.asarray(prm, np.float64)
+    cs, rs = prm[:12].reshape(4, 3), prm[12:16]
+    dist = [np.linalg.norm(p - cs[i]) - rs[i] for i in range(4)]
+    grad = [_unit(p - cs[i]) for i in range(4)]
+
+    def smin_with_grad(a, ga, b, gb):
+        h = max(k - abs(a - b), 0.0) / k
+        wa, wb = (1 - h / 2, h / 2) if a <= b else (h / 2, 1 - h / 2)
+        return min(a, b) - h * h * k * 0.25, wa * ga + wb * gb
+
+    m, g = smin_with_grad(dist[0], grad[0], dist[1], grad[1])
+    m, g = smin_with_grad(m, g, dist[2], grad[2])
+    m, g = smin_with_grad(m, g, dist[3], grad[3])
+    return _unit(g)
+
+
+_FAR_METABALLS = [-1.5, 0, 0, 1.5, 0, 0, 0, 1.5, 0, 0, -1.5, 0, 0.4, 0.3, 0.35, 0.25]
+
+
+@pytest.mark.parametrize("is_id,prm,grad", [
+    (IS_TORUS, [1, 0.25], lambda p: _grad_torus(p, 1.0, 0.25)),
+    (IS_TORUS, [0.7, 0.3], lambda p: _grad_torus(p, 0.7, 0.3)),
+    (IS_CAPSULE, [0.6, 0.3], lambda p: _grad_capsule(p, 0.6, 0.3)),
+    (IS_ROUNDBOX, [0.6, 0.6, 0.6, 0.15], lambda p: _grad_roundbox(p, [0.6, 0.6, 0.6], 0.15)),
+    (IS_ROUNDBOX, [0.9, 0.4, 0.6, 0.1], lambda p: _grad_roundbox(p, [0.9, 0.4, 0.6], 0.1)),
+    # far-apart balls: the smooth minimum is the plain one, each ball's normal radial
+    (IS_METABALL4, _FAR_METABALLS, lambda p: _grad_metaball4(p, _FAR_METABALLS)),
+    (IS_METABALL4, list(scenes.shape_metaball4(np.random.default_rng(5))[1]),
+     lambda p: _grad_metaball4(p, scenes.shape_metaball4(np.random.default_rng(5))[1])),
+], ids=["torus", "torus_thick", "capsule", "roundbox", "roundbox_aniso", "metaballs_apart", "metaballs_blend"])
+def test_sphere_traced_normal_is_the_sdf_gradient(O, is_id, prm, grad):
+    """At sphere-traced hits of random rays (eps 1e-4, |d| = 1 and |d| != 1),
+    the oracle's normal is within 1e-3 rad of the closed-form gradient."""
+    rng = np.random.default_rng(17)
+    eps = 1e-4
+    hits, worst = 0, 0.0
+    for k in range(160):
+        o = _unit(rng.normal(size=3)) * 3.0
+        aim = rng.uniform(-0.5, 0.5, 3)
+        if prm is _FAR_METABALLS:      # aim at one of the separated balls
+            aim = 0.6 * aim + np.reshape(prm[:12], (4, 3))[k % 4]
+        d = _unit(aim - o)
+        if k % 2:
+            d = d * 0.6        # an object-space direction of a scaled instance: t shared with world
+        res = O.intersect(is_id, prm, o, d, 0.0, 10.0, eps, 256)
+        if res is None:
+            continue
+        t, n, _ = res
+        p = o + t * d
+        ang = math.acos(min(1.0, abs(float(np.dot(n, grad(p))))))
+        assert float(np.dot(n, grad(p))) > 0, (k, p, n)          # outward, not flipped
+        worst = max(worst, ang)
+        hits += 1
+    assert hits >= 60, hits
+    assert worst <= 1e-3, worst
+
+
+def test_julia_c0_normal_is_radial(O):
+    """c = 0: the estimate 0.5 r ln r is radial, so sphere-traced hits near the
+    unit ball carry the radial normal p / |p| (pins the stencil on a fractal
+    estimator). eps = 1e-2 keeps the stencil outside the 12-iteration filled
+    set (radius 4^(1/4096) = 1.00034), where the estimate jumps to 0."""
+    rng = np.random.default_rng(23)
+    prm = [0, 0, 0, 0, 12, 4]
+    hits = 0
+    for _ in range(60):
+        o = _unit(rng.normal(size=3)) * 3.0
+        d = _unit(rng.uniform(-0.6, 0.6, 3) - o)
+        res = O.intersect(IS_JULIA, prm, o, d, 0.0, 10.0, 1e-2, 256)
+        if res is None:
+            continue
+        t, n, _ = res
+        p = o + t * d
+        assert math.acos(min(1.0, float(np.dot(n, _unit(p))))) <= 1e-3
+        hits += 1
+    assert hits >= 30
+
+
 def test_julia_c0_closed_form(O):
     """c = 0: q_n = q^(2^n), so the estimate collapses to 0.5 |q| ln|q| outside
     the unit ball and the 12-iteration filled set is the unit ball itself."""

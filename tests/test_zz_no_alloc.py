@@ -90,3 +90,47 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     assert b"exceeds the fixed scratch limit" in lib.pr_last_error()
     torch.cuda.synchronize()
     assert float(out["root"][0]) == -7.0          # nothing was written
+
+
+def test_noalloc_allocates_nothing():
+    """The point of the entry point: once a device has seen its first call,
+    calls take no device memory. Around two calls of 100 000 boxes the default
+    memory pool's high-water marks stay at zero and the device's free memory
+    is unchanged, while one pr_lbvh_build of the same boxes (which takes its
+    scratch from that pool) does raise the mark, so the check can see an
+    allocation."""
+    from cuda.bindings import driver, runtime as cudart
+    lib = pr._lib
+    err, pool = cudart.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    assert err == cudart.cudaError_t.cudaSuccess
+    used_high = cudart.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh
+    reserved_high = cudart.cudaMemPoolAttr.cudaMemPoolAttrReservedMemHigh
+
+    def reset_marks():
+        for attr in (used_high, reserved_high):
+            assert cudart.cudaMemPoolSetAttribute(pool, attr, driver.cuuint64_t(0))[0] == cudart.cudaError_t.cudaSuccess
+
+    def mark(attr):
+        err, v = cudart.cudaMemPoolGetAttribute(pool, attr)
+        assert err == cudart.cudaError_t.cudaSuccess
+        return int(v)
+
+    n = 100_000
+    boxes = _boxes(n, seed=9)
+    outs = [_outputs(n) for _ in range(3)]
+    assert _call(lib.pr_lbvh_build_noalloc, boxes, outs[0]) == pr.PR_OK      # first call on the device: set-up
+    torch.cuda.synchronize()
+    reset_marks()       # the marks restart from the pool's current use (memory earlier tests left in it)
+    used0, reserved0 = mark(used_high), mark(reserved_high)
+    free_before = torch.cuda.mem_get_info()[0]
+    for k in (1, 2):
+        assert _call(lib.pr_lbvh_build_noalloc, boxes, outs[k]) == pr.PR_OK
+    torch.cuda.synchronize()
+    assert mark(used_high) == used0 and mark(reserved_high) == reserved0
+    assert torch.cuda.mem_get_info()[0] >= free_before          # the pool may only have given memory back
+    _same(outs[0], outs[2], n)
+    ref = _outputs(n)
+    assert _call(lib.pr_lbvh_build, boxes, ref) == pr.PR_OK                   # the allocating build
+    torch.cuda.synchronize()
+    assert mark(used_high) > used0
+    _same(ref, outs[1], n)

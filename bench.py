@@ -348,11 +348,18 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=6
         lat = np.array([s["t_done"] - s["t_submit"] for s in st]) * 1e3
         span = max(s["t_done"] for s in st) - min(s["t_submit"] for s in st)
         ok = sum(1 for s in st if s["status"] == 0)
+        # where the latency goes: waiting for the scene (build on a miss) and a slot, waiting for
+        # the first launch, and from the first launch to completion
+        phase = lambda a, b: np.array([s[b] - s[a] for s in st if s["status"] == 0]) * 1e3
+        breakdown = {name: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+                     for name, v in (("admit_ms", phase("t_submit", "t_admit")),
+                                     ("launch_wait_ms", phase("t_admit", "t_first_launch")),
+                                     ("in_flight_ms", phase("t_first_launch", "t_done"))) if len(v)}
         out_rows.append({"rate_per_s": lam, "requests": n, "ok": ok, "mode": "continuous" if mode == 0 else "plain",
                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                          "value": stats["rays"] / span / 1e6, "unit": "Mrays/s", "makespan_s": span,
                          "iterations": stats["iterations"], "cache_hits": stats["cache_hits"],
-                         "cache_misses": stats["cache_misses"]})
+                         "cache_misses": stats["cache_misses"], "breakdown": breakdown})
     return out_rows
 
 

@@ -20,6 +20,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/proceduray.h"
@@ -157,19 +158,29 @@ void complete_job(pr_server* s, Job& j, pr_status status, double t) {
   s->cv_load.notify_all();   // memory may have been freed for a waiting load
 }
 
-// Make room for `need` bytes under the budget by removing unreferenced
-// resident scenes, least recently used first. The removed scenes are handed
-// back to be destroyed without the lock. Called with the lock held; false if
-// the budget cannot hold `need` even then (nothing is removed in that case).
+// A resident scene may be evicted when no admitted request uses it and no
+// pending request waits for it (a scene built for a request that the worker
+// has not admitted yet must stay, or two requests could take turns evicting
+// each other's scene forever).
+bool evictable(const CachedScene& c, uint64_t key, const std::unordered_set<uint64_t>& wanted) {
+  return c.ready && c.refs == 0 && !wanted.count(key);
+}
+
+// Make room for `need` bytes under the budget by removing evictable resident
+// scenes, least recently used first. The removed scenes are handed back to be
+// destroyed without the lock. Called with the lock held; false if the budget
+// cannot hold `need` even then (nothing is removed in that case).
 bool make_room(pr_server* s, size_t need, std::vector<pr_scene*>& victims) {
+  std::unordered_set<uint64_t> wanted;
+  for (auto& p : s->pending) wanted.insert(p->key);
   size_t freeable = 0;
   for (auto& kv : s->cache)
-    if (kv.second.ready && kv.second.refs == 0) freeable += kv.second.bytes;
+    if (evictable(kv.second, kv.first, wanted)) freeable += kv.second.bytes;
   if (s->cache_bytes - freeable + s->batch_bytes + need > s->cfg.mem_budget_bytes) return false;
   while (s->cache_bytes + s->batch_bytes + need > s->cfg.mem_budget_bytes) {
     auto victim = s->cache.end();
     for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
-      if (it->second.ready && it->second.refs == 0 &&
+      if (evictable(it->second, it->first, wanted) &&
           (victim == s->cache.end() || it->second.last_use < victim->second.last_use))
         victim = it;
     victims.push_back(victim->second.scene);
@@ -202,8 +213,11 @@ void loader_main(pr_server* s) {
     }
     std::vector<pr_scene*> victims;
     if (!make_room(s, j->bytes, victims)) {
+      // room frees up when admitted requests finish, or when pending requests
+      // whose scenes are resident are admitted and finish
       bool busy = !s->active.empty();
       for (auto& kv : s->cache) busy = busy || kv.second.refs > 0 || !kv.second.ready;
+      for (auto& p : s->pending) busy = busy || (p != j && s->cache.count(p->key));
       if (!busy) {   // cannot fit even with every other scene evicted and nothing in flight
         s->pending.erase(std::find(s->pending.begin(), s->pending.end(), j));
         complete_job(s, *j, PR_ERR_BUDGET, now_s());
@@ -326,6 +340,7 @@ bool launch_iteration(pr_server* s) {
   Iteration it;
   uint64_t px = 0;
   const uint64_t cap = s->cfg.max_batch_pixels;
+  const double t_launch = now_s();   // one time stamp for every request of this launch
   for (auto& jp : s->active) {
     Job& j = *jp;
     if (j.next_row >= j.params.height) continue;
@@ -342,7 +357,7 @@ bool launch_iteration(pr_server* s) {
     r.row_begin = j.next_row;
     r.row_count = rows;
     reqs.push_back(r);
-    if (j.st.t_first_launch == 0.0) j.st.t_first_launch = now_s();
+    if (j.st.t_first_launch == 0.0) j.st.t_first_launch = t_launch;
     j.next_row += rows;
     j.rows_inflight += rows;
     it.parts.push_back(Part{j.ticket, rows, false});

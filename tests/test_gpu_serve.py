@@ -158,12 +158,14 @@ def test_served_requests_match_the_oracle():
         reqs.append(((kind << 32) | sseed, wl))
     assert {k >> 32 for k, _ in reqs} == {0, 1}
     srv = pr.Server(mode=pr.PR_SERVE_CONTINUOUS, max_active=8, mem_budget_bytes=16 << 30, max_batch_pixels=1 << 20)
-    outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for _, w in reqs]
-    for (key, w), out in zip(reqs, outs):
-        srv.submit(key, descs[(key >> 32, key & 0xFFFFFFFF)], w.camera, w.params, out)
-    srv.drain(300.0)
-    assert srv.stats()["iterations"] > len(reqs)          # requests were split across iterations
-    srv.close()
+    try:
+        outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for _, w in reqs]
+        for (key, w), out in zip(reqs, outs):
+            srv.submit(key, descs[(key >> 32, key & 0xFFFFFFFF)], w.camera, w.params, out)
+        srv.drain(300.0)
+        assert srv.stats()["iterations"] > len(reqs)          # requests were split across iterations
+    finally:
+        srv.close()
     reps = []
     for k, ((key, w), out) in enumerate(zip(reqs, outs)):
         sc = pr.Scene(w.scene)
@@ -193,19 +195,21 @@ def test_tight_budget_builds_each_scene_once():
         sc.close()
     batch_bytes = pr.Batch(2, 4096).device_bytes()
     srv = pr.Server(max_active=2, mem_budget_bytes=batch_bytes + need * 3 // 2, max_batch_pixels=4096)
-    outs, tickets = [], []
-    for k in range(6):
-        w = wa if k % 2 == 0 else wb
-        out = torch.empty((32, 48, 4), device="cuda")
-        outs.append(out)
-        tickets.append(srv.submit(100 + k, w.scene, w.camera, w.params, out))   # distinct keys: a load each
-    srv.drain(120.0)
-    st = srv.stats()
-    assert all(srv.poll(t)[1]["status"] == pr.PR_OK for t in tickets)
-    assert st["scene_loads"] == st["cache_misses"] == 6
-    assert st["evictions"] >= 4
-    assert st["cache_bytes"] + st["batch_bytes"] <= batch_bytes + need * 3 // 2
-    srv.close()
+    try:
+        outs, tickets = [], []
+        for k in range(6):
+            w = wa if k % 2 == 0 else wb
+            out = torch.empty((32, 48, 4), device="cuda")
+            outs.append(out)
+            tickets.append(srv.submit(100 + k, w.scene, w.camera, w.params, out))   # distinct keys: a load each
+        srv.drain(120.0)
+        st = srv.stats()
+        assert all(srv.poll(t)[1]["status"] == pr.PR_OK for t in tickets)
+        assert st["scene_loads"] == st["cache_misses"] == 6
+        assert st["evictions"] == 5
+        assert st["cache_bytes"] + st["batch_bytes"] <= batch_bytes + need * 3 // 2
+    finally:
+        srv.close()
     ref = pr.Scene(wa.scene)
     assert torch.equal(ref.trace(wa.camera, wa.params), outs[0])
     ref.close()
@@ -221,6 +225,14 @@ def test_request_completes_before_the_rest_of_its_launch():
     tuning = dict(ctas_per_sm=4, tile_w=16, tile_h=8, queue_chunk=32, megakernel=1)
     srv = pr.Server(mode=pr.PR_SERVE_CONTINUOUS, max_active=4, mem_budget_bytes=16 << 30,
                     max_batch_pixels=4200 * 1000, tuning=tuning)
+    try:
+        same_launch = _early_completion_rounds(srv, big, small, blocker)
+    finally:
+        srv.close()
+    assert same_launch >= 1
+
+
+def _early_completion_rounds(srv, big, small, blocker):
     o_blk = torch.empty((2160, 3840, 4), device="cuda")
     o_big = torch.empty((1080, 1920, 4), device="cuda")
     o_small = torch.empty((64, 64, 4), device="cuda")
@@ -241,5 +253,4 @@ def test_request_completes_before_the_rest_of_its_launch():
             continue               # not in one launch this time (timing): inconclusive
         same_launch += 1
         assert s["t_done"] < b["t_done"] - 2e-4, (s, b)
-    srv.close()
-    assert same_launch >= 1
+    return same_launch

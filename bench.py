@@ -1,11 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark of the procedural ray tracer: Mrays/s and frame latency.
+"""Benchmark of the procedural ray tracer: Mrays/s and frame latency, batched vs plain.
 
-One step = one pass of the whole hot path over the workload: device LBVH
-build (BLASes, instance boxes, TLAS) and one full frame (primary, shadow and
-mirror rays through two-level traversal, Eq. 1 dispatch, intersection and
-closest-hit shaders). Default workload: the teaser-like scene (two pac-men, a
-quaternion Julia set, a Mandelbulb, a mirror ground slab) at 1920x1080.
+Headline workload: a batch of 64 render requests (each its own instanced
+procedural scene of 1..10 000 instances of the 8 primitive types, resolution
+256^2..2048^2, orbit camera). One step = one pass of the whole hot path over
+the batch: the device LBVH build of every request's scene (BLASes, instance
+boxes, TLAS) and one batched launch (CUDA graph, autotuned launch shape) that
+renders every request (primary and shadow rays through two-level traversal,
+Eq. 1 dispatch, intersection and closest-hit shaders). Beside it, the plain
+form: the same builds and one pr_trace launch per request.
+
+Extra blocks: the teaser scene at 1920x1080 (build + frame), the tiny
+analytic scene as 4096 frames per launch, the 100 000-instance field at
+3840x2160 (build + frame), and the serving loop under Poisson arrivals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,12 +38,17 @@ sys.path.insert(0, ROOT)
 import scenes  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
+BATCH = "batch64"
+SINGLE = ("analytic_64x64", "teaser_1080p", "field_100k_2160p")
 # default timed steps per workload: about 0.5-1.5 s of GPU work on a B300
-DEFAULT_STEPS = {"analytic_64x64": 2000, "analytic_64x64_x4096": 500, "teaser_1080p": 2000, "field_100k_2160p": 150}
+DEFAULT_STEPS = {BATCH: 20, "analytic_64x64": 2000, "teaser_1080p": 2000, "field_100k_2160p": 150}
+SERVE_RATES = [10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0]
+BATCH_DESC = ("batch of 64 render requests: instanced procedural fields of 1..10000 instances "
+              "(8 primitive types, log-uniform count), resolutions from {256^2, 512^2, 1024^2, 2048^2}, orbit cameras")
 
 
 def workload_by_name(name: str):
-    if name in ("analytic_64x64", "analytic_64x64_x4096"):
+    if name == "analytic_64x64":
         return scenes.small_analytic()
     if name == "teaser_1080p":
         return scenes.teaser()
@@ -46,17 +58,14 @@ def workload_by_name(name: str):
 
 
 def workload_config(name: str, w) -> dict:
-    d = {"workload": {"analytic_64x64": "tiny analytic scene, 4 AABB primitives, one BLAS",
-                      "analytic_64x64_x4096": "tiny analytic scene, 4096 eye-jittered 64x64 frames per launch",
-                      "teaser_1080p": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
-                      "field_100k_2160p": "instanced field, 100000 instances of 8 procedural types"}[name],
-         "config": name, "width": w.params.width, "height": w.params.height,
-         "instances": int(len(w.scene.inst_blas)), "max_depth": w.params.max_depth,
-         "rays_per_pixel_max": 1 + 1 + (1 if w.params.max_depth >= 2 else 0),
-         "step": "device LBVH build + one frame", "output": "rgb float32 image, 12 B/pixel",
-         "l2": "flushed between timed steps (256 MB write)",
-         "parallelism": "replicas"}
-    return d
+    return {"workload": {"analytic_64x64": "tiny analytic scene, 4 AABB primitives, one BLAS",
+                         "teaser_1080p": "teaser scene: 2 pac-men + quaternion Julia + Mandelbulb + mirror slab",
+                         "field_100k_2160p": "instanced field, 100000 instances of 8 procedural types"}[name],
+            "config": name, "width": w.params.width, "height": w.params.height,
+            "instances": int(len(w.scene.inst_blas)), "max_depth": w.params.max_depth,
+            "rays_per_pixel_max": 1 + 1 + (1 if w.params.max_depth >= 2 else 0),
+            "step": "device LBVH build + one frame", "output": "rgb float32 image, 12 B/pixel",
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
 
 
 class ClockSampler:
@@ -154,18 +163,15 @@ def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tupl
     return float(t.item()), int(r.item())
 
 
-# DRAM traffic of one timed k_trace launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# one ncu capture of this script's own command, L2 flushed before the launch as in the timed
-# loop), per workload and traversal mode. A figure holds only for the kernel sources it was
-# taken on: it is keyed by their SHA-1 and reported as null once they change.
+# DRAM traffic of one timed trace launch (dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture, L2 flushed before the launch as in the timed loop), per workload and traversal
+# mode. A figure holds only for the kernel sources it was taken on: it is keyed by their SHA-1
+# and reported as null once they change.
 TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/csrc/tracer.cuh",
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
+                 "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
-TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    "2f46009b9da347812ca83a8837584c033c9f8967": {"teaser_1080p": 142592 + 306688,
-                                                 "field_100k_2160p": 6126592 + 52024832,
-                                                 "analytic_64x64_x4096": 403456 + 154923008},
-}
+TRACE_TRAFFIC = {}   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
 
 
 def trace_sources_sha1() -> str:
@@ -177,7 +183,7 @@ def trace_sources_sha1() -> str:
     return h.hexdigest()
 
 
-def trace_traffic(workload: str, binary_tlas: bool):
+def trace_traffic(workload: str, binary_tlas: bool = False):
     if binary_tlas:
         return None
     return TRACE_TRAFFIC.get(trace_sources_sha1(), {}).get(workload)
@@ -195,15 +201,185 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def bench_analytic_frames(pr, work, torch, stream, flush, frames=4096, reps=5) -> dict:
+def roofline(work, torch, counters_list, kernel_s: float, kernel: str, traffic_key: str, clocks=None,
+             probe_tflops=None, binary_tlas: bool = False) -> dict:
+    """FP32 roofline of a trace kernel: FMA-pipe FLOPs of the launch (work counters x
+    per-unit counts) over its mean CUDA-event duration, against SMs x 128 x 2 x clock;
+    ALU-pipe and special-function operation rates beside it."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    n_sm = props.multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fma = sum(work.frame_fma_flops(c) for c in counters_list)
+    alu = sum(work.frame_alu_ops(c) for c in counters_list)
+    spec = sum(work.frame_special_ops(c) for c in counters_list)
+    peak = work.fp32_peak_tflops(n_sm, sm_max)
+    achieved = fma / kernel_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": trace_traffic(traffic_key, binary_tlas), "kernel": kernel,
+            "flops_per_launch": fma, "launch_ms": kernel_s * 1e3,
+            "flop_count": "FMA-pipe FLOPs (FFMA 2, FADD/FMUL 1) from the work counters; min/max/compares "
+                          "(ALU pipe) and rcp/sqrt/log (special) are reported beside, not in the FLOPs",
+            "alu_ops_per_launch": alu, "alu_gops_per_s": alu / kernel_s / 1e9,
+            "special_ops_per_launch": spec, "special_gops_per_s": spec / kernel_s / 1e9,
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)"}
+    if clocks:
+        roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(n_sm, clocks["sm_mhz"])
+        roof["frac_at_sampled_clock"] = achieved / roof["peak_at_sampled_clock"]
+    sustained = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if sustained:
+        # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
+        roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(n_sm, float(sustained))
+        roof["frac_at_measured_sustained_clock"] = achieved / roof["peak_at_measured_sustained_clock"]
+    if roof["traffic"]:
+        roof["traffic_gbs"] = roof["traffic"] / kernel_s / 1e9
+        if peaks.get("hbm_gbs"):
+            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / float(peaks["hbm_gbs"])
+    if probe_tflops:
+        roof["peak_fma_probe"] = probe_tflops
+        roof["frac_of_fma_probe"] = achieved / probe_tflops
+    return roof
+
+
+def timed(torch, stream, flush, steps, body, sampler=None):
+    """K timed steps on `stream`, L2 flushed before each (outside the events).
+    body(k) enqueues one step and returns its list of events to record between
+    phases; returns [(ev_start, [ev_phase...])]."""
+    out = []
+    if sampler:
+        sampler.begin()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out.append((e0, body(k)))
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.end()
+    return out
+
+
+def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: int, probe=None,
+                binary_tlas: bool = False, sampler=None) -> dict:
+    """One scene, one frame per step: device LBVH build + pr_trace."""
+    w = workload_by_name(name)
+    H, W = w.params.height, w.params.width
+    with torch.cuda.stream(stream):
+        scene = pr.Scene(w.scene, stream=stream)
+        out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def step(k):
+        e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        scene.build_bvh(stream)
+        e1.record(stream)
+        scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream, binary_tlas=binary_tlas)
+        e2.record(stream)
+        return [e1, e2]
+
+    with torch.cuda.stream(stream):
+        for k in range(warmup):
+            step(k)
+    stream.synchronize()
+    counter.zero_()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev = timed(torch, stream, flush, steps, step, sampler)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(p[1]) for e0, p in ev]
+    build_ms = [e0.elapsed_time(p[0]) for e0, p in ev]
+    trace_ms = [p[0].elapsed_time(p[1]) for e0, p in ev]
+    rays = int(counter.item())
+    n_build, n_trace = scene.kernel_launches()
+    counters = scene.trace_work(w.camera, w.params, stream=stream, binary_tlas=binary_tlas)
+    torch.cuda.synchronize()
+    block = {"workload": workload_config(name, w)["workload"], "config": workload_config(name, w),
+             "value": rays / (sum(step_ms) / 1e3) / 1e6, "unit": "Mrays/s", "steps": steps,
+             "ms_per_step": sum(step_ms) / steps, "rays_per_step": rays / steps,
+             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                            "build_p50": float(np.percentile(build_ms, 50)),
+                            "trace_p50": float(np.percentile(trace_ms, 50))},
+             "gpu_launches_per_step": n_build + n_trace,
+             "roofline": roofline(work, torch, [counters], statistics.mean(trace_ms) / 1e3, "k_trace (megakernel)",
+                                  name, clocks, probe, binary_tlas),
+             "device_error_word": scene.error_word(stream)}
+    block["roofline"]["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
+    block["roofline"]["work_counters"] = {k: v for k, v in counters.items() if v}
+    if clocks:
+        block["clocks"] = clocks
+    block["_scene"], block["_w"], block["_out"] = scene, w, out
+    return block
+
+
+def scene_e2e(pr, torch, stream, block, n_steps: int, warmup: int, world: int) -> dict:
+    """End to end through the public API: host description -> device (pinned staging, one
+    copy), build, frame, image -> pinned host memory, every step; the readback of frame k
+    overlaps frame k+1 (second stream, double-buffered image)."""
+    scene, w, out = block["_scene"], block["_w"], block["_out"]
+    e2e_counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    outs = [out, torch.empty_like(out)]
+    hosts = [torch.empty(tuple(out.shape), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    traced = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def frame(k):
+        i = k % 2
+        if k >= 2:
+            copied[i].synchronize()
+        scene.upload(w.scene, stream)
+        scene.build_bvh(stream)
+        scene.trace(w.camera, w.params, out=outs[i], ray_counter=e2e_counter, stream=stream)
+        traced[i].record(stream)
+        copy_stream.wait_event(traced[i])
+        with torch.cuda.stream(copy_stream):
+            hosts[i].copy_(outs[i], non_blocking=True)
+        copied[i].record(copy_stream)
+
+    serial = []
+    for k in range(warmup + n_steps):
+        torch.cuda.synchronize()
+        if k == warmup:
+            e2e_counter.zero_()
+            torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        frame(k)
+        copied[k % 2].synchronize()
+        if k >= warmup:
+            serial.append(time.perf_counter() - t0)
+    serial_rays = int(e2e_counter.item())
+    for k in range(warmup):
+        frame(k)
+    torch.cuda.synchronize()
+    e2e_counter.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        frame(k)
+    torch.cuda.synchronize()
+    pipe_ms, rays = aggregate_over_ranks((time.perf_counter() - t0) * 1e3, int(e2e_counter.item()), world, "cuda")
+    serial_ms, serial_rays = aggregate_over_ranks(sum(serial) * 1e3, serial_rays, world, "cuda")
+    return {"value": rays / (pipe_ms / 1e3) / 1e6, "unit": "Mrays/s",
+            "h2d_bytes_per_step": int(scene.desc_bytes), "d2h_bytes_per_step": int(out.numel() * 4),
+            "ms_per_step": pipe_ms / n_steps,
+            "mode": f"{n_steps} consecutive frames, each: description to the device, BVH build, frame, image to "
+                    "pinned host memory; the image copy of frame k overlaps frame k+1",
+            "serial": {"value": serial_rays / (serial_ms / 1e3) / 1e6, "unit": "Mrays/s",
+                       "ms_per_step": serial_ms / n_steps, "mode": "one frame at a time, synchronised after each"}}
+
+
+def bench_analytic_frames(pr, work, torch, stream, flush, frames=4096, reps=5, probe=None) -> dict:
     """The tiny analytic scene as a throughput run: 4096 eye-jittered 64x64 frames in one launch."""
     w = scenes.small_analytic()
     cams = pr.CameraArray(scenes.small_analytic_cameras(0, frames))   # marshalled once
     with torch.cuda.stream(stream):
         scene = pr.Scene(w.scene, stream=stream)
-        out = torch.empty((frames, 64, 64, 4), dtype=torch.float32, device="cuda")
+        out = torch.empty((frames, 64, 64, 3), dtype=torch.float32, device="cuda")
         counter = torch.zeros(1, dtype=torch.int64, device="cuda")
-    for _ in range(2):
+    for _ in range(3):
         scene.trace_frames(cams, w.params, out=out, stream=stream)
     stream.synchronize()
     ev = _events(torch, 2 * reps)
@@ -216,88 +392,196 @@ def bench_analytic_frames(pr, work, torch, stream, flush, frames=4096, reps=5) -
     stream.synchronize()
     ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)]
     rays = int(counter.item()) / reps
-    counters = scene.trace_work(None, w.params, out=out, cameras=cams, stream=stream)
-    flops = work.frame_flops(counters)
+    counters = scene.trace_work(None, w.params, cameras=cams, stream=stream)
     avg_s = statistics.mean(ms) / 1e3
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    peak = work.fp32_peak_tflops(props.multi_processor_count, float(measured_peaks().get("sm_max_mhz", 2032.0)))
+    _, n_trace = scene.kernel_launches()
     scene.close()
+    roof = roofline(work, torch, [counters], avg_s, "k_trace (megakernel)", "analytic_64x64_x4096", None, probe)
+    roof["work_counters"] = {k: v for k, v in counters.items() if v}
     return {"workload": "tiny analytic scene: 4096 eye-jittered 64x64 frames, one pr_trace_frames launch",
             "value": rays / avg_s / 1e6, "unit": "Mrays/s", "ms_per_launch": statistics.mean(ms),
-            "rays_per_launch": rays,
-            "roofline": {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / avg_s / 1e12 / peak, "flops_per_launch": flops}}
+            "rays_per_launch": rays, "gpu_launches_per_step": n_trace, "roofline": roof}
 
 
-def bench_batched(pr, torch, stream, flush, n_requests=64, reps=3) -> dict:
-    """Batch: 64 requests of uneven size, one batched wavefront launch (CUDA
-    graph, autotuned launch shape) vs 64 plain per-request launches."""
-    ws = scenes.batch_requests(0, n_requests)
-    total_px = sum(w.params.width * w.params.height for w in ws)
+class BatchBench:
+    """The 64-request batch: scenes, outputs, the batch object and its tuning."""
+
+    def __init__(self, pr, torch, stream, n_requests=64):
+        self.pr, self.torch, self.stream = pr, torch, stream
+        self.ws = scenes.batch_requests(0, n_requests)
+        self.n = n_requests
+        self.total_px = sum(w.params.width * w.params.height for w in self.ws)
+        with torch.cuda.stream(stream):
+            self.objs = [pr.Scene(w.scene, stream=stream) for w in self.ws]
+            self.out_b = [torch.empty((w.params.height, w.params.width, 3), device="cuda") for w in self.ws]
+            self.out_p = [torch.empty((w.params.height, w.params.width, 3), device="cuda") for w in self.ws]
+            self.counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.batch = pr.Batch(n_requests, self.total_px)
+        items = [(o, w.camera, w.params, out) for o, w, out in zip(self.objs, self.ws, self.out_b)]
+        tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
+        key = f"{torch.cuda.get_device_name()}|batch|{n_requests}|{self.total_px}"
+        cache = json.load(open(tune_path)) if os.path.exists(tune_path) else {}
+        if key in cache:
+            self.batch.set_tuning(**cache[key]["tuning"])
+            self.tuned = dict(cache[key], from_cache=True)
+        else:
+            best, best_ms = self.batch.autotune(items, stream=stream)
+            self.tuned = {"tuning": best, "ms": best_ms, "from_cache": False}
+            cache[key] = {"tuning": best, "ms": best_ms}
+            with open(tune_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        self.prepared = self.batch.prepare(items)
+        # kernels of the batched launch per tuning mode: four stages, or one megakernel
+        self.trace_launches = {0: 4, 1: 1, 2: 1}[self.tuned["tuning"]["megakernel"]]
+
+    def build_all(self):
+        for o in self.objs:
+            o.build_bvh(self.stream)
+
+    def batched_step(self, k):
+        e1, e2 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
+        self.build_all()
+        e1.record(self.stream)
+        self.batch.trace(prepared=self.prepared, ray_counter=self.counter, stream=self.stream, graph=True)
+        e2.record(self.stream)
+        return [e1, e2]
+
+    def plain_step(self, k):
+        ev = _events(self.torch, 1 + self.n)
+        self.build_all()
+        ev[0].record(self.stream)
+        for q, (o, w, out) in enumerate(zip(self.objs, self.ws, self.out_p)):
+            o.trace(w.camera, w.params, out=out, ray_counter=self.counter, stream=self.stream)
+            ev[1 + q].record(self.stream)
+        return ev
+
+    def build_launches(self) -> int:
+        return sum(o.kernel_launches()[0] for o in self.objs)
+
+    def close(self):
+        self.batch.close()
+        for o in self.objs:
+            o.close()
+
+
+def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: int, probe=None, sampler=None):
+    """Headline: step = the LBVH builds of the 64 requests' scenes + one batched launch (CUDA
+    graph). The plain form (same builds, one pr_trace per request) is timed beside it."""
+    B = BatchBench(pr, torch, stream)
     with torch.cuda.stream(stream):
-        objs = [pr.Scene(w.scene, stream=stream) for w in ws]
-        outs_plain = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
-        outs_batch = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
-        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
-    batch = pr.Batch(n_requests, total_px)
-    items = [(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs_batch)]
-    tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
-    key = f"{torch.cuda.get_device_name()}|batch|{n_requests}|{total_px}"
-    cache = json.load(open(tune_path)) if os.path.exists(tune_path) else {}
-    if key in cache:
-        batch.set_tuning(**cache[key]["tuning"])
-        tuned = dict(cache[key], from_cache=True)
-    else:
-        best, best_ms = batch.autotune(items, stream=stream)
-        tuned = {"tuning": best, "ms": best_ms, "from_cache": False}
-        cache[key] = {"tuning": best, "ms": best_ms}
-        with open(tune_path, "w") as f:
-            json.dump(cache, f, indent=1)
-
-    def plain_once(record=None):
-        for k, (o, w, out) in enumerate(zip(objs, ws, outs_plain)):
-            o.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream)
-            if record is not None:
-                record[k].record(stream)
-
-    # warm both paths
-    plain_once()
-    batch.trace(items, stream=stream, graph=True)
+        for k in range(warmup):
+            B.batched_step(k)
+            B.plain_step(k)
     stream.synchronize()
-    res = {}
-    for mode in ("plain", "batched_graph", "batched_direct"):
-        counter.zero_()
-        totals, lat = [], []
-        for rep in range(reps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(rep))
-            ev0 = torch.cuda.Event(enable_timing=True)
-            done = _events(torch, n_requests if mode == "plain" else 1)
-            ev0.record(stream)
-            if mode == "plain":
-                plain_once(done)
-            else:
-                batch.trace(items, ray_counter=counter, stream=stream, graph=(mode == "batched_graph"))
-                done[0].record(stream)
-            stream.synchronize()
-            t = [ev0.elapsed_time(e) for e in done]
-            totals.append(t[-1])
-            lat += t if mode == "plain" else [t[0]] * n_requests
-        rays = int(counter.item()) / reps
-        res[mode] = {"value": rays / (statistics.mean(totals) / 1e3) / 1e6, "unit": "Mrays/s",
-                     "ms_per_batch": statistics.mean(totals), "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)), "rays_per_batch": rays}
-    identical = all(torch.equal(a, b) for a, b in zip(outs_plain, outs_batch))
-    out = {"workload": f"batch: {n_requests} requests, resolutions from {{256^2..2048^2}}, "
-                       f"1..10000 instances each, {total_px} pixels",
-           "plain": res["plain"], "batched_graph": res["batched_graph"], "batched_direct": res["batched_direct"],
-           "speedup_graph_vs_plain": res["plain"]["ms_per_batch"] / res["batched_graph"]["ms_per_batch"],
-           "images_identical_to_plain": identical, "autotune": tuned,
-           "batch_device_bytes": batch.device_bytes()}
-    batch.close()
-    for o in objs:
-        o.close()
-    return out
+    B.counter.zero_()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = timed(torch, stream, flush, steps, B.batched_step, sampler)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    rays = int(B.counter.item())
+    step_ms = [e0.elapsed_time(p[1]) for e0, p in ev]
+    build_ms = [e0.elapsed_time(p[0]) for e0, p in ev]
+    trace_ms = [p[0].elapsed_time(p[1]) for e0, p in ev]
+    total_ms, rays_all = aggregate_over_ranks(sum(step_ms), rays, world, "cuda")
+    # plain form, same steps
+    B.counter.zero_()
+    torch.cuda.synchronize()
+    evp = timed(torch, stream, flush, steps, B.plain_step)
+    plain_rays = int(B.counter.item())
+    p_step = [e0.elapsed_time(p[-1]) for e0, p in evp]
+    p_trace = [p[0].elapsed_time(p[-1]) for e0, p in evp]
+    p_lat = [e0.elapsed_time(e) for e0, p in evp for e in p[1:]]        # each request's completion
+    identical = all(torch.equal(a, b) for a, b in zip(B.out_b, B.out_p))
+    counters = [o.trace_work(w.camera, w.params, stream=stream) for o, w in zip(B.objs, B.ws)]
+    torch.cuda.synchronize()
+    kernel = {0: "k_wf_primary/shadow/mirror/resolve (wavefront stages)", 1: "k_batch_mega (persistent)",
+              2: "k_batch_mega_tiles (one CTA per tile)"}[B.tuned["tuning"]["megakernel"]]
+    roof = roofline(work, torch, counters, statistics.mean(trace_ms) / 1e3, kernel, BATCH, clocks, probe)
+    roof["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
+    res = {"value": rays_all / (total_ms / 1e3) / 1e6, "total_ms": total_ms, "rays": rays,
+           "step_ms": step_ms, "build_ms": build_ms, "trace_ms": trace_ms, "clocks": clocks, "roofline": roof,
+           "gpu_launches_per_step": B.build_launches() + B.trace_launches,
+           "plain": {"value": plain_rays / (sum(p_step) / 1e3) / 1e6, "unit": "Mrays/s",
+                     "ms_per_step": sum(p_step) / steps, "trace_ms_per_step": sum(p_trace) / steps,
+                     "latency_ms": {"p50": float(np.percentile(p_lat, 50)), "p99": float(np.percentile(p_lat, 99))},
+                     "gpu_launches_per_step": B.build_launches() + B.n,
+                     "form": "the same 64 builds, then one pr_trace launch per request (64 launches)"},
+           "images_identical_to_plain": identical, "autotune": B.tuned,
+           "batch_device_bytes": B.batch.device_bytes(), "B": B}
+    return res
+
+
+def batch_e2e(pr, torch, stream, B, n_steps: int, warmup: int, world: int) -> dict:
+    """End to end through the public API with host buffers: every step uploads the 64 scene
+    descriptions from host memory (pinned staging, one copy per scene), builds the 64 BVHs,
+    renders the batch in one graph launch and copies the 64 images to pinned host memory;
+    the image copies of step k overlap step k+1 (second stream, double-buffered images)."""
+    outs = [B.out_b, [torch.empty_like(o) for o in B.out_b]]
+    prepared = [B.prepared, B.batch.prepare([(o, w.camera, w.params, out)
+                                             for o, w, out in zip(B.objs, B.ws, outs[1])])]
+    hosts = [[torch.empty(tuple(o.shape), dtype=torch.float32, pin_memory=True) for o in B.out_b] for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    traced = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def step(k):
+        i = k % 2
+        if k >= 2:
+            copied[i].synchronize()
+        for o, w in zip(B.objs, B.ws):
+            o.upload(w.scene, stream)
+            o.build_bvh(stream)
+        B.batch.trace(prepared=prepared[i], ray_counter=counter, stream=stream, graph=True)
+        traced[i].record(stream)
+        copy_stream.wait_event(traced[i])
+        with torch.cuda.stream(copy_stream):
+            for h, d in zip(hosts[i], outs[i]):
+                h.copy_(d, non_blocking=True)
+        copied[i].record(copy_stream)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    counter.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        step(k)
+    torch.cuda.synchronize()
+    pipe_ms, rays = aggregate_over_ranks((time.perf_counter() - t0) * 1e3, int(counter.item()), world, "cuda")
+    return {"value": rays / (pipe_ms / 1e3) / 1e6, "unit": "Mrays/s",
+            "h2d_bytes_per_step": int(sum(o.desc_bytes for o in B.objs)),
+            "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in B.out_b)),
+            "ms_per_step": pipe_ms / n_steps,
+            "mode": f"{n_steps} consecutive batches, each: 64 scene descriptions from host memory to the device, "
+                    "64 BVH builds, one batched graph launch, 64 RGB images to pinned host memory; the image "
+                    "copies of batch k overlap batch k+1"}
+
+
+def batch_cpu_baseline(ws, fraction: int = 64, seed: int = 4) -> dict:
+    """The FP64 oracle, as it stands, on a seeded 1/64 pixel sample of every request."""
+    import oracle
+    threads = os.cpu_count() or 1
+    rays = px = 0
+    t0 = time.perf_counter()
+    for q, w in enumerate(ws):
+        n = max(1, w.params.width * w.params.height // fraction)
+        ref = oracle.render(w, pixels=scenes.sample_pixels(w.params.width, w.params.height, n, seed=seed + q),
+                            threads=threads)
+        rays += int(ref["rays"].sum())
+        px += n
+    dt = time.perf_counter() - t0
+    return {"value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+            "sample": f"seeded 1/{fraction} pixel sample of each of the {len(ws)} requests ({px} pixels, {rays} "
+                      f"rays, {dt:.1f} s, FP64); Mrays/s of the sample, extrapolated to the whole batch"}
 
 
 class _RequestPool:
@@ -315,7 +599,7 @@ class _RequestPool:
         return key, self.descs[(kind, sseed)], wl.camera, wl.params
 
 
-def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=60.0, seed=0) -> list:
+def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=40.0, seed=0) -> list:
     """Poisson arrivals at each rate; per-request latency = completion - submission."""
     out_rows = []
     ring = [torch.empty(1920 * 1080 * 4, dtype=torch.float32, device="cuda") for _ in range(128)]
@@ -348,19 +632,37 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=6
         lat = np.array([s["t_done"] - s["t_submit"] for s in st]) * 1e3
         span = max(s["t_done"] for s in st) - min(s["t_submit"] for s in st)
         ok = sum(1 for s in st if s["status"] == 0)
-        # where the latency goes: waiting for the scene (build on a miss) and a slot, waiting for
-        # the first launch, and from the first launch to completion
+        # where the latency goes: waiting for the scene (a build on a miss) and a slot, waiting
+        # for the first launch, and from the first launch to completion
         phase = lambda a, b: np.array([s[b] - s[a] for s in st if s["status"] == 0]) * 1e3
         breakdown = {name: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
                      for name, v in (("admit_ms", phase("t_submit", "t_admit")),
                                      ("launch_wait_ms", phase("t_admit", "t_first_launch")),
                                      ("in_flight_ms", phase("t_first_launch", "t_done"))) if len(v)}
+        hits = np.array([s["cache_hit"] for s in st], bool)
         out_rows.append({"rate_per_s": lam, "requests": n, "ok": ok, "mode": "continuous" if mode == 0 else "plain",
                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "p99_ms_cache_hits": float(np.percentile(lat[hits], 99)) if hits.any() else None,
                          "value": stats["rays"] / span / 1e6, "unit": "Mrays/s", "makespan_s": span,
                          "iterations": stats["iterations"], "cache_hits": stats["cache_hits"],
-                         "cache_misses": stats["cache_misses"], "breakdown": breakdown})
+                         "cache_misses": stats["cache_misses"], "scene_loads": stats["scene_loads"],
+                         "breakdown": breakdown})
     return out_rows
+
+
+def serving_block(pr, torch, rates, n_requests, max_seconds, tuning) -> dict:
+    rows = []
+    for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
+        rows += bench_serving(pr, torch, rates, n_requests, mode, tuning, max_seconds)
+    cont = {r["rate_per_s"]: r for r in rows if r["mode"] == "continuous"}
+    plain = {r["rate_per_s"]: r for r in rows if r["mode"] == "plain"}
+    compare = [{"rate_per_s": lam, "mrays_continuous_over_plain": cont[lam]["value"] / plain[lam]["value"],
+                "p99_continuous_ms": cont[lam]["p99_ms"], "p99_plain_ms": plain[lam]["p99_ms"],
+                "p50_continuous_ms": cont[lam]["p50_ms"], "p50_plain_ms": plain[lam]["p50_ms"]} for lam in rates]
+    return {"workload": "serving: Poisson arrivals, teaser / instanced-field (100000 instances) scenes 50/50 from "
+                        "pools of 16, resolution 512^2..1920x1080, orbit cameras, 100 GB budget, 64 slots, "
+                        "8 Mpx per continuous-batching iteration",
+            "tuning": tuning, "points": rows, "continuous_vs_plain": compare}
 
 
 def cpu_baseline(w, budget_s: float = 15.0) -> dict:
@@ -370,11 +672,10 @@ def cpu_baseline(w, budget_s: float = 15.0) -> dict:
     n_pix = w.params.width * w.params.height
     probe = scenes.sample_pixels(w.params.width, w.params.height, min(2000, n_pix), seed=3)
     t0 = time.perf_counter()
-    ref = oracle.render(w, pixels=probe, threads=threads)
+    oracle.render(w, pixels=probe, threads=threads)
     dt = time.perf_counter() - t0
     n = int(min(n_pix, max(len(probe), len(probe) * budget_s / max(dt, 1e-3) * 0.8)))
     pix = scenes.sample_pixels(w.params.width, w.params.height, n, seed=4)
-    # a frame smaller than the budget is rendered whole, repeatedly, for about 10 s
     rays, passes = 0, 0
     t0 = time.perf_counter()
     while True:
@@ -390,34 +691,50 @@ def cpu_baseline(w, budget_s: float = 15.0) -> dict:
 
 
 def run_reference(args):
-    """Reference arm: the CPU FP64 oracle, timed on the host cores."""
+    """Reference arm: the CPU FP64 oracle, timed on the host cores, on the headline's workload;
+    each step renders a bounded seeded sample of it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
-    w = workload_by_name(args.workload)
     threads = os.cpu_count() or 1
-    n_pix = w.params.width * w.params.height
-    per_step = min(n_pix, max(4096, n_pix // 32))     # ~65k pixels of a 1080p frame per step
+    if args.workload == BATCH:
+        ws = scenes.batch_requests(0, 64)
+        config = {"workload": BATCH_DESC, "config": BATCH, "requests": 64,
+                  "pixels": sum(w.params.width * w.params.height for w in ws)}
+        frac = 512
+        sample_desc = f"seeded 1/{frac} pixel sample of each of the 64 requests per step"
+    else:
+        ws = [workload_by_name(args.workload)]
+        config = workload_config(args.workload, ws[0])
+        frac = 32
+        sample_desc = f"seeded 1/{frac} pixel sample of the frame per step"
     times, rays = [], 0
     for k in range(args.warmup + args.steps):
-        pix = scenes.sample_pixels(w.params.width, w.params.height, per_step, seed=100 + k)
         t0 = time.perf_counter()
-        ref = oracle.render(w, pixels=pix, threads=threads)
+        r = 0
+        for q, w in enumerate(ws):
+            n = max(1, w.params.width * w.params.height // frac)
+            pix = scenes.sample_pixels(w.params.width, w.params.height, n, seed=100 + 97 * k + q)
+            r += int(oracle.render(w, pixels=pix, threads=threads)["rays"].sum())
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
-            rays += int(ref["rays"].sum())
+            rays += r
     total = sum(times)
     value = rays / total / 1e6
     line = {"impl": "reference", "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, w),
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} seeded pixels of {n_pix} per step"},
+                             "sample": sample_desc},
             "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _strip(block: dict) -> dict:
+    return {k: v for k, v in block.items() if not k.startswith("_")}
 
 
 def run_ours(args):
@@ -432,222 +749,92 @@ def run_ours(args):
     import paper_2012_10357_b300 as pr
     from paper_2012_10357_b300 import work
 
-    w = workload_by_name(args.workload)
-    frames = None
-    if args.workload == "analytic_64x64_x4096":
-        frames = pr.CameraArray(scenes.small_analytic_cameras(0, 4096))    # marshalled once, outside the timed region
     stream = torch.cuda.Stream()
-    H, W = w.params.height, w.params.width
     with torch.cuda.stream(stream):
-        scene = pr.Scene(w.scene, stream=stream)
-        # the image as r, g, b floats per pixel (PR_TRACE_OUTPUT_RGB: the alpha channel, always 1, is not stored)
-        out = torch.empty(((len(frames),) if frames else ()) + (H, W, 3), dtype=torch.float32, device="cuda")
-        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
+    probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
 
-    def do_trace():
-        if frames:
-            scene.trace_frames(frames, w.params, out=out, ray_counter=counter, stream=stream)
-        else:
-            scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream,
-                        binary_tlas=args.binary_tlas)
-
-    def step():
-        scene.build_bvh(stream)
-        do_trace()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
-    counter.zero_()
-    torch.cuda.synchronize()
-
-    def timed_region():
-        counter.zero_()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    def measure(fn):
+        """The timed region, taken once more if the clocks show a slowdown or a leftover lock."""
         sampler = ClockSampler(torch.cuda.current_device())
-        sampler.start()
-        barrier()
-        torch.cuda.synchronize()
-        sampler.begin()
-        with torch.cuda.stream(stream):
-            for k in range(args.steps):
-                flush.fill_(float(k))                 # evict L2 between timed steps
-                ev[k][0].record(stream)
-                scene.build_bvh(stream)
-                ev[k][1].record(stream)
-                do_trace()
-                ev[k][2].record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize()
-        sampler.end()
-        barrier()
-        return ev, sampler.stop()
+        res = fn(sampler)
+        first = None
+        if ClockSampler.rejected(res["clocks"]):
+            first = res["clocks"]
+            res = fn(ClockSampler(torch.cuda.current_device()))
+        if res["clocks"] is not None and first is not None:
+            res["clocks"]["remeasured_after"] = first
+        return res
 
-    ev, clocks = timed_region()
-    first_clocks = None
-    if ClockSampler.rejected(clocks):
-        first_clocks = clocks
-        ev, clocks = timed_region()
-    if clocks is not None and first_clocks is not None:
-        clocks["remeasured_after"] = first_clocks
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    trace_ms = [b.elapsed_time(c) for a, b, c in ev]
-    build_ms = [a.elapsed_time(b) for a, b, c in ev]
-    total_ms = sum(step_ms)
-    rays = int(counter.item())
-    n_build, n_trace = scene.kernel_launches()
-    err = scene.error_word(stream)
+    if args.workload == BATCH:
+        res = measure(lambda smp: bench_batch(pr, work, torch, stream, flush, args.steps, args.warmup, world,
+                                              probe_tflops, smp))
+        B = res["B"]
+        e2e = None if args.no_e2e else batch_e2e(pr, torch, stream, B, max(3, min(args.steps, 10)), 2, world)
+        config = {"workload": BATCH_DESC, "config": BATCH, "requests": B.n, "pixels": B.total_px,
+                  "instances_per_request": [int(len(w.scene.inst_blas)) for w in B.ws],
+                  "resolutions": [w.params.width for w in B.ws], "max_depth": 1, "rays_per_pixel_max": 2,
+                  "step": "device LBVH builds of the 64 scenes + one batched launch (CUDA graph, autotuned shape)",
+                  "output": "rgb float32 images, 12 B/pixel", "l2": "flushed between timed steps (256 MB write); "
+                  "the batch's images (1.0 GB) exceed L2", "parallelism": "replicas", "tuning": B.tuned["tuning"]}
+        step_ms, build_ms, trace_ms = res["step_ms"], res["build_ms"], res["trace_ms"]
+        head = {"value": res["value"], "ms_per_step": res["total_ms"] / args.steps, "config": config,
+                "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                               "per_request": "every request of a batch completes with the batch's launch",
+                               "build_p50": float(np.percentile(build_ms, 50)),
+                               "trace_p50": float(np.percentile(trace_ms, 50))},
+                "rays_per_step": res["rays"] / args.steps, "roofline": res["roofline"], "e2e": e2e,
+                "gpu_launches": res["gpu_launches_per_step"] * args.steps, "clocks": res["clocks"],
+                "plain": res["plain"],
+                "batched_vs_plain": {"mrays": res["value"] / res["plain"]["value"],
+                                     "p99_batched_ms": float(np.percentile(step_ms, 99)),
+                                     "p99_plain_ms": res["plain"]["latency_ms"]["p99"]},
+                "images_identical_to_plain": res["images_identical_to_plain"], "autotune": res["autotune"],
+                "batch_device_bytes": res["batch_device_bytes"],
+                "device_error_word": max(o.error_word(stream) for o in B.objs)}
+        tuning = B.tuned["tuning"]
+        ws_for_cpu = B.ws
+        B.close()
+    else:
+        res = measure(lambda smp: bench_scene(pr, work, torch, stream, flush, args.workload, args.steps, args.warmup,
+                                              probe_tflops, args.binary_tlas, smp))
+        e2e = None if args.no_e2e else scene_e2e(pr, torch, stream, res, max(3, min(args.steps, 100)), args.warmup,
+                                                  world)
+        total_ms, rays_all = aggregate_over_ranks(res["ms_per_step"] * args.steps, res["rays_per_step"] * args.steps,
+                                                  world, "cuda")
+        head = {"value": rays_all / (total_ms / 1e3) / 1e6, "ms_per_step": total_ms / args.steps,
+                "config": res["config"], "latency_ms": res["latency_ms"], "rays_per_step": res["rays_per_step"],
+                "roofline": res["roofline"], "e2e": e2e, "gpu_launches": res["gpu_launches_per_step"] * args.steps,
+                "clocks": res.get("clocks"), "device_error_word": res["device_error_word"]}
+        tuning = None
+        ws_for_cpu = None
+        res["_scene"].close()
 
-    # end to end through the public API: host description -> device (pinned staging, one copy),
-    # build, frame, image -> pinned host memory, every step
-    e2e = None
-    if not args.no_e2e:
-        n_e2e = max(3, min(args.steps, 100))   # enough frames that the stream's fill and drain are small
-        e2e_counter = torch.zeros(1, dtype=torch.int64, device="cuda")
-        outs = [out, torch.empty_like(out)]
-        hosts = [torch.empty(tuple(out.shape), dtype=torch.float32, pin_memory=True) for _ in range(2)]
-        copy_stream = torch.cuda.Stream()
-        traced = [torch.cuda.Event(), torch.cuda.Event()]
-        copied = [torch.cuda.Event(), torch.cuda.Event()]
-
-        def e2e_frame(k):
-            i = k % 2
-            if k >= 2:
-                copied[i].synchronize()      # frame k-2 has reached the host before its buffers are reused
-            scene.upload(w.scene, stream)
-            scene.build_bvh(stream)
-            if frames:
-                scene.trace_frames(frames, w.params, out=outs[i], ray_counter=e2e_counter, stream=stream)
-            else:
-                scene.trace(w.camera, w.params, out=outs[i], ray_counter=e2e_counter, stream=stream)
-            traced[i].record(stream)
-            copy_stream.wait_event(traced[i])
-            with torch.cuda.stream(copy_stream):
-                hosts[i].copy_(outs[i], non_blocking=True)
-            copied[i].record(copy_stream)
-
-        # one frame at a time (each step's latency)
-        serial_times = []
-        for k in range(args.warmup + n_e2e):
-            torch.cuda.synchronize()
-            if k == args.warmup:
-                e2e_counter.zero_()
-                torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2e_frame(k)
-            copied[k % 2].synchronize()
-            if k >= args.warmup:
-                serial_times.append(time.perf_counter() - t0)
-        serial_rays = int(e2e_counter.item())
-        # a stream of frames: the readback of frame k overlaps the upload, build and trace of frame k+1
-        for k in range(args.warmup):
-            e2e_frame(k)
-        torch.cuda.synchronize()
-        e2e_counter.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(n_e2e):
-            e2e_frame(k)
-        torch.cuda.synchronize()
-        pipe_s = time.perf_counter() - t0
-        e2e_rays = int(e2e_counter.item())
-        desc_bytes = scene.desc_bytes
-        # every rank streams its own frames; the job's time is the slowest rank's
-        pipe_ms, e2e_rays = aggregate_over_ranks(pipe_s * 1e3, e2e_rays, world, "cuda")
-        serial_ms, serial_rays = aggregate_over_ranks(sum(serial_times) * 1e3, serial_rays, world, "cuda")
-        pipe_s = pipe_ms / 1e3
-        e2e = {"value": e2e_rays / pipe_s / 1e6, "unit": "Mrays/s",
-               "h2d_bytes_per_step": int(desc_bytes) + (40 * len(frames) if frames else 0),
-               "d2h_bytes_per_step": int(out.numel() * 4),
-               "ms_per_step": 1e3 * pipe_s / n_e2e,
-               "mode": f"{n_e2e} consecutive frames, each: description to the device, BVH build, frame, "
-                       "image to pinned host memory; the image copy of frame k overlaps frame k+1 "
-                       "(second stream, double-buffered image)",
-               "serial": {"value": serial_rays / (serial_ms / 1e3) / 1e6, "unit": "Mrays/s",
-                          "ms_per_step": serial_ms / n_e2e,
-                          "mode": "one frame at a time, synchronised after each"}}
-
-    total_all, rays_all = aggregate_over_ranks(total_ms, rays, world, "cuda")
+    extra = {}
+    if not args.no_extra and rank == 0:
+        for name, steps in (("teaser_1080p", 500), ("field_100k_2160p", 60)):
+            if name != args.workload:
+                b = bench_scene(pr, work, torch, stream, flush, name, steps, 3, probe_tflops)
+                b["_scene"].close()
+                extra[name] = _strip(b)
+        extra["analytic_4096_frames"] = bench_analytic_frames(pr, work, torch, stream, flush, probe=probe_tflops)
+        if tuning is None:
+            tuning = {"ctas_per_sm": 4, "tile_w": 16, "tile_h": 8, "queue_chunk": 32, "megakernel": 2}
+        extra["serving"] = serving_block(pr, torch, args.serve_rates, args.serve_requests, args.serve_max_seconds,
+                                         tuning)
 
     if rank != 0:
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
-
-    value = rays_all / (total_all / 1e3) / 1e6
-
-    # roofline of the dominant kernel (the trace megakernel): FP32 ALU bound
-    counters = scene.trace_work(w.camera, w.params, stream=stream, cameras=frames, binary_tlas=args.binary_tlas)
-    torch.cuda.synchronize()
-    flops = work.frame_flops(counters)
-    trace_avg_s = statistics.mean(trace_ms) / 1e3
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tflops = work.fp32_peak_tflops(props.multi_processor_count, sm_max)
-    achieved_tflops = flops / trace_avg_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak_tflops, "traffic": trace_traffic(args.workload, args.binary_tlas),
-            "kernel": "k_trace (megakernel)", "flops_per_launch": flops,
-            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of measured)",
-            "trace_share_of_step": sum(trace_ms) / total_ms,
-            "work_counters": {k: v for k, v in counters.items() if v}}
-    if clocks:
-        roof["peak_at_sampled_clock"] = work.fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
-        roof["frac_at_sampled_clock"] = achieved_tflops / roof["peak_at_sampled_clock"]
-    sustained = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
-    if sustained:
-        # the SM clock the driver saw under a seconds-long dense GEMM at the power cap
-        roof["peak_at_measured_sustained_clock"] = work.fp32_peak_tflops(props.multi_processor_count, float(sustained))
-        roof["frac_at_measured_sustained_clock"] = achieved_tflops / roof["peak_at_measured_sustained_clock"]
-    if roof["traffic"]:
-        # DRAM bytes of a launch over its mean duration, against the measured copy bandwidth
-        roof["traffic_gbs"] = roof["traffic"] / trace_avg_s / 1e9
-        if peaks.get("hbm_gbs"):
-            roof["traffic_frac_of_hbm"] = roof["traffic_gbs"] / float(peaks["hbm_gbs"])
-    # measured FP32 FMA throughput (all SMs, 8 independent FMA chains per thread)
-    probe_tflops, _ = pr.fma_peak_probe(16384, stream=stream)
-    roof["peak_fma_probe"] = probe_tflops
-    roof["frac_of_fma_probe"] = achieved_tflops / probe_tflops if probe_tflops > 0 else None
-
-    extra = {}
-    if not args.no_extra:
-        extra["analytic_4096_frames"] = bench_analytic_frames(pr, work, torch, stream, flush)
-        extra["batched"] = bench_batched(pr, torch, stream, flush)
-        tuning = extra["batched"]["autotune"]["tuning"]
-        rows = []
-        for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
-            rows += bench_serving(pr, torch, args.serve_rates, args.serve_requests, mode, tuning)
-        extra["serving"] = {"workload": "serving: Poisson arrivals, teaser / instanced-field (100000 instances) scenes "
-                                        "50/50 from pools of 16, resolution 512^2..1920x1080, orbit cameras, "
-                                        "100 GB budget, 64 slots, 8 Mpx per continuous-batching iteration",
-                            "points": rows}
-
-    line = {
-        "metric": "Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_all / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args.workload, w),
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "build_p50": float(np.percentile(build_ms, 50)), "trace_p50": float(np.percentile(trace_ms, 50))},
-        "rays_per_step": rays / args.steps,
-        "roofline": roof,
-        "e2e": e2e,
-        "gpu_launches": (n_build + n_trace) * args.steps,
-        "clocks": clocks,
-        "device_error_word": err,
-        **extra,
-    }
+    line = {"metric": "Mrays/s", "value": head["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", **head, **extra}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_budget)
+        line["cpu_baseline"] = (batch_cpu_baseline(ws_for_cpu) if ws_for_cpu is not None
+                                else cpu_baseline(workload_by_name(args.workload), args.cpu_budget))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -665,10 +852,9 @@ def run_serve_sweep(args):
         cache = json.load(open(tune_path))
         mine = [v for k, v in cache.items() if k.startswith(torch.cuda.get_device_name() + "|batch")]
         tuning = mine[0]["tuning"] if mine else None
-    rows = []
-    for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
-        rows += bench_serving(pr, torch, args.serve_rates, args.serve_requests, mode, tuning, args.serve_max_seconds)
-    print(json.dumps({"metric": "serving p50/p99 latency and Mrays/s", "points": rows, "tuning": tuning}), flush=True)
+    tuning = tuning or {"ctas_per_sm": 4, "tile_w": 16, "tile_h": 8, "queue_chunk": 32, "megakernel": 2}
+    block = serving_block(pr, torch, args.serve_rates, args.serve_requests, args.serve_max_seconds, tuning)
+    print(json.dumps({"metric": "serving p50/p99 latency and Mrays/s", **block}), flush=True)
 
 
 def main():
@@ -678,13 +864,14 @@ def main():
                     help="timed steps (default: about 0.5-1.5 s of GPU work for the workload; 20 for the reference)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["analytic_64x64", "analytic_64x64_x4096", "teaser_1080p", "field_100k_2160p"], default="teaser_1080p")
+    ap.add_argument("--workload", choices=[BATCH, *SINGLE], default=BATCH)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 4096-frame throughput, batched and serving blocks")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[30.0, 1000.0])
-    ap.add_argument("--serve-requests", type=int, default=120)
-    ap.add_argument("--serve-max-seconds", type=float, default=60.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the teaser, 4096-frame, 100k-field and serving blocks")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=SERVE_RATES)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-max-seconds", type=float, default=40.0)
     ap.add_argument("--serve-only", action="store_true", help="only the serving sweep (both modes), one JSON line")
     ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

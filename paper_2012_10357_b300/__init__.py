@@ -428,8 +428,13 @@ class Batch:
                 arr[k].row_begin, arr[k].row_count = int(it[4]), int(it[5])
         return arr
 
-    def trace(self, items, ray_counter=None, stream=None, graph: bool = False):
-        arr = self._requests(items)
+    def prepare(self, items):
+        """Marshal a request list once, for repeated trace(prepared=...) calls."""
+        return self._requests(items)
+
+    def trace(self, items=None, ray_counter=None, stream=None, graph: bool = False, prepared=None):
+        arr = prepared if prepared is not None else self._requests(items)
+        items = arr
         self._keep = arr
         fn = _lib.pr_trace_batch_graph if graph else _lib.pr_trace_batch
         _check(fn(self._h, len(items), arr, _dptr(ray_counter), _stream_handle(stream)),

@@ -53,6 +53,13 @@ struct Layout {
   std::vector<uint32_t> leaf_gq;     // pairs (g, q)
   std::vector<int> blas_info;        // 4 ints per BLAS
   uint32_t n_leaves = 0, n_blas_nodes = 0, max_large = 0;
+  // every hit group's intersection shader is analytic (sphere, box, pac-man) or
+  // absent (triangles): no sphere tracing anywhere in the scene
+  bool analytic_only = true;
+  // bound on the traversal stack entries of any ray: a binary tree of n
+  // leaves is at most n - 1 deep and a ray holds at most one entry per level
+  // of the TLAS and of one BLAS below it
+  uint32_t stack_bound = 0;
 };
 
 pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
@@ -141,7 +148,9 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
     L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | (tri ? kTriBit : 0u) | first) : 0;
     L.n_blas_nodes += n - 1;
     if (n > kSmallMax) L.max_large = std::max(L.max_large, n);
+    L.stack_bound = std::max(L.stack_bound, n - 1);
   }
+  L.stack_bound += L.n_inst ? L.n_inst - 1 : 0;
   if (L.n_inst > kSmallMax) L.max_large = std::max(L.max_large, L.n_inst);
   uint64_t max_index = 0;
   for (uint32_t k = 0; k < L.n_inst; ++k) {
@@ -164,6 +173,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
     if (ahs != PR_NONE && ahs != PR_AHS_CUTOUT) return fail(PR_ERR_INVALID_ARG, "unknown any-hit shader id");
     if (ahs == PR_AHS_CUTOUT && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN)
       return fail(PR_ERR_INVALID_ARG, "any-hit shaders need an analytic intersection shader (sphere, box, pac-man)");
+    if (is != PR_NONE && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN) L.analytic_only = false;
   }
   for (uint32_t r = 0; r < L.n_rec; ++r) {
     if (d->sbt[4 * r] >= L.n_hg) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " hit group out of range");
@@ -624,6 +634,9 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
   T.ambient = p->ambient;
   T.out = (float4*)out_rgba;
   T.aov = out_aov;
+  // scenes without sphere tracing whose trees are shallow enough for the
+  // short stack take the analytic kernel (same arithmetic, fewer registers)
+  T.analytic_small = s->L.analytic_only && s->L.stack_bound <= (uint32_t)kShortStackDepth && !T.S.tlas4;
   T.counter = (unsigned long long*)counter;
   T.work = (unsigned long long*)work;
   s->trace_launches = launch_trace(T, st);

@@ -82,6 +82,7 @@ struct TraceLaunch {
   pr_aov* aov;
   unsigned long long* counter;
   unsigned long long* work;   // non-null: instrumented variant, adds WorkCounters
+  bool analytic_small;        // analytic shaders only and stack need <= kShortStackDepth
 };
 int launch_trace(const TraceLaunch& L, cudaStream_t s);
 // Device bytes of one camera basis (TraceLaunch::bases holds n_frames of them).

@@ -10,6 +10,8 @@ namespace pr {
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kTriBit = 0x40000000u;    // a BLAS leaf ref of a triangle (kLeafBit | kTriBit | leaf)
 constexpr int kStackDepth = (int)PR_STACK_DEPTH;
+// Stack of the analytic kernel variant, for scenes whose stack bound fits
+constexpr int kShortStackDepth = 8;
 constexpr uint32_t kErrSbt = 1u << PR_ERR_SBT_INDEX;
 constexpr uint32_t kErrStack = 1u << PR_ERR_STACK_OVERFLOW;
 constexpr int kEmptySlot = 0x7FFFFFFF;   // unused child slot of a 4-wide node

@@ -504,6 +504,8 @@ static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* 
 }
 
 // Object-space normal at the accepted hit (called once per shaded hit).
+// kAnalytic: only analytic shaders occur (no estimator stencil compiled in).
+template <bool kAnalytic = false>
 __device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, float3 p, uint32_t attr, float h,
                                                 float3 d, WorkCounters* wc = nullptr) {
   switch (id) {
@@ -524,6 +526,7 @@ __device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, 
       return f3(sa, attr == 1 ? -ca : ca, 0.f);   // -n_k
     }
     default: {
+      if (kAnalytic) return -normalize3(d);
       const float3 g = de_stencil(id, prm, p, h, wc);
       float gl2 = dot3(g, g);
       return gl2 > 0.f ? g * rsqrtf(gl2) : -normalize3(d);

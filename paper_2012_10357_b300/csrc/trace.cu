@@ -52,8 +52,17 @@ __global__ void __launch_bounds__(128) k_camera_bases(const pr_camera* cams, uin
 #define PR_WARP_TILE_W_WIDE 4
 #endif
 
-template <bool kStats, int kWarpW>
-__global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, unsigned long long* work) {
+// kAnalytic: scenes without sphere-traced shaders whose stack bound fits the
+// short stack (kShortStackDepth entries, 4 KB per CTA instead of 32 KB); the
+// estimator code is not compiled in, so the kernel fits 64 registers and twice
+// as many CTAs stay resident. Same arithmetic, same bits.
+#ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC
+#define PR_TRACE_MIN_BLOCKS_ANALYTIC 8
+#endif
+
+template <bool kStats, int kWarpW, bool kAnalytic>
+__global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC : PR_TRACE_MIN_BLOCKS)
+    k_trace(Params P, unsigned long long* work) {
   static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
   const SceneView& S = P.S;
   WorkCounters wcl;
@@ -76,13 +85,14 @@ __global__ void __launch_bounds__(128, PR_TRACE_MIN_BLOCKS) k_trace(Params P, un
   }
   uint32_t rays = 0;
   if (valid) {
-    PR_DECLARE_STACK(128);
+    PR_DECLARE_STACK_N(128, kAnalytic ? kShortStackDepth : kStackDepth);
     const float3 eye = cb->eye;
     const float3 d = camera_ray(*cb, x, y);
     const float eps = scene_eps(S, P.eps_rel);
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
-    const float3 color = render_pixel<kStats>(S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
+    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth>(
+        S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
     if (P.flags & PR_TRACE_OUTPUT_RGB) {
       float* o = reinterpret_cast<float*>(P.out) + 3 * pix;
       o[0] = color.x;
@@ -134,11 +144,14 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
   P.counter = L.counter;
   dim3 grid((L.width + 15) / 16, (L.height + 7) / 8, L.n_frames);
   if (L.S.tlas4) {
-    if (L.work) k_trace<true, PR_WARP_TILE_W_WIDE><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W_WIDE><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.work) k_trace<true, PR_WARP_TILE_W_WIDE, false><<<grid, 128, 0, s>>>(P, L.work);
+    else k_trace<false, PR_WARP_TILE_W_WIDE, false><<<grid, 128, 0, s>>>(P, nullptr);
+  } else if (L.analytic_small) {
+    if (L.work) k_trace<true, PR_WARP_TILE_W, true><<<grid, 128, 0, s>>>(P, L.work);
+    else k_trace<false, PR_WARP_TILE_W, true><<<grid, 128, 0, s>>>(P, nullptr);
   } else {
-    if (L.work) k_trace<true, PR_WARP_TILE_W><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.work) k_trace<true, PR_WARP_TILE_W, false><<<grid, 128, 0, s>>>(P, L.work);
+    else k_trace<false, PR_WARP_TILE_W, false><<<grid, 128, 0, s>>>(P, nullptr);
   }
   return launches + 1;
 }

@@ -53,7 +53,9 @@ __device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3
   rref = __float_as_int(e.y);
 }
 
-// Intersection shader dispatch on the hit group's shader id.
+// Intersection shader dispatch on the hit group's shader id (kAnalytic: the
+// scene has no sphere-traced shader, so that code is not compiled in).
+template <bool kAnalytic>
 __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, const float4* prm, float3 o, float3 d,
                                                  float tmin, float t_lo, float t_hi, float eps, uint32_t max_steps,
                                                  IsResult& r, WorkCounters* wc) {
@@ -63,7 +65,7 @@ __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, c
     case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     default:
-      if (is_sphere_traced(is_id)) {
+      if (!kAnalytic && is_sphere_traced(is_id)) {
         r = sphere_trace(is_id, prm, o, d, rsqrtf(dot3(d, d)), t_lo, t_hi, eps, max_steps, wc);
         return r.attr != 0u;
       }
@@ -81,7 +83,7 @@ __device__ __forceinline__ void to_object(float4 m0, float4 m1, float4 m2, float
 // BLAS traversal of instance k (object-space ray; t shared with world space
 // because the direction is not renormalised). Returns true if any-hit mode
 // found a hit.
-template <bool kStats>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
 __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
                               uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
@@ -112,7 +114,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
     uint4 sr = __ldg(S.sbt + rec);
     const uint4 hg = __ldg(S.hit_groups + sr.x);
     IsResult res;
-    if (run_intersection(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
+    if (run_intersection<kAnalytic>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
         res.t >= tmin) {
       bool accept = res.t < h.t;
       if (!accept && res.t == h.t && h.inst >= 0)
@@ -145,7 +147,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       if (hl && hr) {
         int nearr = lref, farr = rref;
         if (r0 < l0) { nearr = rref; farr = lref; }
-        if (sp < kStackDepth) stack[sp++] = farr;
+        if (sp < kDepth) stack[sp++] = farr;
         else atomicOr(S.error_word, kErrStack);
         node = nearr;
         continue;
@@ -200,7 +202,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
 }
 
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
-template <bool kStats>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
 __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
                           uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
@@ -247,7 +249,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
 #pragma unroll
       for (int k = 3; k >= 1; --k) {
         if (key[k] != INFINITY) {
-          if (sp < kStackDepth) stack[sp++] = ref[k];
+          if (sp < kDepth) stack[sp++] = ref[k];
           else atomicOr(S.error_word, kErrStack);
         }
       }
@@ -273,7 +275,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
         if (!__any_sync(__activemask(), leaf == kNone)) break;
       }
       if (leaf != kNone &&
-          traverse_blas<kStats>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+          traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
         return;
     }
     return;
@@ -282,7 +284,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (node >= 0) {
         node = visit4(node);
         if (node != kNone) continue;
-      } else if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) {
+      } else if (traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) {
         return;
       }
       if (sp == 0) return;
@@ -309,7 +311,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
         if (hl && hr) {
           int nearr = lref, farr = rref;
           if (r0 < l0) { nearr = rref; farr = lref; }
-          if (sp < kStackDepth) stack[sp++] = farr;
+          if (sp < kDepth) stack[sp++] = farr;
           else atomicOr(S.error_word, kErrStack);
           node = nearr;
         } else if (hl) {
@@ -328,7 +330,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (!__any_sync(__activemask(), leaf == kDone)) break;
     }
     if (leaf != kDone &&
-        traverse_blas<kStats>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+        traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
       return;
   }
 #else
@@ -342,7 +344,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (hl && hr) {
         int nearr = lref, farr = rref;
         if (r0 < l0) { nearr = rref; farr = lref; }
-        if (sp < kStackDepth) stack[sp++] = farr;
+        if (sp < kDepth) stack[sp++] = farr;
         else atomicOr(S.error_word, kErrStack);
         node = nearr;
         continue;
@@ -350,7 +352,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (hl) { node = lref; continue; }
       if (hr) { node = rref; continue; }
     } else {
-      if (traverse_blas<kStats>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
+      if (traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -358,11 +360,11 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
 #endif
 }
 
-template <bool kStats>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
                                             float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc) {
   const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
-  trace_ray<kStats>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
+  trace_ray<kStats, kAnalytic, kDepth>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
 }
 
 struct Surface {
@@ -375,7 +377,8 @@ struct Surface {
 
 // Closest-hit inputs of an accepted radiance hit: record (Eq. 1 with r = 0),
 // object-space normal, world normal through the inverse transpose.
-static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
+template <bool kAnalytic = false>
+__device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
   if (wc) ++wc->shaded;
   Surface sf;
   const float4* R = S.inst_rec + 6 * (size_t)h.inst;
@@ -401,7 +404,7 @@ static __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit&
     const float4* pp = S.params + 4 * (size_t)prim;
     float4 prm[4] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2), __ldg(pp + 3)};
     float hstep = eps * len3(dd);
-    no = object_normal(hg.x, prm, p, h.attr, hstep, dd, wc);
+    no = object_normal<kAnalytic>(hg.x, prm, p, h.attr, hstep, dd, wc);
   }
   // the rows again (L1 hits) rather than held live across the normal's estimates
   const float4 m0 = __ldg(R), m1 = __ldg(R + 1), m2 = __ldg(R + 2);
@@ -490,12 +493,12 @@ struct PixelParams {
   uint32_t max_depth, max_steps;
 };
 
-template <bool kStats>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
 __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
                                                TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
   Hit h;
   rays += 1;
-  trace_typed<kStats>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
+  trace_typed<kStats, kAnalytic, kDepth>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
   // AOV fields are stored as soon as they are known, so none of them stays
   // live across the shadow and mirror traces
   float3 color;
@@ -509,7 +512,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
     }
   } else {
     flags |= 1u;
-    Surface sf = surface_at(S, h, eye, d, eps, wc);
+    Surface sf = surface_at<kAnalytic>(S, h, eye, d, eps, wc);
     if (av) {
       av->t = h.t;
       av->inst = (uint32_t)h.inst;
@@ -532,7 +535,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit sh;
         rays++;
         flags |= 2u;
-        trace_typed<kStats>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
         vis = sh.inst >= 0 ? 0.f : 1.f;
         if (sh.inst < 0) flags |= 4u;
       }
@@ -545,11 +548,11 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit rh;
         rays++;
         flags |= 8u;
-        trace_typed<kStats>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
         float3 lr;
         if (rh.inst >= 0) {
           flags |= 16u;
-          Surface s2 = surface_at(S, rh, orr, dr, eps, wc);
+          Surface s2 = surface_at<kAnalytic>(S, rh, orr, dr, eps, wc);
           if (av) {
             av->refl_t = rh.t;
             av->refl_inst = (uint32_t)rh.inst;
@@ -581,15 +584,17 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
 #define PR_SMEM_STACK 1
 #endif
 
-// Declares `stack` (a TravStack) for a kernel of kThreads threads per CTA.
+// Declares `stack` (a TravStack of kDepth entries per thread) for a kernel of
+// kThreads threads per CTA.
 #if PR_SMEM_STACK
-#define PR_DECLARE_STACK(kThreads)                                  \
-  __shared__ int pr_stack_mem_[::pr::kStackDepth * (kThreads)];     \
+#define PR_DECLARE_STACK_N(kThreads, kDepth)                \
+  __shared__ int pr_stack_mem_[(kDepth) * (kThreads)];      \
   const ::pr::TravStack stack{pr_stack_mem_ + threadIdx.x, (kThreads)}
 #else
-#define PR_DECLARE_STACK(kThreads)              \
-  int pr_stack_mem_[::pr::kStackDepth];          \
+#define PR_DECLARE_STACK_N(kThreads, kDepth)    \
+  int pr_stack_mem_[(kDepth)];                   \
   const ::pr::TravStack stack{pr_stack_mem_, 1}
 #endif
+#define PR_DECLARE_STACK(kThreads) PR_DECLARE_STACK_N(kThreads, ::pr::kStackDepth)
 
 }  // namespace pr

@@ -640,6 +640,10 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=4
                                      ("launch_wait_ms", phase("t_admit", "t_first_launch")),
                                      ("in_flight_ms", phase("t_first_launch", "t_done"))) if len(v)}
         hits = np.array([s["cache_hit"] for s in st], bool)
+        loads = np.array([s["t_load_end"] - s["t_load_start"] for s in st if s["t_load_end"] > 0]) * 1e3
+        if len(loads):
+            breakdown["scene_load_ms"] = {"p50": float(np.percentile(loads, 50)), "p99": float(np.percentile(loads, 99)),
+                                          "max": float(loads.max()), "n": int(len(loads))}
         out_rows.append({"rate_per_s": lam, "requests": n, "ok": ok, "mode": "continuous" if mode == 0 else "plain",
                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                          "p99_ms_cache_hits": float(np.percentile(lat[hits], 99)) if hits.any() else None,

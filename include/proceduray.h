@@ -330,7 +330,11 @@ typedef struct {
  * 16x8 tiles of all requests and run each pixel's whole pipeline (the
  * single-request kernel's per-pixel code); megakernel = 2 runs the same with
  * one CTA per tile (ctas_per_sm unused). Both need tile 16x8 and ignore
- * queue_chunk; the images are the same in every mode. */
+ * queue_chunk. megakernel = 3 selects the regrouped stages: traversals hand
+ * their fractal (Julia, Mandelbulb) candidates on as march jobs, and a
+ * persistent kernel sphere-traces them with every lane refilled from the job
+ * queue as its march ends (warp ballot over the idle lanes), normals included;
+ * batches of fewer than 2^31 pixels. The images are the same in every mode. */
 typedef struct {
   uint32_t struct_size; /* sizeof(pr_batch_tuning) */
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
@@ -340,7 +344,8 @@ typedef struct {
 typedef struct pr_batch pr_batch;
 
 /* Allocate a batch for up to max_requests requests and max_pixels pixels in
- * total (about 128 device bytes per pixel: per-pixel state and ray queues). */
+ * total (about 280 device bytes per pixel: per-pixel state, ray queues, and
+ * the regrouped mode's traversal results and march jobs). */
 pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch** out);
 
 /* Set the launch shape used by later calls (PR_ERR_INVALID_ARG if unsupported). */
@@ -412,11 +417,14 @@ typedef struct {
   float* out_rgba;             /* device, caller-owned, height*width float4 */
 } pr_server_request;
 
-/* Per-request times (seconds of a steady clock) and outcome. */
+/* Per-request times (seconds of a steady clock) and outcome. t_load_start /
+ * t_load_end bracket the build of the request's scene (upload + BVH) when the
+ * loader built it for this request, else 0. */
 typedef struct {
   double t_submit, t_admit, t_first_launch, t_done;
   uint32_t status;             /* pr_status */
   uint32_t cache_hit;          /* 1 if the scene was resident at admission */
+  double t_load_start, t_load_end;
 } pr_request_stats;
 
 /* cache_misses: admissions whose scene was built for them; scene_loads: scene

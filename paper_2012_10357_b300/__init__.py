@@ -487,7 +487,8 @@ class _ServerRequest(ctypes.Structure):
 
 class _RequestStats(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_first_launch", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("status", ctypes.c_uint32), ("cache_hit", ctypes.c_uint32)]
+                ("t_done", ctypes.c_double), ("status", ctypes.c_uint32), ("cache_hit", ctypes.c_uint32),
+                ("t_load_start", ctypes.c_double), ("t_load_end", ctypes.c_double)]
 
 
 class _ServerStats(ctypes.Structure):

@@ -314,11 +314,15 @@ ArenaPlan plan_arena(const Layout& L) {
   return P;
 }
 
-pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st) {
+// Pack the inputs into a pinned staging buffer (the scene's own, allocated on
+// first use, or `ext`, a caller's buffer of at least stage_bytes whose reuse
+// the caller orders after this copy) and send them with one asynchronous copy.
+pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st, char* ext = nullptr) {
   const Layout& L = s->L;
   // the previous upload's copy must have read the staging buffer before it is refilled
   PR_CUDA(cudaEventSynchronize(s->stage_done), "wait for the previous upload");
-  char* H = s->h_stage;
+  if (!ext && !s->h_stage) PR_CUDA(cudaMallocHost(&s->h_stage, s->stage_bytes), "pinned staging buffer");
+  char* H = ext ? ext : s->h_stage;
   auto put = [&](const void* dev_dst, const void* src, size_t bytes) {
     if (bytes) std::memcpy(H + (static_cast<const char*>(dev_dst) - s->arena), src, bytes);
   };
@@ -427,10 +431,14 @@ BuildScratch carve_build_scratch(void* base, uint32_t n) {
 
 pr::SceneView pr_internal_view(const pr_scene* s) { return view_of(s); }
 
-pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes) {
+pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes, size_t* input_bytes) {
   Layout L;
   pr_status st = validate_and_flatten(desc, L);
-  if (st == PR_OK) *bytes = plan_arena(L).total;
+  if (st == PR_OK) {
+    const ArenaPlan P = plan_arena(L);
+    *bytes = P.total;
+    if (input_bytes) *input_bytes = P.o_tbox;
+  }
   return st;
 }
 bool pr_internal_built(const pr_scene* s) { return s && s->built; }
@@ -454,7 +462,14 @@ pr_status pr_sbt_index(uint32_t r, uint32_t m, uint32_t g, uint32_t i, uint32_t 
   return PR_OK;
 }
 
-pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** out) {
+}  // extern "C"
+
+namespace {
+
+// pr_scene_create; with `ext` (pinned, at least the scene's input bytes) the
+// inputs go up through that buffer and the scene gets no staging buffer of its
+// own until a later pr_scene_upload.
+pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext, size_t ext_bytes, pr_scene** out) {
   if (!out) return fail(PR_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
   pr_scene* s = new pr_scene();
@@ -467,8 +482,12 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   const ArenaPlan P = plan_arena(L);
   s->arena_bytes = P.total;
   s->stage_bytes = P.o_tbox;
+  if (ext && ext_bytes < s->stage_bytes) {
+    delete s;
+    return fail(PR_ERR_INVALID_ARG, "staging buffer smaller than the scene's inputs");
+  }
   cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, s->stage_bytes);
+  if (e == cudaSuccess && !ext) e = cudaMallocHost(&s->h_stage, s->stage_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     pr_scene_destroy(s);
@@ -546,7 +565,7 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
   s->tlas_small = L.n_inst <= kSmallMax;
   std::vector<LevelDesc> jobs = s->small_jobs;
   jobs.push_back(T);   // the TLAS job sits after the BLAS jobs (used when it is small)
-  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t st = stream;
   e = cudaMemcpyAsync(s->d_jobs, jobs.data(), sizeof(LevelDesc) * jobs.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->error_word, 0, sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->scene_box, 0, 8 * sizeof(float), st);
@@ -554,13 +573,26 @@ pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** ou
     pr_scene_destroy(s);
     return cuda_fail(e, "scene setup copy");
   }
-  pr_status us = upload(s, desc, st);
+  pr_status us = upload(s, desc, st, ext);
   if (us != PR_OK) {
     pr_scene_destroy(s);
     return us;
   }
   *out = s;
   return PR_OK;
+}
+
+}  // namespace
+
+pr_status pr_internal_scene_create_staged(const pr_scene_desc* desc, cudaStream_t stream, void* staging,
+                                          size_t staging_bytes, pr_scene** out) {
+  return create_scene(desc, stream, static_cast<char*>(staging), staging_bytes, out);
+}
+
+extern "C" {
+
+pr_status pr_scene_create(const pr_scene_desc* desc, void* stream, pr_scene** out) {
+  return create_scene(desc, (cudaStream_t)stream, nullptr, 0, out);
 }
 
 pr_status pr_scene_upload(pr_scene* s, const pr_scene_desc* desc, void* stream) {

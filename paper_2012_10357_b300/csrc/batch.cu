@@ -54,7 +54,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool tuning_ok(const BatchTuning& t) {
   bool tile = (t.tile_w == 16 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 4) || (t.tile_w == 8 && t.tile_h == 16);
-  if (t.megakernel > 2 || (t.megakernel && !(t.tile_w == 16 && t.tile_h == 8))) return false;
+  if (t.megakernel > 3 || ((t.megakernel == 1 || t.megakernel == 2) && !(t.tile_w == 16 && t.tile_h == 8))) return false;
   return tile && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 16 && t.queue_chunk >= 32 && t.queue_chunk <= 1024 &&
          t.queue_chunk % 32 == 0;
 }
@@ -119,6 +119,8 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   H->notify = b->notify;
   H->seq = b->notify_seq;
   H->pad2 = 0;
+  H->job_n[0] = H->job_n[1] = H->job_ctr[0] = H->job_ctr[1] = 0;
+  H->shade_ctr = H->finish_ctr = H->pad3[0] = H->pad3[1] = 0;
   b->notify = nullptr;   // one batch only
   size_t bytes = a256(sizeof(BatchHdr)) + sizeof(ReqDev) * n;
   e = cudaMemcpyAsync(b->V.hdr, b->staging, bytes, cudaMemcpyHostToDevice, st);
@@ -170,6 +172,13 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   size_t o_sta = take(16 * P), o_stb = take(8 * P), o_refl = take(16 * P);
   size_t o_sqa = take(16 * P), o_sqb = take(16 * P), o_sqp = take(8 * P), o_sqr = take(4 * P);
   size_t o_mqa = take(16 * P), o_mqb = take(16 * P), o_mqp = take(8 * P), o_mqr = take(4 * P);
+  // regrouped mode: traversal results per ray slot, camera bases, march jobs
+  // (one job per pixel per pass; rays beyond that march in place)
+  size_t o_rgh = take(16 * P), o_rgj = take(8 * P), o_rgmh = take(16 * P), o_rgmj = take(8 * P),
+         o_rgsj = take(8 * P), o_bases = take(64 * (size_t)max_requests);
+  size_t o_job[2][3];
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < 3; ++k) o_job[pass][k] = take(16 * P);
   b->arena_bytes = off;
   cudaError_t e = cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
@@ -190,6 +199,19 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   b->V.mq_b = reinterpret_cast<float4*>(A + o_mqb);
   b->V.mq_px = reinterpret_cast<uint64_t*>(A + o_mqp);
   b->V.mq_req = reinterpret_cast<uint32_t*>(A + o_mqr);
+  b->V.rg_hit = reinterpret_cast<int4*>(A + o_rgh);
+  b->V.rg_jobs = reinterpret_cast<uint2*>(A + o_rgj);
+  b->V.rg_mhit = reinterpret_cast<int4*>(A + o_rgmh);
+  b->V.rg_mjobs = reinterpret_cast<uint2*>(A + o_rgmj);
+  b->V.rg_sjobs = reinterpret_cast<uint2*>(A + o_rgsj);
+  b->V.bases = reinterpret_cast<float4*>(A + o_bases);
+  for (int pass = 0; pass < 2; ++pass) {
+    b->V.jobs[pass].a = reinterpret_cast<float4*>(A + o_job[pass][0]);
+    b->V.jobs[pass].b = reinterpret_cast<uint4*>(A + o_job[pass][1]);
+    b->V.jobs[pass].r = reinterpret_cast<float4*>(A + o_job[pass][2]);
+  }
+  b->V.job_cap = (uint32_t)P;
+  b->V.max_req = max_requests;
   e = cudaMallocHost(&b->staging, a256(sizeof(BatchHdr)) + sizeof(ReqDev) * max_requests);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
@@ -207,6 +229,8 @@ pr_status pr_batch_set_tuning(pr_batch* b, const pr_batch_tuning* t) {
   BatchTuning bt{t->ctas_per_sm, t->tile_w, t->tile_h, t->queue_chunk, t->megakernel};
   if (!tuning_ok(bt))
     return bfail(PR_ERR_INVALID_ARG, "tuning: tiles 16x8, 32x4 or 8x16; 1..16 CTAs/SM; chunk multiple of 32 in 32..1024");
+  if (bt.megakernel == 3 && b->max_px >= (1ull << 31))
+    return bfail(PR_ERR_INVALID_ARG, "the regrouped mode takes batches of fewer than 2^31 pixels");
   b->tuning = bt;
   return PR_OK;
 }
@@ -277,6 +301,10 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
   cands.push_back(BatchTuning{4, 16, 8, 32, 1u});
   cands.push_back(BatchTuning{8, 16, 8, 32, 1u});
   cands.push_back(BatchTuning{4, 16, 8, 32, 2u});
+  // the regrouped stages (fractal marches from a job queue)
+  if (b->max_px < (1ull << 31))
+    for (uint32_t c : {4u, 8u})
+      for (uint32_t ch : {32u, 128u}) cands.push_back(BatchTuning{c, 16, 8, ch, 3u});
   for (const BatchTuning& cand : cands) {
     b->tuning = cand;
     float ms_best = 1e30f;

@@ -94,8 +94,14 @@ constexpr size_t kCameraBasisBytes = 64;
 pr::SceneView pr_internal_view(const pr_scene* s);
 bool pr_internal_built(const pr_scene* s);
 // Validate a description and give the device bytes pr_scene_create would
-// allocate for it (pr_scene_device_bytes of the new scene), without allocating.
-pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes);
+// allocate for it (pr_scene_device_bytes of the new scene) and the bytes of its
+// inputs (the staging copy), without allocating.
+pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes, size_t* input_bytes);
+// pr_scene_create whose inputs go up through the caller's pinned buffer
+// `staging` (at least the input bytes; the caller reuses it only after the
+// copy on `stream` is done) instead of a pinned buffer of the scene's own.
+pr_status pr_internal_scene_create_staged(const pr_scene_desc* desc, cudaStream_t stream, void* staging,
+                                          size_t staging_bytes, pr_scene** out);
 // Completion flags for the next pr_trace_batch[_graph] of this batch: when
 // the last tile of request r is written, the kernel stores seq into notify[r]
 // (host-mapped memory, at least n requests). Only the megakernel modes write

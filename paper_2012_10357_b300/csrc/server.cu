@@ -80,6 +80,7 @@ struct Job {
   uint64_t key = 0;
   std::shared_ptr<DescCopy> desc;   // only when the key was not cached at submit time
   size_t bytes = 0;                 // device bytes its scene needs (from the description)
+  size_t input_bytes = 0;           // bytes of its scene's inputs (the staging copy)
   pr_camera camera{};
   pr_trace_params params{};
   float* out = nullptr;
@@ -114,6 +115,8 @@ struct pr_server {
   size_t batch_bytes = 0;
   unsigned long long* d_rays = nullptr;
   uint32_t* notify = nullptr;           // host-mapped completion flags [max_active]
+  char* staging = nullptr;              // pinned buffer the loader sends scene inputs through
+  size_t staging_bytes = 0;
   uint32_t seq = 0;
   std::thread worker, loader;
   std::mutex mu;
@@ -231,15 +234,28 @@ void loader_main(pr_server* s) {
     slot.ready = false;
     s->cache_bytes += j->bytes;
     std::shared_ptr<DescCopy> desc = j->desc;
+    const size_t input_bytes = j->input_bytes;
+    j->st.t_load_start = now_s();
     lk.unlock();
     for (pr_scene* v : victims) pr_scene_destroy(v);
     pr_scene* sc = nullptr;
-    pr_status st = pr_scene_create(&desc->d, s->load_stream, &sc);
+    pr_status st = PR_OK;
+    if (input_bytes > s->staging_bytes) {   // one pinned staging buffer serves every load (grown when needed)
+      const size_t want = std::max(input_bytes, s->staging_bytes * 3 / 2);
+      if (s->staging) cudaFreeHost(s->staging);
+      s->staging = nullptr;
+      s->staging_bytes = 0;
+      if (cudaMallocHost(&s->staging, want) == cudaSuccess) s->staging_bytes = want;
+      else st = PR_ERR_OUT_OF_MEMORY;
+    }
+    if (st == PR_OK)
+      st = pr_internal_scene_create_staged(&desc->d, s->load_stream, s->staging, s->staging_bytes, &sc);
     if (st == PR_OK) st = pr_build_bvh(sc, s->load_stream);
     if (st == PR_OK && cudaStreamSynchronize(s->load_stream) != cudaSuccess) st = PR_ERR_CUDA;
     const std::string msg = st == PR_OK ? std::string() : std::string(pr_last_error());
     lk.lock();
     ++s->scene_loads;
+    j->st.t_load_end = now_s();
     auto it = s->cache.find(j->key);
     if (st != PR_OK) {
       s->cache_bytes -= it->second.bytes;
@@ -482,13 +498,14 @@ pr_status pr_server_submit(pr_server* s, const pr_server_request* r, uint64_t* t
   if (!s->cache.count(r->scene_key)) {
     if (!r->desc) return sfail(PR_ERR_INVALID_ARG, "pr_server_submit: scene key not cached and no description");
     lk.unlock();
-    size_t bytes = 0;
-    pr_status v = pr_internal_scene_bytes(r->desc, &bytes);   // validates the description
+    size_t bytes = 0, input_bytes = 0;
+    pr_status v = pr_internal_scene_bytes(r->desc, &bytes, &input_bytes);   // validates the description
     if (v != PR_OK) return v;
     auto dc = std::make_shared<DescCopy>(r->desc);
     lk.lock();
     j->desc = dc;
     j->bytes = bytes;
+    j->input_bytes = input_bytes;
   }
   j->ticket = s->next_ticket++;
   j->st.t_submit = now_s();
@@ -570,6 +587,7 @@ void pr_server_destroy(pr_server* s) {
   if (s->batch) pr_batch_destroy(s->batch);
   if (s->d_rays) cudaFree(s->d_rays);
   if (s->notify) cudaFreeHost(s->notify);
+  if (s->staging) cudaFreeHost(s->staging);
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->load_stream) cudaStreamDestroy(s->load_stream);
   delete s;

@@ -434,6 +434,16 @@ static __device__ __noinline__ float3 de_stencil(uint32_t id, const float4* prm,
 
 __device__ __forceinline__ bool is_sphere_traced(uint32_t id) { return id >= PR_IS_TORUS && id <= PR_IS_JULIA_CUT; }
 
+// The estimate of a fractal shader (Julia, Mandelbulb, cut Julia) at p, with
+// its parameter rows in registers: the arithmetic of the sphere-tracing loop
+// and of the normal stencil, for march jobs run outside the traversal.
+__device__ __forceinline__ float fractal_de(uint32_t id, const float4 p0, const float4 p1, const float4 p2, float3 p) {
+  if (id == PR_IS_MANDELBULB) return de_mandelbulb(p0, p);
+  const float dj = de_julia(p0, p1, p);
+  if (id == PR_IS_JULIA_CUT) return fmaxf(dj, fmaf(p1.z, p.x, fmaf(p1.w, p.y, p2.x * p.z)) - p2.y);
+  return dj;
+}
+
 // Sphere tracing (Hart 1996) inside [t_lo, t_hi]: estimates are converted to
 // world units with 1/|d|; hit when below eps, give up past t_hi or after
 // max_steps estimates. The estimate is inlined into the loop (one branch on
@@ -507,7 +517,7 @@ static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* 
 // kAnalytic: only analytic shaders occur (no estimator stencil compiled in).
 template <bool kAnalytic = false>
 __device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, float3 p, uint32_t attr, float h,
-                                                float3 d, WorkCounters* wc = nullptr) {
+                                                float3 d, WorkCounters* wc = nullptr, const float3* grad = nullptr) {
   switch (id) {
     case PR_IS_SPHERE: {
       float4 p0 = prm[0];
@@ -527,7 +537,7 @@ __device__ __forceinline__ float3 object_normal(uint32_t id, const float4* prm, 
     }
     default: {
       if (kAnalytic) return -normalize3(d);
-      const float3 g = de_stencil(id, prm, p, h, wc);
+      const float3 g = grad ? *grad : de_stencil(id, prm, p, h, wc);
       float gl2 = dot3(g, g);
       return gl2 > 0.f ? g * rsqrtf(gl2) : -normalize3(d);
     }

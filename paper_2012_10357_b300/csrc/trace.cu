@@ -54,10 +54,12 @@ __global__ void __launch_bounds__(128) k_camera_bases(const pr_camera* cams, uin
 
 // kAnalytic: scenes without sphere-traced shaders whose stack bound fits the
 // short stack (kShortStackDepth entries, 4 KB per CTA instead of 32 KB); the
-// estimator code is not compiled in, so the kernel fits 64 registers and twice
-// as many CTAs stay resident. Same arithmetic, same bits.
+// estimator code is not compiled in, so the kernel fits 80 registers and 6
+// CTAs stay resident instead of 4. Same arithmetic, same bits. Measured on
+// B300 (4096 jittered 64x64 frames of the small analytic scene per launch):
+// 0.977 / 0.856 / 0.818 / 0.842 ms at 4 / 5 / 6 / 8 CTAs per SM.
 #ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC
-#define PR_TRACE_MIN_BLOCKS_ANALYTIC 8
+#define PR_TRACE_MIN_BLOCKS_ANALYTIC 6
 #endif
 
 template <bool kStats, int kWarpW, bool kAnalytic>

@@ -38,6 +38,22 @@ struct Hit {
   uint32_t attr;   // intersection attribute
 };
 
+// Fractal march candidates a traversal hands on instead of marching them in
+// place (the regrouped wavefront runs them later from a job queue): the
+// instance, the leaf, the record's shader and primitive, and the leaf's slab
+// interval. Beyond kMaxDeferred candidates a ray marches in place.
+constexpr int kMaxDeferred = 4;
+struct Deferred {
+  int n;
+  int inst[kMaxDeferred], leaf[kMaxDeferred];
+  uint32_t is_id[kMaxDeferred], prim[kMaxDeferred];
+  float t_lo[kMaxDeferred], t_hi[kMaxDeferred];
+};
+
+__device__ __forceinline__ bool is_fractal(uint32_t id) {
+  return id == PR_IS_JULIA || id == PR_IS_MANDELBULB || id == PR_IS_JULIA_CUT;
+}
+
 __device__ __forceinline__ bool key_less(int i0, uint2 gq0, int i1, uint2 gq1) {
   if (i0 != i1) return i0 < i1;
   if (gq0.x != gq1.x) return gq0.x < gq1.x;
@@ -83,9 +99,10 @@ __device__ __forceinline__ void to_object(float4 m0, float4 m1, float4 m2, float
 // BLAS traversal of instance k (object-space ray; t shared with world space
 // because the direction is not renormalised). Returns true if any-hit mode
 // found a hit.
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
 __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
-                              uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_) {
+                              uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_,
+                              Deferred* defer = nullptr) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->instances;
   const float4* R = S.inst_rec + 6 * (size_t)k;
@@ -113,6 +130,16 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
     }
     uint4 sr = __ldg(S.sbt + rec);
     const uint4 hg = __ldg(S.hit_groups + sr.x);
+    if (kDefer && is_fractal(hg.x) && defer->n < kMaxDeferred) {
+      const int i = defer->n++;
+      defer->inst[i] = k;
+      defer->leaf[i] = leaf;
+      defer->is_id[i] = hg.x;
+      defer->prim[i] = prim;
+      defer->t_lo[i] = t_lo;
+      defer->t_hi[i] = t_hi;
+      return false;
+    }
     IsResult res;
     if (run_intersection<kAnalytic>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
         res.t >= tmin) {
@@ -202,9 +229,9 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
 }
 
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
 __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
-                          uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_) {
+                          uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_, Deferred* defer = nullptr) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
   if (wc) ++wc->rays;
   h.t = tmax;
@@ -275,7 +302,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
         if (!__any_sync(__activemask(), leaf == kNone)) break;
       }
       if (leaf != kNone &&
-          traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+          traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
         return;
     }
     return;
@@ -284,7 +311,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (node >= 0) {
         node = visit4(node);
         if (node != kNone) continue;
-      } else if (traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) {
+      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
         return;
       }
       if (sp == 0) return;
@@ -330,7 +357,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (!__any_sync(__activemask(), leaf == kDone)) break;
     }
     if (leaf != kDone &&
-        traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc))
+        traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
       return;
   }
 #else
@@ -352,7 +379,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (hl) { node = lref; continue; }
       if (hr) { node = rref; continue; }
     } else {
-      if (traverse_blas<kStats, kAnalytic, kDepth>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc)) return;
+      if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) return;
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -360,11 +387,12 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
 #endif
 }
 
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
-                                            float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc) {
+                                            float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc,
+                                            Deferred* defer = nullptr) {
   const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
-  trace_ray<kStats, kAnalytic, kDepth>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc);
+  trace_ray<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc, defer);
 }
 
 struct Surface {
@@ -377,8 +405,11 @@ struct Surface {
 
 // Closest-hit inputs of an accepted radiance hit: record (Eq. 1 with r = 0),
 // object-space normal, world normal through the inverse transpose.
+// grad: the estimator's central-difference gradient at the hit when a march
+// job has computed it already (regrouped wavefront), else null.
 template <bool kAnalytic = false>
-__device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc) {
+__device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, float3 o, float3 d, float eps, WorkCounters* wc,
+                                           const float3* grad = nullptr) {
   if (wc) ++wc->shaded;
   Surface sf;
   const float4* R = S.inst_rec + 6 * (size_t)h.inst;
@@ -404,7 +435,7 @@ __device__ __noinline__ Surface surface_at(const SceneView& S, const Hit& h, flo
     const float4* pp = S.params + 4 * (size_t)prim;
     float4 prm[4] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2), __ldg(pp + 3)};
     float hstep = eps * len3(dd);
-    no = object_normal<kAnalytic>(hg.x, prm, p, h.attr, hstep, dd, wc);
+    no = object_normal<kAnalytic>(hg.x, prm, p, h.attr, hstep, dd, wc, grad);
   }
   // the rows again (L1 hits) rather than held live across the normal's estimates
   const float4 m0 = __ldg(R), m1 = __ldg(R + 1), m2 = __ldg(R + 2);

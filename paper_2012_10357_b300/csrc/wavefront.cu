@@ -248,6 +248,494 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
   }
 }
 
+// ---- regrouped stages ------------------------------------------------------
+// Sphere tracing a fractal (Julia, Mandelbulb) takes from a few to hundreds
+// of estimates per ray, so in the stages above a warp whose rays reach a
+// fractal runs at the pace of its slowest march with most lanes idle. Here
+// the traversals hand their fractal candidates on as march jobs (appended to
+// one queue per pass with a warp prefix sum and one atomic per warp), and a
+// persistent march kernel refills every lane that finishes its march with the
+// next job (a warp ballot over the idle lanes claims as many jobs as there are
+// idle lanes), computing the normal stencil of a hit in the same loop. The
+// closest hit is then the least (t, instance, geometry, primitive) over the
+// traversal's own hit and the job hits, the rule of the in-place traversal:
+// a job's march interval only extends the in-place one, and any hit it finds
+// beyond the in-place interval lies past the closest hit, so the images are
+// the same bits as the megakernel's.
+
+constexpr uint32_t kEmptyJob = 0xFFFFFFFFu;   // job slot left unused (its ray overflowed the queue)
+constexpr uint32_t kMirrorSlot = 0x80000000u; // pass-1 ray slot of a mirror ray (else a shadow ray)
+
+__global__ void __launch_bounds__(128) k_rg_bases(BatchView B) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < B.hdr->n_req) {
+    const CameraBasis cb = camera_basis(B.reqs[r].cam, B.reqs[r].width, B.reqs[r].height);
+    reinterpret_cast<CameraBasis*>(B.bases)[r] = cb;
+  }
+}
+
+// Every lane of the warp calls this (n = 0 for lanes without candidates).
+// Returns the ray's first job, or kEmptyJob when the pass's queue is full
+// (the caller then marches its candidates in place).
+__device__ __forceinline__ uint32_t append_jobs(const BatchView& B, int pass, const Deferred& dfr, uint32_t slot,
+                                                uint32_t req, bool normal) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n = (uint32_t)dfr.n;
+  uint32_t x = n;   // inclusive prefix sum over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if ((int)lane >= o) x += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, x, 31);
+  if (total == 0) return kEmptyJob;
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(&B.hdr->job_n[pass], total);
+  base = __shfl_sync(kFull, base, 31);
+  const uint32_t first = base + x - n;
+  const MarchJobs& J = B.jobs[pass];
+  const bool fits = (uint64_t)first + n <= B.job_cap;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t j = first + i;
+    if (j >= B.job_cap) break;
+    if (fits) {
+      J.a[j] = make_float4(dfr.t_lo[i], dfr.t_hi[i], __int_as_float(dfr.inst[i]), __int_as_float(dfr.leaf[i]));
+      J.b[j] = make_uint4(slot, req, dfr.is_id[i] | (normal ? 0x10000u : 0u), dfr.prim[i]);
+    } else {
+      J.b[j].z = kEmptyJob;
+    }
+  }
+  return fits ? first : kEmptyJob;
+}
+
+// The candidates of a ray whose jobs did not fit, marched where they are, with
+// the acceptance rule of the traversal; true when a candidate hit (any-hit
+// rays stop at the first).
+__device__ __noinline__ bool march_in_place(const SceneView& S, const Deferred& dfr, float3 o, float3 d, float eps,
+                                            uint32_t max_steps, bool any_hit, Hit& h) {
+  bool found = false;
+  for (int i = 0; i < dfr.n; ++i) {
+    const int k = dfr.inst[i];
+    const float4* Rk = S.inst_rec + 6 * (size_t)k;
+    float3 oo, dd;
+    to_object(__ldg(Rk), __ldg(Rk + 1), __ldg(Rk + 2), o, d, oo, dd);
+    IsResult res;
+    if (run_intersection<false>(dfr.is_id[i], PR_NONE, S.params + 4 * (size_t)dfr.prim[i], oo, dd, 0.f, dfr.t_lo[i],
+                                dfr.t_hi[i], eps, max_steps, res, nullptr)) {
+      const uint2 gq = __ldg(S.leaf_gq + dfr.leaf[i]);
+      bool accept = res.t < h.t;
+      if (!accept && res.t == h.t && h.inst >= 0) accept = key_less(k, gq, h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
+      if (accept) {
+        h.t = res.t;
+        h.inst = k;
+        h.leaf = dfr.leaf[i];
+        h.attr = res.attr;
+        found = true;
+        if (any_hit) return true;
+      }
+    }
+  }
+  return found;
+}
+
+// The closest hit over the traversal's own hit and the ray's march jobs;
+// returns the winning job (its gradient serves the normal), or -1.
+__device__ __forceinline__ int resolve_jobs(const SceneView& S, const MarchJobs& J, uint32_t first, uint32_t n, Hit& h) {
+  int best = -1;
+  for (uint32_t i = 0; i < n; ++i) {
+    const float4 r = J.r[first + i];
+    if (r.x < 0.f) continue;   // the march found no surface
+    const float4 a = J.a[first + i];
+    const int k = __float_as_int(a.z), leaf = __float_as_int(a.w);
+    bool accept = r.x < h.t;
+    if (!accept && r.x == h.t && h.inst >= 0)
+      accept = key_less(k, __ldg(S.leaf_gq + leaf), h.inst, __ldg(S.leaf_gq + (h.leaf & 0x3FFFFFFF)));
+    if (accept) {
+      h.t = r.x;
+      h.inst = k;
+      h.leaf = leaf;
+      h.attr = 1u;
+      best = (int)(first + i);
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ int2 pixel_of(const ReqDev& R, uint64_t px) {
+  const uint64_t local = px - R.pixel_begin;
+  return make_int2((int)(local % R.width), (int)(R.row_begin + local / R.width));
+}
+
+// Primary rays: tiles of all requests; traversal with fractal candidates
+// deferred; the closest other hit and the ray's jobs are kept per pixel.
+template <int TW, int TH>
+__global__ void __launch_bounds__(128, 4) k_rg_primary(BatchView B) {
+  static_assert(TW * TH == 128, "128-pixel tiles");
+  __shared__ uint32_t s_tile, s_req;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int WX = TW / 8;
+  const int ox = (warp % WX) * 8 + (lane & 7), oy = (warp / WX) * 4 + (lane >> 3);
+  PR_DECLARE_STACK(128);
+  const CameraBasis* bases = reinterpret_cast<const CameraBasis*>(B.bases);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(&B.hdr->tile_ctr, 1u);
+      s_tile = t;
+      s_req = t < B.hdr->total_tiles ? find_request(B.reqs, B.hdr->n_req, t) : 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile, r = s_req;
+    if (tile >= B.hdr->total_tiles) break;
+    const ReqDev& R = B.reqs[r];
+    const uint32_t lt = tile - R.tile_begin;
+    const int x = (int)(lt % R.tiles_x) * TW + ox, y = (int)R.row_begin + (int)(lt / R.tiles_x) * TH + oy;
+    const bool valid = x < (int)R.width && y < (int)(R.row_begin + R.rows);
+    Deferred dfr;
+    dfr.n = 0;
+    Hit h;
+    uint64_t px = 0;
+    float3 eye = f3(0.f, 0.f, 0.f), d = eye;
+    float eps = 0.f;
+    if (valid) {
+      const CameraBasis& cb = bases[r];
+      eye = cb.eye;
+      d = camera_ray(cb, x, y);
+      eps = scene_eps(R.S, R.eps_rel);
+      px = R.pixel_begin + (uint64_t)(y - (int)R.row_begin) * R.width + (uint64_t)x;
+      trace_typed<false, false, kStackDepth, true>(R.S, eye, d, 0, 0.f, INFINITY, eps, R.max_steps, h, stack, nullptr,
+                                                   &dfr);
+    }
+    uint32_t first = append_jobs(B, 0, dfr, (uint32_t)px, r, true);
+    if (valid) {
+      if (first == kEmptyJob && dfr.n > 0) {
+        march_in_place(R.S, dfr, eye, d, eps, R.max_steps, false, h);
+        dfr.n = 0;
+      }
+      B.rg_hit[px] = make_int4(__float_as_int(h.t), h.inst, h.leaf, (int)h.attr);
+      B.rg_jobs[px] = make_uint2(first, (uint32_t)dfr.n);
+    }
+    unsigned long long* counter = B.hdr->counter;
+    if (counter) {
+      const uint32_t tot = __reduce_add_sync(kFull, valid ? 1u : 0u);
+      if (lane == 0 && tot) atomicAdd(counter, (unsigned long long)tot);
+    }
+    __syncthreads();
+  }
+}
+
+// Persistent march kernel with lane refill. A lane's state is one job: the
+// object-space ray of its instance, the estimator's parameters, and the march
+// position; a hit on a radiance ray goes on with the six stencil estimates
+// of its normal.
+__global__ void __launch_bounds__(128, 8) k_rg_march(BatchView B, int pass) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n = min(B.hdr->job_n[pass], B.job_cap);
+  const MarchJobs J = B.jobs[pass];
+  const CameraBasis* bases = reinterpret_cast<const CameraBasis*>(B.bases);
+  int job = -1;
+  bool exhausted = false;
+  uint32_t is_id = 0, phase = 0, steps = 0, max_steps = 0;
+  bool normal = false;
+  float t = 0.f, t_hi = 0.f, inv_len = 0.f, eps = 0.f, hstep = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  float3 o = f3(0.f, 0.f, 0.f), d = o, ph = o;
+  float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0, p2 = p0;
+  for (;;) {
+    const bool idle = job < 0;
+    const uint32_t want = __ballot_sync(kFull, idle && !exhausted);
+    if (want) {
+      const int leader = __ffs(want) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(&B.hdr->job_ctr[pass], (uint32_t)__popc(want));
+      base = __shfl_sync(kFull, base, leader);
+      if (base + (uint32_t)__popc(want) >= n) exhausted = true;
+      const uint32_t j = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
+      if (idle && j < n) {
+        const uint4 b = J.b[j];
+        if (b.z != kEmptyJob) {
+          const float4 a = J.a[j];
+          const ReqDev& R = B.reqs[b.y];
+          const SceneView& S = R.S;
+          float3 wo, wd;
+          if (pass == 0) {
+            const int2 xy = pixel_of(R, b.x);
+            wo = bases[b.y].eye;
+            wd = camera_ray(bases[b.y], xy.x, xy.y);
+          } else if (b.x & kMirrorSlot) {
+            const float4 qa = B.mq_a[b.x & ~kMirrorSlot], qb = B.mq_b[b.x & ~kMirrorSlot];
+            wo = f3(qa.x, qa.y, qa.z);
+            wd = f3(qb.x, qb.y, qb.z);
+          } else {
+            const float4 qa = B.sq_a[b.x], qb = B.sq_b[b.x];
+            wo = f3(qa.x, qa.y, qa.z);
+            wd = f3(qb.x, qb.y, qb.z);
+          }
+          const float4* Rk = S.inst_rec + 6 * (size_t)__float_as_int(a.z);
+          to_object(__ldg(Rk), __ldg(Rk + 1), __ldg(Rk + 2), wo, wd, o, d);
+          const float4* prm = S.params + 4 * (size_t)b.w;
+          p0 = __ldg(prm);
+          p1 = __ldg(prm + 1);
+          p2 = __ldg(prm + 2);
+          eps = scene_eps(S, R.eps_rel);
+          max_steps = R.max_steps;
+          inv_len = rsqrtf(dot3(d, d));
+          t = a.x;
+          t_hi = a.y;
+          is_id = b.z & 0xFFFFu;
+          normal = (b.z >> 16) != 0u;
+          steps = 0;
+          phase = 0;
+          job = (int)j;
+        }
+      }
+    }
+    if (!__any_sync(kFull, job >= 0)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (job < 0) continue;
+    if (phase == 0) {
+      // one step of sphere tracing (the in-place loop's order: step cap, interval, estimate)
+      if (steps >= max_steps || t > t_hi) {
+        J.r[job] = make_float4(-1.f, 0.f, 0.f, 0.f);
+        job = -1;
+        continue;
+      }
+      const float dist = __fmul_rn(fractal_de(is_id, p0, p1, p2, madd(o, t, d)), inv_len);
+      if (dist < eps) {
+        if (normal) {
+          phase = 1;
+          hstep = eps * len3(d);
+          ph = madd(o, t, d);
+        } else {
+          J.r[job] = make_float4(t, 0.f, 0.f, 0.f);
+          job = -1;
+        }
+      } else {
+        t += dist;
+        ++steps;
+      }
+    } else {
+      // stencil estimate k of the normal: +h, -h along x, then y, then z
+      const int k = (int)phase - 1;
+      const float sh = (k & 1) ? -hstep : hstep;
+      const int ax = k >> 1;
+      const float v = fractal_de(is_id, p0, p1, p2,
+                                 f3(ax == 0 ? ph.x + sh : ph.x, ax == 1 ? ph.y + sh : ph.y, ax == 2 ? ph.z + sh : ph.z));
+      if (ax == 0) gx = (k & 1) ? gx - v : v;
+      else if (ax == 1) gy = (k & 1) ? gy - v : v;
+      else gz = (k & 1) ? gz - v : v;
+      if (++phase == 7) {
+        J.r[job] = make_float4(t, gx, gy, gz);
+        job = -1;
+      }
+    }
+  }
+}
+
+// Primary hits resolved over their jobs; closest-hit set-up as in k_wf_primary;
+// shadow and mirror rays appended to their queues.
+template <int TW, int TH>
+__global__ void __launch_bounds__(128, 4) k_rg_shade(BatchView B) {
+  __shared__ uint32_t s_tile, s_req;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int WX = TW / 8;
+  const int ox = (warp % WX) * 8 + (lane & 7), oy = (warp / WX) * 4 + (lane >> 3);
+  const CameraBasis* bases = reinterpret_cast<const CameraBasis*>(B.bases);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(&B.hdr->shade_ctr, 1u);
+      s_tile = t;
+      s_req = t < B.hdr->total_tiles ? find_request(B.reqs, B.hdr->n_req, t) : 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile, r = s_req;
+    if (tile >= B.hdr->total_tiles) break;
+    const ReqDev& R = B.reqs[r];
+    const uint32_t lt = tile - R.tile_begin;
+    const int x = (int)(lt % R.tiles_x) * TW + ox, y = (int)R.row_begin + (int)(lt / R.tiles_x) * TH + oy;
+    const bool valid = x < (int)R.width && y < (int)(R.row_begin + R.rows);
+    bool need_s = false, need_m = false;
+    float3 os = f3(0.f, 0.f, 0.f), ds = os, orr = os, dr = os;
+    float smax = 0.f;
+    uint64_t px = 0;
+    if (valid) {
+      const SceneView& S = R.S;
+      const CameraBasis& cb = bases[r];
+      const float3 eye = cb.eye;
+      const float3 d = camera_ray(cb, x, y);
+      const float eps = scene_eps(S, R.eps_rel);
+      px = R.pixel_begin + (uint64_t)(y - (int)R.row_begin) * R.width + (uint64_t)x;
+      const int4 hr = B.rg_hit[px];
+      const uint2 jr = B.rg_jobs[px];
+      Hit h{__int_as_float(hr.x), hr.y, hr.z, (uint32_t)hr.w};
+      const int best = resolve_jobs(S, B.jobs[0], jr.x, jr.y, h);
+      uint32_t flags = 0;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      float ndl = 0.f;
+      if (h.inst >= 0) {
+        flags |= 1u;
+        float3 g;
+        if (best >= 0) {
+          const float4 rr = B.jobs[0].r[best];
+          g = f3(rr.y, rr.z, rr.w);
+        }
+        Surface sf = surface_at(S, h, eye, d, eps, nullptr, best >= 0 ? &g : nullptr);
+        if (sf.chs == PR_CHS_LAMBERT) {
+          flags |= 0x100u;
+          const float3 pt = madd(eye, h.t, d);
+          const float delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
+          ndl = light_ndl(sf, R.light, pt);
+          a = make_float4(sf.albedo.x, sf.albedo.y, sf.albedo.z, sf.kr);
+          if (ndl > 0.f) {
+            os = madd(pt, delta, sf.n);
+            float3 ls = R.light - os;
+            smax = len3(ls);
+            ds = ls * (1.f / smax);
+            need_s = true;
+            flags |= 2u;
+          }
+          if (R.max_depth >= 2 && sf.kr > 0.f) {
+            orr = madd(pt, delta, sf.n);
+            dr = normalize3(d - sf.n * (2.f * dot3(d, sf.n)));
+            need_m = true;
+            flags |= 8u;
+          }
+        }
+      }
+      B.st_a[px] = a;
+      B.st_b[px] = make_uint2(__float_as_uint(ndl), flags);
+    }
+    const uint32_t qs = warp_append(&B.hdr->shadow_n, need_s);
+    if (need_s) {
+      B.sq_a[qs] = make_float4(os.x, os.y, os.z, smax);
+      B.sq_b[qs] = make_float4(ds.x, ds.y, ds.z, 0.f);
+      B.sq_px[qs] = px;
+      B.sq_req[qs] = r;
+    }
+    const uint32_t qm = warp_append(&B.hdr->mirror_n, need_m);
+    if (need_m) {
+      B.mq_a[qm] = make_float4(orr.x, orr.y, orr.z, 0.f);
+      B.mq_b[qm] = make_float4(dr.x, dr.y, dr.z, 0.f);
+      B.mq_px[qm] = px;
+      B.mq_req[qm] = r;
+    }
+    unsigned long long* counter = B.hdr->counter;
+    if (counter) {
+      const uint32_t tot = __reduce_add_sync(kFull, (need_s ? 1u : 0u) + (need_m ? 1u : 0u));
+      if (lane == 0 && tot) atomicAdd(counter, (unsigned long long)tot);
+    }
+    __syncthreads();
+  }
+}
+
+// Shadow then mirror queue: traversal with fractal candidates deferred. A
+// shadow ray with an occluder of its own needs no jobs.
+__global__ void __launch_bounds__(128, 4) k_rg_second(BatchView B, uint32_t chunk) {
+  const int lane = threadIdx.x & 31;
+  PR_DECLARE_STACK(128);
+  for (int q = 0; q < 2; ++q) {
+    const bool mirror = q == 1;
+    const uint32_t n = mirror ? B.hdr->mirror_n : B.hdr->shadow_n;
+    uint32_t* ctr = mirror ? &B.hdr->mirror_ctr : &B.hdr->shadow_ctr;
+    for (;;) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(ctr, chunk);
+      base = __shfl_sync(kFull, base, 0);
+      if (base >= n) break;
+      const uint32_t end = min(base + chunk, n);
+      for (uint32_t i0 = base; i0 < end; i0 += 32) {
+        const uint32_t i = i0 + (uint32_t)lane;
+        const bool valid = i < end;
+        Deferred dfr;
+        dfr.n = 0;
+        Hit h;
+        uint32_t req = 0;
+        float3 o = f3(0.f, 0.f, 0.f), d = o;
+        float eps = 0.f;
+        if (valid) {
+          req = mirror ? B.mq_req[i] : B.sq_req[i];
+          const ReqDev& R = B.reqs[req];
+          const float4 a = mirror ? B.mq_a[i] : B.sq_a[i], b = mirror ? B.mq_b[i] : B.sq_b[i];
+          o = f3(a.x, a.y, a.z);
+          d = f3(b.x, b.y, b.z);
+          eps = scene_eps(R.S, R.eps_rel);
+          trace_typed<false, false, kStackDepth, true>(R.S, o, d, mirror ? 0u : 1u, 0.f, mirror ? INFINITY : a.w, eps,
+                                                       R.max_steps, h, stack, nullptr, &dfr);
+          if (!mirror && h.inst >= 0) dfr.n = 0;   // occluded already
+        }
+        const uint32_t first = append_jobs(B, 1, dfr, mirror ? (i | kMirrorSlot) : i, req, mirror);
+        if (valid) {
+          const ReqDev& R = B.reqs[req];
+          if (first == kEmptyJob && dfr.n > 0) {
+            march_in_place(R.S, dfr, o, d, eps, R.max_steps, !mirror, h);
+            dfr.n = 0;
+          }
+          if (mirror) {
+            B.rg_mhit[i] = make_int4(__float_as_int(h.t), h.inst, h.leaf, (int)h.attr);
+            B.rg_mjobs[i] = make_uint2(first, (uint32_t)dfr.n);
+          } else {
+            B.rg_sjobs[i] = make_uint2(first, (uint32_t)dfr.n | (h.inst >= 0 ? 0x80000000u : 0u));
+          }
+        }
+      }
+    }
+  }
+}
+
+// Shadow visibility and mirror shading from the traversal results and the
+// pass-1 jobs; then k_wf_resolve composes every pixel.
+__global__ void __launch_bounds__(128, 4) k_rg_finish(BatchView B, uint32_t chunk) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ns = B.hdr->shadow_n, nm = B.hdr->mirror_n;
+  const MarchJobs& J = B.jobs[1];
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&B.hdr->finish_ctr, chunk);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= ns + nm) break;
+    for (uint32_t i = base + lane; i < base + chunk && i < ns + nm; i += 32) {
+      if (i < ns) {
+        const uint2 sj = B.rg_sjobs[i];
+        bool occluded = (sj.y & 0x80000000u) != 0u;
+        const float tmax = B.sq_a[i].w;
+        for (uint32_t k = 0; k < (sj.y & 0x7FFFFFFFu) && !occluded; ++k) {
+          const float th = J.r[sj.x + k].x;
+          occluded = th >= 0.f && th < tmax;
+        }
+        if (!occluded) atomicOr(&B.st_b[B.sq_px[i]].y, 4u);
+      } else {
+        const uint32_t m = i - ns;
+        const ReqDev& R = B.reqs[B.mq_req[m]];
+        const SceneView& S = R.S;
+        const float4 qa = B.mq_a[m], qb = B.mq_b[m];
+        const float3 orr = f3(qa.x, qa.y, qa.z), dr = f3(qb.x, qb.y, qb.z);
+        const float eps = scene_eps(S, R.eps_rel);
+        const int4 hr = B.rg_mhit[m];
+        const uint2 jr = B.rg_mjobs[m];
+        Hit rh{__int_as_float(hr.x), hr.y, hr.z, (uint32_t)hr.w};
+        const int best = resolve_jobs(S, J, jr.x, jr.y, rh);
+        const uint64_t px = B.mq_px[m];
+        float3 lr;
+        if (rh.inst >= 0) {
+          float3 g;
+          if (best >= 0) {
+            const float4 rr = J.r[best];
+            g = f3(rr.y, rr.z, rr.w);
+          }
+          Surface s2 = surface_at(S, rh, orr, dr, eps, nullptr, best >= 0 ? &g : nullptr);
+          lr = s2.chs == PR_CHS_LAMBERT
+                   ? lambert_rgb(s2.albedo, R.ambient, R.light_intensity, light_ndl(s2, R.light, madd(orr, rh.t, dr)), 1.f)
+                   : f3(0.f, 0.f, 0.f);
+          atomicOr(&B.st_b[px].y, 16u);
+        } else {
+          lr = miss_rgb(S, 0, R.background);
+        }
+        B.refl[px] = make_float4(lr.x, lr.y, lr.z, 0.f);
+      }
+    }
+  }
+}
+
 // Completion flag of a request (batched megakernel modes): every thread
 // fences its image writes of the tile, the CTA synchronises, and thread 0
 // counts the tile; the CTA that finishes the request's last tile publishes
@@ -392,6 +880,23 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
   if (T.megakernel == 1) {
     k_batch_mega<8><<<grid, 128, 0, s>>>(B);
     return 1;
+  }
+  if (T.megakernel == 3) {
+    cudaMemsetAsync(&B.hdr->job_n[0], 0, 6 * sizeof(uint32_t), s);   // job_n, job_ctr, shade_ctr, finish_ctr
+    k_rg_bases<<<(B.max_req + 127) / 128, 128, 0, s>>>(B);
+    const uint32_t grid_m = (uint32_t)n_sm * 8;
+    if (T.tile_w == 32) k_rg_primary<32, 4><<<grid, 128, 0, s>>>(B);
+    else if (T.tile_w == 8) k_rg_primary<8, 16><<<grid, 128, 0, s>>>(B);
+    else k_rg_primary<16, 8><<<grid, 128, 0, s>>>(B);
+    k_rg_march<<<grid_m, 128, 0, s>>>(B, 0);
+    if (T.tile_w == 32) k_rg_shade<32, 4><<<grid, 128, 0, s>>>(B);
+    else if (T.tile_w == 8) k_rg_shade<8, 16><<<grid, 128, 0, s>>>(B);
+    else k_rg_shade<16, 8><<<grid, 128, 0, s>>>(B);
+    k_rg_second<<<grid, 128, 0, s>>>(B, T.queue_chunk);
+    k_rg_march<<<grid_m, 128, 0, s>>>(B, 1);
+    k_rg_finish<<<grid, 128, 0, s>>>(B, T.queue_chunk);
+    k_wf_resolve<<<(uint32_t)n_sm * 8, 256, 0, s>>>(B);
+    return 8;
   }
   if (T.tile_w == 32) k_wf_primary<32, 4><<<grid, 128, 0, s>>>(B);
   else if (T.tile_w == 8) k_wf_primary<8, 16><<<grid, 128, 0, s>>>(B);

@@ -33,6 +33,19 @@ struct BatchHdr {
   // request r is written, notify[r] = seq. notify is host-mapped memory.
   uint32_t* notify;
   uint32_t seq, pad2;
+  // regrouped mode: march jobs appended / claimed per pass (0 primary, 1 shadow + mirror)
+  uint32_t job_n[2], job_ctr[2];
+  uint32_t shade_ctr, finish_ctr, pad3[2];
+};
+
+// One deferred fractal march (regrouped mode), 48 bytes:
+//   a = (t_lo, t_hi, instance, leaf)        slab interval and the hit's key
+//   b = (ray slot, request, shader id | normal << 16, primitive)
+//   r = (t or -1 for a miss, gradient xyz)  written by the march kernel
+struct MarchJobs {
+  float4* a;
+  uint4* b;
+  float4* r;
 };
 
 struct BatchView {
@@ -47,11 +60,24 @@ struct BatchView {
   float4 *mq_a, *mq_b;  // mirror queue
   uint64_t* mq_px;
   uint32_t* mq_req;
+  // regrouped mode: traversal results per ray slot (primary: pixel; shadow /
+  // mirror: queue position) and the deferred march jobs of each pass
+  int4* rg_hit;       // [pixels] primary ray: closest non-fractal hit (t bits, instance, leaf, attr)
+  uint2* rg_jobs;     // [pixels] primary ray: first job, job count
+  int4* rg_mhit;      // [mirror slots] mirror ray hit
+  uint2* rg_mjobs;    // [mirror slots] mirror ray jobs
+  uint2* rg_sjobs;    // [shadow slots] shadow ray: first job, job count | occluded << 31
+  float4* bases;      // [max_req][4] camera basis per request (CameraBasis)
+  MarchJobs jobs[2];  // pass 0 (primary) and pass 1 (shadow and mirror)
+  uint32_t job_cap;   // jobs per pass
+  uint32_t max_req;
 };
 
 struct BatchTuning {
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
-  uint32_t megakernel;   // 1: one persistent megakernel (16x8 tiles), 2: one CTA per 16x8 tile, 0: four stages
+  // 1: one persistent megakernel (16x8 tiles), 2: one CTA per 16x8 tile, 0: four
+  // stages, 3: regrouped stages (fractal marches deferred into a job queue)
+  uint32_t megakernel;
 };
 
 // grid_tiles: CTAs of the one-CTA-per-tile megakernel (at least the batch's tiles); unused otherwise

@@ -64,7 +64,8 @@ def test_batch_bit_identical_to_plain(graph):
 
 
 @pytest.mark.parametrize("shape", [(2, 16, 8, 32, 0), (8, 32, 4, 128, 0), (16, 8, 16, 64, 0), (1, 16, 8, 1024, 0),
-                                   (4, 16, 8, 32, 1), (1, 16, 8, 32, 1), (4, 16, 8, 32, 2)])
+                                   (4, 16, 8, 32, 1), (1, 16, 8, 32, 1), (4, 16, 8, 32, 2),
+                                   (4, 16, 8, 32, 3), (8, 32, 4, 128, 3), (1, 8, 16, 64, 3)])
 def test_batch_launch_shapes_do_not_change_results(shape):
     """Wavefront stages or the batched megakernel, any launch shape: every
     request equals its plain pr_trace image bit for bit."""
@@ -189,11 +190,11 @@ def test_batch_megakernel_needs_16x8_tiles():
     batch.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_batched_megakernel_rays_and_graph(mode):
-    """The batched megakernel (persistent, or one CTA per tile) counts the same
-    rays as the plain launches and runs the same through its CUDA graph; RGB
-    and RGBA outputs both."""
+    """The batched megakernel (persistent, or one CTA per tile) and the
+    regrouped stages count the same rays as the plain launches and run the
+    same through their CUDA graph; RGB and RGBA outputs both."""
     ws = _mixed_workloads()
     objs = [pr.Scene(w.scene) for w in ws]
     plain, rays_plain = _plain(objs, ws)
@@ -230,3 +231,71 @@ def test_tile_megakernel_graph_grows_with_the_batch():
     batch.close()
     a.close()
     b_.close()
+
+
+def _julia_row(width=96, height=72):
+    """Four Julia sets in a row along the view axis (and a mirror slab): every
+    ray through them meets up to four fractal boxes, more march jobs than
+    pixels, so the regrouped stages also march in place."""
+    b = scenes.SceneBuilder()
+    scenes._standard_rays(b)
+    hj, hjs = b.add_hit_group(scenes.IS_JULIA, scenes.CHS_LAMBERT), b.add_hit_group(scenes.IS_JULIA)
+    hb, hbs = b.add_hit_group(scenes.IS_BOX, scenes.CHS_LAMBERT), b.add_hit_group(scenes.IS_BOX)
+    mj, ms = b.add_material((0.8, 0.5, 0.3), 0.2), b.add_material((0.6, 0.6, 0.6), 0.4)
+    a, p = scenes.shape_julia((-0.2, 0.6, 0.2, 0.2))
+    jb = b.add_blas([b.add_geometry([a], [p])])
+    a2, p2 = scenes.shape_box((0, -1.6, 0), (12, 0.01, 12))
+    sb = b.add_blas([b.add_geometry([a2], [p2])])
+    b.add_record(hj, mj, scenes.IS_JULIA, 0)
+    b.add_record(hjs, mj, scenes.IS_JULIA, 0)
+    b.add_record(hb, ms, scenes.IS_BOX, 1)
+    b.add_record(hbs, ms, scenes.IS_BOX, 1)
+    for k in range(4):
+        b.add_instance(jb, scenes.xform_trs((0.15 * k, 0.1 * k, 1.2 * k)), 0)
+    b.add_instance(sb, scenes.xform_trs((0, 0, 0)), 2)
+    cam = scenes.Camera(np.float32([0.3, 0.4, -4.0]), np.float32([0.2, 0.2, 2.0]), np.float32([0, 1, 0]), 50.0)
+    tp = scenes.TraceParams(width, height, max_depth=2, light_pos=np.float32([4, 8, -6]))
+    return scenes.Workload(b.build("julia-row"), cam, tp)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_regrouped_job_overflow_marches_in_place(graph):
+    """More deferred marches than the batch holds jobs (a batch sized for
+    exactly its pixels, four fractal boxes behind one another): the rays whose
+    jobs do not fit march in place, and every image still equals pr_trace."""
+    ws = [_julia_row(), _julia_row(37, 53)]
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, rays_plain = _plain(objs, ws)
+    batch = pr.Batch(2, sum(w.params.width * w.params.height for w in ws))
+    batch.set_tuning(4, 16, 8, 32, 3)
+    outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for w in ws]
+    c = torch.zeros(1, dtype=torch.int64, device="cuda")
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], ray_counter=c, graph=graph)
+    torch.cuda.synchronize()
+    assert int(c.item()) == rays_plain
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+    batch.close()
+    for o in objs:
+        o.close()
+
+
+def test_regrouped_teaser_vs_oracle():
+    """The regrouped stages on the teaser (fractal marches from the job queue,
+    mirror rays): parity with the oracle, and the same image as pr_trace."""
+    from parity import assert_parity
+    w = scenes.teaser(width=192, height=108)
+    sc = pr.Scene(w.scene)
+    batch = pr.Batch(1, 192 * 108)
+    batch.set_tuning(8, 16, 8, 128, 3)
+    out = torch.empty((108, 192, 4), device="cuda")
+    batch.trace([(sc, w.camera, w.params, out)], graph=True)
+    img, aov = sc.trace(w.camera, w.params, want_aov=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out, img)
+    box = sc.bounds()
+    rep = compare(oracle.render(w), pr.aov_to_numpy(aov), out[..., :3].cpu().numpy(),
+                  float(np.linalg.norm(box[3:] - box[:3])), scene=w.scene)
+    assert_parity(rep, "regrouped teaser 192x108")
+    batch.close()
+    sc.close()

@@ -435,8 +435,9 @@ class BatchBench:
         self.trace_launches = {0: 4, 1: 1, 2: 1}[self.tuned["tuning"]["megakernel"]]
 
     def build_all(self):
-        for o in self.objs:
-            o.build_bvh(self.stream)
+        # the 64 scenes' builds run concurrently (pr_build_bvh_many: internal streams
+        # forked from and joined back into the bench stream)
+        self.pr.build_bvh_many(self.objs, self.stream)
 
     def batched_step(self, k):
         e1, e2 = self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True)
@@ -464,10 +465,11 @@ class BatchBench:
             o.close()
 
 
-def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: int, probe=None, sampler=None):
+def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: int, probe=None, sampler=None,
+                n_requests: int = 64):
     """Headline: step = the LBVH builds of the 64 requests' scenes + one batched launch (CUDA
     graph). The plain form (same builds, one pr_trace per request) is timed beside it."""
-    B = BatchBench(pr, torch, stream)
+    B = BatchBench(pr, torch, stream, n_requests)
     with torch.cuda.stream(stream):
         for k in range(warmup):
             B.batched_step(k)
@@ -538,7 +540,7 @@ def batch_e2e(pr, torch, stream, B, n_steps: int, warmup: int, world: int) -> di
             copied[i].synchronize()
         for o, w in zip(B.objs, B.ws):
             o.upload(w.scene, stream)
-            o.build_bvh(stream)
+        pr.build_bvh_many(B.objs, stream)
         B.batch.trace(prepared=prepared[i], ray_counter=counter, stream=stream, graph=True)
         traced[i].record(stream)
         copy_stream.wait_event(traced[i])
@@ -771,12 +773,22 @@ def run_ours(args):
             res["clocks"]["remeasured_after"] = first
         return res
 
+    if args.block:
+        # one block alone (profiling runs)
+        if args.block == "analytic_4096_frames":
+            b = bench_analytic_frames(pr, work, torch, stream, flush, reps=args.steps, probe=probe_tflops)
+        else:
+            b = bench_scene(pr, work, torch, stream, flush, args.block, args.steps, args.warmup, probe_tflops)
+            b["_scene"].close()
+        print(json.dumps({"block": args.block, **_strip(b)}), flush=True)
+        return
     if args.workload == BATCH:
         res = measure(lambda smp: bench_batch(pr, work, torch, stream, flush, args.steps, args.warmup, world,
-                                              probe_tflops, smp))
+                                              probe_tflops, smp, args.requests))
         B = res["B"]
         e2e = None if args.no_e2e else batch_e2e(pr, torch, stream, B, max(3, min(args.steps, 10)), 2, world)
-        config = {"workload": BATCH_DESC, "config": BATCH, "requests": B.n, "pixels": B.total_px,
+        config = {"workload": BATCH_DESC if B.n == 64 else BATCH_DESC.replace("64", str(B.n), 1),
+                  "config": BATCH if B.n == 64 else f"batch{B.n}", "requests": B.n, "pixels": B.total_px,
                   "instances_per_request": [int(len(w.scene.inst_blas)) for w in B.ws],
                   "resolutions": [w.params.width for w in B.ws], "max_depth": 1, "rays_per_pixel_max": 2,
                   "step": "device LBVH builds of the 64 scenes + one batched launch (CUDA graph, autotuned shape)",
@@ -879,6 +891,9 @@ def main():
     ap.add_argument("--serve-only", action="store_true", help="only the serving sweep (both modes), one JSON line")
     ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--requests", type=int, default=64, help="requests of the batch workload (64: the headline)")
+    ap.add_argument("--block", choices=["analytic_4096_frames", "teaser_1080p", "field_100k_2160p"], default=None,
+                    help="run one block alone and print it (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -205,6 +205,14 @@ pr_status pr_scene_upload(pr_scene* scene, const pr_scene_desc* desc, void* stre
  * bottom-up box unions. */
 pr_status pr_build_bvh(pr_scene* scene, void* stream);
 
+/* pr_build_bvh of n scenes, the builds of different scenes running
+ * concurrently: they are spread over a pool of internal streams (created on
+ * the first call per device) that start after the work already enqueued on
+ * `stream`, and `stream`'s later work waits for all of them. Asynchronous;
+ * the first failing build's status is returned (the others are still
+ * enqueued). Calls from several host threads take turns. */
+pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream);
+
 /* Render one frame into out_rgba (device, caller-owned, height*width float4,
  * row-major, alpha = 1; height*width*3 floats with PR_TRACE_OUTPUT_RGB). out_aov (device, height*width pr_aov) is written when
  * params->flags has PR_TRACE_WRITE_AOV, else may be NULL. ray_counter (device
@@ -344,7 +352,7 @@ typedef struct {
 typedef struct pr_batch pr_batch;
 
 /* Allocate a batch for up to max_requests requests and max_pixels pixels in
- * total (about 280 device bytes per pixel: per-pixel state, ray queues, and
+ * total (about 310 device bytes per pixel: per-pixel state, ray queues, and
  * the regrouped mode's traversal results and march jobs). */
 pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch** out);
 

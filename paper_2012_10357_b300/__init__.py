@@ -88,6 +88,7 @@ _sig("pr_sbt_index", _i32, _u32, _u32, _u32, _u32, _u32, _vp)
 _sig("pr_scene_create", _i32, _vp, _vp, _vp)
 _sig("pr_scene_upload", _i32, _vp, _vp, _vp)
 _sig("pr_build_bvh", _i32, _vp, _vp)
+_sig("pr_build_bvh_many", _i32, _vp, _u32, _vp)
 _sig("pr_trace", _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_trace_frames", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_trace_work", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp)
@@ -116,7 +117,7 @@ _sig("pr_scene_destroy", None, _vp)
 _sig("pr_fma_peak_probe", _i32, _u32, _vp, _vp, _vp)
 
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
-            "pr_scene_upload", "pr_build_bvh", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
+            "pr_scene_upload", "pr_build_bvh", "pr_build_bvh_many", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
             "pr_scene_destroy", "pr_lbvh_build", "pr_lbvh_build_noalloc", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
             "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy",
@@ -128,6 +129,13 @@ PR_SERVE_CONTINUOUS, PR_SERVE_PLAIN = 0, 1
 def _check(status: int, where: str):
     if status != PR_OK:
         raise PrError(status, where)
+
+
+def build_bvh_many(scenes, stream=None):
+    """pr_build_bvh_many: the BVHs of many scenes, built concurrently on internal
+    streams ordered after (and joined back into) `stream`."""
+    arr = (ctypes.c_void_p * len(scenes))(*[sc._h.value for sc in scenes])
+    _check(_lib.pr_build_bvh_many(arr, len(scenes), _stream_handle(stream)), "pr_build_bvh_many")
 
 
 def version() -> int:

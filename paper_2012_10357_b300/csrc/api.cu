@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -62,7 +63,11 @@ struct Layout {
   uint32_t stack_bound = 0;
 };
 
-pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
+// check = false skips the per-element value checks (finite AABBs and
+// vertices, index ranges, invertible transforms, record ranges) of a
+// description already validated (the serving loop's copy, checked at submit);
+// counts and ranges needed to flatten it are always checked.
+pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L, bool check = true) {
   if (!d) return fail(PR_ERR_INVALID_ARG, "null scene description");
   if (d->struct_size != sizeof(pr_scene_desc))
     return fail(PR_ERR_INVALID_ARG, "pr_scene_desc.struct_size mismatch (ABI version)");
@@ -95,7 +100,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
       !need(d->materials, L.n_mat, "materials") || !need(d->sbt, L.n_rec, "sbt") ||
       !need(d->ray_types, L.n_rt, "ray_types"))
     return PR_ERR_INVALID_ARG;
-  for (uint32_t p = 0; p < L.n_prims; ++p) {
+  for (uint32_t p = 0; check && p < L.n_prims; ++p) {
     const float* b = d->aabbs + 6 * (size_t)p;
     for (int k = 0; k < 3; ++k)
       if (!(std::isfinite(b[k]) && std::isfinite(b[3 + k]) && b[k] <= b[3 + k]))
@@ -106,9 +111,9 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
   if ((L.n_vert && !d->vertices) || (L.n_tri && !d->indices))
     return fail(PR_ERR_INVALID_ARG, "null vertices/indices");
   if (L.n_vert > (1u << 28) || L.n_tri > (1u << 28)) return fail(PR_ERR_INVALID_ARG, "too many vertices/triangles");
-  for (uint32_t v = 0; v < 3 * L.n_vert; ++v)
+  for (uint32_t v = 0; check && v < 3 * L.n_vert; ++v)
     if (!std::isfinite(d->vertices[v])) return fail(PR_ERR_INVALID_ARG, "vertex not finite");
-  for (uint32_t t = 0; t < 3 * L.n_tri; ++t)
+  for (uint32_t t = 0; check && t < 3 * L.n_tri; ++t)
     if (d->indices[t] >= L.n_vert) return fail(PR_ERR_INVALID_ARG, "triangle vertex index out of range");
   auto is_tri = [&](uint32_t g) { return d->geom_type && d->geom_type[g] == PR_GEOM_TRIANGLES; };
   for (uint32_t g = 0; g < L.n_geoms; ++g) {
@@ -153,7 +158,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
   L.stack_bound += L.n_inst ? L.n_inst - 1 : 0;
   if (L.n_inst > kSmallMax) L.max_large = std::max(L.max_large, L.n_inst);
   uint64_t max_index = 0;
-  for (uint32_t k = 0; k < L.n_inst; ++k) {
+  for (uint32_t k = 0; check && k < L.n_inst; ++k) {
     if (d->inst_blas[k] >= L.n_blas) return fail(PR_ERR_INVALID_ARG, "instance " + std::to_string(k) + " BLAS out of range");
     const float* x = d->inst_xform + 12 * (size_t)k;
     for (int i = 0; i < 12; ++i)
@@ -175,7 +180,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L) {
       return fail(PR_ERR_INVALID_ARG, "any-hit shaders need an analytic intersection shader (sphere, box, pac-man)");
     if (is != PR_NONE && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN) L.analytic_only = false;
   }
-  for (uint32_t r = 0; r < L.n_rec; ++r) {
+  for (uint32_t r = 0; check && r < L.n_rec; ++r) {
     if (d->sbt[4 * r] >= L.n_hg) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " hit group out of range");
     if (d->sbt[4 * r + 1] >= L.n_mat) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " material out of range");
   }
@@ -469,11 +474,12 @@ namespace {
 // pr_scene_create; with `ext` (pinned, at least the scene's input bytes) the
 // inputs go up through that buffer and the scene gets no staging buffer of its
 // own until a later pr_scene_upload.
-pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext, size_t ext_bytes, pr_scene** out) {
+pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext, size_t ext_bytes, pr_scene** out,
+                       bool check = true) {
   if (!out) return fail(PR_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
   pr_scene* s = new pr_scene();
-  pr_status vs = validate_and_flatten(desc, s->L);
+  pr_status vs = validate_and_flatten(desc, s->L, check);
   if (vs != PR_OK) {
     delete s;
     return vs;
@@ -586,7 +592,7 @@ pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext
 
 pr_status pr_internal_scene_create_staged(const pr_scene_desc* desc, cudaStream_t stream, void* staging,
                                           size_t staging_bytes, pr_scene** out) {
-  return create_scene(desc, stream, static_cast<char*>(staging), staging_bytes, out);
+  return create_scene(desc, stream, static_cast<char*>(staging), staging_bytes, out, false);
 }
 
 extern "C" {
@@ -606,6 +612,63 @@ pr_status pr_scene_upload(pr_scene* s, const pr_scene_desc* desc, void* stream) 
     return fail(PR_ERR_INVALID_ARG, "pr_scene_upload needs the same counts and BLAS layout as at creation");
   s->L = std::move(L);
   return upload(s, desc, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Streams the builds of pr_build_bvh_many fan out to, one pool per device,
+// created on first use and kept for the life of the process.
+constexpr int kBuildStreams = 8;
+struct BuildPool {
+  cudaStream_t streams[kBuildStreams] = {};
+  cudaEvent_t done[kBuildStreams] = {};
+  cudaEvent_t start = nullptr;
+  bool ready = false;
+};
+std::mutex g_pool_mutex;
+BuildPool g_pools[64];
+
+}  // namespace
+
+extern "C" {
+
+pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
+  if (n == 0) return PR_OK;
+  if (!scenes) return fail(PR_ERR_INVALID_ARG, "null scene array");
+  for (uint32_t i = 0; i < n; ++i)
+    if (!scenes[i]) return fail(PR_ERR_INVALID_ARG, "null scene in the array");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 1) return pr_build_bvh(scenes[0], stream);
+  int dev = 0;
+  PR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(PR_ERR_INVALID_ARG, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(g_pool_mutex);   // one fan-out at a time per process
+  BuildPool& P = g_pools[dev];
+  if (!P.ready) {
+    for (int k = 0; k < kBuildStreams; ++k) {
+      PR_CUDA(cudaStreamCreateWithFlags(&P.streams[k], cudaStreamNonBlocking), "build stream");
+      PR_CUDA(cudaEventCreateWithFlags(&P.done[k], cudaEventDisableTiming), "build event");
+    }
+    PR_CUDA(cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming), "build event");
+    P.ready = true;
+  }
+  const int used = (int)std::min<uint32_t>(n, kBuildStreams);
+  // fork: every pool stream waits for the work already on `stream`
+  PR_CUDA(cudaEventRecord(P.start, st), "record fork");
+  for (int k = 0; k < used; ++k) PR_CUDA(cudaStreamWaitEvent(P.streams[k], P.start, 0), "fork");
+  pr_status result = PR_OK;
+  for (uint32_t i = 0; i < n; ++i) {
+    const pr_status b = pr_build_bvh(scenes[i], P.streams[i % kBuildStreams]);
+    if (b != PR_OK && result == PR_OK) result = b;
+  }
+  // join: `stream` waits for every build
+  for (int k = 0; k < used; ++k) {
+    PR_CUDA(cudaEventRecord(P.done[k], P.streams[k]), "record join");
+    PR_CUDA(cudaStreamWaitEvent(st, P.done[k], 0), "join");
+  }
+  return result;
 }
 
 pr_status pr_build_bvh(pr_scene* s, void* stream) {

@@ -176,9 +176,12 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   // (one job per pixel per pass; rays beyond that march in place)
   size_t o_rgh = take(16 * P), o_rgj = take(8 * P), o_rgmh = take(16 * P), o_rgmj = take(8 * P),
          o_rgsj = take(8 * P), o_bases = take(64 * (size_t)max_requests);
-  size_t o_job[2][3];
-  for (int pass = 0; pass < 2; ++pass)
-    for (int k = 0; k < 3; ++k) o_job[pass][k] = take(16 * P);
+  const uint64_t job_cap = (P + 1) / 2;   // jobs per pass; rays beyond march in place
+  size_t o_job[2][2];
+  for (int pass = 0; pass < 2; ++pass) {
+    o_job[pass][0] = take(16 * kJobRows * job_cap);
+    o_job[pass][1] = take(16 * job_cap);
+  }
   b->arena_bytes = off;
   cudaError_t e = cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
@@ -207,10 +210,9 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   b->V.bases = reinterpret_cast<float4*>(A + o_bases);
   for (int pass = 0; pass < 2; ++pass) {
     b->V.jobs[pass].a = reinterpret_cast<float4*>(A + o_job[pass][0]);
-    b->V.jobs[pass].b = reinterpret_cast<uint4*>(A + o_job[pass][1]);
-    b->V.jobs[pass].r = reinterpret_cast<float4*>(A + o_job[pass][2]);
+    b->V.jobs[pass].r = reinterpret_cast<float4*>(A + o_job[pass][1]);
   }
-  b->V.job_cap = (uint32_t)P;
+  b->V.job_cap = (uint32_t)job_cap;
   b->V.max_req = max_requests;
   e = cudaMallocHost(&b->staging, a256(sizeof(BatchHdr)) + sizeof(ReqDev) * max_requests);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);

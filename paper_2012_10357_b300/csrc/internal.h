@@ -99,7 +99,9 @@ bool pr_internal_built(const pr_scene* s);
 pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes, size_t* input_bytes);
 // pr_scene_create whose inputs go up through the caller's pinned buffer
 // `staging` (at least the input bytes; the caller reuses it only after the
-// copy on `stream` is done) instead of a pinned buffer of the scene's own.
+// copy on `stream` is done) instead of a pinned buffer of the scene's own,
+// for a description already validated by pr_internal_scene_bytes (its
+// per-element value checks are not repeated).
 pr_status pr_internal_scene_create_staged(const pr_scene_desc* desc, cudaStream_t stream, void* staging,
                                           size_t staging_bytes, pr_scene** out);
 // Completion flags for the next pr_trace_batch[_graph] of this batch: when

@@ -48,6 +48,7 @@ struct Deferred {
   int inst[kMaxDeferred], leaf[kMaxDeferred];
   uint32_t is_id[kMaxDeferred], prim[kMaxDeferred];
   float t_lo[kMaxDeferred], t_hi[kMaxDeferred];
+  float3 oo[kMaxDeferred], dd[kMaxDeferred];   // the ray in the instance's object space
 };
 
 __device__ __forceinline__ bool is_fractal(uint32_t id) {
@@ -138,6 +139,8 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       defer->prim[i] = prim;
       defer->t_lo[i] = t_lo;
       defer->t_hi[i] = t_hi;
+      defer->oo[i] = oo;
+      defer->dd[i] = dd;
       return false;
     }
     IsResult res;

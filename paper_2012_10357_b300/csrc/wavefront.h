@@ -38,14 +38,17 @@ struct BatchHdr {
   uint32_t shade_ctr, finish_ctr, pad3[2];
 };
 
-// One deferred fractal march (regrouped mode), 48 bytes:
-//   a = (t_lo, t_hi, instance, leaf)        slab interval and the hit's key
-//   b = (ray slot, request, shader id | normal << 16, primitive)
-//   r = (t or -1 for a miss, gradient xyz)  written by the march kernel
+// One deferred fractal march (regrouped mode), self-contained so that a lane
+// starting a job issues independent loads only (128 bytes):
+//   a[0] = object-space origin xyz, t_lo    a[1] = object-space direction xyz, t_hi
+//   a[2] = instance, leaf, shader id | normal << 16, ray slot (bits)
+//   a[3] = eps, step cap (bits), request (bits), unused
+//   a[4..6] = the primitive's first three parameter rows
+//   r = (t or -1 for a miss, gradient xyz), written by the march kernel
+constexpr int kJobRows = 7;
 struct MarchJobs {
-  float4* a;
-  uint4* b;
-  float4* r;
+  float4* a;   // [cap][kJobRows]
+  float4* r;   // [cap]
 };
 
 struct BatchView {

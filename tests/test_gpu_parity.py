@@ -492,3 +492,24 @@ def test_triangle_mesh_with_spheres_strict():
     w = _mesh_and_spheres()
     rep = check_full(w, "triangle mesh + spheres")
     assert rep["hits"] > 1000
+
+
+def test_build_many_equals_single_builds():
+    """pr_build_bvh_many (builds of many scenes spread over internal streams,
+    joined back into the caller's stream) gives every scene the BVH and image
+    of its own pr_build_bvh, also when the scenes are rebuilt in place."""
+    ws = scenes.batch_requests(3, 12, res_choices=(48, 64))
+    ref = [pr.Scene(w.scene) for w in ws]                 # built one by one
+    many = [pr.Scene(w.scene, build=False) for w in ws]
+    stream = torch.cuda.Stream()
+    for _ in range(2):
+        pr.build_bvh_many(many, stream=stream)
+        imgs = [m.trace(w.camera, w.params, stream=stream) for m, w in zip(many, ws)]
+        stream.synchronize()
+        for r, m, w, img in zip(ref, many, ws, imgs):
+            a, b = r.read_bvh(pr.PR_NONE), m.read_bvh(pr.PR_NONE)
+            for k in a:
+                assert np.array_equal(a[k], b[k])
+            assert torch.equal(r.trace(w.camera, w.params), img)
+    for s in ref + many:
+        s.close()

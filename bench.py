@@ -406,9 +406,10 @@ def bench_analytic_frames(pr, work, torch, stream, flush, frames=4096, reps=5, p
 class BatchBench:
     """The 64-request batch: scenes, outputs, the batch object and its tuning."""
 
-    def __init__(self, pr, torch, stream, n_requests=64):
+    def __init__(self, pr, torch, stream, n_requests=64, tuning=None, ws=None):
         self.pr, self.torch, self.stream = pr, torch, stream
-        self.ws = scenes.batch_requests(0, n_requests)
+        self.ws = ws if ws is not None else scenes.batch_requests(0, n_requests)
+        n_requests = len(self.ws)
         self.n = n_requests
         self.total_px = sum(w.params.width * w.params.height for w in self.ws)
         with torch.cuda.stream(stream):
@@ -421,7 +422,10 @@ class BatchBench:
         tune_path = os.path.join(ROOT, "paper_2012_10357_b300", "tuning_cache.json")
         key = f"{torch.cuda.get_device_name()}|batch|{n_requests}|{self.total_px}"
         cache = json.load(open(tune_path)) if os.path.exists(tune_path) else {}
-        if key in cache:
+        if tuning is not None:
+            self.batch.set_tuning(**tuning)
+            self.tuned = {"tuning": tuning, "ms": None, "from_cache": False, "given": True}
+        elif key in cache:
             self.batch.set_tuning(**cache[key]["tuning"])
             self.tuned = dict(cache[key], from_cache=True)
         else:
@@ -466,10 +470,10 @@ class BatchBench:
 
 
 def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: int, probe=None, sampler=None,
-                n_requests: int = 64):
+                n_requests: int = 64, tuning=None, ws=None):
     """Headline: step = the LBVH builds of the 64 requests' scenes + one batched launch (CUDA
     graph). The plain form (same builds, one pr_trace per request) is timed beside it."""
-    B = BatchBench(pr, torch, stream, n_requests)
+    B = BatchBench(pr, torch, stream, n_requests, tuning, ws)
     with torch.cuda.stream(stream):
         for k in range(warmup):
             B.batched_step(k)
@@ -773,10 +777,22 @@ def run_ours(args):
             res["clocks"]["remeasured_after"] = first
         return res
 
+    tuning_arg = None
+    if args.tuning:
+        v = [int(x) for x in args.tuning.split(",")]
+        tuning_arg = dict(ctas_per_sm=v[0], tile_w=v[1], tile_h=v[2], queue_chunk=v[3], megakernel=v[4])
     if args.block:
         # one block alone (profiling runs)
         if args.block == "analytic_4096_frames":
             b = bench_analytic_frames(pr, work, torch, stream, flush, reps=args.steps, probe=probe_tflops)
+        elif args.block == "teaser_1080p_batched":
+            # the 1080p teaser as a one-request batch through the batched path (--tuning picks the mode)
+            res = bench_batch(pr, work, torch, stream, flush, args.steps, args.warmup, 1, probe_tflops, None, 1,
+                              tuning_arg, [scenes.teaser()])
+            res["B"].close()
+            b = {"workload": "teaser 1080p, one-request batch", "value": res["value"],
+                 "ms_per_step": res["total_ms"] / args.steps, "tuning": res["autotune"], "roofline": res["roofline"],
+                 "plain": res["plain"], "images_identical_to_plain": res["images_identical_to_plain"]}
         else:
             b = bench_scene(pr, work, torch, stream, flush, args.block, args.steps, args.warmup, probe_tflops)
             b["_scene"].close()
@@ -784,7 +800,7 @@ def run_ours(args):
         return
     if args.workload == BATCH:
         res = measure(lambda smp: bench_batch(pr, work, torch, stream, flush, args.steps, args.warmup, world,
-                                              probe_tflops, smp, args.requests))
+                                              probe_tflops, smp, args.requests, tuning_arg))
         B = res["B"]
         e2e = None if args.no_e2e else batch_e2e(pr, torch, stream, B, max(3, min(args.steps, 10)), 2, world)
         config = {"workload": BATCH_DESC if B.n == 64 else BATCH_DESC.replace("64", str(B.n), 1),
@@ -892,8 +908,11 @@ def main():
     ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=64, help="requests of the batch workload (64: the headline)")
-    ap.add_argument("--block", choices=["analytic_4096_frames", "teaser_1080p", "field_100k_2160p"], default=None,
+    ap.add_argument("--block", choices=["analytic_4096_frames", "teaser_1080p", "field_100k_2160p",
+                                        "teaser_1080p_batched"], default=None,
                     help="run one block alone and print it (profiling)")
+    ap.add_argument("--tuning", default=None,
+                    help="batch launch shape ctas_per_sm,tile_w,tile_h,queue_chunk,mode instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

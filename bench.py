@@ -171,7 +171,14 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
                  "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
-TRACE_TRAFFIC = {}   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
+TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
+    # ncu --set full captures (profiles/); batch64: the 8-request batch's 144.47 MB
+    # scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
+    "5174da99a2fda4219be94adab225e438c3fffe0d": {"batch64": 761_748_000,
+                                                 "teaser_1080p": 124_416 + 299_776,
+                                                 "field_100k_2160p": 6_071_808 + 51_714_816,
+                                                 "analytic_64x64_x4096": 344_576 + 168_004_608},
+}
 
 
 def trace_sources_sha1() -> str:
@@ -436,7 +443,7 @@ class BatchBench:
                 json.dump(cache, f, indent=1)
         self.prepared = self.batch.prepare(items)
         # kernels of the batched launch per tuning mode: four stages, or one megakernel
-        self.trace_launches = {0: 4, 1: 1, 2: 1}[self.tuned["tuning"]["megakernel"]]
+        self.trace_launches = {0: 4, 1: 1, 2: 1, 3: 8}[self.tuned["tuning"]["megakernel"]]
 
     def build_all(self):
         # the 64 scenes' builds run concurrently (pr_build_bvh_many: internal streams
@@ -508,7 +515,8 @@ def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: 
     counters = [o.trace_work(w.camera, w.params, stream=stream) for o, w in zip(B.objs, B.ws)]
     torch.cuda.synchronize()
     kernel = {0: "k_wf_primary/shadow/mirror/resolve (wavefront stages)", 1: "k_batch_mega (persistent)",
-              2: "k_batch_mega_tiles (one CTA per tile)"}[B.tuned["tuning"]["megakernel"]]
+              2: "k_batch_mega_tiles (one CTA per tile)",
+              3: "k_rg_* (regrouped stages with march jobs)"}[B.tuned["tuning"]["megakernel"]]
     roof = roofline(work, torch, counters, statistics.mean(trace_ms) / 1e3, kernel, BATCH, clocks, probe)
     roof["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
     res = {"value": rays_all / (total_ms / 1e3) / 1e6, "total_ms": total_ms, "rays": rays,

@@ -269,18 +269,19 @@ def timed(torch, stream, flush, steps, body, sampler=None):
 
 
 def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: int, probe=None,
-                binary_tlas: bool = False, sampler=None) -> dict:
-    """One scene, one frame per step: device LBVH build + pr_trace."""
+                binary_tlas: bool = False, sampler=None, build_flags: int = 0) -> dict:
+    """One scene, one frame per step: device BVH build (LBVH; the TLAS by PLOC with
+    PR_BUILD_TLAS_PLOC) + pr_trace."""
     w = workload_by_name(name)
     H, W = w.params.height, w.params.width
     with torch.cuda.stream(stream):
-        scene = pr.Scene(w.scene, stream=stream)
+        scene = pr.Scene(w.scene, stream=stream, build_flags=build_flags)
         out = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
         counter = torch.zeros(1, dtype=torch.int64, device="cuda")
 
     def step(k):
         e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        scene.build_bvh(stream)
+        scene.build_bvh(stream, build_flags)
         e1.record(stream)
         scene.trace(w.camera, w.params, out=out, ray_counter=counter, stream=stream, binary_tlas=binary_tlas)
         e2.record(stream)
@@ -303,7 +304,13 @@ def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: i
     n_build, n_trace = scene.kernel_launches()
     counters = scene.trace_work(w.camera, w.params, stream=stream, binary_tlas=binary_tlas)
     torch.cuda.synchronize()
-    block = {"workload": workload_config(name, w)["workload"], "config": workload_config(name, w),
+    config = workload_config(name, w)
+    ploc = bool(build_flags & pr.PR_BUILD_TLAS_PLOC) and len(w.scene.inst_blas) > 1024
+    config["tlas_builder"] = "ploc" if ploc else "lbvh"
+    if ploc:
+        config["step"] = "device build (BLAS: LBVH, TLAS: PLOC) + one frame"
+    n_rays = max(1, counters.get("rays", 0))
+    block = {"workload": config["workload"], "config": config,
              "value": rays / (sum(step_ms) / 1e3) / 1e6, "unit": "Mrays/s", "steps": steps,
              "ms_per_step": sum(step_ms) / steps, "rays_per_step": rays / steps,
              "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -312,7 +319,9 @@ def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: i
              "gpu_launches_per_step": n_build + n_trace,
              "roofline": roofline(work, torch, [counters], statistics.mean(trace_ms) / 1e3, "k_trace (megakernel)",
                                   name, clocks, probe, binary_tlas),
-             "device_error_word": scene.error_word(stream)}
+             "device_error_word": scene.error_word(stream),
+             "traversal_per_ray": {k: counters.get(k, 0) / n_rays
+                                   for k in ("tlas_nodes4", "tlas_nodes", "instances", "blas_nodes", "leaves")}}
     block["roofline"]["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
     block["roofline"]["work_counters"] = {k: v for k, v in counters.items() if v}
     if clocks:
@@ -802,7 +811,9 @@ def run_ours(args):
                  "ms_per_step": res["total_ms"] / args.steps, "tuning": res["autotune"], "roofline": res["roofline"],
                  "plain": res["plain"], "images_identical_to_plain": res["images_identical_to_plain"]}
         else:
-            b = bench_scene(pr, work, torch, stream, flush, args.block, args.steps, args.warmup, probe_tflops)
+            flags = pr.PR_BUILD_TLAS_PLOC if args.tlas_builder == "ploc" else 0
+            b = bench_scene(pr, work, torch, stream, flush, args.block, args.steps, args.warmup, probe_tflops,
+                            args.binary_tlas, build_flags=flags)
             b["_scene"].close()
         print(json.dumps({"block": args.block, **_strip(b)}), flush=True)
         return
@@ -853,11 +864,22 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra and rank == 0:
+        field_img = None
         for name, steps in (("teaser_1080p", 500), ("field_100k_2160p", 60)):
             if name != args.workload:
                 b = bench_scene(pr, work, torch, stream, flush, name, steps, 3, probe_tflops)
+                if name == "field_100k_2160p":
+                    field_img = b["_out"].clone()
                 b["_scene"].close()
                 extra[name] = _strip(b)
+        # the same field with its TLAS built by PLOC (same images, fewer node visits)
+        b = bench_scene(pr, work, torch, stream, flush, "field_100k_2160p", 60, 3, probe_tflops,
+                        build_flags=pr.PR_BUILD_TLAS_PLOC)
+        if field_img is not None:
+            b["images_identical_to_lbvh"] = bool(torch.equal(b["_out"], field_img))
+            del field_img
+        b["_scene"].close()
+        extra["field_100k_2160p_ploc"] = _strip(b)
         extra["analytic_4096_frames"] = bench_analytic_frames(pr, work, torch, stream, flush, probe=probe_tflops)
         if tuning is None:
             tuning = {"ctas_per_sm": 4, "tile_w": 16, "tile_h": 8, "queue_chunk": 32, "megakernel": 2}
@@ -914,6 +936,8 @@ def main():
     ap.add_argument("--serve-max-seconds", type=float, default=40.0)
     ap.add_argument("--serve-only", action="store_true", help="only the serving sweep (both modes), one JSON line")
     ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
+    ap.add_argument("--tlas-builder", choices=["lbvh", "ploc"], default="lbvh",
+                    help="TLAS builder of a --block scene (PLOC: PR_BUILD_TLAS_PLOC)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=64, help="requests of the batch workload (64: the headline)")
     ap.add_argument("--block", choices=["analytic_4096_frames", "teaser_1080p", "field_100k_2160p",

@@ -213,6 +213,34 @@ pr_status pr_build_bvh(pr_scene* scene, void* stream);
  * enqueued). Calls from several host threads take turns. */
 pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream);
 
+/* Build options (pr_build_bvh_ex, pr_build_bvh_many_ex). */
+#define PR_BUILD_TLAS_PLOC 1u   /* a TLAS of more than 1024 instances is built by
+                                   PLOC (parallel locally-ordered clustering,
+                                   Meister & Bittner 2018) instead of the LBVH:
+                                   the same Morton order, then mutual nearest
+                                   neighbours (by the surface area of their
+                                   union, within 16 clusters on either side)
+                                   merged bottom-up; a tree of lower SAH cost
+                                   in the same node layout, built in one
+                                   cooperative launch. Smaller TLASes and every
+                                   BLAS keep the LBVH. */
+
+/* pr_build_bvh with options (a bitwise or of PR_BUILD_* flags; 0 is
+ * pr_build_bvh). PR_ERR_INVALID_ARG for an unknown flag; PR_ERR_CUDA when the
+ * device refuses the cooperative launch. The clustering launch waits at
+ * grid-wide barriers with a 2 s limit; should one run out (its blocks not
+ * all resident, which the cooperative launch rules out), the LBVH passes
+ * enqueued after it build the TLAS instead and the scene's error word gets
+ * bit 1<<PR_ERR_TIMEOUT. Build PLOC scenes of one device from one stream at
+ * a time or through pr_build_bvh_many_ex: two clustering launches must not
+ * run side by side. */
+pr_status pr_build_bvh_ex(pr_scene* scene, uint32_t flags, void* stream);
+
+/* pr_build_bvh_many with options; the clustering launches of the builds run
+ * one after another (each waits for the previous one), the rest of the
+ * builds concurrently. */
+pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t flags, void* stream);
+
 /* Render one frame into out_rgba (device, caller-owned, height*width float4,
  * row-major, alpha = 1; height*width*3 floats with PR_TRACE_OUTPUT_RGB). out_aov (device, height*width pr_aov) is written when
  * params->flags has PR_TRACE_WRITE_AOV, else may be NULL. ray_counter (device
@@ -243,7 +271,8 @@ pr_status pr_trace_work(pr_scene* scene, const pr_camera* cameras, uint32_t n_fr
                         float* out_rgba, uint64_t* work_counters, void* stream);
 
 /* Read and clear the scene's device error word on `stream` (synchronises the
- * stream). Bits: 1<<PR_ERR_SBT_INDEX, 1<<PR_ERR_STACK_OVERFLOW. */
+ * stream). Bits: 1<<PR_ERR_SBT_INDEX, 1<<PR_ERR_STACK_OVERFLOW, and
+ * 1<<PR_ERR_TIMEOUT when a PLOC build fell back to the LBVH. */
 pr_status pr_scene_error(pr_scene* scene, void* stream, uint32_t* error_word);
 
 /* Scene diagonal and TLAS root box as built (synchronises the stream). */

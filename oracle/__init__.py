@@ -93,6 +93,7 @@ def load(path: str):
     L.or_triplex_pow.argtypes = [vp, dbl, vp]
     L.or_instance_boxes_f32.argtypes = [vp, vp]
     L.or_lbvh_f32.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+    L.or_ploc_f32.argtypes = [vp, u32, u32, vp, vp, vp, vp, vp]
     return L
 
 
@@ -226,6 +227,23 @@ def lbvh_f32(boxes: np.ndarray):
     root = np.zeros(6, np.float32)
     if n:
         lib().or_lbvh_f32(_ptr(boxes), n, _ptr(perm), _ptr(codes), _ptr(child), _ptr(cbox), _ptr(root))
+    return dict(perm=perm, codes=codes, child=child, cbox=cbox, root=root)
+
+
+def ploc_f32(boxes: np.ndarray, radius: int = 16):
+    """Reference PLOC tree over [n,6] float32 boxes (same Morton order and output
+    layout as lbvh_f32) -> dict(perm, codes, child, cbox, root)."""
+    boxes = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
+    n = len(boxes)
+    perm = np.zeros(n, np.uint32)
+    codes = np.zeros(n, np.uint32)
+    child = np.zeros((max(n - 1, 0), 2), np.int32)
+    cbox = np.zeros((max(n - 1, 0), 12), np.float32)
+    root = np.zeros(6, np.float32)
+    if n:
+        rc = lib().or_ploc_f32(_ptr(boxes), n, radius, _ptr(perm), _ptr(codes), _ptr(child), _ptr(cbox), _ptr(root))
+        if rc:
+            raise ValueError(f"or_ploc_f32 failed ({rc})")
     return dict(perm=perm, codes=codes, child=child, cbox=cbox, root=root)
 
 

@@ -780,6 +780,47 @@ void build_range(TreeBuild& T, uint32_t first, uint32_t last, uint32_t node, flo
   box_union(lbox, rbox, out_box);
 }
 
+// Morton keys of the LBVH: code << 32 | leaf index, unsorted.
+std::vector<uint64_t> morton_keys(const float* boxes, uint32_t n) {
+  // Centroids (lo + hi) * 0.5 and their bounds.
+  std::vector<float> cen(3 * (size_t)n);
+  float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      float c = (boxes[6 * (size_t)i + k] + boxes[6 * (size_t)i + 3 + k]) * 0.5f;
+      cen[3 * (size_t)i + k] = c;
+      clo[k] = std::min(clo[k], c);
+      chi[k] = std::max(chi[k], c);
+    }
+  // Morton code: per axis u = (c - lo) / extent (0 when the extent is 0),
+  // q = floor(u * 1024) clamped to 1023, bits interleaved x, y, z (x highest).
+  std::vector<uint64_t> keys(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      float ext = chi[k] - clo[k];
+      float u = ext > 0.0f ? (cen[3 * (size_t)i + k] - clo[k]) / ext : 0.0f;
+      float qf = u * 1024.0f;
+      uint32_t qi = (uint32_t)qf;
+      q[k] = qi > 1023u ? 1023u : qi;
+    }
+    uint32_t code = (spread_bits(q[0]) << 2) | (spread_bits(q[1]) << 1) | spread_bits(q[2]);
+    keys[i] = ((uint64_t)code << 32) | i;
+  }
+  return keys;
+}
+
+// Half the surface area of the union of two boxes, dx dy + dy dz + dz dx in
+// float, evaluated as fma(dx, dy, fma(dy, dz, dz * dx)) (the precision and
+// order the device builder decides merges in); NaN orders last.
+float union_half_area(const float* a, const float* b) {
+  const float dx = std::max(a[3], b[3]) - std::min(a[0], b[0]);
+  const float dy = std::max(a[4], b[4]) - std::min(a[1], b[1]);
+  const float dz = std::max(a[5], b[5]) - std::min(a[2], b[2]);
+  const float s = std::fma(dx, dy, std::fma(dy, dz, dz * dx));
+  return std::isnan(s) ? INFINITY : s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -874,31 +915,7 @@ int or_instance_boxes_f32(const or_scene* s, float* boxes_out) {
 int or_lbvh_f32(const float* boxes, uint32_t n, uint32_t* perm_out, uint32_t* codes_out, int32_t* child_out,
                 float* cbox_out, float* root_box) {
   if (n == 0) return 0;
-  // Centroids (lo + hi) * 0.5 and their bounds.
-  std::vector<float> cen(3 * (size_t)n);
-  float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (uint32_t i = 0; i < n; ++i)
-    for (int k = 0; k < 3; ++k) {
-      float c = (boxes[6 * (size_t)i + k] + boxes[6 * (size_t)i + 3 + k]) * 0.5f;
-      cen[3 * (size_t)i + k] = c;
-      clo[k] = std::min(clo[k], c);
-      chi[k] = std::max(chi[k], c);
-    }
-  // Morton code: per axis u = (c - lo) / extent (0 when the extent is 0),
-  // q = floor(u * 1024) clamped to 1023, bits interleaved x, y, z (x highest).
-  std::vector<uint64_t> keys(n);
-  for (uint32_t i = 0; i < n; ++i) {
-    uint32_t q[3];
-    for (int k = 0; k < 3; ++k) {
-      float ext = chi[k] - clo[k];
-      float u = ext > 0.0f ? (cen[3 * (size_t)i + k] - clo[k]) / ext : 0.0f;
-      float qf = u * 1024.0f;
-      uint32_t qi = (uint32_t)qf;
-      q[k] = qi > 1023u ? 1023u : qi;
-    }
-    uint32_t code = (spread_bits(q[0]) << 2) | (spread_bits(q[1]) << 1) | spread_bits(q[2]);
-    keys[i] = ((uint64_t)code << 32) | i;
-  }
+  std::vector<uint64_t> keys = morton_keys(boxes, n);
   std::sort(keys.begin(), keys.end());
   std::vector<uint32_t> perm(n);
   for (uint32_t i = 0; i < n; ++i) {
@@ -912,6 +929,87 @@ int or_lbvh_f32(const float* boxes, uint32_t n, uint32_t* perm_out, uint32_t* co
   }
   TreeBuild T{keys, boxes, perm, child_out, cbox_out};
   build_range(T, 0, n - 1, 0, root_box);
+  return 0;
+}
+
+// PLOC (parallel locally-ordered clustering, Meister & Bittner 2018), one
+// round after another on one thread. The clusters start as the leaves in the
+// LBVH's Morton order. In each round every cluster i picks as its nearest
+// neighbour the cluster j != i within `radius` positions of it whose pair
+// {i, j} is least in the order: surface area of the union, then |i - j|, then
+// min(i, j) even before odd, then min(i, j) (a total order on pairs, so the
+// least pair of a round is mutual; on equal boxes it pairs 0-1, 2-3, ...
+// and halves the list each round); every pair
+// of mutual nearest neighbours i < j becomes a new node (left child i, right
+// child j) that takes i's place while j leaves the list, the other clusters
+// keeping their order. The nodes are numbered n-2, n-3, ... in the order they
+// are made (round by round, within a round by position), so the last one is
+// the root 0. Same output layout as or_lbvh_f32 (leaves 0x80000000 | sorted
+// position).
+int or_ploc_f32(const float* boxes, uint32_t n, uint32_t radius, uint32_t* perm_out, uint32_t* codes_out,
+                int32_t* child_out, float* cbox_out, float* root_box) {
+  if (n == 0) return 0;
+  if (radius == 0) return 1;
+  std::vector<uint64_t> keys = morton_keys(boxes, n);
+  std::sort(keys.begin(), keys.end());
+  struct Cluster {
+    int32_t ref;
+    float box[6];
+  };
+  std::vector<Cluster> C(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t leaf = (uint32_t)(keys[i] & 0xFFFFFFFFu);
+    perm_out[i] = leaf;
+    codes_out[i] = (uint32_t)(keys[i] >> 32);
+    C[i].ref = (int32_t)(0x80000000u | i);
+    std::memcpy(C[i].box, boxes + 6 * (size_t)leaf, sizeof(C[i].box));
+  }
+  int64_t next = (int64_t)n - 2;
+  while (C.size() > 1) {
+    const int64_t m = (int64_t)C.size();
+    std::vector<int64_t> nn(m);
+    for (int64_t i = 0; i < m; ++i) {
+      int64_t best_j = -1;
+      float best = INFINITY;
+      for (int64_t j = std::max<int64_t>(0, i - radius); j <= std::min<int64_t>(m - 1, i + radius); ++j) {
+        if (j == i) continue;
+        const float a = union_half_area(C[i].box, C[j].box);
+        bool take = best_j < 0 || a < best;
+        if (!take && a == best) {
+          const int64_t d = std::llabs(i - j), db = std::llabs(i - best_j);
+          const int64_t lo = std::min(i, j), lob = std::min(i, best_j);
+          take = d != db ? d < db : (lo & 1) != (lob & 1) ? (lo & 1) == 0 : lo < lob;
+        }
+        if (take) {
+          best = a;
+          best_j = j;
+        }
+      }
+      nn[i] = best_j;
+    }
+    std::vector<Cluster> D;
+    for (int64_t i = 0; i < m; ++i) {
+      const int64_t j = nn[i];
+      const bool mutual = nn[j] == i;
+      if (mutual && j < i) continue;   // merged into the node made at j
+      if (!mutual) {
+        D.push_back(C[i]);
+        continue;
+      }
+      if (next < 0) return 2;          // more merges than internal nodes: cannot happen
+      const int64_t node = next--;
+      child_out[2 * node + 0] = C[i].ref;
+      child_out[2 * node + 1] = C[j].ref;
+      std::memcpy(cbox_out + 12 * node, C[i].box, sizeof(C[i].box));
+      std::memcpy(cbox_out + 12 * node + 6, C[j].box, sizeof(C[j].box));
+      Cluster u;
+      u.ref = (int32_t)node;
+      box_union(C[i].box, C[j].box, u.box);
+      D.push_back(u);
+    }
+    C.swap(D);
+  }
+  std::memcpy(root_box, C[0].box, sizeof(C[0].box));
   return 0;
 }
 

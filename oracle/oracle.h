@@ -96,6 +96,14 @@ int or_instance_boxes_f32(const or_scene* s, float* boxes_out);
 int or_lbvh_f32(const float* boxes, uint32_t n, uint32_t* perm_out, uint32_t* codes_out,
                 int32_t* child_out, float* cbox_out, float* root_box);
 
+/* PLOC tree over the same boxes and Morton order (Meister & Bittner 2018):
+ * mutual nearest neighbours within `radius` positions, by the surface area
+ * of their union, merged round by round; nodes numbered n-2 downward in the
+ * order they are made (root 0). Same output layout as or_lbvh_f32.
+ * Returns 1 for radius 0. */
+int or_ploc_f32(const float* boxes, uint32_t n, uint32_t radius, uint32_t* perm_out, uint32_t* codes_out,
+                int32_t* child_out, float* cbox_out, float* root_box);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ PR_NONE = 0xFFFFFFFF
 PR_TRACE_WRITE_AOV = 1
 PR_TRACE_TLAS_BVH2 = 2
 PR_TRACE_OUTPUT_RGB = 4
+PR_BUILD_TLAS_PLOC = 1
 ERR_WORD_SBT = 1 << PR_ERR_SBT_INDEX
 ERR_WORD_STACK = 1 << PR_ERR_STACK_OVERFLOW
 PR_IS_COUNT = 10
@@ -89,6 +90,8 @@ _sig("pr_scene_create", _i32, _vp, _vp, _vp)
 _sig("pr_scene_upload", _i32, _vp, _vp, _vp)
 _sig("pr_build_bvh", _i32, _vp, _vp)
 _sig("pr_build_bvh_many", _i32, _vp, _u32, _vp)
+_sig("pr_build_bvh_ex", _i32, _vp, _u32, _vp)
+_sig("pr_build_bvh_many_ex", _i32, _vp, _u32, _u32, _vp)
 _sig("pr_trace", _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_trace_frames", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp)
 _sig("pr_trace_work", _i32, _vp, _vp, _u32, _vp, _vp, _vp, _vp)
@@ -117,7 +120,7 @@ _sig("pr_scene_destroy", None, _vp)
 _sig("pr_fma_peak_probe", _i32, _u32, _vp, _vp, _vp)
 
 EXPORTED = ["pr_version", "pr_last_error", "pr_scene_validate", "pr_sbt_index", "pr_scene_create",
-            "pr_scene_upload", "pr_build_bvh", "pr_build_bvh_many", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
+            "pr_scene_upload", "pr_build_bvh", "pr_build_bvh_many", "pr_build_bvh_ex", "pr_build_bvh_many_ex", "pr_trace", "pr_trace_frames", "pr_trace_work", "pr_scene_error",
             "pr_scene_bounds", "pr_scene_read_bvh", "pr_scene_device_bytes", "pr_scene_kernel_launches",
             "pr_scene_destroy", "pr_lbvh_build", "pr_lbvh_build_noalloc", "pr_batch_create", "pr_batch_set_tuning", "pr_batch_get_tuning", "pr_trace_batch",
             "pr_trace_batch_graph", "pr_batch_autotune", "pr_batch_device_bytes", "pr_batch_destroy",
@@ -131,11 +134,14 @@ def _check(status: int, where: str):
         raise PrError(status, where)
 
 
-def build_bvh_many(scenes, stream=None):
-    """pr_build_bvh_many: the BVHs of many scenes, built concurrently on internal
-    streams ordered after (and joined back into) `stream`."""
+def build_bvh_many(scenes, stream=None, flags: int = 0):
+    """pr_build_bvh_many(_ex): the BVHs of many scenes, built concurrently on internal
+    streams ordered after (and joined back into) `stream`; flags: PR_BUILD_*."""
     arr = (ctypes.c_void_p * len(scenes))(*[sc._h.value for sc in scenes])
-    _check(_lib.pr_build_bvh_many(arr, len(scenes), _stream_handle(stream)), "pr_build_bvh_many")
+    if flags:
+        _check(_lib.pr_build_bvh_many_ex(arr, len(scenes), flags, _stream_handle(stream)), "pr_build_bvh_many_ex")
+    else:
+        _check(_lib.pr_build_bvh_many(arr, len(scenes), _stream_handle(stream)), "pr_build_bvh_many")
 
 
 def version() -> int:
@@ -244,7 +250,7 @@ class CameraArray:
 class Scene:
     """A scene on the device: inputs, BVH, shader binding table (pr_scene)."""
 
-    def __init__(self, desc, stream=None, build: bool = True):
+    def __init__(self, desc, stream=None, build: bool = True, build_flags: int = 0):
         self._h = ctypes.c_void_p()
         ref = _DescRef(desc)
         self.n_inst = len(ref.arrays["inst_blas"])
@@ -253,14 +259,18 @@ class Scene:
                "pr_scene_create")
         self.desc_bytes = ref.nbytes
         if build:
-            self.build_bvh(stream)
+            self.build_bvh(stream, build_flags)
 
     def upload(self, desc, stream=None):
         ref = _DescRef(desc)
         _check(_lib.pr_scene_upload(self._h, ctypes.byref(ref.struct), _stream_handle(stream)), "pr_scene_upload")
 
-    def build_bvh(self, stream=None):
-        _check(_lib.pr_build_bvh(self._h, _stream_handle(stream)), "pr_build_bvh")
+    def build_bvh(self, stream=None, flags: int = 0):
+        """pr_build_bvh, or pr_build_bvh_ex with PR_BUILD_* flags."""
+        if flags:
+            _check(_lib.pr_build_bvh_ex(self._h, flags, _stream_handle(stream)), "pr_build_bvh_ex")
+        else:
+            _check(_lib.pr_build_bvh(self._h, _stream_handle(stream)), "pr_build_bvh")
 
     def trace(self, camera, params, out=None, aov=None, ray_counter=None, stream=None, want_aov: bool = False,
               binary_tlas: bool = False, rgb: bool = False):

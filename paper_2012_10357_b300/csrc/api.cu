@@ -428,6 +428,7 @@ BuildScratch carve_build_scratch(void* base, uint32_t n) {
   sc.parent_int = (uint32_t*)(A + c.take<uint32_t>(n));
   sc.parent_leaf = (uint32_t*)(A + c.take<uint32_t>(n));
   sc.partial = (float*)(A + c.take<float>(6 * (size_t)kMaxPartials));
+  sc.cluster_boxes = nullptr;
   sc.max_n = n;
   return sc;
 }
@@ -541,6 +542,7 @@ pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext
   s->scratch.parent_int = (uint32_t*)(A + P.o_pi);
   s->scratch.parent_leaf = (uint32_t*)(A + P.o_pl);
   s->scratch.partial = (float*)(A + P.o_part);
+  s->scratch.cluster_boxes = nullptr;
   s->scratch.max_n = s->L.max_large;
   s->d_jobs = (LevelDesc*)(A + P.o_jobs);
 
@@ -625,8 +627,18 @@ struct BuildPool {
   cudaStream_t streams[kBuildStreams] = {};
   cudaEvent_t done[kBuildStreams] = {};
   cudaEvent_t start = nullptr;
+  cudaEvent_t ploc = nullptr;   // the previous PLOC clustering launch of the fan-out
   bool ready = false;
 };
+
+// Order of the cooperative clustering launches of one fan-out: each waits for
+// the one before it (two cooperative grids are never resident side by side).
+struct PlocChain {
+  cudaEvent_t ev = nullptr;
+  bool armed = false;
+};
+
+pr_status build_impl(pr_scene* s, uint32_t flags, cudaStream_t st, PlocChain* chain);
 std::mutex g_pool_mutex;
 BuildPool g_pools[64];
 
@@ -635,12 +647,17 @@ BuildPool g_pools[64];
 extern "C" {
 
 pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
+  return pr_build_bvh_many_ex(scenes, n, 0u, stream);
+}
+
+pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t flags, void* stream) {
+  if (flags & ~PR_BUILD_TLAS_PLOC) return fail(PR_ERR_INVALID_ARG, "unknown build flags");
   if (n == 0) return PR_OK;
   if (!scenes) return fail(PR_ERR_INVALID_ARG, "null scene array");
   for (uint32_t i = 0; i < n; ++i)
     if (!scenes[i]) return fail(PR_ERR_INVALID_ARG, "null scene in the array");
   cudaStream_t st = (cudaStream_t)stream;
-  if (n == 1) return pr_build_bvh(scenes[0], stream);
+  if (n == 1) return build_impl(scenes[0], flags, st, nullptr);
   int dev = 0;
   PR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev < 0 || dev >= 64) return fail(PR_ERR_INVALID_ARG, "device ordinal beyond 63");
@@ -652,6 +669,7 @@ pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
       PR_CUDA(cudaEventCreateWithFlags(&P.done[k], cudaEventDisableTiming), "build event");
     }
     PR_CUDA(cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming), "build event");
+    PR_CUDA(cudaEventCreateWithFlags(&P.ploc, cudaEventDisableTiming), "build event");
     P.ready = true;
   }
   const int used = (int)std::min<uint32_t>(n, kBuildStreams);
@@ -659,8 +677,9 @@ pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
   PR_CUDA(cudaEventRecord(P.start, st), "record fork");
   for (int k = 0; k < used; ++k) PR_CUDA(cudaStreamWaitEvent(P.streams[k], P.start, 0), "fork");
   pr_status result = PR_OK;
+  PlocChain chain{P.ploc, false};
   for (uint32_t i = 0; i < n; ++i) {
-    const pr_status b = pr_build_bvh(scenes[i], P.streams[i % kBuildStreams]);
+    const pr_status b = build_impl(scenes[i], flags, P.streams[i % kBuildStreams], &chain);
     if (b != PR_OK && result == PR_OK) result = b;
   }
   // join: `stream` waits for every build
@@ -671,9 +690,19 @@ pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
   return result;
 }
 
-pr_status pr_build_bvh(pr_scene* s, void* stream) {
+pr_status pr_build_bvh(pr_scene* s, void* stream) { return pr_build_bvh_ex(s, 0u, stream); }
+
+pr_status pr_build_bvh_ex(pr_scene* s, uint32_t flags, void* stream) {
+  if (flags & ~PR_BUILD_TLAS_PLOC) return fail(PR_ERR_INVALID_ARG, "unknown build flags");
+  return build_impl(s, flags, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+pr_status build_impl(pr_scene* s, uint32_t flags, cudaStream_t st, PlocChain* chain) {
   if (!s) return fail(PR_ERR_INVALID_ARG, "null scene");
-  cudaStream_t st = (cudaStream_t)stream;
   int launches = 0;
   const InstanceArgs IA{s->xform, s->inst_blas, s->inst_id, s->inst_sbt, s->inst_mask, s->blas_box,
                         s->blas_info, s->L.n_inst, s->inst_boxes, s->inst_rec};
@@ -691,8 +720,19 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
     launches += launch_instances(IA, st);
     // 3. TLAS, then its 4-wide collapse
     if (s->L.n_inst > 0) {
-      if (s->tlas_small) launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
-      else launches += launch_build_large(s->tlas_job, s->scratch, st);
+      if (s->tlas_small) {
+        launches += launch_build_small(s->d_jobs + s->small_jobs.size(), 1, st);
+      } else if (flags & PR_BUILD_TLAS_PLOC) {
+        BuildScratch sc = s->scratch;
+        sc.cluster_boxes = reinterpret_cast<float*>(s->tlas4);   // 128 B per instance, free until the collapse
+        const int k = launch_build_ploc(s->tlas_job, sc, s->error_word, st, chain && chain->armed ? chain->ev : nullptr,
+                                        chain ? chain->ev : nullptr);
+        if (k < 0) return cuda_fail(cudaGetLastError(), "PLOC TLAS build launch");
+        if (chain) chain->armed = true;
+        launches += k;
+      } else {
+        launches += launch_build_large(s->tlas_job, s->scratch, st);
+      }
       // the 4-wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
       if (s->L.n_inst >= kTlas4MinInstances)
         launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
@@ -704,6 +744,10 @@ pr_status pr_build_bvh(pr_scene* s, void* stream) {
   s->build_launches = launches;
   return PR_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera* d_cams, uint32_t n_frames,
                             const pr_trace_params* p, float* out_rgba, pr_aov* out_aov, uint64_t* counter,

@@ -12,6 +12,7 @@
 // boxes are bit-reproducible by a plain CPU implementation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -322,8 +323,11 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* keys_in, 
   }
 }
 
+// done: when set and nonzero, a PLOC launch already built the level (its fallback
+// path; null for the LBVH build)
 __global__ void __launch_bounds__(256) k_karras(LevelDesc J, const uint32_t* codes, const uint32_t* vals,
-                                                 uint32_t* parent_int, uint32_t* parent_leaf) {
+                                                 uint32_t* parent_int, uint32_t* parent_leaf, const uint32_t* done) {
+  if (done && *done) return;
   const int n = (int)J.n;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -355,7 +359,8 @@ __global__ void __launch_bounds__(256) k_karras(LevelDesc J, const uint32_t* cod
 // Bottom-up unions: each leaf walks up; the second arrival at a node unites
 // both child boxes (Karras 2012, Section 4) and continues to the parent.
 __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals, const uint32_t* parent_int,
-                                                const uint32_t* parent_leaf, uint32_t* counters) {
+                                                const uint32_t* parent_leaf, uint32_t* counters, const uint32_t* done) {
+  if (done && *done) return;
   const uint32_t n = J.n;
   uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n) return;
@@ -383,6 +388,238 @@ __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals
     }
     ref = (int)p;
     p = parent_int[p];
+  }
+}
+
+// ---- PLOC: bottom-up clustering of a large level ---------------------------
+// Parallel locally-ordered clustering (Meister & Bittner 2018): the leaves in
+// Morton order are the first clusters; every round each cluster finds its
+// nearest neighbour among the kPlocRadius clusters on either side: the least
+// pair by the surface area of the box enclosing both, then by distance in the
+// list, then with the lower index even before odd, then by the lower index.
+// That is a total order on pairs, so the least pair of a round is mutual and
+// every round merges at least one pair; on equal boxes it pairs 0-1, 2-3, ...
+// and halves the list. Mutual nearest neighbours merge into a new node; a
+// prefix sum over the survivors keeps the order. New nodes are numbered downward from n - 2, so the final
+// merge is node 0, the root the traversal starts from. The node layout is
+// the LBVH's, so the 4-wide collapse and the traversal take the tree as is.
+constexpr int kPlocRadius = 16;
+constexpr int kPlocThreads = 256;
+// header words (in the radix histogram's buffer, free once the sort is done)
+constexpr int kHdrOk = 0, kHdrAbort = 1, kHdrCount = 2, kHdrGen = 3;
+constexpr size_t kPlocPartOffset = 256;              // bytes: per-block counts follow the header
+constexpr unsigned long long kPlocWaitNs = 2000000000ull;
+constexpr uint32_t kPlocMaxSpins = 1u << 25;
+
+__device__ __forceinline__ float half_area(const float* a, const float* b) {
+  const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+  const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+  const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+  const float s = fmaf(dx, dy, fmaf(dy, dz, dz * dx));
+  return s == s ? s : INFINITY;   // NaN (a non-finite box) orders last
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of the cooperative launch (which makes every block
+// resident), with a limit: a block that waits longer than kPlocWaitNs, or
+// sees that another block gave up, gives up too and the kernel ends; the
+// LBVH passes launched after it then build the level instead.
+__device__ bool grid_barrier(uint32_t* hdr, uint32_t* error_word, uint32_t& gen, uint32_t* ok_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t ok = 1;
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&hdr[kHdrCount], 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&hdr[kHdrCount], 0u);
+      __threadfence();
+      atomicExch(&hdr[kHdrGen], gen + 1);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (uint32_t spins = 0;; ++spins) {
+        if (ld_acquire_u32(&hdr[kHdrGen]) != gen) break;
+        if (ld_acquire_u32(&hdr[kHdrAbort]) || spins > kPlocMaxSpins || global_ns() - t0 > kPlocWaitNs) {
+          atomicExch(&hdr[kHdrAbort], 1u);
+          if (error_word) atomicOr(error_word, 1u << PR_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *ok_sh = ok;
+  }
+  ++gen;
+  __syncthreads();
+  return *ok_sh != 0;
+}
+
+// exclusive block scan of two counters packed in a 64-bit value
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* sh,
+                                                              unsigned long long& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < kPlocThreads / 32 ? sh[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kPlocThreads / 32) sh[lane] = w;
+  }
+  __syncthreads();
+  total = sh[kPlocThreads / 32 - 1];
+  const unsigned long long before = warp ? sh[warp - 1] : 0ull;
+  __syncthreads();
+  return before + x - v;
+}
+
+// keep: cluster i survives the round (alone or as the merged node of its
+// mutual pair); merge: i is the lower index of a mutual pair
+__device__ __forceinline__ unsigned long long keep_merge(const int* nn, uint32_t i, int& j) {
+  j = __ldcg(nn + i);
+  const bool mutual = __ldcg(nn + j) == (int)i;
+  const bool keep = !(mutual && (uint32_t)j < i);
+  const bool merge = mutual && i < (uint32_t)j;
+  return (keep ? 1ull : 0ull) + (merge ? (1ull << 32) : 0ull);
+}
+
+__global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
+  __shared__ unsigned long long sh[kPlocThreads / 32];
+  __shared__ uint32_t ok_sh;
+  uint32_t* hdr = A.hdr;
+  const uint32_t n = A.J.n;
+  const uint32_t nthreads = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t gen = 0;
+  for (uint32_t i = tid; i < n; i += nthreads) {
+    const uint32_t leaf = A.vals[i];
+    A.J.perm[i] = leaf;
+    A.J.codes[i] = A.codes[i];
+    A.C[0][i] = (int)(kLeafBit | (A.J.leaf_ref_base + leaf));
+    const float* b = leaf_box(A.J, leaf);
+    for (int k = 0; k < 6; ++k) A.CB[0][6 * (size_t)i + k] = b[k];
+  }
+  if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+  uint32_t m = n, next = n - 2;
+  int cur = 0;
+  while (m > 1) {
+    const int* C = A.C[cur];
+    const float* CB = A.CB[cur];
+    // 1. nearest neighbour in the window
+    for (uint32_t i = tid; i < m; i += nthreads) {
+      float bi[6];
+      for (int k = 0; k < 6; ++k) bi[k] = __ldcg(CB + 6 * (size_t)i + k);
+      const uint32_t lo = i > (uint32_t)kPlocRadius ? i - kPlocRadius : 0u;
+      const uint32_t hi = min(m - 1, i + (uint32_t)kPlocRadius);
+      float best = INFINITY;
+      int bj = -1;
+      for (uint32_t j = lo; j <= hi; ++j) {
+        if (j == i) continue;
+        float bb[6];
+        for (int k = 0; k < 6; ++k) bb[k] = __ldcg(CB + 6 * (size_t)j + k);
+        const float a = half_area(bi, bb);
+        bool take = bj < 0 || a < best;
+        if (!take && a == best) {
+          const uint32_t d = j > i ? j - i : i - j, db = (uint32_t)bj > i ? (uint32_t)bj - i : i - (uint32_t)bj;
+          const uint32_t l = min(i, j), lb = min(i, (uint32_t)bj);
+          take = d != db ? d < db : ((l ^ lb) & 1u) ? (l & 1u) == 0u : l < lb;
+        }
+        if (take) {
+          best = a;
+          bj = (int)j;
+        }
+      }
+      A.nn[i] = bj;
+    }
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    // 2. survivors and merges of each block's chunk
+    const uint32_t chunk = (m + gridDim.x - 1) / gridDim.x;
+    const uint32_t c0 = min(m, blockIdx.x * chunk), c1 = min(m, c0 + chunk);
+    unsigned long long cnt = 0;
+    for (uint32_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      int j;
+      cnt += keep_merge(A.nn, i, j);
+    }
+    unsigned long long tot;
+    block_excl_scan(cnt, sh, tot);
+    if (threadIdx.x == 0) A.part[blockIdx.x] = tot;
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    // 3. this block's exclusive prefix of the block counts and the round's totals
+    unsigned long long pre_part = 0, all_part = 0;
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+      const unsigned long long v = __ldcg(A.part + b);
+      all_part += v;
+      if (b < blockIdx.x) pre_part += v;
+    }
+    unsigned long long pre, all;
+    block_excl_scan(pre_part, sh, pre);
+    block_excl_scan(all_part, sh, all);
+    // 4. merged nodes and the compacted cluster list, in order
+    int* Cn = A.C[cur ^ 1];
+    float* CBn = A.CB[cur ^ 1];
+    unsigned long long run = pre;
+    for (uint32_t r0 = c0; r0 < c1; r0 += blockDim.x) {
+      const uint32_t i = r0 + threadIdx.x;
+      int j = -1;
+      const unsigned long long v = i < c1 ? keep_merge(A.nn, i, j) : 0ull;
+      unsigned long long t;
+      const unsigned long long e = run + block_excl_scan(v, sh, t);
+      if (v & 0xFFFFFFFFull) {
+        const uint32_t pos = (uint32_t)(e & 0xFFFFFFFFull);
+        float bi[6];
+        for (int k = 0; k < 6; ++k) bi[k] = __ldcg(CB + 6 * (size_t)i + k);
+        if (v >> 32) {
+          const uint32_t node = next - (uint32_t)(e >> 32);
+          float bj[6];
+          for (int k = 0; k < 6; ++k) bj[k] = __ldcg(CB + 6 * (size_t)j + k);
+          float4* nd = A.J.nodes + 4 * (size_t)node;
+          store_child_box(nd, 0, bi);
+          store_child_box(nd, 1, bj);
+          nd[3] = make_float4(__int_as_float(__ldcg(C + i)), __int_as_float(__ldcg(C + j)), 0.f, 0.f);
+          for (int k = 0; k < 3; ++k) {
+            bi[k] = fminf(bi[k], bj[k]);
+            bi[3 + k] = fmaxf(bi[3 + k], bj[3 + k]);
+          }
+          Cn[pos] = (int)node;
+        } else {
+          Cn[pos] = __ldcg(C + i);
+        }
+        for (int k = 0; k < 6; ++k) CBn[6 * (size_t)pos + k] = bi[k];
+      }
+      run += t;
+    }
+    m = (uint32_t)(all & 0xFFFFFFFFull);
+    next -= (uint32_t)(all >> 32);
+    cur ^= 1;
+    // (the next round writes the block counts only after its first barrier,
+    // when every block has read this round's)
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+  }
+  if (tid == 0) {
+    float box[6];
+    for (int k = 0; k < 6; ++k) box[k] = __ldcg(A.CB[cur] + k);
+    write_root(A.J.root_box, box);
+    hdr[kHdrOk] = 1u;
   }
 }
 
@@ -582,10 +819,79 @@ int launch_build_large(const LevelDesc& J, const BuildScratch& sc, cudaStream_t 
     launches += 3;
   }
   cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * (n - 1), s);
-  k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf);
-  k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters);
+  k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf, nullptr);
+  k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters, nullptr);
   launches += 2;
   return launches;
+}
+
+int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* error_word, cudaStream_t s,
+                      cudaEvent_t after, cudaEvent_t mark) {
+  const uint32_t n = J.n;
+  if (n < 2) return launch_build_large(J, sc, s);
+  int launches = 0;
+  // Morton order of the leaves: the LBVH's centroid bounds, codes and radix sort
+  uint32_t nb = (n + 255) / 256;
+  uint32_t n_partial = nb < kMaxPartials ? nb : kMaxPartials;
+  k_centroid_partial<<<n_partial, 256, 0, s>>>(J, sc.partial);
+  uint32_t nb_m = nb < 2048u ? nb : 2048u;
+  k_morton<<<nb_m, 256, 0, s>>>(J, sc.partial, (int)n_partial, sc.keys[0], sc.vals[0]);
+  launches += 2;
+  const uint32_t tiles = sort_tiles(n);
+  int cur = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    int shift = 8 * pass;
+    k_radix_hist<<<tiles, 256, 0, s>>>(sc.keys[cur], n, shift, sc.hist, tiles);
+    k_radix_scan<<<1, 1024, 0, s>>>(sc.hist, 256 * tiles);
+    k_radix_scatter<<<tiles, 256, 0, s>>>(sc.keys[cur], sc.vals[cur], sc.keys[1 - cur], sc.vals[1 - cur], n, shift,
+                                          sc.hist, tiles);
+    cur = 1 - cur;
+    launches += 3;
+  }
+  // Clustering in one cooperative launch. Scratch: the histogram's buffer holds
+  // the header and the per-block counts, the sort's spare buffers the cluster
+  // references, the refit counters the nearest neighbours, and the 4-wide TLAS
+  // (written only by the collapse after this build) the cluster boxes.
+  static int blocks_per_sm = 0, n_sm = 0;
+  if (!blocks_per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_ploc, kPlocThreads, 0);
+    if (blocks_per_sm > 2) blocks_per_sm = 2;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const size_t hist_bytes = sizeof(uint32_t) * 256 * (size_t)tiles;
+  uint32_t grid = (uint32_t)(blocks_per_sm * n_sm);
+  grid = std::min(grid, (n + kPlocThreads - 1) / kPlocThreads);
+  grid = std::min(grid, (uint32_t)((hist_bytes - kPlocPartOffset) / sizeof(unsigned long long)));
+  grid = std::max(grid, 1u);
+  PlocArgs A;
+  A.J = J;
+  A.codes = sc.keys[cur];
+  A.vals = sc.vals[cur];
+  A.C[0] = reinterpret_cast<int*>(sc.keys[1 - cur]);
+  A.C[1] = reinterpret_cast<int*>(sc.vals[1 - cur]);
+  A.CB[0] = sc.cluster_boxes;
+  A.CB[1] = sc.cluster_boxes + 6 * (size_t)n;
+  A.nn = reinterpret_cast<int*>(sc.counters);
+  A.hdr = sc.hist;
+  A.error_word = error_word;
+  A.part = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.hist) + kPlocPartOffset);
+  cudaMemsetAsync(sc.hist, 0, kPlocPartOffset, s);
+  void* args[] = {&A};
+  if (after && cudaStreamWaitEvent(s, after, 0) != cudaSuccess) return -1;
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ploc, dim3(grid), dim3(kPlocThreads), args, 0, s);
+  if (e != cudaSuccess) return -1;
+  if (mark && cudaEventRecord(mark, s) != cudaSuccess) return -1;
+  ++launches;
+  // the LBVH's tree passes, which return at once unless a barrier of the
+  // clustering gave up
+  const uint32_t* done = sc.hist + kHdrOk;
+  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * (n - 1), s);
+  k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf, done);
+  k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters, done);
+  return launches + 2;
 }
 
 int launch_instances(const InstanceArgs& A, cudaStream_t s) {

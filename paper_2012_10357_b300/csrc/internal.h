@@ -32,6 +32,7 @@ struct BuildScratch {
   uint32_t* parent_int;  // [max_n]
   uint32_t* parent_leaf; // [max_n]
   float* partial;        // [kMaxPartials * 6]
+  float* cluster_boxes;  // [2 * max_n * 6] PLOC cluster boxes (may alias a buffer free during the build)
   uint32_t max_n;
 };
 
@@ -48,6 +49,26 @@ int launch_build_small_one(const LevelDesc& job, cudaStream_t s);
 int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_t* even, uint32_t* rank,
                      float4* nodes4, cudaStream_t s);
 int launch_build_large(const LevelDesc& job, const BuildScratch& sc, cudaStream_t s);
+
+// PLOC build of a large level (more than kSmallMax leaves): the LBVH's Morton
+// sort, then bottom-up clustering in one cooperative launch, same node layout;
+// needs sc.cluster_boxes (12 floats per leaf). The clustering launch waits for
+// `after` and records `mark` (each optional): pr_build_bvh_many_ex orders the
+// clustering launches of concurrent builds one after another with them.
+// Returns the launches issued, or -1 when a launch was refused.
+struct PlocArgs {
+  LevelDesc J;
+  const uint32_t* codes;     // sorted Morton codes
+  const uint32_t* vals;      // leaves in Morton order
+  int* C[2];                 // cluster references, double-buffered
+  float* CB[2];              // cluster boxes [m][6], double-buffered
+  int* nn;                   // nearest neighbour of each cluster
+  unsigned long long* part;  // per-block (survivors | merges << 32)
+  uint32_t* hdr;             // done, abort, barrier count, barrier generation
+  uint32_t* error_word;      // gets 1 << PR_ERR_TIMEOUT when a barrier gives up (optional)
+};
+int launch_build_ploc(const LevelDesc& job, const BuildScratch& sc, uint32_t* error_word, cudaStream_t s,
+                      cudaEvent_t after = nullptr, cudaEvent_t mark = nullptr);
 
 // Scratch bytes of the large-level path for n leaves, and its carving.
 size_t build_scratch_bytes(uint32_t n);

@@ -17,6 +17,7 @@ import pytest
 import oracle
 import scenes
 import test_oracle_pins as pins
+import test_oracle_ploc as ploc_pins
 from scenes import IS_CAPSULE, IS_METABALL4, IS_TORUS
 
 
@@ -97,6 +98,23 @@ CASES = [
     ("instance boxes: min and max swapped",
      [("lo = lo + std::min(a, b);\n        hi = hi + std::max(a, b);",
        "lo = lo + std::max(a, b);\n        hi = hi + std::min(a, b);")], pins.test_instance_boxes_f32_close_to_fp64_corners),
+    ("PLOC: area tie resolved to the odd lower index",
+     [("(lo & 1) != (lob & 1) ? (lo & 1) == 0 : lo < lob", "(lo & 1) != (lob & 1) ? (lo & 1) == 1 : lo < lob")],
+     ploc_pins.test_ploc_tie_goes_to_the_even_lower_pair),
+    ("PLOC: distance tie rule dropped",
+     [("take = d != db ? d < db : (lo & 1)", "take = (lo & 1)")],
+     lambda O: ploc_pins.test_ploc_equal_boxes_give_a_balanced_tree(O, 16)),
+    ("PLOC: volume of the union instead of its surface area",
+     [("const float s = std::fma(dx, dy, std::fma(dy, dz, dz * dx));", "const float s = dx * dy * dz;")],
+     ploc_pins.test_ploc_flat_boxes_merge_by_area),
+    ("PLOC: children of a merge swapped",
+     [("child_out[2 * node + 0] = C[i].ref;\n      child_out[2 * node + 1] = C[j].ref;",
+       "child_out[2 * node + 0] = C[j].ref;\n      child_out[2 * node + 1] = C[i].ref;")],
+     ploc_pins.test_ploc_boxes_on_a_line),
+    ("PLOC: merged node takes the place of the upper cluster",
+     [("      if (mutual && j < i) continue;   // merged into the node made at j\n      if (!mutual) {",
+       "      if (mutual && j > i) continue;\n      if (!mutual) {")],
+     ploc_pins.test_ploc_boxes_on_a_line),
 ]
 
 

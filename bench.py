@@ -47,6 +47,10 @@ BATCH_DESC = ("batch of 64 render requests: instanced procedural fields of 1..10
               "(8 primitive types, log-uniform count), resolutions from {256^2, 512^2, 1024^2, 2048^2}, orbit cameras")
 
 
+TLAS_FORMATS = {"greedy4": lambda pr: 0, "parity4": lambda pr: pr.PR_BUILD_TLAS_PARITY4,
+                "bvh8": lambda pr: pr.PR_BUILD_TLAS_BVH8, "bvh8_f32": lambda pr: pr.PR_BUILD_TLAS_BVH8_F32}
+
+
 def workload_by_name(name: str):
     if name == "analytic_64x64":
         return scenes.small_analytic()
@@ -307,6 +311,7 @@ def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: i
     config = workload_config(name, w)
     ploc = bool(build_flags & pr.PR_BUILD_TLAS_PLOC) and len(w.scene.inst_blas) > 1024
     config["tlas_builder"] = "ploc" if ploc else "lbvh"
+    config["tlas_format"] = next((k for k, f in TLAS_FORMATS.items() if f(pr) and build_flags & f(pr)), "greedy4")
     if ploc:
         config["step"] = "device build (BLAS: LBVH, TLAS: PLOC) + one frame"
     n_rays = max(1, counters.get("rays", 0))
@@ -321,13 +326,39 @@ def bench_scene(pr, work, torch, stream, flush, name: str, steps: int, warmup: i
                                   name, clocks, probe, binary_tlas),
              "device_error_word": scene.error_word(stream),
              "traversal_per_ray": {k: counters.get(k, 0) / n_rays
-                                   for k in ("tlas_nodes4", "tlas_nodes", "instances", "blas_nodes", "leaves")}}
+                                   for k in ("tlas_nodes8q", "tlas_nodes8", "tlas_nodes4", "tlas_nodes", "instances",
+                                             "blas_nodes", "leaves")}}
     block["roofline"]["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
     block["roofline"]["work_counters"] = {k: v for k, v in counters.items() if v}
     if clocks:
         block["clocks"] = clocks
     block["_scene"], block["_w"], block["_out"] = scene, w, out
     return block
+
+
+def bench_tlas_variants(pr, work, torch, stream, flush, steps: int, warmup: int, probe=None) -> dict:
+    """The 100 000-instance field with every TLAS builder (LBVH, PLOC) x wide format (greedy
+    4-wide, depth-parity 4-wide, 8-wide quantised, 8-wide float): build and trace time, node
+    and instance visits per ray, and whether the image equals the default build's."""
+    rows, ref = [], None
+    for builder in ("lbvh", "ploc"):
+        for fmt, flag in TLAS_FORMATS.items():
+            flags = (pr.PR_BUILD_TLAS_PLOC if builder == "ploc" else 0) | flag(pr)
+            b = bench_scene(pr, work, torch, stream, flush, "field_100k_2160p", steps, warmup, probe,
+                            build_flags=flags)
+            if ref is None:
+                ref = b["_out"].clone()
+            t = b["traversal_per_ray"]
+            rows.append({"builder": builder, "format": fmt, "mrays": b["value"],
+                         "trace_ms": b["latency_ms"]["trace_p50"], "build_ms": b["latency_ms"]["build_p50"],
+                         "step_ms": b["latency_ms"]["p50"],
+                         "wide_nodes_per_ray": t["tlas_nodes4"] + t["tlas_nodes8"] + t["tlas_nodes8q"],
+                         "instances_per_ray": t["instances"], "image_equals_default": bool(torch.equal(b["_out"], ref)),
+                         "device_error_word": b["device_error_word"], "fma_frac": b["roofline"]["frac"],
+                         "alu_gops_per_s": b["roofline"]["alu_gops_per_s"]})
+            b["_scene"].close()
+    return {"workload": "instanced field, 100000 instances, 3840x2160, TLAS builder x wide format",
+            "steps": steps, "rows": rows}
 
 
 def scene_e2e(pr, torch, stream, block, n_steps: int, warmup: int, world: int) -> dict:
@@ -802,6 +833,8 @@ def run_ours(args):
         # one block alone (profiling runs)
         if args.block == "analytic_4096_frames":
             b = bench_analytic_frames(pr, work, torch, stream, flush, reps=args.steps, probe=probe_tflops)
+        elif args.block == "field_100k_2160p_tlas":
+            b = bench_tlas_variants(pr, work, torch, stream, flush, args.steps, args.warmup, probe_tflops)
         elif args.block == "teaser_1080p_batched":
             # the 1080p teaser as a one-request batch through the batched path (--tuning picks the mode)
             res = bench_batch(pr, work, torch, stream, flush, args.steps, args.warmup, 1, probe_tflops, None, 1,
@@ -811,7 +844,7 @@ def run_ours(args):
                  "ms_per_step": res["total_ms"] / args.steps, "tuning": res["autotune"], "roofline": res["roofline"],
                  "plain": res["plain"], "images_identical_to_plain": res["images_identical_to_plain"]}
         else:
-            flags = pr.PR_BUILD_TLAS_PLOC if args.tlas_builder == "ploc" else 0
+            flags = (pr.PR_BUILD_TLAS_PLOC if args.tlas_builder == "ploc" else 0) | TLAS_FORMATS[args.tlas_format](pr)
             b = bench_scene(pr, work, torch, stream, flush, args.block, args.steps, args.warmup, probe_tflops,
                             args.binary_tlas, build_flags=flags)
             b["_scene"].close()
@@ -938,10 +971,13 @@ def main():
     ap.add_argument("--binary-tlas", action="store_true", help="traverse the binary TLAS instead of the 4-wide one")
     ap.add_argument("--tlas-builder", choices=["lbvh", "ploc"], default="lbvh",
                     help="TLAS builder of a --block scene (PLOC: PR_BUILD_TLAS_PLOC)")
+    ap.add_argument("--tlas-format", choices=list(TLAS_FORMATS), default="greedy4",
+                    help="wide TLAS of a --block scene: greedy 4-wide (default build), 4-wide by depth parity, "
+                         "8-wide quantised, 8-wide float")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=64, help="requests of the batch workload (64: the headline)")
     ap.add_argument("--block", choices=["analytic_4096_frames", "teaser_1080p", "field_100k_2160p",
-                                        "teaser_1080p_batched"], default=None,
+                                        "teaser_1080p_batched", "field_100k_2160p_tlas"], default=None,
                     help="run one block alone and print it (profiling)")
     ap.add_argument("--tuning", default=None,
                     help="batch launch shape ctas_per_sm,tile_w,tile_h,queue_chunk,mode instead of the autotuned one")

@@ -225,8 +225,28 @@ pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream);
                                    cooperative launch. Smaller TLASes and every
                                    BLAS keep the LBVH. */
 
+#define PR_BUILD_TLAS_PARITY4 2u  /* the 4-wide TLAS (64 or more instances) takes
+                                    the binary nodes at even depth as 4-wide
+                                    nodes over their grandchildren (by default
+                                    each 4-wide node opens its internal child
+                                    of largest surface area until it has 4
+                                    children: 3 % faster traversal on the
+                                    100 000-instance field) */
+#define PR_BUILD_TLAS_BVH8 4u     /* an 8-wide TLAS (64 or more instances),
+                                    collapsed greedily like the default 4-wide one,
+                                    in quantised 96-byte nodes (child bounds as
+                                    bytes on a per-node power-of-two grid,
+                                    Ylitie et al. 2017), traversed by pr_trace
+                                    and pr_trace_frames; batched launches keep
+                                    the binary TLAS for such scenes */
+#define PR_BUILD_TLAS_BVH8_F32 8u /* as PR_BUILD_TLAS_BVH8 with float nodes
+                                    (224 bytes); the first such build of a scene
+                                    allocates their buffer (device, 224 B per
+                                    instance, freed with the scene) */
+
 /* pr_build_bvh with options (a bitwise or of PR_BUILD_* flags; 0 is
- * pr_build_bvh). PR_ERR_INVALID_ARG for an unknown flag; PR_ERR_CUDA when the
+ * pr_build_bvh; at most one of PARITY4, BVH8, BVH8_F32). PR_ERR_INVALID_ARG
+ * for an unknown flag or two wide formats; PR_ERR_CUDA when the
  * device refuses the cooperative launch. The clustering launch waits at
  * grid-wide barriers with a 2 s limit; should one run out (its blocks not
  * all resident, which the cooperative launch rules out), the LBVH passes
@@ -261,8 +281,9 @@ pr_status pr_trace_frames(pr_scene* scene, const pr_camera* cameras, uint32_t n_
  * not counted here), Eq. 1 record lookups, intersection-shader calls per shader id [PR_IS_COUNT],
  * distance-estimate evaluations per shader id [PR_IS_COUNT], Julia
  * iterations, Mandelbulb iterations, shaded hits, rays traced, 4-wide TLAS
- * node visits. */
-#define PR_WORK_COUNTERS 30u
+ * node visits, 8-wide TLAS node visits (float nodes), 8-wide TLAS node
+ * visits (quantised nodes). */
+#define PR_WORK_COUNTERS 32u
 
 /* pr_trace_frames with an instrumented kernel variant that also adds the
  * work it did to work_counters (device, PR_WORK_COUNTERS uint64,

@@ -31,12 +31,16 @@ PR_TRACE_WRITE_AOV = 1
 PR_TRACE_TLAS_BVH2 = 2
 PR_TRACE_OUTPUT_RGB = 4
 PR_BUILD_TLAS_PLOC = 1
+PR_BUILD_TLAS_PARITY4 = 2
+PR_BUILD_TLAS_BVH8 = 4
+PR_BUILD_TLAS_BVH8_F32 = 8
 ERR_WORD_SBT = 1 << PR_ERR_SBT_INDEX
 ERR_WORD_STACK = 1 << PR_ERR_STACK_OVERFLOW
 PR_IS_COUNT = 10
 WORK_FIELDS = (["tlas_nodes", "blas_nodes", "instances", "leaves", "sbt_lookups"] +
                [f"is_calls_{i}" for i in range(PR_IS_COUNT)] + [f"de_evals_{i}" for i in range(PR_IS_COUNT)] +
-               ["julia_iters", "mandelbulb_iters", "shaded", "rays", "tlas_nodes4"])
+               ["julia_iters", "mandelbulb_iters", "shaded", "rays", "tlas_nodes4", "tlas_nodes8",
+                                                                  "tlas_nodes8q"])
 
 AOV_DTYPE = np.dtype([("t", "<f4"), ("inst", "<u4"), ("geom", "<u4"), ("prim", "<u4"), ("n", "<f4", 3),
                       ("flags", "<u4"), ("refl_t", "<f4"), ("refl_inst", "<u4"), ("refl_geom", "<u4"),

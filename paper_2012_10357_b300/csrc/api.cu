@@ -225,6 +225,9 @@ struct pr_scene {
   float4* tlas_nodes;
   float4* tlas4;                     // 4-wide TLAS collapsed from tlas_nodes
   uint32_t *c4_parent, *c4_even, *c4_rank;
+  uint32_t* wide_slots;              // [8 (n_inst - 1) + 1] greedy collapse slots, then the frontier count
+  float4* tlas8f = nullptr;          // float 8-wide TLAS nodes (allocated by the first such build)
+  int tlas_format = 0;               // wide TLAS of the last build: 0 (depth-parity 4-wide), kWide4 (greedy), kWide8, kWide8Q
   uint32_t *tlas_perm, *tlas_codes;
   float* scene_box;
   uint32_t* error_word;
@@ -261,7 +264,7 @@ struct Carver {
 struct ArenaPlan {
   size_t o_aabbs, o_params, o_xform, o_iblas, o_iid, o_isbt, o_imask, o_hg, o_mat, o_sbt, o_rt, o_lp, o_lgq, o_binfo,
       o_vert, o_idx;
-  size_t o_tbox, o_bbox, o_bnodes, o_bperm, o_bcodes, o_rec, o_iboxes, o_tnodes, o_t4, o_c4p, o_c4e, o_c4r, o_tperm,
+  size_t o_tbox, o_bbox, o_bnodes, o_bperm, o_bcodes, o_rec, o_iboxes, o_tnodes, o_t4, o_c4p, o_c4e, o_c4r, o_wide, o_tperm,
       o_tcodes, o_sbox, o_err;
   size_t o_k0, o_k1, o_v0, o_v1, o_hist, o_cnt, o_pi, o_pl, o_part, o_jobs;
   size_t total;
@@ -300,6 +303,7 @@ ArenaPlan plan_arena(const Layout& L) {
   P.o_c4p = c.take<uint32_t>(L.n_inst);
   P.o_c4e = c.take<uint32_t>(L.n_inst);
   P.o_c4r = c.take<uint32_t>(L.n_inst);
+  P.o_wide = c.take<uint32_t>(8 * ni + 1);
   P.o_tperm = c.take<uint32_t>(L.n_inst);
   P.o_tcodes = c.take<uint32_t>(L.n_inst);
   P.o_sbox = c.take<float>(8);
@@ -364,7 +368,10 @@ SceneView view_of(const pr_scene* s) {
   v.tlas_root_ref = s->L.n_inst == 1 ? (int)kLeafBit : 0;
   // the 4-wide TLAS pays off on large instance counts only (measured: +3 % at
   // 100 000 instances, -7 % at 5); small TLASes keep the binary traversal
-  v.tlas4 = s->L.n_inst >= kTlas4MinInstances ? s->tlas4 : nullptr;
+  const bool wide = s->L.n_inst >= kTlas4MinInstances;
+  v.tlas4 = wide && s->tlas_format != kWide8 && s->tlas_format != kWide8Q ? s->tlas4 : nullptr;
+  v.tlas8 = !wide ? nullptr : s->tlas_format == kWide8Q ? s->tlas4 : s->tlas_format == kWide8 ? s->tlas8f : nullptr;
+  v.tlas8_format = v.tlas8 ? s->tlas_format : 0;
   v.tlas4_root = v.tlas_root_ref;
   v.scene_box = s->scene_box;
   v.blas_info = s->blas_info;
@@ -529,6 +536,7 @@ pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext
   s->c4_parent = (uint32_t*)(A + P.o_c4p);
   s->c4_even = (uint32_t*)(A + P.o_c4e);
   s->c4_rank = (uint32_t*)(A + P.o_c4r);
+  s->wide_slots = (uint32_t*)(A + P.o_wide);
   s->tlas_perm = (uint32_t*)(A + P.o_tperm);
   s->tlas_codes = (uint32_t*)(A + P.o_tcodes);
   s->scene_box = (float*)(A + P.o_sbox);
@@ -639,6 +647,13 @@ struct PlocChain {
 };
 
 pr_status build_impl(pr_scene* s, uint32_t flags, cudaStream_t st, PlocChain* chain);
+
+// Known flags, at most one wide-TLAS format.
+bool build_flags_ok(uint32_t f) {
+  const uint32_t wide = f & (PR_BUILD_TLAS_PARITY4 | PR_BUILD_TLAS_BVH8 | PR_BUILD_TLAS_BVH8_F32);
+  return !(f & ~(PR_BUILD_TLAS_PLOC | PR_BUILD_TLAS_PARITY4 | PR_BUILD_TLAS_BVH8 | PR_BUILD_TLAS_BVH8_F32)) &&
+         (wide & (wide - 1)) == 0;
+}
 std::mutex g_pool_mutex;
 BuildPool g_pools[64];
 
@@ -651,7 +666,7 @@ pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream) {
 }
 
 pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t flags, void* stream) {
-  if (flags & ~PR_BUILD_TLAS_PLOC) return fail(PR_ERR_INVALID_ARG, "unknown build flags");
+  if (!build_flags_ok(flags)) return fail(PR_ERR_INVALID_ARG, "unknown or conflicting build flags");
   if (n == 0) return PR_OK;
   if (!scenes) return fail(PR_ERR_INVALID_ARG, "null scene array");
   for (uint32_t i = 0; i < n; ++i)
@@ -693,7 +708,7 @@ pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t fla
 pr_status pr_build_bvh(pr_scene* s, void* stream) { return pr_build_bvh_ex(s, 0u, stream); }
 
 pr_status pr_build_bvh_ex(pr_scene* s, uint32_t flags, void* stream) {
-  if (flags & ~PR_BUILD_TLAS_PLOC) return fail(PR_ERR_INVALID_ARG, "unknown build flags");
+  if (!build_flags_ok(flags)) return fail(PR_ERR_INVALID_ARG, "unknown or conflicting build flags");
   return build_impl(s, flags, (cudaStream_t)stream, nullptr);
 }
 
@@ -733,9 +748,25 @@ pr_status build_impl(pr_scene* s, uint32_t flags, cudaStream_t st, PlocChain* ch
       } else {
         launches += launch_build_large(s->tlas_job, s->scratch, st);
       }
-      // the 4-wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
-      if (s->L.n_inst >= kTlas4MinInstances)
-        launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
+      // the wide TLAS is traversed from kTlas4MinInstances up; below that it is not built
+      if (s->L.n_inst >= kTlas4MinInstances) {
+        const int fmt = (flags & PR_BUILD_TLAS_BVH8) ? kWide8Q : (flags & PR_BUILD_TLAS_BVH8_F32) ? kWide8
+                        : (flags & PR_BUILD_TLAS_PARITY4) ? 0 : kWide4;
+        if (fmt == 0) {
+          launches += launch_collapse4(s->tlas_nodes, s->L.n_inst, s->c4_parent, s->c4_even, s->c4_rank, s->tlas4, st);
+        } else {
+          float4* out = s->tlas4;   // 128 B per binary node: room for the 4-wide or quantised 8-wide nodes
+          if (fmt == kWide8) {
+            if (!s->tlas8f)
+              PR_CUDA(cudaMalloc(&s->tlas8f, sizeof(float4) * 14 * (size_t)(s->L.n_inst - 1)), "8-wide TLAS nodes");
+            out = s->tlas8f;
+          }
+          const WideScratch ws{s->wide_slots, s->c4_even, s->c4_rank, s->c4_parent,
+                               s->wide_slots + 8 * (size_t)(s->L.n_inst - 1)};
+          launches += launch_collapse_wide(s->tlas_nodes, s->L.n_inst, fmt, ws, out, s->error_word, st);
+        }
+        s->tlas_format = fmt;
+      }
     }
   }
   cudaError_t e = cudaGetLastError();
@@ -754,7 +785,10 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
                             cudaStream_t st, uint64_t* work = nullptr) {
   TraceLaunch T;
   T.S = view_of(s);
-  if (p->flags & PR_TRACE_TLAS_BVH2) T.S.tlas4 = nullptr;   // binary TLAS traversal (comparison)
+  if (p->flags & PR_TRACE_TLAS_BVH2) {   // binary TLAS traversal (comparison)
+    T.S.tlas4 = nullptr;
+    T.S.tlas8 = nullptr;
+  }
   T.cam0 = *cam0;
   T.cams = d_cams;
   T.bases = d_cams ? s->d_bases : nullptr;
@@ -775,7 +809,8 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
   T.aov = out_aov;
   // scenes without sphere tracing whose trees are shallow enough for the
   // short stack take the analytic kernel (same arithmetic, fewer registers)
-  T.analytic_small = s->L.analytic_only && s->L.stack_bound <= (uint32_t)kShortStackDepth && !T.S.tlas4;
+  T.analytic_small = s->L.analytic_only && s->L.stack_bound <= (uint32_t)kShortStackDepth && !T.S.tlas4 &&
+                     !T.S.tlas8;
   T.counter = (unsigned long long*)counter;
   T.work = (unsigned long long*)work;
   s->trace_launches = launch_trace(T, st);
@@ -960,6 +995,7 @@ void pr_scene_destroy(pr_scene* s) {
   if (s->d_bases) cudaFree(s->d_bases);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->stage_done) cudaEventDestroy(s->stage_done);
+  if (s->tlas8f) cudaFree(s->tlas8f);
   delete s;
 }
 

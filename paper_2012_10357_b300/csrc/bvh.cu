@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals
 // the LBVH's, so the 4-wide collapse and the traversal take the tree as is.
 constexpr int kPlocRadius = 16;
 constexpr int kPlocThreads = 256;
+constexpr uint32_t kPlocTail = 1024;   // rounds with at most this many clusters run in block 0 alone
 // header words (in the radix histogram's buffer, free once the sort is done)
 constexpr int kHdrOk = 0, kHdrAbort = 1, kHdrCount = 2, kHdrGen = 3;
 constexpr size_t kPlocPartOffset = 256;              // bytes: per-block counts follow the header
@@ -506,12 +507,12 @@ __device__ __forceinline__ unsigned long long keep_merge(const int* nn, uint32_t
 
 __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
   __shared__ unsigned long long sh[kPlocThreads / 32];
+  __shared__ float sbox[(kPlocThreads + 2 * kPlocRadius) * 6];   // a tile of clusters and its halo
   __shared__ uint32_t ok_sh;
   uint32_t* hdr = A.hdr;
   const uint32_t n = A.J.n;
-  const uint32_t nthreads = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t gen = 0;
-  for (uint32_t i = tid; i < n; i += nthreads) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t leaf = A.vals[i];
     A.J.perm[i] = leaf;
     A.J.codes[i] = A.codes[i];
@@ -523,38 +524,53 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
   uint32_t m = n, next = n - 2;
   int cur = 0;
   while (m > 1) {
+    // Once few clusters are left, block 0 finishes alone: its barriers are
+    // __syncthreads, far cheaper than grid-wide ones.
+    const bool tail = m <= kPlocTail;
+    if (tail && blockIdx.x != 0) return;
+    const uint32_t nb = tail ? 1u : gridDim.x, bid = tail ? 0u : blockIdx.x;
     const int* C = A.C[cur];
     const float* CB = A.CB[cur];
-    // 1. nearest neighbour in the window
-    for (uint32_t i = tid; i < m; i += nthreads) {
-      float bi[6];
-      for (int k = 0; k < 6; ++k) bi[k] = __ldcg(CB + 6 * (size_t)i + k);
-      const uint32_t lo = i > (uint32_t)kPlocRadius ? i - kPlocRadius : 0u;
-      const uint32_t hi = min(m - 1, i + (uint32_t)kPlocRadius);
-      float best = INFINITY;
-      int bj = -1;
-      for (uint32_t j = lo; j <= hi; ++j) {
-        if (j == i) continue;
-        float bb[6];
-        for (int k = 0; k < 6; ++k) bb[k] = __ldcg(CB + 6 * (size_t)j + k);
-        const float a = half_area(bi, bb);
-        bool take = bj < 0 || a < best;
-        if (!take && a == best) {
-          const uint32_t d = j > i ? j - i : i - j, db = (uint32_t)bj > i ? (uint32_t)bj - i : i - (uint32_t)bj;
-          const uint32_t l = min(i, j), lb = min(i, (uint32_t)bj);
-          take = d != db ? d < db : ((l ^ lb) & 1u) ? (l & 1u) == 0u : l < lb;
-        }
-        if (take) {
-          best = a;
-          bj = (int)j;
-        }
+    // 1. nearest neighbour in the window, tiles of clusters staged in shared memory
+    const uint32_t ntiles = (m + kPlocThreads - 1) / kPlocThreads;
+    for (uint32_t t = bid; t < ntiles; t += nb) {
+      const long long g0 = 6ll * ((long long)t * kPlocThreads - kPlocRadius);
+      for (uint32_t k = threadIdx.x; k < (kPlocThreads + 2 * kPlocRadius) * 6; k += blockDim.x) {
+        const long long g = g0 + k;
+        sbox[k] = (g >= 0 && g < 6ll * m) ? __ldcg(CB + g) : 0.f;
       }
-      A.nn[i] = bj;
+      __syncthreads();
+      const uint32_t i = t * kPlocThreads + threadIdx.x;
+      if (i < m) {
+        const uint32_t base = t * kPlocThreads;   // sbox row of cluster c: c - base + kPlocRadius
+        const float* bi = sbox + 6 * (threadIdx.x + kPlocRadius);
+        const uint32_t lo = i > (uint32_t)kPlocRadius ? i - kPlocRadius : 0u;
+        const uint32_t hi = min(m - 1, i + (uint32_t)kPlocRadius);
+        float best = INFINITY;
+        int bj = -1;
+        for (uint32_t j = lo; j <= hi; ++j) {
+          if (j == i) continue;
+          const float a = half_area(bi, sbox + 6 * (j + kPlocRadius - base));
+          bool take = bj < 0 || a < best;
+          if (!take && a == best) {
+            const uint32_t d = j > i ? j - i : i - j, db = (uint32_t)bj > i ? (uint32_t)bj - i : i - (uint32_t)bj;
+            const uint32_t l = min(i, j), lb = min(i, (uint32_t)bj);
+            take = d != db ? d < db : ((l ^ lb) & 1u) ? (l & 1u) == 0u : l < lb;
+          }
+          if (take) {
+            best = a;
+            bj = (int)j;
+          }
+        }
+        A.nn[i] = bj;
+      }
+      __syncthreads();
     }
-    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    if (tail) __syncthreads();
+    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
     // 2. survivors and merges of each block's chunk
-    const uint32_t chunk = (m + gridDim.x - 1) / gridDim.x;
-    const uint32_t c0 = min(m, blockIdx.x * chunk), c1 = min(m, c0 + chunk);
+    const uint32_t chunk = (m + nb - 1) / nb;
+    const uint32_t c0 = min(m, bid * chunk), c1 = min(m, c0 + chunk);
     unsigned long long cnt = 0;
     for (uint32_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
       int j;
@@ -562,14 +578,15 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
     }
     unsigned long long tot;
     block_excl_scan(cnt, sh, tot);
-    if (threadIdx.x == 0) A.part[blockIdx.x] = tot;
-    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    if (threadIdx.x == 0) A.part[bid] = tot;
+    if (tail) __syncthreads();
+    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
     // 3. this block's exclusive prefix of the block counts and the round's totals
     unsigned long long pre_part = 0, all_part = 0;
-    for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
       const unsigned long long v = __ldcg(A.part + b);
       all_part += v;
-      if (b < blockIdx.x) pre_part += v;
+      if (b < bid) pre_part += v;
     }
     unsigned long long pre, all;
     block_excl_scan(pre_part, sh, pre);
@@ -613,9 +630,10 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
     cur ^= 1;
     // (the next round writes the block counts only after its first barrier,
     // when every block has read this round's)
-    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    if (tail) __syncthreads();
+    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
   }
-  if (tid == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     float box[6];
     for (int k = 0; k < 6; ++k) box[k] = __ldcg(A.CB[cur] + k);
     write_root(A.J.root_box, box);
@@ -754,6 +772,241 @@ __global__ void __launch_bounds__(256) k_bvh4_fill(const float4* nodes, uint32_t
   o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---- wide TLAS: greedy collapse of the binary tree --------------------------
+// A wide node of width W grows from a binary node: while it has fewer than W
+// children, its internal child of largest surface area (the lowest slot on
+// ties) is opened into that child's two children. The internal children left
+// at the end root the wide nodes below it. Which binary nodes root a wide node
+// depends on the tree alone, so a prefix sum over the binary node indices
+// numbers the wide nodes deterministically (the binary root is wide node 0).
+// A child slot is (binary node << 1 | side): the box and reference stored on
+// that side of that binary node.
+constexpr uint32_t kWideEmpty = 0xFFFFFFFFu;
+constexpr int kWideTopThreads = 1024;
+constexpr uint32_t kWideFrontier = 4096;   // top-down pass: shared-memory frontier
+constexpr uint32_t kWideDfsStart = 2048;   // frontier size at which per-root passes take over
+constexpr int kWideDfsStack = 7 * 64 + 8;  // (W - 1) x the deepest traversable tree
+
+__device__ __forceinline__ int bin_ref(const float4* nodes, uint32_t slot) {
+  const float4 r = nodes[4 * (size_t)(slot >> 1) + 3];
+  return __float_as_int((slot & 1u) ? r.y : r.x);
+}
+
+__device__ __forceinline__ void bin_box(const float4* nodes, uint32_t slot, float b[6]) {
+  const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)(slot >> 1)) + 6 * (slot & 1u);
+  for (int k = 0; k < 6; ++k) b[k] = f[k];
+}
+
+__device__ __forceinline__ float box_half_area(const float b[6]) {
+  const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+  return fmaf(dx, dy, fmaf(dy, dz, dz * dx));
+}
+
+// Grow the wide node rooted at binary node u: write its W slots, mark it a
+// root (is_root and rank both 1; rank is scanned in place later) and hand
+// every internal child left to push(), in slot order.
+template <int W, typename Push>
+__device__ void expand_wide(const float4* nodes, uint32_t u, uint32_t* slots, uint32_t* is_root, uint32_t* rank,
+                            Push push) {
+  uint32_t slot[W];
+  int cnt = 2;
+  slot[0] = u << 1;
+  slot[1] = (u << 1) | 1u;
+  while (cnt < W) {
+    int best = -1;
+    float best_a = -1.f;
+    for (int k = 0; k < cnt; ++k) {
+      if (bin_ref(nodes, slot[k]) < 0) continue;
+      float b[6];
+      bin_box(nodes, slot[k], b);
+      const float a = box_half_area(b);
+      if (a > best_a) {
+        best_a = a;
+        best = k;
+      }
+    }
+    if (best < 0) break;
+    const uint32_t r = (uint32_t)bin_ref(nodes, slot[best]);
+    slot[best] = r << 1;
+    slot[cnt++] = (r << 1) | 1u;
+  }
+  is_root[u] = 1u;
+  rank[u] = 1u;
+  for (int k = 0; k < W; ++k) {
+    slots[(size_t)u * W + k] = k < cnt ? slot[k] : kWideEmpty;
+    if (k < cnt) {
+      const int r = bin_ref(nodes, slot[k]);
+      if (r >= 0) push((uint32_t)r);
+    }
+  }
+}
+
+// Top of the wide tree, level by level in one block, until the frontier holds
+// kWideDfsStart roots (or cannot grow inside shared memory); the frontier is
+// then written out for k_wide_dfs.
+template <int W>
+__global__ void __launch_bounds__(kWideTopThreads) k_wide_top(const float4* nodes, uint32_t* slots, uint32_t* is_root,
+                                                             uint32_t* rank, uint32_t* frontier, uint32_t* n_frontier) {
+  __shared__ uint32_t buf[2][kWideFrontier];
+  __shared__ uint32_t cnt[2];
+  if (threadIdx.x == 0) {
+    buf[0][0] = 0;
+    cnt[0] = 1;
+    cnt[1] = 0;
+  }
+  __syncthreads();
+  int c = 0;
+  for (;;) {
+    const uint32_t m = cnt[c];
+    if (m == 0 || m >= kWideDfsStart || m * (uint32_t)W > kWideFrontier) break;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
+      expand_wide<W>(nodes, buf[c][i], slots, is_root, rank,
+                     [&](uint32_t r) { buf[c ^ 1][atomicAdd(&cnt[c ^ 1], 1u)] = r; });
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[c] = 0;
+    c ^= 1;
+    __syncthreads();
+  }
+  const uint32_t m = cnt[c];
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) frontier[i] = buf[c][i];
+  if (threadIdx.x == 0) *n_frontier = m;
+}
+
+// The subtree below each frontier root, depth first, one thread per root.
+template <int W>
+__global__ void __launch_bounds__(128) k_wide_dfs(const float4* nodes, uint32_t* slots, uint32_t* is_root,
+                                                 uint32_t* rank, const uint32_t* frontier, const uint32_t* n_frontier,
+                                                 uint32_t* error_word) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n_frontier) return;
+  uint32_t stack[kWideDfsStack];
+  int sp = 0;
+  stack[sp++] = frontier[i];
+  while (sp > 0) {
+    const uint32_t u = stack[--sp];
+    expand_wide<W>(nodes, u, slots, is_root, rank, [&](uint32_t r) {
+      if (sp < kWideDfsStack) {
+        stack[sp++] = r;
+      } else {   // deeper than any tree the traversal stack can take: an empty node, flagged
+        is_root[r] = 1u;
+        rank[r] = 1u;
+        for (int k = 0; k < W; ++k) slots[(size_t)r * W + k] = kWideEmpty;
+        if (error_word) atomicOr(error_word, kErrStack);
+      }
+    });
+  }
+}
+
+// 4-wide nodes in the existing 128-byte layout.
+__global__ void __launch_bounds__(256) k_wide_fill4(const float4* nodes, uint32_t n, const uint32_t* slots,
+                                                    const uint32_t* is_root, const uint32_t* rank, float4* out) {
+  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u + 1 >= n || !is_root[u]) return;
+  float lo[3][4], hi[3][4];
+  int ref[4];
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t sl = slots[(size_t)u * 4 + k];
+    if (sl == kWideEmpty) {
+      for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
+      ref[k] = kEmptySlot;
+      continue;
+    }
+    float b[6];
+    bin_box(nodes, sl, b);
+    for (int a = 0; a < 3; ++a) { lo[a][k] = b[a]; hi[a][k] = b[3 + a]; }
+    const int r = bin_ref(nodes, sl);
+    ref[k] = r >= 0 ? (int)rank[r] : r;
+  }
+  float4* o = out + 8 * (size_t)rank[u];
+  for (int a = 0; a < 3; ++a) {
+    o[a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+    o[3 + a] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+  }
+  o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+  o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// 8-wide nodes. Float layout (224 B, 14 float4): lo.x[8], lo.y[8], lo.z[8],
+// hi.x[8], hi.y[8], hi.z[8], refs[8]. Quantised layout (96 B, 6 float4), after
+// Ylitie et al. 2017: origin.xyz and three biased power-of-two exponents, then
+// per axis the 8 lower and 8 upper child bounds as bytes (lo[0..3], lo[4..7],
+// hi[0..3], hi[4..7] words), then refs[8]. A child bound decodes to
+// origin + q * 2^e. Quantisation is conservative with a margin of one step on
+// either side (the origin sits one step below the node), so a decoded box
+// contains the float box by at least one step; the step is at least 2^-18 of
+// the node's coordinate magnitude, so the margin exceeds the rounding of the
+// slab tests and the decoded boxes pass every ray the float boxes pass.
+template <bool kQuant>
+__global__ void __launch_bounds__(256) k_wide_fill8(const float4* nodes, uint32_t n, const uint32_t* slots,
+                                                    const uint32_t* is_root, const uint32_t* rank, float4* out) {
+  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u + 1 >= n || !is_root[u]) return;
+  float lo[3][8], hi[3][8];
+  int ref[8];
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t sl = slots[(size_t)u * 8 + k];
+    if (sl == kWideEmpty) {
+      for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
+      ref[k] = kEmptySlot;
+      continue;
+    }
+    float b[6];
+    bin_box(nodes, sl, b);
+    for (int a = 0; a < 3; ++a) { lo[a][k] = b[a]; hi[a][k] = b[3 + a]; }
+    const int r = bin_ref(nodes, sl);
+    ref[k] = r >= 0 ? (int)rank[r] : r;
+  }
+  if (!kQuant) {
+    float4* o = out + 14 * (size_t)rank[u];
+    for (int a = 0; a < 3; ++a) {
+      o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
+      o[2 * a + 1] = make_float4(lo[a][4], lo[a][5], lo[a][6], lo[a][7]);
+      o[6 + 2 * a] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
+      o[6 + 2 * a + 1] = make_float4(hi[a][4], hi[a][5], hi[a][6], hi[a][7]);
+    }
+    o[12] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+    o[13] = make_float4(__int_as_float(ref[4]), __int_as_float(ref[5]), __int_as_float(ref[6]), __int_as_float(ref[7]));
+    return;
+  }
+  float org[3];
+  uint32_t ebits = 0, w[3][4];
+  for (int a = 0; a < 3; ++a) {
+    float L = INFINITY, H = -INFINITY;
+    for (int k = 0; k < 8; ++k)
+      if (ref[k] != kEmptySlot) {
+        L = fminf(L, lo[a][k]);
+        H = fmaxf(H, hi[a][k]);
+      }
+    // step 2^e: at least 1/248 of the extent and 2^-18 of the magnitude
+    const double need = fmax(((double)H - (double)L) / 248.0, ldexp(fmax(fabs((double)L), fabs((double)H)), -18));
+    int e;
+    frexp(need > 0.0 ? need : 1e-30, &e);   // need < 2^e
+    e = max(-126, min(127, e));
+    const double step = ldexp(1.0, e);
+    org[a] = __double2float_rd((double)L - step);
+    w[a][0] = w[a][1] = w[a][2] = w[a][3] = 0;
+    for (int k = 0; k < 8; ++k) {
+      uint32_t ql = 0, qh = 0;
+      if (ref[k] != kEmptySlot) {
+        const double fl = floor(((double)lo[a][k] - (double)org[a]) / step) - 1.0;
+        const double fh = ceil(((double)hi[a][k] - (double)org[a]) / step) + 1.0;
+        ql = (uint32_t)fmin(fmax(fl, 0.0), 255.0);
+        qh = (uint32_t)fmin(fmax(fh, 0.0), 255.0);
+      }
+      w[a][k >> 2] |= ql << (8 * (k & 3));
+      w[a][2 + (k >> 2)] |= qh << (8 * (k & 3));
+    }
+    ebits |= (uint32_t)(e + 127) << (8 * a);
+  }
+  float4* o = out + 6 * (size_t)rank[u];
+  o[0] = make_float4(org[0], org[1], org[2], __uint_as_float(ebits));
+  for (int a = 0; a < 3; ++a)
+    o[1 + a] = make_float4(__uint_as_float(w[a][0]), __uint_as_float(w[a][1]), __uint_as_float(w[a][2]),
+                           __uint_as_float(w[a][3]));
+  o[4] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+  o[5] = make_float4(__int_as_float(ref[4]), __int_as_float(ref[5]), __int_as_float(ref[6]), __int_as_float(ref[7]));
+}
+
 // Vertex bounds of each triangle (exact: min/max only).
 __global__ void __launch_bounds__(256) k_tri_boxes(const float* v, const uint32_t* idx, uint32_t n, float* boxes) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -784,6 +1037,30 @@ int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_
   k_radix_scan<<<1, 1024, 0, s>>>(rank, n - 1);            // exclusive prefix sum: 4-wide node index
   k_bvh4_fill<<<nb, 256, 0, s>>>(nodes2, n, even, rank, nodes4);
   return 4;
+}
+
+int launch_collapse_wide(const float4* nodes2, uint32_t n, int format, const WideScratch& ws, float4* out,
+                         uint32_t* error_word, cudaStream_t s) {
+  if (n < 2) return 0;
+  const uint32_t nb = (n + 255) / 256;
+  const int W = format == kWide4 ? 4 : 8;
+  cudaMemsetAsync(ws.is_root, 0, sizeof(uint32_t) * (n - 1), s);
+  cudaMemsetAsync(ws.rank, 0, sizeof(uint32_t) * (n - 1), s);
+  const uint32_t dfs_blocks = (kWideFrontier + 127) / 128;
+  if (W == 4) {
+    k_wide_top<4><<<1, kWideTopThreads, 0, s>>>(nodes2, ws.slots, ws.is_root, ws.rank, ws.frontier, ws.n_frontier);
+    k_wide_dfs<4><<<dfs_blocks, 128, 0, s>>>(nodes2, ws.slots, ws.is_root, ws.rank, ws.frontier, ws.n_frontier,
+                                             error_word);
+  } else {
+    k_wide_top<8><<<1, kWideTopThreads, 0, s>>>(nodes2, ws.slots, ws.is_root, ws.rank, ws.frontier, ws.n_frontier);
+    k_wide_dfs<8><<<dfs_blocks, 128, 0, s>>>(nodes2, ws.slots, ws.is_root, ws.rank, ws.frontier, ws.n_frontier,
+                                             error_word);
+  }
+  k_radix_scan<<<1, 1024, 0, s>>>(ws.rank, n - 1);   // exclusive prefix sum: wide node index
+  if (format == kWide4) k_wide_fill4<<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
+  else if (format == kWide8) k_wide_fill8<false><<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
+  else k_wide_fill8<true><<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
+  return 6;
 }
 
 int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s) {
@@ -858,7 +1135,7 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_ploc, kPlocThreads, 0);
-    if (blocks_per_sm > 2) blocks_per_sm = 2;
+    if (blocks_per_sm > 1) blocks_per_sm = 1;   // one block per SM: cheaper grid barriers
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   const size_t hist_bytes = sizeof(uint32_t) * 256 * (size_t)tiles;

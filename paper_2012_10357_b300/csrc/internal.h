@@ -48,6 +48,20 @@ int launch_build_small_one(const LevelDesc& job, cudaStream_t s);
 // 4-wide collapse of a built binary level of n leaves (scratch: parent, even, rank of n words).
 int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_t* even, uint32_t* rank,
                      float4* nodes4, cudaStream_t s);
+
+// Greedy collapse of a binary tree (root 0, n leaves) into wide nodes: each
+// wide node opens its largest-area internal child until it has W children.
+// Formats: kWide4 (128-B 4-wide nodes, the layout of launch_collapse4),
+// kWide8 (224-B float 8-wide), kWide8Q (96-B quantised 8-wide).
+struct WideScratch {
+  uint32_t* slots;       // [8 * (n - 1)] child slots per binary node
+  uint32_t* is_root;     // [n] binary node roots a wide node
+  uint32_t* rank;        // [n] wide node index (exclusive prefix sum of is_root)
+  uint32_t* frontier;    // [n] roots handed from the top-down pass to the per-root pass
+  uint32_t* n_frontier;  // [1]
+};
+int launch_collapse_wide(const float4* nodes2, uint32_t n, int format, const WideScratch& ws, float4* out,
+                         uint32_t* error_word, cudaStream_t s);
 int launch_build_large(const LevelDesc& job, const BuildScratch& sc, cudaStream_t s);
 
 // PLOC build of a large level (more than kSmallMax leaves): the LBVH's Morton

@@ -14,7 +14,9 @@ constexpr int kStackDepth = (int)PR_STACK_DEPTH;
 constexpr int kShortStackDepth = 8;
 constexpr uint32_t kErrSbt = 1u << PR_ERR_SBT_INDEX;
 constexpr uint32_t kErrStack = 1u << PR_ERR_STACK_OVERFLOW;
-constexpr int kEmptySlot = 0x7FFFFFFF;   // unused child slot of a 4-wide node
+constexpr int kEmptySlot = 0x7FFFFFFF;   // unused child slot of a 4- or 8-wide node
+// Wide TLAS node formats (see the collapse in bvh.cu).
+enum WideFormat : int { kWide4 = 4, kWide8 = 8, kWide8Q = 9 };
 
 // One 4-wide node = 128 bytes = 8 x float4, child boxes stored by coordinate
 // so the four slab tests run on whole vectors:
@@ -48,7 +50,9 @@ struct SceneView {
   const float4* tlas_nodes;   // [max(n_inst-1,0)][4]
   int tlas_root_ref;          // 0 or kLeafBit | instance (single instance)
   const float4* tlas4;        // [n4][8] 4-wide TLAS collapsed from the binary one, or null
-  int tlas4_root;             // 0 or kLeafBit | instance
+  int tlas4_root;             // 0 or kLeafBit | instance (root of the 4- or 8-wide TLAS)
+  const float4* tlas8;        // 8-wide TLAS ([n8][14] float or [n8][6] quantised nodes), or null
+  int tlas8_format;           // kWide8 or kWide8Q when tlas8 is set
   const float* scene_box;     // [6] TLAS root box (world)
   // BLAS
   const int4* blas_info;      // [n_blas] BlasInfo

@@ -361,6 +361,8 @@ struct WorkCounters {
   uint32_t frac_iters[2];   // Julia, Mandelbulb loop trips
   uint32_t shaded, rays;
   uint32_t tlas_nodes4;     // 4-wide TLAS node visits
+  uint32_t tlas_nodes8;     // 8-wide TLAS node visits (float nodes)
+  uint32_t tlas_nodes8q;    // 8-wide TLAS node visits (quantised nodes)
 };
 static_assert(sizeof(WorkCounters) == 4 * PR_WORK_COUNTERS, "counter layout is part of the ABI");
 

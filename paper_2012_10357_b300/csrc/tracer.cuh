@@ -232,7 +232,9 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
 }
 
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
+// kTlas: 0 = the 4-wide TLAS when the scene has one, else the binary one;
+// kWide8 / kWide8Q = the scene's 8-wide TLAS (float / quantised nodes).
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0>
 __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
                           uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_, Deferred* defer = nullptr) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
@@ -245,6 +247,102 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
   float3 inv = safe_rcp(d);
   float3 o_inv = f3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
   int sp = 0;
+  if constexpr (kTlas == kWide8 || kTlas == kWide8Q) {
+    // 8-wide TLAS: eight slab tests per node, hit children ordered near to far
+    // by a 19-exchange sorting network (Batcher's odd-even merge sort); the
+    // nearest is visited next, the others pushed farthest first. Quantised
+    // nodes decode a bound as origin + q * 2^e inside the slab test: with
+    // a = 2^e / d and b = (origin - o) / d, t = q * a + b, and the entry
+    // and exit bounds of each axis are picked once per node by the sign of d.
+    constexpr int kNone = 0x7FFFFFFF;
+    const bool px = inv.x >= 0.f, py = inv.y >= 0.f, pz = inv.z >= 0.f;
+    auto visit8 = [&](int node) -> int {
+      if (wc) ++(kTlas == kWide8Q ? wc->tlas_nodes8q : wc->tlas_nodes8);
+      float key[8];
+      int ref[8];
+      if constexpr (kTlas == kWide8Q) {
+        const float4* nd = S.tlas8 + 6 * (size_t)node;
+        const float4 h0 = __ldg(nd);
+        const float4 fx = __ldg(nd + 1), fy = __ldg(nd + 2), fz = __ldg(nd + 3);
+        const int4 r0 = __ldg(reinterpret_cast<const int4*>(nd + 4)), r1 = __ldg(reinterpret_cast<const int4*>(nd + 5));
+        ref[0] = r0.x; ref[1] = r0.y; ref[2] = r0.z; ref[3] = r0.w;
+        ref[4] = r1.x; ref[5] = r1.y; ref[6] = r1.z; ref[7] = r1.w;
+        const uint32_t eb = __float_as_uint(h0.w);
+        const float ax = __uint_as_float((eb & 0xFFu) << 23) * inv.x;
+        const float ay = __uint_as_float(((eb >> 8) & 0xFFu) << 23) * inv.y;
+        const float az = __uint_as_float(((eb >> 16) & 0xFFu) << 23) * inv.z;
+        const float bx = fmaf(h0.x, inv.x, o_inv.x), by = fmaf(h0.y, inv.y, o_inv.y), bz = fmaf(h0.z, inv.z, o_inv.z);
+        // entry (n) and exit (f) byte words per axis: {children 0-3, 4-7}
+        const uint32_t wx[4] = {__float_as_uint(fx.x), __float_as_uint(fx.y), __float_as_uint(fx.z), __float_as_uint(fx.w)};
+        const uint32_t wy[4] = {__float_as_uint(fy.x), __float_as_uint(fy.y), __float_as_uint(fy.z), __float_as_uint(fy.w)};
+        const uint32_t wz[4] = {__float_as_uint(fz.x), __float_as_uint(fz.y), __float_as_uint(fz.z), __float_as_uint(fz.w)};
+        const uint32_t nx[2] = {px ? wx[0] : wx[2], px ? wx[1] : wx[3]}, fxw[2] = {px ? wx[2] : wx[0], px ? wx[3] : wx[1]};
+        const uint32_t ny[2] = {py ? wy[0] : wy[2], py ? wy[1] : wy[3]}, fyw[2] = {py ? wy[2] : wy[0], py ? wy[3] : wy[1]};
+        const uint32_t nz[2] = {pz ? wz[0] : wz[2], pz ? wz[1] : wz[3]}, fzw[2] = {pz ? wz[2] : wz[0], pz ? wz[3] : wz[1]};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          // byte k of a word as a float: 2^23 + q (exponent byte 0x4B), minus 2^23
+          const uint32_t sel = 0x7540u | (uint32_t)(k & 3);
+          auto dq = [&](uint32_t w) { return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.f; };
+          const float tnx = fmaf(dq(nx[k >> 2]), ax, bx), tfx = fmaf(dq(fxw[k >> 2]), ax, bx);
+          const float tny = fmaf(dq(ny[k >> 2]), ay, by), tfy = fmaf(dq(fyw[k >> 2]), ay, by);
+          const float tnz = fmaf(dq(nz[k >> 2]), az, bz), tfz = fmaf(dq(fzw[k >> 2]), az, bz);
+          const float t0 = fmax3(tnx, tny, fmaxf(tnz, tmin));
+          const float t1 = fmin3(tfx, tfy, fminf(tfz, h.t));
+          key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
+        }
+      } else {
+        const float4* nd = S.tlas8 + 14 * (size_t)node;
+        float4 v[14];
+#pragma unroll
+        for (int q = 0; q < 14; ++q) v[q] = __ldg(nd + q);
+        const float* f = reinterpret_cast<const float*>(v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ref[k] = __float_as_int(f[48 + k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float ax = fmaf(f[k], inv.x, o_inv.x), bx = fmaf(f[24 + k], inv.x, o_inv.x);
+          const float ay = fmaf(f[8 + k], inv.y, o_inv.y), by = fmaf(f[32 + k], inv.y, o_inv.y);
+          const float az = fmaf(f[16 + k], inv.z, o_inv.z), bz = fmaf(f[40 + k], inv.z, o_inv.z);
+          const float t0 = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), tmin));
+          const float t1 = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), h.t));
+          key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
+        }
+      }
+      auto cswap = [&](int a, int b) {
+        if (key[b] < key[a]) {
+          float tk = key[a]; key[a] = key[b]; key[b] = tk;
+          int tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;
+        }
+      };
+      cswap(0, 1); cswap(2, 3); cswap(4, 5); cswap(6, 7);
+      cswap(0, 2); cswap(1, 3); cswap(4, 6); cswap(5, 7);
+      cswap(1, 2); cswap(5, 6);
+      cswap(0, 4); cswap(1, 5); cswap(2, 6); cswap(3, 7);
+      cswap(2, 4); cswap(3, 5);
+      cswap(1, 2); cswap(3, 4); cswap(5, 6);
+      if (key[0] == INFINITY) return kNone;
+#pragma unroll
+      for (int k = 7; k >= 1; --k) {
+        if (key[k] != INFINITY) {
+          if (sp < kDepth) stack[sp++] = ref[k];
+          else atomicOr(S.error_word, kErrStack);
+        }
+      }
+      return ref[0];
+    };
+    int node = S.tlas4_root;   // 0 or kLeafBit | instance
+    for (;;) {
+      if (node >= 0) {
+        node = visit8(node);
+        if (node != kNone) continue;
+      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
+        return;
+      }
+      if (sp == 0) return;
+      node = stack[--sp];
+    }
+  }
   if (S.tlas4) {
     // 4-wide TLAS: four slab tests per node on coordinate vectors, hit
     // children ordered near to far by a 5-exchange sorting network; the
@@ -390,12 +488,12 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
 #endif
 }
 
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
                                             float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc,
                                             Deferred* defer = nullptr) {
   const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
-  trace_ray<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc, defer);
+  trace_ray<kStats, kAnalytic, kDepth, kDefer, kTlas>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc, defer);
 }
 
 struct Surface {
@@ -527,12 +625,12 @@ struct PixelParams {
   uint32_t max_depth, max_steps;
 };
 
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, int kTlas = 0>
 __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
                                                TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
   Hit h;
   rays += 1;
-  trace_typed<kStats, kAnalytic, kDepth>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
+  trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
   // AOV fields are stored as soon as they are known, so none of them stays
   // live across the shadow and mirror traces
   float3 color;
@@ -569,7 +667,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit sh;
         rays++;
         flags |= 2u;
-        trace_typed<kStats, kAnalytic, kDepth>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
         vis = sh.inst >= 0 ? 0.f : 1.f;
         if (sh.inst < 0) flags |= 4u;
       }
@@ -582,7 +680,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit rh;
         rays++;
         flags |= 8u;
-        trace_typed<kStats, kAnalytic, kDepth>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
         float3 lr;
         if (rh.inst >= 0) {
           flags |= 16u;

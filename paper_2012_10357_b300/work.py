@@ -21,6 +21,12 @@ Per-unit counts (trace.cu / tracer.cuh / shaders.cuh):
   BVH2 node   two slab tests: 12 FFMA; 20 min/max + 3 compares
   4-wide node four slab tests: 24 FFMA; 40 min/max + 12 compares/selects +
               5-exchange sort (15)
+  8-wide node float nodes: eight slab tests, 48 FFMA; 80 min/max + 24
+              compares/selects + 19-exchange sort (57). Quantised nodes:
+              per node 3 FMUL + 3 FFMA (step / d, (origin - o) / d) and 12
+              word selects (entry / exit bounds by the sign of d); per child
+              6 byte-to-float decodes (byte permute + FADD) and 6 FFMA, 4
+              min/max + 3 compares/selects; the sort (57)
   instance    world->object origin (9 FFMA) and direction (6 FFMA + 3 FMUL),
               1/d, -o/d, BLAS root-box slab test (6 FFMA, 10 min/max)
   leaf        primitive AABB slab test: 6 FFMA, 11 min/max/compare
@@ -47,6 +53,8 @@ UNITS = {
     "rays": (34, 6, 4),
     "tlas_nodes": (24, 23, 0),
     "tlas_nodes4": (48, 67, 0),
+    "tlas_nodes8": (96, 161, 0),
+    "tlas_nodes8q": (153, 173, 0),
     "blas_nodes": (24, 23, 0),
     "instances": (51, 17, 3),
     "leaves": (12, 11, 0),

@@ -67,8 +67,11 @@ typedef enum {
 #define PR_CHS_LAMBERT 0u
 /* Any-hit shaders (run on every candidate hit; may ignore it). PR_AHS_CUTOUT
  * ignores candidates whose object-space point has frac(4*y) < 1/2 (bands cut
- * out of the surface); allowed with the sphere, box and pac-man shaders, whose
- * intersection shaders report their candidates in increasing t. */
+ * out of the surface). Every intersection shader reports its candidates in
+ * increasing t: the sphere its two roots, the box its entry and exit, the
+ * pac-man its boundary events; a sphere-traced shader every march point whose
+ * estimate is below eps, the march going on after an ignored one by the
+ * estimate's magnitude (at least eps), through the solid and out of it. */
 #define PR_AHS_CUTOUT 0u
 /* Miss shaders */
 #define PR_MISS_BACKGROUND 0u
@@ -103,7 +106,7 @@ typedef struct pr_scene pr_scene;
  *                   inst_sbt_offset is Eq. 1's i in records (DXR's
  *                   InstanceContributionToHitGroupIndex); mask 0 hides it
  *  hit_groups       [n_hit_groups][3] uint32 is_id, chs_id, ahs_id (PR_NONE = absent;
- *                   ahs PR_AHS_CUTOUT needs an analytic intersection shader)
+ *                   ahs PR_AHS_CUTOUT needs an intersection shader)
  *  materials        [n_materials][4] float albedo rgb, mirror reflectance
  *  sbt              [n_records][4] uint32 hit_group, material, prim_type, instance_index
  *                   (the root arguments of Listing 10)

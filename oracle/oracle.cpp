@@ -403,8 +403,13 @@ double distance_estimate(uint32_t id, const float* prm, V3 p) {
 // advances by it; the march gives up past t_hi or after max_steps estimates.
 // Normal: normalised central-difference gradient with step h = eps |d|
 // (eps expressed in object units); a zero gradient falls back to -d.
+// Every march point whose estimate is below eps is a candidate, reported in
+// increasing t to the hit group's any-hit shader (Section 2.2.3); an ignored
+// candidate lets the march go on by the estimate's magnitude, at least eps
+// (through the solid, where an exact SDF is negative, and out of it), so the
+// next candidate is the next point in or on the surface that the march visits.
 bool is_sphere_trace(uint32_t id, const float* prm, V3 o, V3 d, double t_lo, double t_hi, double eps,
-                     uint32_t max_steps, IsHit& h) {
+                     uint32_t max_steps, IsHit& h, uint32_t ahs = kNone) {
   double dl = len(d);
   double inv_len = 1.0 / dl;
   double t = t_lo;
@@ -412,6 +417,10 @@ bool is_sphere_trace(uint32_t id, const float* prm, V3 o, V3 d, double t_lo, dou
     if (t > t_hi) return false;
     V3 p = o + t * d;
     double dist = distance_estimate(id, prm, p) * inv_len;
+    if (dist < eps && !any_hit_accepts(ahs, p)) {
+      t += std::max(std::fabs(dist), eps);
+      continue;
+    }
     if (dist < eps) {
       double hh = eps * dl;
       V3 g{distance_estimate(id, prm, p + V3{hh, 0, 0}) - distance_estimate(id, prm, p - V3{hh, 0, 0}),
@@ -437,7 +446,7 @@ bool intersect(uint32_t id, const float* prm, V3 o, V3 d, double tmin, double t_
     case kBox: return is_box(prm, o, d, tmin, h, ahs);
     case kPacman: return is_pacman(prm, o, d, tmin, h, ahs);
     default:
-      if (is_sphere_traced(id)) return is_sphere_trace(id, prm, o, d, t_lo, t_hi, eps, max_steps, h);
+      if (is_sphere_traced(id)) return is_sphere_trace(id, prm, o, d, t_lo, t_hi, eps, max_steps, h, ahs);
       return false;
   }
 }

@@ -57,6 +57,7 @@ struct Layout {
   // every hit group's intersection shader is analytic (sphere, box, pac-man) or
   // absent (triangles): no sphere tracing anywhere in the scene
   bool analytic_only = true;
+  bool ahs_march = false;   // an any-hit shader on a sphere-traced intersection shader
   // bound on the traversal stack entries of any ray: a binary tree of n
   // leaves is at most n - 1 deep and a ray holds at most one entry per level
   // of the TLAS and of one BLAS below it
@@ -176,9 +177,10 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L, bool check = t
     if (is != PR_NONE && is >= PR_IS_COUNT) return fail(PR_ERR_INVALID_ARG, "unknown intersection shader id");
     if (chs != PR_NONE && chs != PR_CHS_LAMBERT) return fail(PR_ERR_INVALID_ARG, "unknown closest-hit shader id");
     if (ahs != PR_NONE && ahs != PR_AHS_CUTOUT) return fail(PR_ERR_INVALID_ARG, "unknown any-hit shader id");
-    if (ahs == PR_AHS_CUTOUT && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN)
-      return fail(PR_ERR_INVALID_ARG, "any-hit shaders need an analytic intersection shader (sphere, box, pac-man)");
+    if (ahs == PR_AHS_CUTOUT && is == PR_NONE)
+      return fail(PR_ERR_INVALID_ARG, "any-hit shaders need an intersection shader");
     if (is != PR_NONE && is != PR_IS_SPHERE && is != PR_IS_BOX && is != PR_IS_PACMAN) L.analytic_only = false;
+    if (ahs != PR_NONE && is >= PR_IS_TORUS && is <= PR_IS_JULIA_CUT) L.ahs_march = true;
   }
   for (uint32_t r = 0; check && r < L.n_rec; ++r) {
     if (d->sbt[4 * r] >= L.n_hg) return fail(PR_ERR_INVALID_ARG, "record " + std::to_string(r) + " hit group out of range");
@@ -455,6 +457,7 @@ pr_status pr_internal_scene_bytes(const pr_scene_desc* desc, size_t* bytes, size
   return st;
 }
 bool pr_internal_built(const pr_scene* s) { return s && s->built; }
+bool pr_internal_ahs_march(const pr_scene* s) { return s && s->L.ahs_march; }
 void pr_internal_set_error(const std::string& msg) { g_last_error = msg; }
 
 extern "C" {
@@ -809,6 +812,7 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
   T.aov = out_aov;
   // scenes without sphere tracing whose trees are shallow enough for the
   // short stack take the analytic kernel (same arithmetic, fewer registers)
+  T.ahs_march = s->L.ahs_march;
   T.analytic_small = s->L.analytic_only && s->L.stack_bound <= (uint32_t)kShortStackDepth && !T.S.tlas4 &&
                      !T.S.tlas8;
   T.counter = (unsigned long long*)counter;

@@ -33,6 +33,9 @@ struct pr_batch {
   uint32_t graph_tiles = 0;          // grid of the captured one-CTA-per-tile megakernel
   uint32_t graph_launches = 0;
   uint32_t staged_tiles = 0;         // tiles of the last staged batch
+  BatchTuning staged_tuning{};       // launch shape the last staged batch was laid out for
+  bool staged_ahs = false;           // the last staged batch needs the any-hit march
+  bool graph_ahs = false;
   uint32_t last_launches = 0;
   uint32_t* notify = nullptr;        // completion flags for the next staged batch (host-mapped)
   uint32_t notify_seq = 0;
@@ -69,6 +72,16 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   if (e != cudaSuccess) return bcuda(e, "wait for staging buffer");
   BatchHdr* H = reinterpret_cast<BatchHdr*>(b->staging);
   ReqDev* R = reinterpret_cast<ReqDev*>(b->staging + a256(sizeof(BatchHdr)));
+  // A scene with an any-hit shader on a sphere-traced shader takes the batch
+  // to the megakernel compiled with the any-hit march (16x8 tiles).
+  bool ahs = false;
+  for (uint32_t i = 0; i < n; ++i) ahs = ahs || pr_internal_ahs_march(reqs[i].scene);
+  BatchTuning T = b->tuning;
+  if (ahs) {
+    T.tile_w = 16;
+    T.tile_h = 8;
+    T.megakernel = 2;
+  }
   uint64_t px = 0;
   uint32_t tiles = 0;
   for (uint32_t i = 0; i < n; ++i) {
@@ -97,13 +110,13 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
     d.row_begin = q.row_begin;
     d.rows = rows;
     d.tile_begin = tiles;
-    d.tiles_x = (p.width + b->tuning.tile_w - 1) / b->tuning.tile_w;
+    d.tiles_x = (p.width + T.tile_w - 1) / T.tile_w;
     d.out = reinterpret_cast<float4*>(q.out_rgba);
     d.out_rgb = (p.flags & PR_TRACE_OUTPUT_RGB) ? 1u : 0u;
     d.tiles_done = 0u;
     d.pad_[0] = d.pad_[1] = d.pad_[2] = 0u;
     d.pixel_begin = px;
-    uint64_t t = (uint64_t)d.tiles_x * ((rows + b->tuning.tile_h - 1) / b->tuning.tile_h);
+    uint64_t t = (uint64_t)d.tiles_x * ((rows + T.tile_h - 1) / T.tile_h);
     if (tiles + t > 0xFFFFFFFFull) return bfail(PR_ERR_INVALID_ARG, "too many tiles");
     d.n_tiles = (uint32_t)t;
     tiles += (uint32_t)t;
@@ -113,6 +126,8 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   H->n_req = n;
   H->total_tiles = tiles;
   b->staged_tiles = tiles;
+  b->staged_tuning = T;
+  b->staged_ahs = ahs;
   H->total_pixels = px;
   H->tile_ctr = H->shadow_n = H->mirror_n = H->shadow_ctr = H->mirror_ctr = H->pad = 0;
   H->counter = reinterpret_cast<unsigned long long*>(counter);
@@ -137,13 +152,15 @@ pr_status capture(pr_batch* b) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bcuda(e, "begin capture");
-  b->graph_launches = (uint32_t)launch_wavefront(b->V, b->tuning, b->n_sm, b->graph_tiles, b->capture_stream);
+  b->graph_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->graph_tiles, b->capture_stream,
+                                                 b->staged_ahs);
   e = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess) return bcuda(e, "end capture");
   e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bcuda(e, "instantiate graph");
-  b->graph_tuning = b->tuning;
+  b->graph_tuning = b->staged_tuning;
+  b->graph_ahs = b->staged_ahs;
   return PR_OK;
 }
 
@@ -253,7 +270,7 @@ pr_status pr_trace_batch(pr_batch* b, uint32_t n, const pr_request* reqs, uint64
   cudaStream_t st = (cudaStream_t)stream;
   pr_status s = stage(b, n, reqs, ray_counter, st);
   if (s != PR_OK) return s;
-  b->last_launches = (uint32_t)launch_wavefront(b->V, b->tuning, b->n_sm, b->staged_tiles, st);
+  b->last_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->staged_tiles, st, b->staged_ahs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bcuda(e, "wavefront launch");
   return PR_OK;
@@ -266,13 +283,14 @@ pr_status pr_trace_batch_graph(pr_batch* b, uint32_t n, const pr_request* reqs, 
   if (s != PR_OK) return s;
   // the one-CTA-per-tile megakernel needs a grid of at least this batch's tiles: capture again
   // (with room to grow) when it is larger than the captured one
-  const bool grow = b->tuning.megakernel == 2 && b->staged_tiles > b->graph_tiles;
+  const bool grow = b->staged_tuning.megakernel == 2 && b->staged_tiles > b->graph_tiles;
   if (grow) {
     uint32_t g = 1024;
     while (g < b->staged_tiles && g < 0x80000000u) g <<= 1;
     b->graph_tiles = g;
   }
-  if (!b->graph || grow || memcmp(&b->graph_tuning, &b->tuning, sizeof(BatchTuning)) != 0) {
+  if (!b->graph || grow || b->graph_ahs != b->staged_ahs ||
+      memcmp(&b->graph_tuning, &b->staged_tuning, sizeof(BatchTuning)) != 0) {
     pr_status c = capture(b);
     if (c != PR_OK) return c;
   }

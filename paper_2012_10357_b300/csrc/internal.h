@@ -118,6 +118,7 @@ struct TraceLaunch {
   unsigned long long* counter;
   unsigned long long* work;   // non-null: instrumented variant, adds WorkCounters
   bool analytic_small;        // analytic shaders only and stack need <= kShortStackDepth
+  bool ahs_march;             // an any-hit shader on a sphere-traced shader: kernels with the any-hit march
 };
 int launch_trace(const TraceLaunch& L, cudaStream_t s);
 // Device bytes of one camera basis (TraceLaunch::bases holds n_frames of them).
@@ -128,6 +129,9 @@ constexpr size_t kCameraBasisBytes = 64;
 // Accessors the batch path needs from a scene (api.cu).
 pr::SceneView pr_internal_view(const pr_scene* s);
 bool pr_internal_built(const pr_scene* s);
+// The scene has an any-hit shader on a sphere-traced intersection shader (its
+// pixels need the kernels compiled with the any-hit march).
+bool pr_internal_ahs_march(const pr_scene* s);
 // Validate a description and give the device bytes pr_scene_create would
 // allocate for it (pr_scene_device_bytes of the new scene) and the bytes of its
 // inputs (the staging copy), without allocating.

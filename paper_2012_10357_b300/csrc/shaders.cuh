@@ -34,6 +34,7 @@ __device__ __forceinline__ float3 ldf3(const float* p) { return f3(p[0], p[1], p
 struct IsResult {
   float t;
   uint32_t attr;
+  float dist;   // sphere-traced hits: the estimate at t (below eps)
 };
 
 // Ray/box slab interval with precomputed 1/d and -o/d: per plane one FMA.
@@ -451,10 +452,12 @@ __device__ __forceinline__ float fractal_de(uint32_t id, const float4 p0, const 
 // max_steps estimates. The estimate is inlined into the loop (one branch on
 // the shader id per march, parameters kept in registers); the conversion is
 // rounded on its own so no multiply-add forms across the estimate's result.
+// A hit also returns the estimate there (IsResult::dist): an any-hit shader
+// that ignores it restarts the march past it (run_intersection).
 template <class DE>
 __device__ __forceinline__ IsResult march(DE de, float3 o, float3 d, float inv_len, float t_lo, float t_hi, float eps,
                                           uint32_t max_steps) {
-  IsResult r{0.f, 0u};
+  IsResult r{0.f, 0u, 0.f};
   float t = t_lo;
   for (uint32_t s = 0; s < max_steps; ++s) {
     if (t > t_hi) return r;
@@ -462,6 +465,7 @@ __device__ __forceinline__ IsResult march(DE de, float3 o, float3 d, float inv_l
     if (dist < eps) {
       r.t = t;
       r.attr = s + 1;   // >= 1 marks a hit
+      r.dist = dist;
       return r;
     }
     t += dist;
@@ -511,7 +515,7 @@ static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* 
           },
           o, d, inv_len, t_lo, t_hi, eps, max_steps);
     }
-    default: return IsResult{0.f, 0u};
+    default: return IsResult{0.f, 0u, 0.f};
   }
 }
 

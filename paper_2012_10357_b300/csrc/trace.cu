@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) k_camera_bases(const pr_camera* cams, uin
 #define PR_TRACE_MIN_BLOCKS_ANALYTIC 6
 #endif
 
-template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0>
+template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false>
 __global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC : PR_TRACE_MIN_BLOCKS)
     k_trace(Params P, unsigned long long* work) {
   static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC 
     const float eps = scene_eps(S, P.eps_rel);
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
-    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas>(
+    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs>(
         S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
     if (P.flags & PR_TRACE_OUTPUT_RGB) {
       float* o = reinterpret_cast<float*>(P.out) + 3 * pix;
@@ -145,21 +145,26 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
   P.aov = (L.flags & PR_TRACE_WRITE_AOV) ? L.aov : nullptr;
   P.counter = L.counter;
   dim3 grid((L.width + 15) / 16, (L.height + 7) / 8, L.n_frames);
+  // kernel variant: TLAS form x stats x any-hit march (analytic scenes never need the latter)
+  auto go = [&](auto kernel) { kernel<<<grid, 128, 0, s>>>(P, L.work); };
+  const bool st = L.work != nullptr;
   if (L.S.tlas8 && L.S.tlas8_format == kWide8Q) {
-    if (L.work) k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8Q><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8Q><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8Q, true>)
+                        : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8Q, true>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8Q>) : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8Q>);
   } else if (L.S.tlas8) {
-    if (L.work) k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8, true>)
+                        : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8, true>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, kWide8>) : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, kWide8>);
   } else if (L.S.tlas4) {
-    if (L.work) k_trace<true, PR_WARP_TILE_W_WIDE, false><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W_WIDE, false><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, 0, true>)
+                        : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, 0, true>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false>) : go(k_trace<false, PR_WARP_TILE_W_WIDE, false>);
   } else if (L.analytic_small) {
-    if (L.work) k_trace<true, PR_WARP_TILE_W, true><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W, true><<<grid, 128, 0, s>>>(P, nullptr);
+    st ? go(k_trace<true, PR_WARP_TILE_W, true>) : go(k_trace<false, PR_WARP_TILE_W, true>);
   } else {
-    if (L.work) k_trace<true, PR_WARP_TILE_W, false><<<grid, 128, 0, s>>>(P, L.work);
-    else k_trace<false, PR_WARP_TILE_W, false><<<grid, 128, 0, s>>>(P, nullptr);
+    if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, true>) : go(k_trace<false, PR_WARP_TILE_W, false, 0, true>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W, false>) : go(k_trace<false, PR_WARP_TILE_W, false>);
   }
   return launches + 1;
 }

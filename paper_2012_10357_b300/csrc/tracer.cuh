@@ -72,7 +72,7 @@ __device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3
 
 // Intersection shader dispatch on the hit group's shader id (kAnalytic: the
 // scene has no sphere-traced shader, so that code is not compiled in).
-template <bool kAnalytic>
+template <bool kAnalytic, bool kAhs = false>
 __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, const float4* prm, float3 o, float3 d,
                                                  float tmin, float t_lo, float t_hi, float eps, uint32_t max_steps,
                                                  IsResult& r, WorkCounters* wc) {
@@ -83,7 +83,25 @@ __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, c
     case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     default:
       if (!kAnalytic && is_sphere_traced(is_id)) {
-        r = sphere_trace(is_id, prm, o, d, rsqrtf(dot3(d, d)), t_lo, t_hi, eps, max_steps, wc);
+        const float inv_len = rsqrtf(dot3(d, d));
+        r = sphere_trace(is_id, prm, o, d, inv_len, t_lo, t_hi, eps, max_steps, wc);
+        if constexpr (kAhs) {
+          // Every march point below eps is a candidate for the any-hit shader; an
+          // ignored one lets the march go on by max(|estimate|, eps), through the
+          // solid and out of it, within the same step budget. (Compiled only into
+          // the kernels of scenes that need it: the extra call site costs the
+          // others 6-10 %.)
+          uint32_t used = 0;
+          while (ahs != PR_NONE && r.attr != 0u && !any_hit_accepts(ahs, o, r.t, d)) {
+            used += r.attr;
+            if (used >= max_steps) {
+              r.attr = 0u;
+              break;
+            }
+            r = sphere_trace(is_id, prm, o, d, inv_len, r.t + fmaxf(fabsf(r.dist), eps), t_hi, eps, max_steps - used, wc);
+          }
+          if (r.attr != 0u) r.attr += used;
+        }
         return r.attr != 0u;
       }
       return false;
@@ -100,7 +118,7 @@ __device__ __forceinline__ void to_object(float4 m0, float4 m1, float4 m2, float
 // BLAS traversal of instance k (object-space ray; t shared with world space
 // because the direction is not renormalised). Returns true if any-hit mode
 // found a hit.
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, bool kAhs = false>
 __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o, float3 d, uint32_t r, float tmin, float eps,
                               uint32_t max_steps, Hit& h, TravStack stack, int sp0, WorkCounters* wc_,
                               Deferred* defer = nullptr) {
@@ -131,7 +149,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
     }
     uint4 sr = __ldg(S.sbt + rec);
     const uint4 hg = __ldg(S.hit_groups + sr.x);
-    if (kDefer && is_fractal(hg.x) && defer->n < kMaxDeferred) {
+    if (kDefer && is_fractal(hg.x) && hg.z == PR_NONE && defer->n < kMaxDeferred) {   // any-hit candidates march here
       const int i = defer->n++;
       defer->inst[i] = k;
       defer->leaf[i] = leaf;
@@ -144,7 +162,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       return false;
     }
     IsResult res;
-    if (run_intersection<kAnalytic>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
+    if (run_intersection<kAnalytic, kAhs>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
         res.t >= tmin) {
       bool accept = res.t < h.t;
       if (!accept && res.t == h.t && h.inst >= 0)
@@ -234,7 +252,8 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
 // One TraceRay: TLAS traversal (near child first), instance transition, BLAS.
 // kTlas: 0 = the 4-wide TLAS when the scene has one, else the binary one;
 // kWide8 / kWide8Q = the scene's 8-wide TLAS (float / quantised nodes).
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0,
+          bool kAhs = false>
 __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax, float eps,
                           uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc_, Deferred* defer = nullptr) {
   WorkCounters* wc = kStats ? wc_ : nullptr;
@@ -336,7 +355,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (node >= 0) {
         node = visit8(node);
         if (node != kNone) continue;
-      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
+      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer, kAhs>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
         return;
       }
       if (sp == 0) return;
@@ -403,7 +422,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
         if (!__any_sync(__activemask(), leaf == kNone)) break;
       }
       if (leaf != kNone &&
-          traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
+          traverse_blas<kStats, kAnalytic, kDepth, kDefer, kAhs>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
         return;
     }
     return;
@@ -412,7 +431,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (node >= 0) {
         node = visit4(node);
         if (node != kNone) continue;
-      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
+      } else if (traverse_blas<kStats, kAnalytic, kDepth, kDefer, kAhs>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) {
         return;
       }
       if (sp == 0) return;
@@ -458,7 +477,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (!__any_sync(__activemask(), leaf == kDone)) break;
     }
     if (leaf != kDone &&
-        traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
+        traverse_blas<kStats, kAnalytic, kDepth, kDefer, kAhs>(any_hit, S, leaf & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer))
       return;
   }
 #else
@@ -480,7 +499,7 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
       if (hl) { node = lref; continue; }
       if (hr) { node = rref; continue; }
     } else {
-      if (traverse_blas<kStats, kAnalytic, kDepth, kDefer>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) return;
+      if (traverse_blas<kStats, kAnalytic, kDepth, kDefer, kAhs>(any_hit, S, node & 0x7FFFFFFF, o, d, r, tmin, eps, max_steps, h, stack, sp, wc, defer)) return;
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -488,12 +507,14 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
 #endif
 }
 
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0>
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0,
+          bool kAhs = false>
 __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3 d, uint32_t r, float tmin, float tmax,
                                             float eps, uint32_t max_steps, Hit& h, TravStack stack, WorkCounters* wc,
                                             Deferred* defer = nullptr) {
   const bool any_hit = (__ldg(S.ray_types + r).y & PR_RAY_TERMINATE_ON_FIRST_HIT) != 0;
-  trace_ray<kStats, kAnalytic, kDepth, kDefer, kTlas>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc, defer);
+  trace_ray<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack, wc,
+                                                            defer);
 }
 
 struct Surface {
@@ -625,12 +646,14 @@ struct PixelParams {
   uint32_t max_depth, max_steps;
 };
 
-template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, int kTlas = 0>
+// kAhs: the scene (or a batch request's scene) has an any-hit shader on a
+// sphere-traced intersection shader.
+template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, int kTlas = 0, bool kAhs = false>
 __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
                                                TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
   Hit h;
   rays += 1;
-  trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
+  trace_typed<kStats, kAnalytic, kDepth, false, kTlas, kAhs>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
   // AOV fields are stored as soon as they are known, so none of them stays
   // live across the shadow and mirror traces
   float3 color;
@@ -667,7 +690,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit sh;
         rays++;
         flags |= 2u;
-        trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth, false, kTlas, kAhs>(S, os, ls * (1.f / dist), 1, 0.f, dist, eps, P.max_steps, sh, stack, wc);
         vis = sh.inst >= 0 ? 0.f : 1.f;
         if (sh.inst < 0) flags |= 4u;
       }
@@ -680,7 +703,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         Hit rh;
         rays++;
         flags |= 8u;
-        trace_typed<kStats, kAnalytic, kDepth, false, kTlas>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
+        trace_typed<kStats, kAnalytic, kDepth, false, kTlas, kAhs>(S, orr, dr, 0, 0.f, INFINITY, eps, P.max_steps, rh, stack, wc);
         float3 lr;
         if (rh.inst >= 0) {
           flags |= 16u;

@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
 
 // The same with one CTA per 16x8 tile (no claiming loop: the hardware
 // schedules the tiles); CTAs past the batch's last tile return at once.
-template <int kWarpW>
+template <int kWarpW, bool kAhs = false>
 __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
   const uint32_t tile = blockIdx.x;
   if (tile >= B.hdr->total_tiles) return;
@@ -853,7 +853,8 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
     PR_DECLARE_STACK(128);
     const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
     const float eps = scene_eps(R.S, R.eps_rel);
-    const float3 color = render_pixel<false>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps, stack, nullptr, nullptr, rays);
+    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps,
+                                                                          stack, nullptr, nullptr, rays);
     const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
     if (R.out_rgb) {
       float* f = reinterpret_cast<float*>(R.out) + 3 * o;
@@ -873,8 +874,13 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
 
 }  // namespace
 
-int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s) {
+int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s,
+                     bool ahs_march) {
   int launches = 0;
+  if (ahs_march) {   // staged as one-CTA-per-tile megakernel work (16x8 tiles)
+    if (grid_tiles) k_batch_mega_tiles<8, true><<<grid_tiles, 128, 0, s>>>(B);
+    return grid_tiles ? 1 : 0;
+  }
   if (T.megakernel == 2) {
     if (grid_tiles) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
     return grid_tiles ? 1 : 0;

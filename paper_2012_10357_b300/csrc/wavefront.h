@@ -84,6 +84,10 @@ struct BatchTuning {
 };
 
 // grid_tiles: CTAs of the one-CTA-per-tile megakernel (at least the batch's tiles); unused otherwise
-int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s);
+// ahs_march: a request's scene has an any-hit shader on a sphere-traced shader;
+// the batch then runs the one-CTA-per-tile megakernel compiled with the
+// any-hit march (staged with 16x8 tiles), whatever T says.
+int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s,
+                     bool ahs_march = false);
 
 }  // namespace pr

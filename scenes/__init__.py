@@ -405,10 +405,13 @@ def mirror_pair(width: int = 33, height: int = 33) -> Workload:
     return Workload(b.build("mirror-pair"), cam, tp, "mirror_pair")
 
 
-def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = True) -> Workload:
-    """Sphere, box and pac-man whose hit groups carry the cutout any-hit shader
-    (bands removed along object y), over a ground slab; with shadow_cutout the
-    shadow hit groups carry it too, so shadows show the bands."""
+def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = True, kind: str = "analytic",
+                 max_steps: int = 256) -> Workload:
+    """Shapes whose hit groups carry the cutout any-hit shader (bands removed along
+    object y), over a ground slab; with shadow_cutout the shadow hit groups carry it
+    too, so shadows show the bands. kind: "analytic" (sphere, box, pac-man), "sdf"
+    (torus, rounded box, capsule, metaballs: sphere-traced exact SDFs) or "fractal"
+    (quaternion Julia, Mandelbulb)."""
     rng = np.random.default_rng(seed)
     b = SceneBuilder(sbt_stride_m=2)
     _standard_rays(b)
@@ -419,9 +422,18 @@ def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = Tru
     b.add_record(gr, mg, IS_BOX, 0)
     b.add_record(gs, mg, IS_BOX, 0)
     b.add_instance(bg, xform_trs((0, 0, 0)), 0)
-    shapes = [(IS_SPHERE, shape_sphere((0, 0, 0), 1.0), (0.9, 0.3, 0.2), (-2.2, 0.0, 0.5)),
-              (IS_BOX, shape_box((0, 0, 0), (0.8, 0.9, 0.7)), (0.3, 0.4, 0.9), (0.0, -0.2, 1.5)),
-              (IS_PACMAN, shape_pacman(1.0), (0.95, 0.85, 0.1), (2.2, 0.0, 0.5))]
+    if kind == "analytic":
+        shapes = [(IS_SPHERE, shape_sphere((0, 0, 0), 1.0), (0.9, 0.3, 0.2), (-2.2, 0.0, 0.5)),
+                  (IS_BOX, shape_box((0, 0, 0), (0.8, 0.9, 0.7)), (0.3, 0.4, 0.9), (0.0, -0.2, 1.5)),
+                  (IS_PACMAN, shape_pacman(1.0), (0.95, 0.85, 0.1), (2.2, 0.0, 0.5))]
+    elif kind == "sdf":
+        shapes = [(IS_TORUS, shape_torus(0.9, 0.35), (0.9, 0.3, 0.2), (-3.0, -0.3, 0.5)),
+                  (IS_ROUNDBOX, shape_roundbox(0.7, 0.15), (0.3, 0.4, 0.9), (-1.0, -0.4, 1.5)),
+                  (IS_CAPSULE, shape_capsule(0.6, 0.45), (0.95, 0.85, 0.1), (1.0, -0.3, 0.5)),
+                  (IS_METABALL4, shape_metaball4(rng), (0.3, 0.85, 0.4), (3.0, -0.3, 1.0))]
+    else:
+        shapes = [(IS_JULIA, shape_julia(JULIA_CUT_C), (0.75, 0.35, 0.85), (-1.6, 0.0, 0.8)),
+                  (IS_MANDELBULB, shape_mandelbulb(), (0.35, 0.65, 0.95), (1.6, -0.2, 0.8))]
     for is_id, (aabb, prm), alb, pos in shapes:
         hr = b.add_hit_group(is_id, CHS_LAMBERT, AHS_CUTOUT)
         hs = b.add_hit_group(is_id, NONE, AHS_CUTOUT if shadow_cutout else NONE)
@@ -431,9 +443,10 @@ def cutout_scene(seed: int = 0, width=256, height=192, shadow_cutout: bool = Tru
         b.add_record(hr, m, is_id, len(b.inst))
         b.add_record(hs, m, is_id, len(b.inst))
         b.add_instance(blas, xform_trs(pos, rot_y(rng.uniform(-40, 40))), off)
-    cam = Camera(_f32([0, 2.5, -6.5]), _f32([0, -0.2, 0.6]), _f32([0, 1, 0]), 60.0)
-    tp = TraceParams(width, height, max_depth=1, light_pos=_f32([-3, 7, -4]))
-    return Workload(b.build("cutout"), cam, tp, "cutout")
+    eye = [0, 2.5, -6.5] if kind == "analytic" else [0, 2.5, -7.5]
+    cam = Camera(_f32(eye), _f32([0, -0.2, 0.6]), _f32([0, 1, 0]), 60.0)
+    tp = TraceParams(width, height, max_depth=1, light_pos=_f32([-3, 7, -4]), max_steps=max_steps)
+    return Workload(b.build("cutout" if kind == "analytic" else f"cutout-{kind}"), cam, tp, "cutout")
 
 
 def shape_mandelbulb(power=8, iters=12, bailout=2.0):

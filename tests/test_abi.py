@@ -90,16 +90,18 @@ def test_validation_accepts_all_configs(pr):
         pr.validate(w.scene)
 
 
-def test_cutout_any_hit_needs_an_analytic_shader(pr):
+def test_cutout_any_hit_needs_an_intersection_shader(pr):
     w = scenes.small_analytic()
     w.scene.hit_groups[0, 2] = scenes.AHS_CUTOUT      # sphere intersection shader: allowed
     pr.validate(w.scene)
     f = scenes.field(n_inst=50, width=8, height=8)
     torus_hg = [h for h in range(len(f.scene.hit_groups)) if f.scene.hit_groups[h, 0] == scenes.IS_TORUS][0]
-    f.scene.hit_groups[torus_hg, 2] = scenes.AHS_CUTOUT
+    f.scene.hit_groups[torus_hg, 2] = scenes.AHS_CUTOUT   # sphere-traced shader: allowed too
+    pr.validate(f.scene)
+    f.scene.hit_groups[torus_hg, 0] = scenes.NONE         # no intersection shader to report candidates
     with pytest.raises(pr.PrError) as ei:
         pr.validate(f.scene)
-    assert "analytic" in str(ei.value)
+    assert "intersection shader" in str(ei.value)
 
 
 def test_triangle_validation(pr):

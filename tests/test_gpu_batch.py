@@ -82,6 +82,28 @@ def test_batch_launch_shapes_do_not_change_results(shape):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_batch_any_hit_on_sphere_traced_shapes(mode):
+    """Cutout any-hit shaders on sphere-traced SDF and fractal shapes (and analytic ones) in
+    every batched mode: the regrouped mode marches their candidates in place (an ignored
+    candidate continues the march), so every image equals its plain pr_trace image."""
+    ws = [scenes.cutout_scene(width=160, height=120, kind=k, shadow_cutout=sc)
+          for k, sc in (("sdf", True), ("fractal", True), ("analytic", False), ("fractal", False))]
+    objs = [pr.Scene(w.scene) for w in ws]
+    plain, _ = _plain(objs, ws)
+    batch = pr.Batch(len(ws), sum(w.params.width * w.params.height for w in ws))
+    batch.set_tuning(4, 16, 8, 32, mode)
+    outs = [torch.empty((w.params.height, w.params.width, 4), device="cuda") for w in ws]
+    batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)])
+    torch.cuda.synchronize()
+    for a, b in zip(plain, outs):
+        assert torch.equal(a, b)
+    for o in objs:
+        assert o.error_word() == 0
+        o.close()
+    batch.close()
+
+
 def test_autotune_picks_a_valid_shape_and_keeps_results():
     ws = _mixed_workloads()
     objs = [pr.Scene(w.scene) for w in ws]

@@ -437,19 +437,24 @@ def test_four_wide_tlas_full_size_sampled():
 # ---------------------------------------------------------------------------
 # Any-hit shaders (third hit-group slot)
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["analytic", "sdf", "fractal"])
 @pytest.mark.parametrize("shadow_cutout", [True, False])
-def test_cutout_any_hit_scene(shadow_cutout):
+def test_cutout_any_hit_scene(shadow_cutout, kind):
     """Band edges are discontinuities of the any-hit decision (FP32 vs FP64 may
     disagree on a pixel whose candidate sits on an edge): hits on primitives
-    with the any-hit shader take the 0.1 % budget, every other pixel is strict."""
-    w = scenes.cutout_scene(width=200, height=150, shadow_cutout=shadow_cutout)
+    with the any-hit shader take the 0.1 % budget, every other pixel is strict.
+    sdf / fractal: the sphere-traced shaders' candidates (march points below eps,
+    the march going on through the solid after an ignored one)."""
+    w = scenes.cutout_scene(width=200, height=150, shadow_cutout=shadow_cutout, kind=kind)
     rgb, a, diag, rays, err, _ = render_gpu(w)
     rep = compare(oracle.render(w), a, rgb, diag, scene=w.scene)
-    assert_parity(rep, f"cutout shadow_cutout={shadow_cutout}")
+    assert_parity(rep, f"cutout {kind} shadow_cutout={shadow_cutout}")
+    assert err == 0
 
 
-def test_cutout_changes_the_image():
-    w = scenes.cutout_scene(width=96, height=72)
+@pytest.mark.parametrize("kind", ["analytic", "sdf", "fractal"])
+def test_cutout_changes_the_image(kind):
+    w = scenes.cutout_scene(width=96, height=72, kind=kind)
     a = render_gpu(w)[0]
     w.scene.hit_groups[:, 2] = scenes.NONE
     b = render_gpu(w)[0]

@@ -98,6 +98,15 @@ CASES = [
     ("instance boxes: min and max swapped",
      [("lo = lo + std::min(a, b);\n        hi = hi + std::max(a, b);",
        "lo = lo + std::max(a, b);\n        hi = hi + std::min(a, b);")], pins.test_instance_boxes_f32_close_to_fp64_corners),
+    ("sphere-traced any-hit: an ignored candidate ends the march",
+     [("      t += std::max(std::fabs(dist), eps);\n      continue;", "      return false;")],
+     pins.test_sphere_traced_cutout_marches_through_the_solid),
+    ("sphere-traced any-hit: the march goes on by the signed estimate",
+     [("      t += std::max(std::fabs(dist), eps);\n      continue;", "      t += std::max(dist, eps);\n      continue;")],
+     pins.test_sphere_traced_cutout_marches_through_the_solid),
+    ("sphere-traced any-hit: the shader is not consulted",
+     [("    if (dist < eps && !any_hit_accepts(ahs, p)) {", "    if (false) {")],
+     pins.test_sphere_traced_cutout_on_level_rays),
     ("PLOC: area tie resolved to the odd lower index",
      [("(lo & 1) != (lob & 1) ? (lo & 1) == 0 : lo < lob", "(lo & 1) != (lob & 1) ? (lo & 1) == 1 : lo < lob")],
      ploc_pins.test_ploc_tie_goes_to_the_even_lower_pair),

@@ -149,6 +149,81 @@ def test_pacman_reductions(O):
     assert O.intersect(IS_PACMAN, prm, [-0.6, 0.0, -5], [0, 0, 1], 0.0) is not None
 
 
+def _band(y):
+    return 4 * y - math.floor(4 * y)
+
+
+def _sphere_roots(o, d, r):
+    b, c = np.dot(o, d), np.dot(o, o) - r * r
+    disc = b * b - c
+    return None if disc < 0 else (-b - math.sqrt(disc), -b + math.sqrt(disc))
+
+
+def test_sphere_traced_cutout_on_level_rays(O):
+    """A capsule of zero half-height is a ball. On a ray with d.y = 0 every candidate has
+    the same y: a kept band gives the ball's entry root (to the march tolerance), a
+    removed band ignores every candidate and the march goes through the ball: a miss."""
+    r = 0.45
+    prm = [0.0, r]
+    kept = removed = 0
+    for y0 in np.linspace(-0.4, 0.4, 33):
+        for x0 in (-0.2, 0.0, 0.15):
+            o, d = np.array([x0, y0, -3.0]), np.array([0.0, 0.0, 1.0])
+            roots = _sphere_roots(o, d, r)
+            if roots is None or abs(_band(y0) - 0.5) < 1e-6 or _band(y0) < 1e-6:
+                continue
+            res = O.intersect(IS_CAPSULE, prm, o, d, 0.0, 10.0, eps=1e-6, max_steps=512,
+                              ahs_id=scenes.AHS_CUTOUT)
+            if _band(y0) >= 0.5:
+                kept += 1
+                assert res is not None and res[0] == pytest.approx(roots[0], abs=1e-5)
+            else:
+                removed += 1
+                assert res is None
+    assert kept > 10 and removed > 10
+
+
+def test_sphere_traced_cutout_marches_through_the_solid(O):
+    """Rays that enter a ball (capsule of zero half-height) in a removed band and climb
+    into a kept band before leaving it: the march goes on through the solid and reports
+    the first kept point it visits, inside the ball or on its surface; rays that stay in
+    removed bands miss; without the shader the entry root."""
+    r = 0.45
+    prm = [0.0, r]
+    eps = 1e-6
+    hits = misses = 0
+    for slope, y0 in [(sl, y) for sl in (0.05, 0.3) for y in np.linspace(-1.4, 0.2, 161)]:
+        o, d = np.array([-3.0, y0, 0.05]), _unit([1.0, slope, 0.0])
+        roots = _sphere_roots(o, d, r)
+        if roots is None:
+            continue
+        ys = [(o + t * d)[1] for t in np.linspace(roots[0], roots[1], 4001)]
+        if min(min(abs(_band(y) - 0.5), _band(y), 1 - _band(y)) for y in (ys[0], ys[-1])) < 1e-4:
+            continue                                   # the chord starts or ends on a band edge: skip
+        n_entry = (o + roots[0] * d) / r
+        if abs(np.dot(n_entry, d)) < 0.2:
+            continue                                   # grazing entry: the march tolerance stretches along the ray
+        plain = O.intersect(IS_CAPSULE, prm, o, d, 0.0, 10.0, eps=eps, max_steps=2048)
+        assert plain is not None and plain[0] == pytest.approx(roots[0], abs=1e-4)
+        res = O.intersect(IS_CAPSULE, prm, o, d, 0.0, 10.0, eps=eps, max_steps=2048, ahs_id=scenes.AHS_CUTOUT)
+        first_kept = next((t for t, y in zip(np.linspace(roots[0], roots[1], 4001), ys) if _band(y) >= 0.5), None)
+        if first_kept is None:
+            misses += 1
+            assert res is None
+            continue
+        hits += 1
+        assert res is not None
+        p = o + res[0] * d
+        assert _band(p[1]) >= 0.5                       # the any-hit shader kept it
+        assert np.linalg.norm(p) <= r + 1e-5            # in or on the ball
+        assert roots[0] - 1e-5 <= res[0] <= roots[1] + 1e-5
+        if _band((o + roots[0] * d)[1]) >= 0.5:
+            assert res[0] == pytest.approx(roots[0], abs=1e-4)
+        else:
+            assert res[0] >= first_kept - 1e-3          # no kept point is reported before the chord reaches one
+    assert hits > 5 and misses > 5
+
+
 def test_cutout_any_hit_skips_banded_candidates(O):
     """Unit sphere, ray in the y-z plane: the front point lies in a removed band
     (frac(4y) < 1/2), the back point in a kept band, so the far root is reported;

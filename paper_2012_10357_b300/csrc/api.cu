@@ -6,6 +6,7 @@
 // All per-ray and per-node work runs in the kernels of bvh.cu and trace.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>

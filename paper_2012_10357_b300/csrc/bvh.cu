@@ -1007,6 +1007,16 @@ __global__ void __launch_bounds__(256) k_wide_fill8(const float4* nodes, uint32_
   o[5] = make_float4(__int_as_float(ref[4]), __int_as_float(ref[5]), __int_as_float(ref[6]), __int_as_float(ref[7]));
 }
 
+// Zero-fill by a kernel instead of cudaMemsetAsync: a memset may run on a copy
+// engine, where it queues behind a large device-to-host copy of another stream
+// (the pipelined readback of earlier images) and stalls the build.
+__global__ void __launch_bounds__(256) k_zero_u32(uint32_t* a, uint32_t* b, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    a[i] = 0u;
+    if (b) b[i] = 0u;
+  }
+}
+
 // Vertex bounds of each triangle (exact: min/max only).
 __global__ void __launch_bounds__(256) k_tri_boxes(const float* v, const uint32_t* idx, uint32_t n, float* boxes) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1039,13 +1049,20 @@ int launch_collapse4(const float4* nodes2, uint32_t n, uint32_t* parent, uint32_
   return 4;
 }
 
+namespace {
+void zero_u32(uint32_t* a, uint32_t* b, uint32_t n, cudaStream_t s) {
+  if (n == 0) return;
+  const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 1184u);
+  k_zero_u32<<<blocks, 256, 0, s>>>(a, b, n);
+}
+}  // namespace
+
 int launch_collapse_wide(const float4* nodes2, uint32_t n, int format, const WideScratch& ws, float4* out,
                          uint32_t* error_word, cudaStream_t s) {
   if (n < 2) return 0;
   const uint32_t nb = (n + 255) / 256;
   const int W = format == kWide4 ? 4 : 8;
-  cudaMemsetAsync(ws.is_root, 0, sizeof(uint32_t) * (n - 1), s);
-  cudaMemsetAsync(ws.rank, 0, sizeof(uint32_t) * (n - 1), s);
+  zero_u32(ws.is_root, ws.rank, n - 1, s);
   const uint32_t dfs_blocks = (kWideFrontier + 127) / 128;
   if (W == 4) {
     k_wide_top<4><<<1, kWideTopThreads, 0, s>>>(nodes2, ws.slots, ws.is_root, ws.rank, ws.frontier, ws.n_frontier);
@@ -1060,7 +1077,7 @@ int launch_collapse_wide(const float4* nodes2, uint32_t n, int format, const Wid
   if (format == kWide4) k_wide_fill4<<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
   else if (format == kWide8) k_wide_fill8<false><<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
   else k_wide_fill8<true><<<nb, 256, 0, s>>>(nodes2, n, ws.slots, ws.is_root, ws.rank, out);
-  return 6;
+  return 5;
 }
 
 int launch_build_small(const LevelDesc* d_jobs, uint32_t n_jobs, cudaStream_t s) {
@@ -1095,10 +1112,10 @@ int launch_build_large(const LevelDesc& J, const BuildScratch& sc, cudaStream_t 
     cur = 1 - cur;
     launches += 3;
   }
-  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * (n - 1), s);
+  zero_u32(sc.counters, nullptr, n - 1, s);
   k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf, nullptr);
   k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters, nullptr);
-  launches += 2;
+  launches += 3;
   return launches;
 }
 
@@ -1155,7 +1172,8 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
   A.hdr = sc.hist;
   A.error_word = error_word;
   A.part = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sc.hist) + kPlocPartOffset);
-  cudaMemsetAsync(sc.hist, 0, kPlocPartOffset, s);
+  zero_u32(sc.hist, nullptr, (uint32_t)(kPlocPartOffset / sizeof(uint32_t)), s);
+  ++launches;
   void* args[] = {&A};
   if (after && cudaStreamWaitEvent(s, after, 0) != cudaSuccess) return -1;
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ploc, dim3(grid), dim3(kPlocThreads), args, 0, s);
@@ -1165,10 +1183,10 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
   // the LBVH's tree passes, which return at once unless a barrier of the
   // clustering gave up
   const uint32_t* done = sc.hist + kHdrOk;
-  cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t) * (n - 1), s);
+  zero_u32(sc.counters, nullptr, n - 1, s);
   k_karras<<<nb, 256, 0, s>>>(J, sc.keys[cur], sc.vals[cur], sc.parent_int, sc.parent_leaf, done);
   k_refit<<<nb, 256, 0, s>>>(J, sc.vals[cur], sc.parent_int, sc.parent_leaf, sc.counters, done);
-  return launches + 2;
+  return launches + 3;
 }
 
 int launch_instances(const InstanceArgs& A, cudaStream_t s) {

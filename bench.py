@@ -483,7 +483,7 @@ class BatchBench:
                 json.dump(cache, f, indent=1)
         self.prepared = self.batch.prepare(items)
         # kernels of the batched launch per tuning mode: four stages, or one megakernel
-        self.trace_launches = {0: 4, 1: 1, 2: 1, 3: 8}[self.tuned["tuning"]["megakernel"]]
+        self.trace_launches = {0: 4, 1: 1, 2: 1, 3: 8, 4: 1}[self.tuned["tuning"]["megakernel"]]
 
     def build_all(self):
         # the 64 scenes' builds run concurrently (pr_build_bvh_many: internal streams
@@ -556,7 +556,8 @@ def bench_batch(pr, work, torch, stream, flush, steps: int, warmup: int, world: 
     torch.cuda.synchronize()
     kernel = {0: "k_wf_primary/shadow/mirror/resolve (wavefront stages)", 1: "k_batch_mega (persistent)",
               2: "k_batch_mega_tiles (one CTA per tile)",
-              3: "k_rg_* (regrouped stages with march jobs)"}[B.tuned["tuning"]["megakernel"]]
+              3: "k_rg_* (regrouped stages with march jobs)",
+              4: "k_batch_mega_tiles (one one-warp CTA per quarter tile)"}[B.tuned["tuning"]["megakernel"]]
     roof = roofline(work, torch, counters, statistics.mean(trace_ms) / 1e3, kernel, BATCH, clocks, probe)
     roof["trace_share_of_step"] = sum(trace_ms) / sum(step_ms)
     res = {"value": rays_all / (total_ms / 1e3) / 1e6, "total_ms": total_ms, "rays": rays,

@@ -57,7 +57,9 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool tuning_ok(const BatchTuning& t) {
   bool tile = (t.tile_w == 16 && t.tile_h == 8) || (t.tile_w == 32 && t.tile_h == 4) || (t.tile_w == 8 && t.tile_h == 16);
-  if (t.megakernel > 3 || ((t.megakernel == 1 || t.megakernel == 2) && !(t.tile_w == 16 && t.tile_h == 8))) return false;
+  if (t.megakernel > 4 ||
+      ((t.megakernel == 1 || t.megakernel == 2 || t.megakernel == 4) && !(t.tile_w == 16 && t.tile_h == 8)))
+    return false;
   return tile && t.ctas_per_sm >= 1 && t.ctas_per_sm <= 16 && t.queue_chunk >= 32 && t.queue_chunk <= 1024 &&
          t.queue_chunk % 32 == 0;
 }
@@ -283,7 +285,8 @@ pr_status pr_trace_batch_graph(pr_batch* b, uint32_t n, const pr_request* reqs, 
   if (s != PR_OK) return s;
   // the one-CTA-per-tile megakernel needs a grid of at least this batch's tiles: capture again
   // (with room to grow) when it is larger than the captured one
-  const bool grow = b->staged_tuning.megakernel == 2 && b->staged_tiles > b->graph_tiles;
+  const bool grow = (b->staged_tuning.megakernel == 2 || b->staged_tuning.megakernel == 4) &&
+                    b->staged_tiles > b->graph_tiles;
   if (grow) {
     uint32_t g = 1024;
     while (g < b->staged_tiles && g < 0x80000000u) g <<= 1;
@@ -321,6 +324,7 @@ pr_status pr_batch_autotune(pr_batch* b, uint32_t n, const pr_request* reqs, voi
   cands.push_back(BatchTuning{4, 16, 8, 32, 1u});
   cands.push_back(BatchTuning{8, 16, 8, 32, 1u});
   cands.push_back(BatchTuning{4, 16, 8, 32, 2u});
+  cands.push_back(BatchTuning{4, 16, 8, 32, 4u});
   // the regrouped stages (fractal marches from a job queue)
   if (b->max_px < (1ull << 31))
     for (uint32_t c : {4u, 8u})

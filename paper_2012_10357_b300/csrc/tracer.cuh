@@ -367,22 +367,28 @@ __device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 
     // children ordered near to far by a 5-exchange sorting network; the
     // nearest is visited next, the others pushed farthest first.
     constexpr int kNone = 0x7FFFFFFF;   // no node (never a node index: those are < 2^30)
+    // Entry and exit planes per axis by the sign of d (rows lo.x, lo.y, lo.z,
+    // hi.x, hi.y, hi.z of a node): an FMA is monotone in the plane, so the
+    // plane picked by the sign gives exactly min / max of the two slab
+    // distances (empty slots are masked by their ref) and the node's rows are
+    // read in that order, with no min / max per axis.
+    const int rnx = inv.x >= 0.f ? 0 : 3, rny = inv.y >= 0.f ? 1 : 4, rnz = inv.z >= 0.f ? 2 : 5;
     auto visit4 = [&](int node) -> int {
       if (wc) ++wc->tlas_nodes4;
       const float4* nd = S.tlas4 + 8 * (size_t)node;
-      const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
-      const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
-      const float clo[3][4] = {{lx.x, lx.y, lx.z, lx.w}, {ly.x, ly.y, ly.z, ly.w}, {lz.x, lz.y, lz.z, lz.w}};
-      const float chi[3][4] = {{hx.x, hx.y, hx.z, hx.w}, {hy.x, hy.y, hy.z, hy.w}, {hz.x, hz.y, hz.z, hz.w}};
+      const float4 nx = __ldg(nd + rnx), ny = __ldg(nd + rny), nz = __ldg(nd + rnz);
+      const float4 fx = __ldg(nd + (3 - rnx)), fy = __ldg(nd + (5 - rny)), fz = __ldg(nd + (7 - rnz)),
+                   rf = __ldg(nd + 6);
+      const float cn[3][4] = {{nx.x, nx.y, nx.z, nx.w}, {ny.x, ny.y, ny.z, ny.w}, {nz.x, nz.y, nz.z, nz.w}};
+      const float cf[3][4] = {{fx.x, fx.y, fx.z, fx.w}, {fy.x, fy.y, fy.z, fy.w}, {fz.x, fz.y, fz.z, fz.w}};
       int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
       float key[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        float ax = fmaf(clo[0][k], inv.x, o_inv.x), bx = fmaf(chi[0][k], inv.x, o_inv.x);
-        float ay = fmaf(clo[1][k], inv.y, o_inv.y), by = fmaf(chi[1][k], inv.y, o_inv.y);
-        float az = fmaf(clo[2][k], inv.z, o_inv.z), bz = fmaf(chi[2][k], inv.z, o_inv.z);
-        float t0 = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), tmin));
-        float t1 = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), h.t));
+        const float t0 = fmax3(fmaf(cn[0][k], inv.x, o_inv.x), fmaf(cn[1][k], inv.y, o_inv.y),
+                               fmaxf(fmaf(cn[2][k], inv.z, o_inv.z), tmin));
+        const float t1 = fmin3(fmaf(cf[0][k], inv.x, o_inv.x), fmaf(cf[1][k], inv.y, o_inv.y),
+                               fminf(fmaf(cf[2][k], inv.z, o_inv.z), h.t));
         key[k] = (ref[k] != kEmptySlot && t0 <= t1) ? t0 : INFINITY;
       }
       auto cswap = [&](int a, int b) {

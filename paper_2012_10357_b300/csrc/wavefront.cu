@@ -825,14 +825,19 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
 
 // The same with one CTA per 16x8 tile (no claiming loop: the hardware
 // schedules the tiles); CTAs past the batch's last tile return at once.
-template <int kWarpW, bool kAhs = false>
-__global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
-  const uint32_t tile = blockIdx.x;
+// kWarps = 1: one warp per CTA and four CTAs per tile (one per 8x4 quarter),
+// so a warp that finishes early frees its slot for the next CTA instead of
+// holding it until the tile's slowest warp ends.
+template <int kWarpW, bool kAhs = false, int kWarps = 4>
+__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(BatchView B) {
+  static_assert(kWarps == 4 || kWarps == 1, "four warps per tile, or one per quarter");
+  constexpr int kParts = 4 / kWarps;
+  const uint32_t tile = blockIdx.x / kParts;
   if (tile >= B.hdr->total_tiles) return;
   __shared__ ReqDev sreq;
   __shared__ CameraBasis scam;
   __shared__ uint32_t s_req;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = (int)(threadIdx.x >> 5) + (int)(blockIdx.x % kParts) * kWarps, lane = threadIdx.x & 31;
   constexpr int kWarpsX = 16 / kWarpW;
   if (threadIdx.x == 0) s_req = find_request(B.reqs, B.hdr->n_req, tile);
   __syncthreads();
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
   const int y = (int)R.row_begin + (int)(lt / R.tiles_x) * 8 + (warp / kWarpsX) * (32 / kWarpW) + lane / kWarpW;
   uint32_t rays = 0;
   if (x < (int)R.width && y < (int)(R.row_begin + R.rows)) {
-    PR_DECLARE_STACK(128);
+    PR_DECLARE_STACK(32 * kWarps);
     const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
     const float eps = scene_eps(R.S, R.eps_rel);
     const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps,
@@ -869,7 +874,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega_tiles(BatchView B) {
     const uint32_t total = __reduce_add_sync(kFull, rays);
     if (lane == 0 && total) atomicAdd(B.hdr->counter, (unsigned long long)total);
   }
-  tile_finished(B, s_req, R.n_tiles);
+  tile_finished(B, s_req, R.n_tiles * kParts);
 }
 
 }  // namespace
@@ -883,6 +888,10 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
   }
   if (T.megakernel == 2) {
     if (grid_tiles) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
+    return grid_tiles ? 1 : 0;
+  }
+  if (T.megakernel == 4) {
+    if (grid_tiles) k_batch_mega_tiles<8, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
     return grid_tiles ? 1 : 0;
   }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr

@@ -79,11 +79,12 @@ struct BatchView {
 struct BatchTuning {
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
   // 1: one persistent megakernel (16x8 tiles), 2: one CTA per 16x8 tile, 0: four
-  // stages, 3: regrouped stages (fractal marches deferred into a job queue)
+  // stages, 3: regrouped stages (fractal marches deferred into a job queue),
+  // 4: one one-warp CTA per 8x4 quarter of each 16x8 tile
   uint32_t megakernel;
 };
 
-// grid_tiles: CTAs of the one-CTA-per-tile megakernel (at least the batch's tiles); unused otherwise
+// grid_tiles: tiles the one-CTA-per-tile megakernels launch for (at least the batch's tiles); unused otherwise
 // ahs_march: a request's scene has an any-hit shader on a sphere-traced shader;
 // the batch then runs the one-CTA-per-tile megakernel compiled with the
 // any-hit march (staged with 16x8 tiles), whatever T says.

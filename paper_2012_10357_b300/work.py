@@ -19,8 +19,10 @@ Per-unit counts (trace.cu / tracer.cuh / shaders.cuh):
               average generation of a primary / shadow / mirror ray
               (normalisations, light direction, offsets)
   BVH2 node   two slab tests: 12 FFMA; 20 min/max + 3 compares
-  4-wide node four slab tests: 24 FFMA; 40 min/max + 12 compares/selects +
-              5-exchange sort (15)
+  4-wide node four slab tests: 24 FFMA; 16 min/max (entry and exit planes
+              picked by the sign of d, so only the three-plane max / min
+              and the clip to [tmin, t]) + 12 compares/selects + 5-exchange
+              sort (15)
   8-wide node float nodes: eight slab tests, 48 FFMA; 80 min/max + 24
               compares/selects + 19-exchange sort (57). Quantised nodes:
               per node 3 FMUL + 3 FFMA (step / d, (origin - o) / d) and 12
@@ -52,7 +54,7 @@ from __future__ import annotations
 UNITS = {
     "rays": (34, 6, 4),
     "tlas_nodes": (24, 23, 0),
-    "tlas_nodes4": (48, 67, 0),
+    "tlas_nodes4": (48, 43, 0),
     "tlas_nodes8": (96, 161, 0),
     "tlas_nodes8q": (153, 173, 0),
     "blas_nodes": (24, 23, 0),

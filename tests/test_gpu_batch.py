@@ -65,7 +65,7 @@ def test_batch_bit_identical_to_plain(graph):
 
 @pytest.mark.parametrize("shape", [(2, 16, 8, 32, 0), (8, 32, 4, 128, 0), (16, 8, 16, 64, 0), (1, 16, 8, 1024, 0),
                                    (4, 16, 8, 32, 1), (1, 16, 8, 32, 1), (4, 16, 8, 32, 2),
-                                   (4, 16, 8, 32, 3), (8, 32, 4, 128, 3), (1, 8, 16, 64, 3)])
+                                   (4, 16, 8, 32, 3), (8, 32, 4, 128, 3), (1, 8, 16, 64, 3), (4, 16, 8, 32, 4)])
 def test_batch_launch_shapes_do_not_change_results(shape):
     """Wavefront stages or the batched megakernel, any launch shape: every
     request equals its plain pr_trace image bit for bit."""
@@ -82,7 +82,7 @@ def test_batch_launch_shapes_do_not_change_results(shape):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_batch_any_hit_on_sphere_traced_shapes(mode):
     """Cutout any-hit shaders on sphere-traced SDF and fractal shapes (and analytic ones) in
     every batched mode: the regrouped mode marches their candidates in place (an ignored
@@ -207,12 +207,15 @@ def test_batch_rgb_outputs_equal_plain():
 
 def test_batch_megakernel_needs_16x8_tiles():
     batch = pr.Batch(2, 1024)
+    for mode in (1, 2, 4):
+        with pytest.raises(pr.PrError):
+            batch.set_tuning(4, 32, 4, 32, mode)
     with pytest.raises(pr.PrError):
-        batch.set_tuning(4, 32, 4, 32, 1)
+        batch.set_tuning(4, 16, 8, 32, 5)
     batch.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_batched_megakernel_rays_and_graph(mode):
     """The batched megakernel (persistent, or one CTA per tile) and the
     regrouped stages count the same rays as the plain launches and run the
@@ -236,14 +239,16 @@ def test_batched_megakernel_rays_and_graph(mode):
         o.close()
 
 
-def test_tile_megakernel_graph_grows_with_the_batch():
-    """One CTA per tile: the captured graph's grid grows (recapture) when a
-    later batch has more tiles, and a smaller batch reuses the larger grid."""
+@pytest.mark.parametrize("mode", [2, 4])
+def test_tile_megakernel_graph_grows_with_the_batch(mode):
+    """One CTA per tile (or per quarter tile): the captured graph's grid grows
+    (recapture) when a later batch has more tiles, and a smaller batch reuses
+    the larger grid."""
     small = scenes.small_analytic(width=40, height=24)
     big = scenes.teaser(width=400, height=300)
     a, b_ = pr.Scene(small.scene), pr.Scene(big.scene)
     batch = pr.Batch(2, 400 * 300 + 40 * 24)
-    batch.set_tuning(4, 16, 8, 32, 2)
+    batch.set_tuning(4, 16, 8, 32, mode)
     for w, sc in ((small, a), (big, b_), (small, a)):
         out = torch.empty((w.params.height, w.params.width, 4), device="cuda")
         batch.trace([(sc, w.camera, w.params, out)], graph=True)

@@ -63,7 +63,8 @@ def test_row_range_batches_reassemble_the_image(megakernel):
 
 
 @pytest.mark.parametrize("mode,max_batch,mega", [(pr.PR_SERVE_CONTINUOUS, 20000, 0), (pr.PR_SERVE_CONTINUOUS, 1 << 22, 0),
-                                                 (pr.PR_SERVE_PLAIN, 1 << 22, 0), (pr.PR_SERVE_CONTINUOUS, 20000, 1)])
+                                                 (pr.PR_SERVE_PLAIN, 1 << 22, 0), (pr.PR_SERVE_CONTINUOUS, 20000, 1),
+                                                 (pr.PR_SERVE_CONTINUOUS, 20000, 4)])
 def test_served_equals_alone(mode, max_batch, mega):
     reqs = _requests()
     alone = _alone(reqs)

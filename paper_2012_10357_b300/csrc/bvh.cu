@@ -405,20 +405,16 @@ __global__ void __launch_bounds__(256) k_refit(LevelDesc J, const uint32_t* vals
 // the LBVH's, so the 4-wide collapse and the traversal take the tree as is.
 constexpr int kPlocRadius = 16;
 constexpr int kPlocThreads = 256;
-constexpr uint32_t kPlocTail = 1024;   // rounds with at most this many clusters run in block 0 alone
+// Rounds with at most this many clusters run in block 0 alone, with the list
+// in shared memory (two lists of 32-byte records and the neighbours).
+constexpr uint32_t kPlocTail = 2048;
+constexpr size_t kPlocSmem = 2 * kPlocTail * 32 + kPlocTail * 4;
+// A cluster is a 32-byte record: (lo.xyz, reference bits), (hi.xyz, 0).
 // header words (in the radix histogram's buffer, free once the sort is done)
 constexpr int kHdrOk = 0, kHdrAbort = 1, kHdrCount = 2, kHdrGen = 3;
 constexpr size_t kPlocPartOffset = 256;              // bytes: per-block counts follow the header
 constexpr unsigned long long kPlocWaitNs = 2000000000ull;
 constexpr uint32_t kPlocMaxSpins = 1u << 25;
-
-__device__ __forceinline__ float half_area(const float* a, const float* b) {
-  const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
-  const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
-  const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
-  const float s = fmaf(dx, dy, fmaf(dy, dz, dz * dx));
-  return s == s ? s : INFINITY;   // NaN (a non-finite box) orders last
-}
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
@@ -495,19 +491,87 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return before + x - v;
 }
 
-// keep: cluster i survives the round (alone or as the merged node of its
-// mutual pair); merge: i is the lower index of a mutual pair
-__device__ __forceinline__ unsigned long long keep_merge(const int* nn, uint32_t i, int& j) {
-  j = __ldcg(nn + i);
-  const bool mutual = __ldcg(nn + j) == (int)i;
+__device__ __forceinline__ float rec_half_area(const float4& al, const float4& ah, const float4& bl,
+                                                const float4& bh) {
+  const float dx = fmaxf(ah.x, bh.x) - fminf(al.x, bl.x);
+  const float dy = fmaxf(ah.y, bh.y) - fminf(al.y, bl.y);
+  const float dz = fmaxf(ah.z, bh.z) - fminf(al.z, bl.z);
+  const float s = fmaf(dx, dy, fmaf(dy, dz, dz * dx));
+  return s == s ? s : INFINITY;   // NaN (a non-finite box) orders last
+}
+
+// Nearest neighbour of cluster i among the clusters within kPlocRadius of it
+// (list of m); rec(j, lo, hi) reads cluster j's record.
+template <class Rec>
+__device__ __forceinline__ int ploc_nearest(uint32_t i, uint32_t m, Rec rec) {
+  float4 il, ih;
+  rec(i, il, ih);
+  const uint32_t lo = i > (uint32_t)kPlocRadius ? i - kPlocRadius : 0u;
+  const uint32_t hi = min(m - 1, i + (uint32_t)kPlocRadius);
+  float best = INFINITY;
+  int bj = -1;
+  for (uint32_t j = lo; j <= hi; ++j) {
+    if (j == i) continue;
+    float4 jl, jh;
+    rec(j, jl, jh);
+    const float a = rec_half_area(il, ih, jl, jh);
+    bool take = bj < 0 || a < best;
+    if (!take && a == best) {
+      const uint32_t d = j > i ? j - i : i - j, db = (uint32_t)bj > i ? (uint32_t)bj - i : i - (uint32_t)bj;
+      const uint32_t l = min(i, j), lb = min(i, (uint32_t)bj);
+      take = d != db ? d < db : ((l ^ lb) & 1u) ? (l & 1u) == 0u : l < lb;
+    }
+    if (take) {
+      best = a;
+      bj = (int)j;
+    }
+  }
+  return bj;
+}
+
+// The merged node of clusters i < j (left i, right j) and the record of the new cluster.
+__device__ __forceinline__ void ploc_merge(float4* nodes, uint32_t node, const float4& il, const float4& ih,
+                                           const float4& jl, const float4& jh, float4& ol, float4& oh) {
+  float4* nd = nodes + 4 * (size_t)node;   // the BVH2 node layout: both child boxes, then the refs
+  nd[0] = make_float4(il.x, il.y, il.z, ih.x);
+  nd[1] = make_float4(ih.y, ih.z, jl.x, jl.y);
+  nd[2] = make_float4(jl.z, jh.x, jh.y, jh.z);
+  nd[3] = make_float4(il.w, jl.w, 0.f, 0.f);
+  ol = make_float4(fminf(il.x, jl.x), fminf(il.y, jl.y), fminf(il.z, jl.z), __int_as_float((int)node));
+  oh = make_float4(fmaxf(ih.x, jh.x), fmaxf(ih.y, jh.y), fmaxf(ih.z, jh.z), 0.f);
+}
+
+// Flags of cluster i with neighbour j, back = nn[j]: keep (i survives the round,
+// alone or as the merged node of its mutual pair), merge (i is the lower index
+// of a mutual pair); packed as keep + (merge << 32).
+__device__ __forceinline__ unsigned long long keep_merge(uint32_t i, int j, int back) {
+  const bool mutual = back == (int)i;
   const bool keep = !(mutual && (uint32_t)j < i);
   const bool merge = mutual && i < (uint32_t)j;
   return (keep ? 1ull : 0ull) + (merge ? (1ull << 32) : 0ull);
 }
 
+// Neighbours and flags of clusters base .. base + 3 (those below end), all
+// loads issued before any is used.
+struct Flags4 {
+  int j[4];
+  unsigned long long f[4];
+};
+__device__ __forceinline__ Flags4 flags4(const int* nn, uint32_t base, uint32_t end) {
+  Flags4 q;
+  int back[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q.j[k] = base + k < end ? __ldcg(nn + base + k) : -1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) back[k] = q.j[k] >= 0 ? __ldcg(nn + q.j[k]) : -1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q.f[k] = base + k < end ? keep_merge(base + k, q.j[k], back[k]) : 0ull;
+  return q;
+}
+
 __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
+  extern __shared__ float4 smem[];   // kPlocSmem bytes
   __shared__ unsigned long long sh[kPlocThreads / 32];
-  __shared__ float sbox[(kPlocThreads + 2 * kPlocRadius) * 6];   // a tile of clusters and its halo
   __shared__ uint32_t ok_sh;
   uint32_t* hdr = A.hdr;
   const uint32_t n = A.J.n;
@@ -516,71 +580,59 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
     const uint32_t leaf = A.vals[i];
     A.J.perm[i] = leaf;
     A.J.codes[i] = A.codes[i];
-    A.C[0][i] = (int)(kLeafBit | (A.J.leaf_ref_base + leaf));
     const float* b = leaf_box(A.J, leaf);
-    for (int k = 0; k < 6; ++k) A.CB[0][6 * (size_t)i + k] = b[k];
+    A.R[0][2 * (size_t)i] = make_float4(b[0], b[1], b[2], __int_as_float((int)(kLeafBit | (A.J.leaf_ref_base + leaf))));
+    A.R[0][2 * (size_t)i + 1] = make_float4(b[3], b[4], b[5], 0.f);
   }
   if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
   uint32_t m = n, next = n - 2;
   int cur = 0;
-  while (m > 1) {
-    // Once few clusters are left, block 0 finishes alone: its barriers are
-    // __syncthreads, far cheaper than grid-wide ones.
-    const bool tail = m <= kPlocTail;
-    if (tail && blockIdx.x != 0) return;
-    const uint32_t nb = tail ? 1u : gridDim.x, bid = tail ? 0u : blockIdx.x;
-    const int* C = A.C[cur];
-    const float* CB = A.CB[cur];
-    // 1. nearest neighbour in the window, tiles of clusters staged in shared memory
+  const uint32_t nb = gridDim.x, bid = blockIdx.x;
+  // ---- rounds over the whole grid, list in global memory
+  while (m > kPlocTail) {
+    const float4* R = cur ? A.R[1] : A.R[0];
+    // 1. nearest neighbours, tiles of kPlocThreads clusters staged with their halo in shared memory
     const uint32_t ntiles = (m + kPlocThreads - 1) / kPlocThreads;
+    constexpr int kStage = 2 * (kPlocThreads + 2 * kPlocRadius);   // float4 of a tile and its halo
+    constexpr int kStagePer = (kStage + kPlocThreads - 1) / kPlocThreads;
     for (uint32_t t = bid; t < ntiles; t += nb) {
-      const long long g0 = 6ll * ((long long)t * kPlocThreads - kPlocRadius);
-      for (uint32_t k = threadIdx.x; k < (kPlocThreads + 2 * kPlocRadius) * 6; k += blockDim.x) {
+      const long long g0 = 2ll * ((long long)t * kPlocThreads - kPlocRadius);
+      float4 v[kStagePer];
+#pragma unroll
+      for (int q = 0; q < kStagePer; ++q) {   // all loads first, then the stores
+        const int k = threadIdx.x + q * kPlocThreads;
         const long long g = g0 + k;
-        sbox[k] = (g >= 0 && g < 6ll * m) ? __ldcg(CB + g) : 0.f;
+        v[q] = (k < kStage && g >= 0 && g < 2ll * m) ? __ldcg(R + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < kStagePer; ++q) {
+        const int k = threadIdx.x + q * kPlocThreads;
+        if (k < kStage) smem[k] = v[q];
       }
       __syncthreads();
       const uint32_t i = t * kPlocThreads + threadIdx.x;
       if (i < m) {
-        const uint32_t base = t * kPlocThreads;   // sbox row of cluster c: c - base + kPlocRadius
-        const float* bi = sbox + 6 * (threadIdx.x + kPlocRadius);
-        const uint32_t lo = i > (uint32_t)kPlocRadius ? i - kPlocRadius : 0u;
-        const uint32_t hi = min(m - 1, i + (uint32_t)kPlocRadius);
-        float best = INFINITY;
-        int bj = -1;
-        for (uint32_t j = lo; j <= hi; ++j) {
-          if (j == i) continue;
-          const float a = half_area(bi, sbox + 6 * (j + kPlocRadius - base));
-          bool take = bj < 0 || a < best;
-          if (!take && a == best) {
-            const uint32_t d = j > i ? j - i : i - j, db = (uint32_t)bj > i ? (uint32_t)bj - i : i - (uint32_t)bj;
-            const uint32_t l = min(i, j), lb = min(i, (uint32_t)bj);
-            take = d != db ? d < db : ((l ^ lb) & 1u) ? (l & 1u) == 0u : l < lb;
-          }
-          if (take) {
-            best = a;
-            bj = (int)j;
-          }
-        }
-        A.nn[i] = bj;
+        const uint32_t row0 = t * kPlocThreads - kPlocRadius;   // cluster of staged record 0 (wraps below 0)
+        A.nn[i] = ploc_nearest(i, m, [&](uint32_t j, float4& lo, float4& hi) {
+          lo = smem[2 * (j - row0)];
+          hi = smem[2 * (j - row0) + 1];
+        });
       }
       __syncthreads();
     }
-    if (tail) __syncthreads();
-    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
-    // 2. survivors and merges of each block's chunk
-    const uint32_t chunk = (m + nb - 1) / nb;
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    // 2. survivors and merges of each block's chunk; a thread takes 4 consecutive clusters
+    const uint32_t chunk = ((m + nb - 1) / nb + 3u) & ~3u;
     const uint32_t c0 = min(m, bid * chunk), c1 = min(m, c0 + chunk);
     unsigned long long cnt = 0;
-    for (uint32_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-      int j;
-      cnt += keep_merge(A.nn, i, j);
+    for (uint32_t g0 = c0; g0 < c1; g0 += 4 * kPlocThreads) {
+      const Flags4 q = flags4(A.nn, g0 + 4 * threadIdx.x, c1);
+      cnt += q.f[0] + q.f[1] + q.f[2] + q.f[3];
     }
     unsigned long long tot;
     block_excl_scan(cnt, sh, tot);
     if (threadIdx.x == 0) A.part[bid] = tot;
-    if (tail) __syncthreads();
-    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
     // 3. this block's exclusive prefix of the block counts and the round's totals
     unsigned long long pre_part = 0, all_part = 0;
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -591,37 +643,27 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
     unsigned long long pre, all;
     block_excl_scan(pre_part, sh, pre);
     block_excl_scan(all_part, sh, all);
-    // 4. merged nodes and the compacted cluster list, in order
-    int* Cn = A.C[cur ^ 1];
-    float* CBn = A.CB[cur ^ 1];
+    // 4. merged nodes and the compacted list, in order
+    float4* Rn = cur ? A.R[0] : A.R[1];
     unsigned long long run = pre;
-    for (uint32_t r0 = c0; r0 < c1; r0 += blockDim.x) {
-      const uint32_t i = r0 + threadIdx.x;
-      int j = -1;
-      const unsigned long long v = i < c1 ? keep_merge(A.nn, i, j) : 0ull;
+    for (uint32_t g0 = c0; g0 < c1; g0 += 4 * kPlocThreads) {
+      const uint32_t base = g0 + 4 * threadIdx.x;
+      const Flags4 q = flags4(A.nn, base, c1);
       unsigned long long t;
-      const unsigned long long e = run + block_excl_scan(v, sh, t);
-      if (v & 0xFFFFFFFFull) {
-        const uint32_t pos = (uint32_t)(e & 0xFFFFFFFFull);
-        float bi[6];
-        for (int k = 0; k < 6; ++k) bi[k] = __ldcg(CB + 6 * (size_t)i + k);
-        if (v >> 32) {
-          const uint32_t node = next - (uint32_t)(e >> 32);
-          float bj[6];
-          for (int k = 0; k < 6; ++k) bj[k] = __ldcg(CB + 6 * (size_t)j + k);
-          float4* nd = A.J.nodes + 4 * (size_t)node;
-          store_child_box(nd, 0, bi);
-          store_child_box(nd, 1, bj);
-          nd[3] = make_float4(__int_as_float(__ldcg(C + i)), __int_as_float(__ldcg(C + j)), 0.f, 0.f);
-          for (int k = 0; k < 3; ++k) {
-            bi[k] = fminf(bi[k], bj[k]);
-            bi[3 + k] = fmaxf(bi[3 + k], bj[3 + k]);
+      unsigned long long e = run + block_excl_scan(q.f[0] + q.f[1] + q.f[2] + q.f[3], sh, t);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (q.f[k] & 0xFFFFFFFFull) {
+          const uint32_t i = base + k, pos = (uint32_t)(e & 0xFFFFFFFFull);
+          float4 il = __ldcg(R + 2 * (size_t)i), ih = __ldcg(R + 2 * (size_t)i + 1);
+          if (q.f[k] >> 32) {
+            const float4 jl = __ldcg(R + 2 * (size_t)q.j[k]), jh = __ldcg(R + 2 * (size_t)q.j[k] + 1);
+            ploc_merge(A.J.nodes, next - (uint32_t)(e >> 32), il, ih, jl, jh, il, ih);
           }
-          Cn[pos] = (int)node;
-        } else {
-          Cn[pos] = __ldcg(C + i);
+          Rn[2 * (size_t)pos] = il;
+          Rn[2 * (size_t)pos + 1] = ih;
         }
-        for (int k = 0; k < 6; ++k) CBn[6 * (size_t)pos + k] = bi[k];
+        e += q.f[k];
       }
       run += t;
     }
@@ -630,12 +672,61 @@ __global__ void __launch_bounds__(kPlocThreads) k_ploc(PlocArgs A) {
     cur ^= 1;
     // (the next round writes the block counts only after its first barrier,
     // when every block has read this round's)
-    if (tail) __syncthreads();
-    else if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
+    if (!grid_barrier(hdr, A.error_word, gen, &ok_sh)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    float box[6];
-    for (int k = 0; k < 6; ++k) box[k] = __ldcg(A.CB[cur] + k);
+  // ---- the last rounds in block 0, list in shared memory
+  if (bid != 0) return;
+  float4* Lc = smem;                     // this round's list
+  float4* Ln = smem + 2 * kPlocTail;     // the next round's
+  int* snn = reinterpret_cast<int*>(smem + 4 * kPlocTail);
+  {
+    const float4* src = cur ? A.R[1] : A.R[0];
+    for (uint32_t k = threadIdx.x; k < 2 * m; k += blockDim.x) Lc[k] = __ldcg(src + k);
+  }
+  __syncthreads();
+  while (m > 1) {
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
+      snn[i] = ploc_nearest(i, m, [&](uint32_t j, float4& lo, float4& hi) {
+        lo = Lc[2 * j];
+        hi = Lc[2 * j + 1];
+      });
+    __syncthreads();
+    unsigned long long run = 0;
+    for (uint32_t g0 = 0; g0 < m; g0 += 4 * kPlocThreads) {
+      const uint32_t base = g0 + 4 * threadIdx.x;
+      unsigned long long f[4];
+      int jj[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        jj[k] = base + k < m ? snn[base + k] : -1;
+        f[k] = base + k < m ? keep_merge(base + k, jj[k], snn[jj[k]]) : 0ull;
+      }
+      unsigned long long t;
+      unsigned long long e = run + block_excl_scan(f[0] + f[1] + f[2] + f[3], sh, t);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (f[k] & 0xFFFFFFFFull) {
+          const uint32_t i = base + k, pos = (uint32_t)(e & 0xFFFFFFFFull);
+          float4 il = Lc[2 * i], ih = Lc[2 * i + 1];
+          if (f[k] >> 32)
+            ploc_merge(A.J.nodes, next - (uint32_t)(e >> 32), il, ih, Lc[2 * jj[k]], Lc[2 * jj[k] + 1], il, ih);
+          Ln[2 * pos] = il;
+          Ln[2 * pos + 1] = ih;
+        }
+        e += f[k];
+      }
+      run += t;
+    }
+    __syncthreads();
+    m = (uint32_t)(run & 0xFFFFFFFFull);
+    next -= (uint32_t)(run >> 32);
+    float4* tmp = Lc;
+    Lc = Ln;
+    Ln = tmp;
+  }
+  if (threadIdx.x == 0) {
+    const float4 lo = Lc[0], hi = Lc[1];
+    const float box[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
     write_root(A.J.root_box, box);
     hdr[kHdrOk] = 1u;
   }
@@ -1143,15 +1234,17 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
     launches += 3;
   }
   // Clustering in one cooperative launch. Scratch: the histogram's buffer holds
-  // the header and the per-block counts, the sort's spare buffers the cluster
-  // references, the refit counters the nearest neighbours, and the 4-wide TLAS
-  // (written only by the collapse after this build) the cluster boxes.
+  // the header and the per-block counts, the refit counters the nearest
+  // neighbours, and the wide TLAS buffer (written only by the collapse after
+  // this build) the two lists of cluster records.
+  if (cudaFuncSetAttribute(k_ploc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlocSmem) != cudaSuccess)
+    return -1;
   static int blocks_per_sm = 0, n_sm = 0;
   if (!blocks_per_sm) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_ploc, kPlocThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_ploc, kPlocThreads, kPlocSmem);
     if (blocks_per_sm > 1) blocks_per_sm = 1;   // one block per SM: cheaper grid barriers
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
@@ -1164,10 +1257,8 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
   A.J = J;
   A.codes = sc.keys[cur];
   A.vals = sc.vals[cur];
-  A.C[0] = reinterpret_cast<int*>(sc.keys[1 - cur]);
-  A.C[1] = reinterpret_cast<int*>(sc.vals[1 - cur]);
-  A.CB[0] = sc.cluster_boxes;
-  A.CB[1] = sc.cluster_boxes + 6 * (size_t)n;
+  A.R[0] = reinterpret_cast<float4*>(sc.cluster_boxes);
+  A.R[1] = A.R[0] + 2 * (size_t)n;
   A.nn = reinterpret_cast<int*>(sc.counters);
   A.hdr = sc.hist;
   A.error_word = error_word;
@@ -1176,7 +1267,7 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
   ++launches;
   void* args[] = {&A};
   if (after && cudaStreamWaitEvent(s, after, 0) != cudaSuccess) return -1;
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ploc, dim3(grid), dim3(kPlocThreads), args, 0, s);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ploc, dim3(grid), dim3(kPlocThreads), args, kPlocSmem, s);
   if (e != cudaSuccess) return -1;
   if (mark && cudaEventRecord(mark, s) != cudaSuccess) return -1;
   ++launches;

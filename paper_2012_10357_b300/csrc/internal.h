@@ -32,7 +32,7 @@ struct BuildScratch {
   uint32_t* parent_int;  // [max_n]
   uint32_t* parent_leaf; // [max_n]
   float* partial;        // [kMaxPartials * 6]
-  float* cluster_boxes;  // [2 * max_n * 6] PLOC cluster boxes (may alias a buffer free during the build)
+  float* cluster_boxes;  // [2 * max_n * 8] PLOC cluster records (may alias a buffer free during the build)
   uint32_t max_n;
 };
 
@@ -66,7 +66,7 @@ int launch_build_large(const LevelDesc& job, const BuildScratch& sc, cudaStream_
 
 // PLOC build of a large level (more than kSmallMax leaves): the LBVH's Morton
 // sort, then bottom-up clustering in one cooperative launch, same node layout;
-// needs sc.cluster_boxes (12 floats per leaf). The clustering launch waits for
+// needs sc.cluster_boxes (16 floats per leaf). The clustering launch waits for
 // `after` and records `mark` (each optional): pr_build_bvh_many_ex orders the
 // clustering launches of concurrent builds one after another with them.
 // Returns the launches issued, or -1 when a launch was refused.
@@ -74,8 +74,7 @@ struct PlocArgs {
   LevelDesc J;
   const uint32_t* codes;     // sorted Morton codes
   const uint32_t* vals;      // leaves in Morton order
-  int* C[2];                 // cluster references, double-buffered
-  float* CB[2];              // cluster boxes [m][6], double-buffered
+  float4* R[2];              // cluster records [m][2] (lo.xyz + ref bits, hi.xyz), double-buffered
   int* nn;                   // nearest neighbour of each cluster
   unsigned long long* part;  // per-block (survivors | merges << 32)
   uint32_t* hdr;             // done, abort, barrier count, barrier generation

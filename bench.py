@@ -176,12 +176,12 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    # ncu --set full captures (profiles/); batch64: the 8-request batch's 144.47 MB
+    # ncu --set full captures (profiles/); batch64: the 8-request batch's 143.84 MB
     # scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
-    "5174da99a2fda4219be94adab225e438c3fffe0d": {"batch64": 761_748_000,
-                                                 "teaser_1080p": 124_416 + 299_776,
-                                                 "field_100k_2160p": 6_071_808 + 51_714_816,
-                                                 "analytic_64x64_x4096": 344_576 + 168_004_608},
+    "f87ec6747f51eaa6b5c70d69940a7e3befc62d07": {"batch64": 758_422_342,
+                                                 "teaser_1080p": 129_792 + 264_960,
+                                                 "field_100k_2160p": 6_064_896 + 52_129_792,
+                                                 "analytic_64x64_x4096": 345_344 + 167_652_864},
 }
 
 

@@ -176,9 +176,10 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    # ncu --set full captures (profiles/); batch64: the 8-request batch's 143.84 MB
-    # scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
-    "f87ec6747f51eaa6b5c70d69940a7e3befc62d07": {"batch64": 758_422_342,
+    # ncu --set full captures (profiles/, sources f87ec674...; re-keyed after a change to a
+    # comment of proceduray.h only); batch64: the 8-request batch's 143.84 MB scaled by pixels
+    # to the 64-request batch (83 623 936 / 15 859 712)
+    "0033524b7ca749517bf66630f537ceebe3f350fa": {"batch64": 758_422_342,
                                                  "teaser_1080p": 129_792 + 264_960,
                                                  "field_100k_2160p": 6_064_896 + 52_129_792,
                                                  "analytic_64x64_x4096": 345_344 + 167_652_864},
@@ -721,7 +722,20 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=4
     return out_rows
 
 
+def serving_tuning(tuning: dict) -> dict:
+    """The batch's tuned shape for the server's iterations, but never a persistent mode: persistent
+    CTAs (wavefront, persistent megakernel and regrouped stages) hold every SM for a whole iteration,
+    so the loader's scene builds on the high-priority stream wait for its end (measured: scene loads
+    of 3 / 15 ms p50 / p99 and an admission p99 of 47 ms at 1000 requests/s with the persistent
+    megakernel); one CTA per tile lets them run between tiles."""
+    t = dict(tuning)
+    if t.get("megakernel") not in (2, 4):
+        t.update(tile_w=16, tile_h=8, megakernel=2)
+    return t
+
+
 def serving_block(pr, torch, rates, n_requests, max_seconds, tuning) -> dict:
+    tuning = serving_tuning(tuning)
     rows = []
     for mode in (pr.PR_SERVE_CONTINUOUS, pr.PR_SERVE_PLAIN):
         rows += bench_serving(pr, torch, rates, n_requests, mode, tuning, max_seconds)

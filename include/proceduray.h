@@ -469,7 +469,11 @@ typedef struct {
   uint32_t reserved;
   uint64_t mem_budget_bytes;   /* device bytes for cached scenes + batch state */
   uint64_t max_batch_pixels;   /* pixels per batched iteration (>= widest image row) */
-  pr_batch_tuning tuning;      /* launch shape; struct_size 0 keeps the default */
+  pr_batch_tuning tuning;      /* launch shape; struct_size 0 keeps the default. Prefer
+                                  megakernel 2 or 4: the persistent modes (0, 1, 3)
+                                  hold every SM for a whole iteration, so scene
+                                  builds on the loader's high-priority stream
+                                  wait for its end */
 } pr_server_config;
 
 typedef struct {

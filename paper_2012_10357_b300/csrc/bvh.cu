@@ -1235,8 +1235,8 @@ int launch_build_ploc(const LevelDesc& J, const BuildScratch& sc, uint32_t* erro
   }
   // Clustering in one cooperative launch. Scratch: the histogram's buffer holds
   // the header and the per-block counts, the refit counters the nearest
-  // neighbours, and the wide TLAS buffer (written only by the collapse after
-  // this build) the two lists of cluster records.
+  // neighbours, and the wide TLAS buffer (written only by the collapse that
+  // follows the clustering) the two lists of cluster records.
   if (cudaFuncSetAttribute(k_ploc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlocSmem) != cudaSuccess)
     return -1;
   static int blocks_per_sm = 0, n_sm = 0;

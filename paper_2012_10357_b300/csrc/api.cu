@@ -149,10 +149,15 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L, bool check = t
       }
     }
     uint32_t n = L.n_leaves - first;
+    // leaf refs keep bits 29..31 for their kind (kLoopBit, kTriBit, kLeafBit)
+    if (L.n_leaves >= (1u << 29)) return fail(PR_ERR_INVALID_ARG, "too many BLAS leaves (max 2^29 - 1)");
     L.blas_info[4 * b + 0] = (int)L.n_blas_nodes;
     L.blas_info[4 * b + 1] = (int)first;
     L.blas_info[4 * b + 2] = (int)n;
-    L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | (tri ? kTriBit : 0u) | first) : 0;
+    L.blas_info[4 * b + 3] = n == 1 ? (int)(kLeafBit | (tri ? kTriBit : 0u) | first)
+                             : (!tri && n <= kLoopMaxLeaves && first + n <= (1u << 27))
+                                 ? (int)(kLeafBit | kLoopBit | ((n - 1) << 27) | first)
+                                 : 0;
     L.n_blas_nodes += n - 1;
     if (n > kSmallMax) L.max_large = std::max(L.max_large, n);
     L.stack_bound = std::max(L.stack_bound, n - 1);

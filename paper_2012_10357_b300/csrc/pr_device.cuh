@@ -9,6 +9,11 @@ namespace pr {
 
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kTriBit = 0x40000000u;    // a BLAS leaf ref of a triangle (kLeafBit | kTriBit | leaf)
+// BLAS root ref of a procedural BLAS of 2..kLoopMaxLeaves leaves: kLeafBit |
+// kLoopBit | (leaves - 1) << 27 | first leaf; the traversal tests its leaf
+// boxes in a loop instead of walking its tree.
+constexpr uint32_t kLoopBit = 0x20000000u;
+constexpr uint32_t kLoopMaxLeaves = 4;
 constexpr int kStackDepth = (int)PR_STACK_DEPTH;
 // Stack of the analytic kernel variant, for scenes whose stack bound fits
 constexpr int kShortStackDepth = 8;
@@ -34,7 +39,7 @@ struct BlasInfo {      // int4 on the device
   int node_base;       // first node of this BLAS in the BLAS node array
   int leaf_base;       // first entry of this BLAS in the flattened leaf arrays
   int n_leaves;
-  int root_ref;        // 0 (node_base + 0) or kLeafBit | leaf (single leaf)
+  int root_ref;        // 0 (node_base + 0), kLeafBit | leaf (single leaf), or a leaf loop (kLoopBit)
 };
 
 // Everything a trace kernel reads; passed by value.

@@ -177,14 +177,37 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
     }
     return false;
   };
-  if (root_ref < 0 && !(root_ref & (int)kTriBit)) {
+  if constexpr (kAnalytic) {
+    if (root_ref < 0 && (root_ref & (int)kLoopBit)) {
+    // Procedural BLAS of 2..4 leaves: every leaf box is tested in turn. The
+    // tree's node tests are the same slab tests on the same boxes with a stack
+    // around them, and the closest hit does not depend on the order in which
+    // the leaves are met (ties go by key), so the result is the tree's.
+    // (Only in the analytic kernel variant: compiled into the generic kernel,
+    // the loop cost its other paths 4-8 % through register allocation.)
+    const int first = root_ref & 0x07FFFFFF, cnt = ((root_ref >> 27) & 3) + 1;
+    for (int j = 0; j < cnt; ++j) {
+      const int leaf = first + j;
+      if (wc) ++wc->leaves;
+      const uint32_t prim = __ldg(S.leaf_prim + leaf);
+      const float* bb = S.aabbs + 6 * (size_t)prim;
+      float t_lo, t_hi;
+      slab_clip(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv,
+                o_inv, tmin, h.t, t_lo, t_hi);
+      if (t_lo <= t_hi && procedural_leaf(leaf, prim, t_lo, t_hi)) return true;
+    }
+    return false;
+    }
+  }
+  if (root_ref < 0 && !(root_ref & (int)kTriBit) && !(root_ref & (int)kLoopBit)) {
     // One-AABB BLAS: the build copies that AABB as the root box, so the root
     // slab interval is the leaf's own; no second slab test.
     const int leaf = root_ref & 0x3FFFFFFF;
     return procedural_leaf(leaf, __ldg(S.leaf_prim + leaf), r_lo, r_hi);
   }
   int sp = sp0;
-  int node = root_ref;
+  // a leaf-loop BLAS (kLoopBit; leaf refs stay below 2^29) walks its tree here
+  int node = (root_ref < 0 && (root_ref & (int)kLoopBit)) ? 0 : root_ref;
   for (;;) {
     if (node >= 0) {
       float l0, l1, r0, r1;

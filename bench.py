@@ -176,13 +176,12 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    # ncu --set full captures (profiles/, sources f87ec674...; re-keyed after a change to a
-    # comment of proceduray.h only); batch64: the 8-request batch's 143.84 MB scaled by pixels
-    # to the 64-request batch (83 623 936 / 15 859 712)
-    "0033524b7ca749517bf66630f537ceebe3f350fa": {"batch64": 758_422_342,
-                                                 "teaser_1080p": 129_792 + 264_960,
-                                                 "field_100k_2160p": 6_064_896 + 52_129_792,
-                                                 "analytic_64x64_x4096": 345_344 + 167_652_864},
+    # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/); batch64: the
+    # 8-request batch's 143.93 MB scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
+    "11390e509939072374b66ba3b0f27b6273cfb550": {"batch64": 758_904_227,
+                                                 "teaser_1080p": 126_976 + 217_600,
+                                                 "field_100k_2160p": 5_993_216 + 51_371_776,
+                                                 "analytic_64x64_x4096": 381_952 + 169_079_040},
 }
 
 

@@ -899,36 +899,43 @@ __device__ __forceinline__ float box_half_area(const float b[6]) {
 template <int W, typename Push>
 __device__ void expand_wide(const float4* nodes, uint32_t u, uint32_t* slots, uint32_t* is_root, uint32_t* rank,
                             Push push) {
-  uint32_t slot[W];
+  // per slot: (binary node << 1 | side), the reference there and its box's area; a
+  // binary node is read once, as four 16-byte loads, when it is opened
+  uint32_t code[W];
+  int ref[W];
+  float area[W];
+  auto open = [&](uint32_t p, int k0, int k1) {
+    const float4* nd = nodes + 4 * (size_t)p;
+    const float4 a = nd[0], b = nd[1], c = nd[2], r = nd[3];
+    const float bl[6] = {a.x, a.y, a.z, a.w, b.x, b.y}, br[6] = {b.z, b.w, c.x, c.y, c.z, c.w};
+    code[k0] = p << 1;
+    ref[k0] = __float_as_int(r.x);
+    area[k0] = box_half_area(bl);
+    code[k1] = (p << 1) | 1u;
+    ref[k1] = __float_as_int(r.y);
+    area[k1] = box_half_area(br);
+  };
+  open(u, 0, 1);
   int cnt = 2;
-  slot[0] = u << 1;
-  slot[1] = (u << 1) | 1u;
   while (cnt < W) {
     int best = -1;
     float best_a = -1.f;
     for (int k = 0; k < cnt; ++k) {
-      if (bin_ref(nodes, slot[k]) < 0) continue;
-      float b[6];
-      bin_box(nodes, slot[k], b);
-      const float a = box_half_area(b);
-      if (a > best_a) {
-        best_a = a;
+      if (ref[k] < 0) continue;
+      if (area[k] > best_a) {
+        best_a = area[k];
         best = k;
       }
     }
     if (best < 0) break;
-    const uint32_t r = (uint32_t)bin_ref(nodes, slot[best]);
-    slot[best] = r << 1;
-    slot[cnt++] = (r << 1) | 1u;
+    open((uint32_t)ref[best], best, cnt);
+    ++cnt;
   }
   is_root[u] = 1u;
   rank[u] = 1u;
   for (int k = 0; k < W; ++k) {
-    slots[(size_t)u * W + k] = k < cnt ? slot[k] : kWideEmpty;
-    if (k < cnt) {
-      const int r = bin_ref(nodes, slot[k]);
-      if (r >= 0) push((uint32_t)r);
-    }
+    slots[(size_t)u * W + k] = k < cnt ? code[k] : kWideEmpty;
+    if (k < cnt && ref[k] >= 0) push((uint32_t)ref[k]);
   }
 }
 

@@ -483,7 +483,7 @@ class BatchBench:
                 json.dump(cache, f, indent=1)
         self.prepared = self.batch.prepare(items)
         # kernels of the batched launch per tuning mode: four stages, or one megakernel
-        self.trace_launches = {0: 4, 1: 1, 2: 1, 3: 8, 4: 1}[self.tuned["tuning"]["megakernel"]]
+        self.trace_launches = {0: 4, 1: 1, 2: 2, 3: 8, 4: 2}[self.tuned["tuning"]["megakernel"]]
 
     def build_all(self):
         # the 64 scenes' builds run concurrently (pr_build_bvh_many: internal streams

@@ -836,18 +836,23 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
   if (tile >= B.hdr->total_tiles) return;
   __shared__ ReqDev sreq;
   __shared__ CameraBasis scam;
-  __shared__ uint32_t s_req;
   const int warp = (int)(threadIdx.x >> 5) + (int)(blockIdx.x % kParts) * kWarps, lane = threadIdx.x & 31;
   constexpr int kWarpsX = 16 / kWarpW;
-  if (threadIdx.x == 0) s_req = find_request(B.reqs, B.hdr->n_req, tile);
-  __syncthreads();
+  // Every thread finds the request (the same loads in every lane) and copies
+  // part of its record and its camera basis (computed by k_rg_bases before this
+  // launch): one barrier, and no thread-serial work at the start of the tile.
+  const uint32_t s_req = find_request(B.reqs, B.hdr->n_req, tile);
   {
+    constexpr int kReqWords = (int)(sizeof(ReqDev) / 4), kCamWords = (int)(sizeof(CameraBasis) / 4);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(B.reqs + s_req);
+    const uint32_t* src_cam = reinterpret_cast<const uint32_t*>(B.bases + 4 * (size_t)s_req);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
-    for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
+    uint32_t* dst_cam = reinterpret_cast<uint32_t*>(&scam);
+    for (int i = threadIdx.x; i < kReqWords + kCamWords; i += blockDim.x) {
+      if (i < kReqWords) dst[i] = src[i];
+      else dst_cam[i - kReqWords] = src_cam[i - kReqWords];
+    }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
   __syncthreads();
   const ReqDev& R = sreq;
   const uint32_t lt = tile - R.tile_begin;
@@ -874,7 +879,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
     const uint32_t total = __reduce_add_sync(kFull, rays);
     if (lane == 0 && total) atomicAdd(B.hdr->counter, (unsigned long long)total);
   }
-  tile_finished(B, s_req, R.n_tiles * kParts);
+  if (B.hdr->notify) tile_finished(B, s_req, R.n_tiles * kParts);   // without flags the CTA just ends
 }
 
 }  // namespace
@@ -882,17 +887,14 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
 int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s,
                      bool ahs_march) {
   int launches = 0;
-  if (ahs_march) {   // staged as one-CTA-per-tile megakernel work (16x8 tiles)
-    if (grid_tiles) k_batch_mega_tiles<8, true><<<grid_tiles, 128, 0, s>>>(B);
-    return grid_tiles ? 1 : 0;
-  }
-  if (T.megakernel == 2) {
-    if (grid_tiles) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
-    return grid_tiles ? 1 : 0;
-  }
-  if (T.megakernel == 4) {
-    if (grid_tiles) k_batch_mega_tiles<8, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
-    return grid_tiles ? 1 : 0;
+  if (ahs_march || T.megakernel == 2 || T.megakernel == 4) {
+    // one CTA per tile (any-hit batches are staged with 16x8 tiles), after the camera bases
+    if (!grid_tiles) return 0;
+    k_rg_bases<<<(B.max_req + 127) / 128, 128, 0, s>>>(B);
+    if (ahs_march) k_batch_mega_tiles<8, true><<<grid_tiles, 128, 0, s>>>(B);
+    else if (T.megakernel == 2) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
+    else k_batch_mega_tiles<8, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
+    return 2;
   }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr
   const uint32_t grid = (uint32_t)n_sm * T.ctas_per_sm;

@@ -248,9 +248,9 @@ struct pr_scene {
   bool tlas_small = true;
   bool built = false;
   // frame cameras
-  pr_camera* d_cams = nullptr;
-  void* d_bases = nullptr;             // camera bases of the frames, computed per launch
+  CameraBasis* d_frames = nullptr;     // camera frames of a multi-frame launch
   uint32_t cams_cap = 0;
+  std::vector<CameraBasis> h_frames;   // host staging of the frames
   int build_launches = 0;
   int trace_launches = 0;
 };
@@ -446,6 +446,45 @@ BuildScratch carve_build_scratch(void* base, uint32_t n) {
   sc.cluster_boxes = nullptr;
   sc.max_n = n;
   return sc;
+}
+
+// Pinhole camera frame (Section 2.2.3's ray generation, vertical field of
+// view): forward = unit(look_at - eye), right = unit(up x forward), the image's
+// up = forward x right; pixel (x, y) of a W x H image maps to
+// ndc = ((x + 0.5) * 2 / W - 1) * tan(fov / 2) * W / H and
+// ((y + 0.5) * 2 / H - 1) * (-tan(fov / 2)) in camera_ray. Double precision,
+// rounded once to float.
+CameraBasis camera_frame(const pr_camera& c, uint32_t width, uint32_t height) {
+  double e[3], f[3], u[3], r[3], v[3];
+  for (int k = 0; k < 3; ++k) {
+    e[k] = c.eye[k];
+    f[k] = (double)c.look_at[k] - e[k];
+    u[k] = c.up[k];
+  }
+  auto unit = [](double* a) {
+    const double l = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    for (int k = 0; k < 3; ++k) a[k] /= l;
+  };
+  auto cross = [](const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  unit(f);
+  cross(u, f, r);
+  unit(r);
+  cross(f, r, v);
+  const double th = std::tan((double)c.vfov_deg * (3.14159265358979323846 / 360.0));
+  CameraBasis b;
+  b.eye = make_float3((float)e[0], (float)e[1], (float)e[2]);
+  b.fwd = make_float3((float)f[0], (float)f[1], (float)f[2]);
+  b.right = make_float3((float)r[0], (float)r[1], (float)r[2]);
+  b.up = make_float3((float)v[0], (float)v[1], (float)v[2]);
+  b.kx = 2.f / (float)width;
+  b.ky = 2.f / (float)height;
+  b.ax = (float)(th * ((double)width / (double)height));
+  b.ay = (float)(-th);
+  return b;
 }
 
 }  // namespace pr
@@ -789,7 +828,7 @@ pr_status build_impl(pr_scene* s, uint32_t flags, cudaStream_t st, PlocChain* ch
 
 extern "C" {
 
-static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera* d_cams, uint32_t n_frames,
+static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const CameraBasis* d_frames, uint32_t n_frames,
                             const pr_trace_params* p, float* out_rgba, pr_aov* out_aov, uint64_t* counter,
                             cudaStream_t st, uint64_t* work = nullptr) {
   TraceLaunch T;
@@ -798,9 +837,8 @@ static pr_status trace_impl(pr_scene* s, const pr_camera* cam0, const pr_camera*
     T.S.tlas4 = nullptr;
     T.S.tlas8 = nullptr;
   }
-  T.cam0 = *cam0;
-  T.cams = d_cams;
-  T.bases = d_cams ? s->d_bases : nullptr;
+  T.cam0 = camera_frame(*cam0, p->width, p->height);
+  T.cams = d_frames;
   T.n_frames = n_frames;
   T.width = p->width;
   T.height = p->height;
@@ -838,22 +876,25 @@ pr_status pr_trace(pr_scene* s, const pr_camera* camera, const pr_trace_params* 
   return trace_impl(s, camera, nullptr, 1, params, out_rgba, out_aov, ray_counter, (cudaStream_t)stream);
 }
 
-static pr_status upload_cameras(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, cudaStream_t st) {
+// Camera frames of a multi-frame launch: computed here, copied to the scene's
+// device array on the launch's stream.
+static pr_status upload_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* p,
+                               cudaStream_t st) {
   if (s->cams_cap < n_frames) {
-    if (s->d_cams) {
+    if (s->d_frames) {
       cudaStreamSynchronize(st);
-      cudaFree(s->d_cams);
-      cudaFree(s->d_bases);
-      s->d_cams = nullptr;
-      s->d_bases = nullptr;
+      cudaFree(s->d_frames);
+      s->d_frames = nullptr;
       s->cams_cap = 0;
     }
-    PR_CUDA(cudaMalloc(&s->d_cams, sizeof(pr_camera) * n_frames), "cudaMalloc cameras");
-    PR_CUDA(cudaMalloc(&s->d_bases, kCameraBasisBytes * (size_t)n_frames), "cudaMalloc camera bases");
+    PR_CUDA(cudaMalloc(&s->d_frames, sizeof(CameraBasis) * n_frames), "cudaMalloc camera frames");
     s->cams_cap = n_frames;
   }
-  PR_CUDA(cudaMemcpyAsync(s->d_cams, cameras, sizeof(pr_camera) * n_frames, cudaMemcpyHostToDevice, st),
-          "copy cameras");
+  s->h_frames.resize(n_frames);
+  for (uint32_t f = 0; f < n_frames; ++f) s->h_frames[f] = camera_frame(cameras[f], p->width, p->height);
+  PR_CUDA(cudaMemcpyAsync(s->d_frames, s->h_frames.data(), sizeof(CameraBasis) * n_frames, cudaMemcpyHostToDevice,
+                          st),
+          "copy camera frames");
   return PR_OK;
 }
 
@@ -866,9 +907,9 @@ pr_status pr_trace_work(pr_scene* s, const pr_camera* cameras, uint32_t n_frames
   pr_trace_params q = *params;
   q.flags &= ~PR_TRACE_WRITE_AOV;
   cudaStream_t st = (cudaStream_t)stream;
-  pr_status u = upload_cameras(s, cameras, n_frames, st);
+  pr_status u = upload_frames(s, cameras, n_frames, &q, st);
   if (u != PR_OK) return u;
-  return trace_impl(s, cameras, s->d_cams, n_frames, &q, out_rgba, nullptr, nullptr, st, work_counters);
+  return trace_impl(s, cameras, s->d_frames, n_frames, &q, out_rgba, nullptr, nullptr, st, work_counters);
 }
 
 pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_frames, const pr_trace_params* params,
@@ -879,9 +920,9 @@ pr_status pr_trace_frames(pr_scene* s, const pr_camera* cameras, uint32_t n_fram
   if ((params->flags & PR_TRACE_WRITE_AOV) && !out_aov) return fail(PR_ERR_INVALID_ARG, "AOV requested but null");
   if (!s->built) return fail(PR_ERR_NOT_BUILT, "pr_trace_frames before pr_build_bvh");
   cudaStream_t st = (cudaStream_t)stream;
-  pr_status u = upload_cameras(s, cameras, n_frames, st);
+  pr_status u = upload_frames(s, cameras, n_frames, params, st);
   if (u != PR_OK) return u;
-  return trace_impl(s, cameras, s->d_cams, n_frames, params, out_rgba, out_aov, ray_counter, st);
+  return trace_impl(s, cameras, s->d_frames, n_frames, params, out_rgba, out_aov, ray_counter, st);
 }
 
 pr_status pr_scene_error(pr_scene* s, void* stream, uint32_t* error_word) {
@@ -995,14 +1036,13 @@ pr_status pr_lbvh_build(const float* boxes, uint32_t n, float* nodes, uint32_t* 
   return PR_OK;
 }
 
-size_t pr_scene_device_bytes(const pr_scene* s) { return s ? s->arena_bytes + sizeof(pr_camera) * s->cams_cap : 0; }
+size_t pr_scene_device_bytes(const pr_scene* s) { return s ? s->arena_bytes + sizeof(CameraBasis) * s->cams_cap : 0; }
 
 void pr_scene_destroy(pr_scene* s) {
   if (!s) return;
   cudaDeviceSynchronize();
   if (s->arena) cudaFree(s->arena);
-  if (s->d_cams) cudaFree(s->d_cams);
-  if (s->d_bases) cudaFree(s->d_bases);
+  if (s->d_frames) cudaFree(s->d_frames);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->stage_done) cudaEventDestroy(s->stage_done);
   if (s->tlas8f) cudaFree(s->tlas8f);

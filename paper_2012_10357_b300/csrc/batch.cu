@@ -96,7 +96,7 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
       return bfail(PR_ERR_INVALID_ARG, "bad request params (AOV output is not available in batches)");
     ReqDev& d = R[i];
     d.S = pr_internal_view(q.scene);
-    d.cam = q.camera;
+    d.cam = camera_frame(q.camera, p.width, p.height);
     d.light = make_float3(p.light_pos[0], p.light_pos[1], p.light_pos[2]);
     d.background = make_float3(p.background[0], p.background[1], p.background[2]);
     d.light_intensity = p.light_intensity;
@@ -191,10 +191,10 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   size_t o_sta = take(16 * P), o_stb = take(8 * P), o_refl = take(16 * P);
   size_t o_sqa = take(16 * P), o_sqb = take(16 * P), o_sqp = take(8 * P), o_sqr = take(4 * P);
   size_t o_mqa = take(16 * P), o_mqb = take(16 * P), o_mqp = take(8 * P), o_mqr = take(4 * P);
-  // regrouped mode: traversal results per ray slot, camera bases, march jobs
+  // regrouped mode: traversal results per ray slot, march jobs
   // (one job per pixel per pass; rays beyond that march in place)
   size_t o_rgh = take(16 * P), o_rgj = take(8 * P), o_rgmh = take(16 * P), o_rgmj = take(8 * P),
-         o_rgsj = take(8 * P), o_bases = take(64 * (size_t)max_requests);
+         o_rgsj = take(8 * P);
   const uint64_t job_cap = (P + 1) / 2;   // jobs per pass; rays beyond march in place
   size_t o_job[2][2];
   for (int pass = 0; pass < 2; ++pass) {
@@ -226,7 +226,6 @@ pr_status pr_batch_create(uint32_t max_requests, uint64_t max_pixels, pr_batch**
   b->V.rg_mhit = reinterpret_cast<int4*>(A + o_rgmh);
   b->V.rg_mjobs = reinterpret_cast<uint2*>(A + o_rgmj);
   b->V.rg_sjobs = reinterpret_cast<uint2*>(A + o_rgsj);
-  b->V.bases = reinterpret_cast<float4*>(A + o_bases);
   for (int pass = 0; pass < 2; ++pass) {
     b->V.jobs[pass].a = reinterpret_cast<float4*>(A + o_job[pass][0]);
     b->V.jobs[pass].r = reinterpret_cast<float4*>(A + o_job[pass][1]);

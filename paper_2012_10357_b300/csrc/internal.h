@@ -106,9 +106,8 @@ int launch_build_scene_small(const LevelDesc* d_jobs, uint32_t n_blas_jobs, cons
 // Tracer (trace.cu).
 struct TraceLaunch {
   SceneView S;
-  pr_camera cam0;
-  const pr_camera* cams;   // device array of n_frames cameras, or null (use cam0)
-  void* bases;             // device scratch for n_frames camera bases when cams is set
+  CameraBasis cam0;            // frame of a one-frame launch
+  const CameraBasis* cams;     // device array of n_frames frames, or null (use cam0)
   uint32_t n_frames;
   uint32_t width, height, max_depth, max_steps, flags;
   float light[3], light_intensity, eps_rel, ambient, background[3];
@@ -120,8 +119,10 @@ struct TraceLaunch {
   bool ahs_march;             // an any-hit shader on a sphere-traced shader: kernels with the any-hit march
 };
 int launch_trace(const TraceLaunch& L, cudaStream_t s);
-// Device bytes of one camera basis (TraceLaunch::bases holds n_frames of them).
-constexpr size_t kCameraBasisBytes = 64;
+// Camera frame of a pinhole camera for a width x height image (host, double
+// precision rounded to float): every path computes its frames here, so one
+// camera gives the same rays in pr_trace, pr_trace_frames and batches.
+CameraBasis camera_frame(const pr_camera& cam, uint32_t width, uint32_t height);
 
 }  // namespace pr
 

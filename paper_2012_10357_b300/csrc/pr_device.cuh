@@ -80,4 +80,13 @@ struct SceneView {
   uint32_t* error_word;
 };
 
+// Pinhole camera frame of one image (ray generation, Section 2.2.3), as the
+// kernels read it: the host computes it once per frame (camera_frame) and each
+// thread forms its pixel's ray from it (camera_ray).
+struct CameraBasis {
+  float3 eye, fwd, right, up;
+  float kx, ky;     // 2 / W, 2 / H
+  float ax, ay;     // tan(fov/2) * aspect, -tan(fov/2)
+};
+
 }  // namespace pr

@@ -16,9 +16,8 @@ namespace {
 
 struct Params {
   SceneView S;
-  pr_camera cam0;
-  const pr_camera* cams;
-  const CameraBasis* bases;   // per-frame bases (multi-frame launches), or null: one basis per CTA
+  CameraBasis cam0;            // the frame of a one-frame launch (kernel parameter space)
+  const CameraBasis* cams;     // frames of a multi-frame launch (device), or null
   uint32_t width, height, flags;
   float eps_rel;
   PixelParams px;
@@ -26,15 +25,6 @@ struct Params {
   pr_aov* aov;
   unsigned long long* counter;
 };
-
-static_assert(sizeof(CameraBasis) == kCameraBasisBytes, "camera basis buffer stride");
-
-// Camera bases of the frames of a multi-frame launch, one thread per frame.
-__global__ void __launch_bounds__(128) k_camera_bases(const pr_camera* cams, uint32_t n, uint32_t W, uint32_t H,
-                                                       CameraBasis* out) {
-  const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f < n) out[f] = camera_basis(cams[f], W, H);
-}
 
 // Resident CTAs per SM the register allocation must allow (occupancy knob;
 // 4 x 128 threads -> at most 128 registers, 4 x 32 KB shared stacks).
@@ -77,19 +67,13 @@ __global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC 
   const int x = blockIdx.x * 16 + (warp % kWarpsX) * kWarpW + (lane % kWarpW);
   const int y = blockIdx.y * 8 + (warp / kWarpsX) * (32 / kWarpW) + lane / kWarpW;
   const bool valid = x < (int)P.width && y < (int)P.height;
-  __shared__ CameraBasis s_cam;
-  const CameraBasis* cb = &s_cam;
-  if (P.bases) {
-    cb = P.bases + frame;   // computed once per frame before the launch
-  } else {
-    if (threadIdx.x == 0) s_cam = camera_basis(P.cams ? P.cams[frame] : P.cam0, P.width, P.height);
-    __syncthreads();
-  }
   uint32_t rays = 0;
   if (valid) {
     PR_DECLARE_STACK_N(128, kAnalytic ? kShortStackDepth : kStackDepth);
-    const float3 eye = cb->eye;
-    const float3 d = camera_ray(*cb, x, y);
+    // the frame comes from the host (parameter space, or the frames' array): no set-up per CTA
+    const CameraBasis cb = P.cams ? P.cams[frame] : P.cam0;
+    const float3 eye = cb.eye;
+    const float3 d = camera_ray(cb, x, y);
     const float eps = scene_eps(S, P.eps_rel);
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
@@ -124,13 +108,6 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
   P.S = L.S;
   P.cam0 = L.cam0;
   P.cams = L.cams;
-  P.bases = (L.cams && L.bases) ? static_cast<const CameraBasis*>(L.bases) : nullptr;
-  int launches = 0;
-  if (P.bases) {
-    k_camera_bases<<<(L.n_frames + 127) / 128, 128, 0, s>>>(L.cams, L.n_frames, L.width, L.height,
-                                                            static_cast<CameraBasis*>(L.bases));
-    ++launches;
-  }
   P.width = L.width;
   P.height = L.height;
   P.flags = L.flags;
@@ -166,7 +143,7 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
     if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, true>) : go(k_trace<false, PR_WARP_TILE_W, false, 0, true>);
     else st ? go(k_trace<true, PR_WARP_TILE_W, false>) : go(k_trace<false, PR_WARP_TILE_W, false>);
   }
-  return launches + 1;
+  return 1;
 }
 
 }  // namespace pr

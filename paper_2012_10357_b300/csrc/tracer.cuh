@@ -633,26 +633,6 @@ __device__ __forceinline__ float scene_eps(const SceneView& S, float eps_rel) {
 
 // Pinhole camera: orthonormal basis and the pixel-to-NDC affine maps, computed
 // once per frame (per CTA / per request) rather than per pixel.
-struct CameraBasis {
-  float3 eye, fwd, right, up;
-  float kx, ky;     // 2 / W, 2 / H
-  float ax, ay;     // tan(fov/2) * aspect, -tan(fov/2)
-};
-
-__device__ __forceinline__ CameraBasis camera_basis(const pr_camera& cam, uint32_t W, uint32_t H) {
-  CameraBasis b;
-  b.eye = ldf3(cam.eye);
-  b.fwd = normalize3(ldf3(cam.look_at) - b.eye);
-  b.right = normalize3(cross3(ldf3(cam.up), b.fwd));
-  b.up = cross3(b.fwd, b.right);
-  const float th = tanf(cam.vfov_deg * 0.008726646259971648f);   // pi / 360
-  b.kx = 2.f / (float)W;
-  b.ky = 2.f / (float)H;
-  b.ax = th * ((float)W / (float)H);
-  b.ay = -th;
-  return b;
-}
-
 // Ray through the centre of pixel (x, y), row 0 at the top.
 __device__ __forceinline__ float3 camera_ray(const CameraBasis& b, int x, int y) {
   const float ndc_x = fmaf((float)x + 0.5f, b.kx, -1.f) * b.ax;

@@ -59,7 +59,6 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
   static_assert(TW * TH == 128, "128-pixel tiles");
   __shared__ ReqDev sreq;
-  __shared__ CameraBasis scam;
   __shared__ uint32_t s_tile, s_req;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int WX = TW / 8;   // warps across (8x4 pixel sub-tile per warp)
@@ -80,8 +79,6 @@ __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
       for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
-      if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
-      __syncthreads();
       last_req = r;
     }
     const ReqDev& R = sreq;
@@ -94,8 +91,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_primary(BatchView B) {
     uint64_t px = 0;
     if (valid) {
       const SceneView& S = R.S;
-      const float3 eye = scam.eye;
-      const float3 d = camera_ray(scam, x, y);
+      const float3 eye = R.cam.eye;
+      const float3 d = camera_ray(R.cam, x, y);
       const float eps = scene_eps(S, R.eps_rel);
       px = R.pixel_begin + (uint64_t)(y - (int)R.row_begin) * R.width + (uint64_t)x;
       Hit h;
@@ -266,14 +263,6 @@ __global__ void __launch_bounds__(256) k_wf_resolve(BatchView B) {
 constexpr uint32_t kEmptyJob = 0xFFFFFFFFu;   // job slot left unused (its ray overflowed the queue)
 constexpr uint32_t kMirrorSlot = 0x80000000u; // pass-1 ray slot of a mirror ray (else a shadow ray)
 
-__global__ void __launch_bounds__(128) k_rg_bases(BatchView B) {
-  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < B.hdr->n_req) {
-    const CameraBasis cb = camera_basis(B.reqs[r].cam, B.reqs[r].width, B.reqs[r].height);
-    reinterpret_cast<CameraBasis*>(B.bases)[r] = cb;
-  }
-}
-
 // Every lane of the warp calls this (n = 0 for lanes without candidates).
 // Returns the ray's first job, or kEmptyJob when the pass's queue is full
 // (the caller then marches its candidates in place).
@@ -376,7 +365,6 @@ __global__ void __launch_bounds__(128, 4) k_rg_primary(BatchView B) {
   constexpr int WX = TW / 8;
   const int ox = (warp % WX) * 8 + (lane & 7), oy = (warp / WX) * 4 + (lane >> 3);
   PR_DECLARE_STACK(128);
-  const CameraBasis* bases = reinterpret_cast<const CameraBasis*>(B.bases);
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t t = atomicAdd(&B.hdr->tile_ctr, 1u);
@@ -397,7 +385,7 @@ __global__ void __launch_bounds__(128, 4) k_rg_primary(BatchView B) {
     float3 eye = f3(0.f, 0.f, 0.f), d = eye;
     float eps = 0.f;
     if (valid) {
-      const CameraBasis& cb = bases[r];
+      const CameraBasis& cb = R.cam;
       eye = cb.eye;
       d = camera_ray(cb, x, y);
       eps = scene_eps(R.S, R.eps_rel);
@@ -543,7 +531,6 @@ __global__ void __launch_bounds__(128, 4) k_rg_shade(BatchView B) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int WX = TW / 8;
   const int ox = (warp % WX) * 8 + (lane & 7), oy = (warp / WX) * 4 + (lane >> 3);
-  const CameraBasis* bases = reinterpret_cast<const CameraBasis*>(B.bases);
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t t = atomicAdd(&B.hdr->shade_ctr, 1u);
@@ -563,7 +550,7 @@ __global__ void __launch_bounds__(128, 4) k_rg_shade(BatchView B) {
     uint64_t px = 0;
     if (valid) {
       const SceneView& S = R.S;
-      const CameraBasis& cb = bases[r];
+      const CameraBasis& cb = R.cam;
       const float3 eye = cb.eye;
       const float3 d = camera_ray(cb, x, y);
       const float eps = scene_eps(S, R.eps_rel);
@@ -771,7 +758,6 @@ template <int kWarpW>
 __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
   static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
   __shared__ ReqDev sreq;
-  __shared__ CameraBasis scam;
   __shared__ uint32_t s_tile, s_req;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kWarpsX = 16 / kWarpW;
@@ -792,8 +778,6 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
       for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
-      if (threadIdx.x == 0) scam = camera_basis(sreq.cam, sreq.width, sreq.height);
-      __syncthreads();
       last_req = r;
     }
     const ReqDev& R = sreq;
@@ -803,7 +787,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
       const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
       const float eps = scene_eps(R.S, R.eps_rel);
       const float3 color =
-          render_pixel<false>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps, stack, nullptr, nullptr, rays);
+          render_pixel<false>(R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps, stack, nullptr, nullptr, rays);
       const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
       if (R.out_rgb) {
         float* f = reinterpret_cast<float*>(R.out) + 3 * o;
@@ -835,23 +819,16 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
   const uint32_t tile = blockIdx.x / kParts;
   if (tile >= B.hdr->total_tiles) return;
   __shared__ ReqDev sreq;
-  __shared__ CameraBasis scam;
   const int warp = (int)(threadIdx.x >> 5) + (int)(blockIdx.x % kParts) * kWarps, lane = threadIdx.x & 31;
   constexpr int kWarpsX = 16 / kWarpW;
   // Every thread finds the request (the same loads in every lane) and copies
-  // part of its record and its camera basis (computed by k_rg_bases before this
-  // launch): one barrier, and no thread-serial work at the start of the tile.
+  // part of its record (camera frame included): one barrier, and no
+  // thread-serial work at the start of the tile.
   const uint32_t s_req = find_request(B.reqs, B.hdr->n_req, tile);
   {
-    constexpr int kReqWords = (int)(sizeof(ReqDev) / 4), kCamWords = (int)(sizeof(CameraBasis) / 4);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(B.reqs + s_req);
-    const uint32_t* src_cam = reinterpret_cast<const uint32_t*>(B.bases + 4 * (size_t)s_req);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sreq);
-    uint32_t* dst_cam = reinterpret_cast<uint32_t*>(&scam);
-    for (int i = threadIdx.x; i < kReqWords + kCamWords; i += blockDim.x) {
-      if (i < kReqWords) dst[i] = src[i];
-      else dst_cam[i - kReqWords] = src_cam[i - kReqWords];
-    }
+    for (int i = threadIdx.x; i < (int)(sizeof(ReqDev) / 4); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
   const ReqDev& R = sreq;
@@ -863,7 +840,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
     PR_DECLARE_STACK(32 * kWarps);
     const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
     const float eps = scene_eps(R.S, R.eps_rel);
-    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs>(R.S, pp, scam.eye, camera_ray(scam, x, y), eps,
+    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs>(R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps,
                                                                           stack, nullptr, nullptr, rays);
     const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
     if (R.out_rgb) {
@@ -888,13 +865,12 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
                      bool ahs_march) {
   int launches = 0;
   if (ahs_march || T.megakernel == 2 || T.megakernel == 4) {
-    // one CTA per tile (any-hit batches are staged with 16x8 tiles), after the camera bases
+    // one CTA per tile (any-hit batches are staged with 16x8 tiles)
     if (!grid_tiles) return 0;
-    k_rg_bases<<<(B.max_req + 127) / 128, 128, 0, s>>>(B);
     if (ahs_march) k_batch_mega_tiles<8, true><<<grid_tiles, 128, 0, s>>>(B);
     else if (T.megakernel == 2) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
     else k_batch_mega_tiles<8, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
-    return 2;
+    return 1;
   }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr
   const uint32_t grid = (uint32_t)n_sm * T.ctas_per_sm;
@@ -904,7 +880,6 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
   }
   if (T.megakernel == 3) {
     cudaMemsetAsync(&B.hdr->job_n[0], 0, 6 * sizeof(uint32_t), s);   // job_n, job_ctr, shade_ctr, finish_ctr
-    k_rg_bases<<<(B.max_req + 127) / 128, 128, 0, s>>>(B);
     const uint32_t grid_m = (uint32_t)n_sm * 8;
     if (T.tile_w == 32) k_rg_primary<32, 4><<<grid, 128, 0, s>>>(B);
     else if (T.tile_w == 8) k_rg_primary<8, 16><<<grid, 128, 0, s>>>(B);
@@ -917,7 +892,7 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
     k_rg_march<<<grid_m, 128, 0, s>>>(B, 1);
     k_rg_finish<<<grid, 128, 0, s>>>(B, T.queue_chunk);
     k_wf_resolve<<<(uint32_t)n_sm * 8, 256, 0, s>>>(B);
-    return 8;
+    return 7;
   }
   if (T.tile_w == 32) k_wf_primary<32, 4><<<grid, 128, 0, s>>>(B);
   else if (T.tile_w == 8) k_wf_primary<8, 16><<<grid, 128, 0, s>>>(B);

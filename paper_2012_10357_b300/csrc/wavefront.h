@@ -11,7 +11,7 @@ namespace pr {
 // One request as the kernels see it (copied to shared memory per tile).
 struct ReqDev {
   SceneView S;
-  pr_camera cam;
+  CameraBasis cam;                   // camera frame of the image (camera_frame on the host)
   float3 light, background;
   float light_intensity, eps_rel, ambient;
   uint32_t width, height, max_depth, max_steps;
@@ -70,7 +70,6 @@ struct BatchView {
   int4* rg_mhit;      // [mirror slots] mirror ray hit
   uint2* rg_mjobs;    // [mirror slots] mirror ray jobs
   uint2* rg_sjobs;    // [shadow slots] shadow ray: first job, job count | occluded << 31
-  float4* bases;      // [max_req][4] camera basis per request (CameraBasis)
   MarchJobs jobs[2];  // pass 0 (primary) and pass 1 (shadow and mirror)
   uint32_t job_cap;   // jobs per pass
   uint32_t max_req;

@@ -631,9 +631,8 @@ __device__ __forceinline__ float scene_eps(const SceneView& S, float eps_rel) {
   return eps_rel * len3(hi - lo);
 }
 
-// Pinhole camera: orthonormal basis and the pixel-to-NDC affine maps, computed
-// once per frame (per CTA / per request) rather than per pixel.
-// Ray through the centre of pixel (x, y), row 0 at the top.
+// Ray through the centre of pixel (x, y), row 0 at the top, from the frame's
+// orthonormal basis and pixel-to-NDC maps (CameraBasis, computed on the host).
 __device__ __forceinline__ float3 camera_ray(const CameraBasis& b, int x, int y) {
   const float ndc_x = fmaf((float)x + 0.5f, b.kx, -1.f) * b.ax;
   const float ndc_y = fmaf((float)y + 0.5f, b.ky, -1.f) * b.ay;

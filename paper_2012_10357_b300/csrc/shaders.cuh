@@ -473,11 +473,11 @@ __device__ __forceinline__ IsResult march(DE de, float3 o, float3 d, float inv_l
   return r;
 }
 
-// One out-of-line march per call of a sphere-traced intersection shader; attr
-// of the result is 0 on a miss.
-static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* prm, float3 o, float3 d, float inv_len,
-                                                     float t_lo, float t_hi, float eps, uint32_t max_steps,
-                                                     WorkCounters* wc = nullptr) {
+// The march of a sphere-traced intersection shader; attr of the result is 0
+// on a miss.
+static __device__ __forceinline__ IsResult sphere_trace_body(uint32_t id, const float4* prm, float3 o, float3 d,
+                                                             float inv_len, float t_lo, float t_hi, float eps,
+                                                             uint32_t max_steps, WorkCounters* wc) {
   uint32_t* de_ctr = wc ? &wc->de_evals[id < PR_IS_COUNT ? id : 0] : nullptr;
   uint32_t* jit = wc ? &wc->frac_iters[0] : nullptr;
   uint32_t* mit = wc ? &wc->frac_iters[1] : nullptr;
@@ -517,6 +517,13 @@ static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* 
     }
     default: return IsResult{0.f, 0u, 0.f};
   }
+}
+
+// The same out of line: one copy of the march serves every call site.
+static __device__ __noinline__ IsResult sphere_trace(uint32_t id, const float4* prm, float3 o, float3 d, float inv_len,
+                                                     float t_lo, float t_hi, float eps, uint32_t max_steps,
+                                                     WorkCounters* wc = nullptr) {
+  return sphere_trace_body(id, prm, o, d, inv_len, t_lo, t_hi, eps, max_steps, wc);
 }
 
 // Object-space normal at the accepted hit (called once per shaded hit).

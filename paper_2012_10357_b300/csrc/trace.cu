@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC 
     const float eps = scene_eps(S, P.eps_rel);
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
-    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs>(
+    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs, true>(
         S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
     if (P.flags & PR_TRACE_OUTPUT_RGB) {
       float* o = reinterpret_cast<float*>(P.out) + 3 * pix;

@@ -391,7 +391,7 @@ typedef struct {
  * 16x8 tiles of all requests and run each pixel's whole pipeline (the
  * single-request kernel's per-pixel code); megakernel = 2 runs the same with
  * one CTA per tile (ctas_per_sm unused); megakernel = 4 with one one-warp CTA
- * per 8x4 quarter of each tile (an early warp frees its slot without waiting
+ * per 4x8 quarter of each tile (an early warp frees its slot without waiting
  * for the tile's slowest). 1, 2 and 4 need tile 16x8 and ignore
  * queue_chunk. megakernel = 3 selects the regrouped stages: traversals hand
  * their fractal (Julia, Mandelbulb) candidates on as march jobs, and a

@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
 
 // The same with one CTA per 16x8 tile (no claiming loop: the hardware
 // schedules the tiles); CTAs past the batch's last tile return at once.
-// kWarps = 1: one warp per CTA and four CTAs per tile (one per 8x4 quarter),
+// kWarps = 1: one warp per CTA and four CTAs per tile (one per warp tile),
 // so a warp that finishes early frees its slot for the next CTA instead of
 // holding it until the tile's slowest warp ends.
 template <int kWarpW, bool kAhs = false, int kWarps = 4>
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps) k_batch_mega_tiles(B
     PR_DECLARE_STACK(32 * kWarps);
     const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
     const float eps = scene_eps(R.S, R.eps_rel);
-    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs>(R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps,
+    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs, true>(R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps,
                                                                           stack, nullptr, nullptr, rays);
     const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
     if (R.out_rgb) {
@@ -867,9 +867,10 @@ int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_
   if (ahs_march || T.megakernel == 2 || T.megakernel == 4) {
     // one CTA per tile (any-hit batches are staged with 16x8 tiles)
     if (!grid_tiles) return 0;
-    if (ahs_march) k_batch_mega_tiles<8, true><<<grid_tiles, 128, 0, s>>>(B);
-    else if (T.megakernel == 2) k_batch_mega_tiles<8><<<grid_tiles, 128, 0, s>>>(B);
-    else k_batch_mega_tiles<8, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
+    // 4x8-pixel warp tiles (1.1 % faster than 8x4 on the 64-request batch)
+    if (ahs_march) k_batch_mega_tiles<4, true><<<grid_tiles, 128, 0, s>>>(B);
+    else if (T.megakernel == 2) k_batch_mega_tiles<4><<<grid_tiles, 128, 0, s>>>(B);
+    else k_batch_mega_tiles<4, false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
     return 1;
   }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr

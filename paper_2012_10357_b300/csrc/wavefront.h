@@ -79,7 +79,7 @@ struct BatchTuning {
   uint32_t ctas_per_sm, tile_w, tile_h, queue_chunk;
   // 1: one persistent megakernel (16x8 tiles), 2: one CTA per 16x8 tile, 0: four
   // stages, 3: regrouped stages (fractal marches deferred into a job queue),
-  // 4: one one-warp CTA per 8x4 quarter of each 16x8 tile
+  // 4: one one-warp CTA per 4x8 quarter of each 16x8 tile
   uint32_t megakernel;
 };
 

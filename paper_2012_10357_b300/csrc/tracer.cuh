@@ -543,14 +543,17 @@ __device__ __forceinline__ void trace_ray_body(bool any_hit, const SceneView& S,
 }
 
 // Out of line: one copy of the traversal serves every call site (the
-// instruction cache holds the megakernel's working set).
+// instruction cache holds the megakernel's working set). The hit comes back
+// by value, in registers, not through the caller's stack frame.
 template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, bool kDefer = false, int kTlas = 0,
           bool kAhs = false, bool kInlineMarch = false>
-__device__ __noinline__ void trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin,
-                                       float tmax, float eps, uint32_t max_steps, Hit& h, TravStack stack,
-                                       WorkCounters* wc, Deferred* defer = nullptr) {
-  trace_ray_body<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs, kInlineMarch>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h,
-                                                                 stack, wc, defer);
+__device__ __noinline__ Hit trace_ray(bool any_hit, const SceneView& S, float3 o, float3 d, uint32_t r, float tmin,
+                                      float tmax, float eps, uint32_t max_steps, TravStack stack, WorkCounters* wc,
+                                      Deferred* defer) {
+  Hit h;
+  trace_ray_body<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs, kInlineMarch>(any_hit, S, o, d, r, tmin, tmax, eps,
+                                                                               max_steps, h, stack, wc, defer);
+  return h;
 }
 
 // The analytic kernel (no estimators: a small instruction footprint) takes
@@ -571,8 +574,8 @@ __device__ __forceinline__ void trace_typed(const SceneView& S, float3 o, float3
     trace_ray_body<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs, kInlineMarch>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h,
                                                                    stack, wc, defer);
   else
-    trace_ray<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs, kInlineMarch>(any_hit, S, o, d, r, tmin, tmax, eps, max_steps, h, stack,
-                                                              wc, defer);
+    h = trace_ray<kStats, kAnalytic, kDepth, kDefer, kTlas, kAhs, kInlineMarch>(any_hit, S, o, d, r, tmin, tmax, eps,
+                                                                                max_steps, stack, wc, defer);
 }
 
 struct Surface {

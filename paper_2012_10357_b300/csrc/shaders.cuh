@@ -389,7 +389,9 @@ __device__ __forceinline__ float3 stencil_one_by_one(float3 p, float h, DE de) {
   return f3(gx, gy, gz);
 }
 
-static __device__ __noinline__ float3 de_stencil(uint32_t id, const float4* prm, float3 p, float h,
+// Inline at its call sites (the surface reconstruction of a sphere-traced hit):
+// teaser 15.5 -> 15.7 Grays/s, field and batch within 0.7 % faster.
+static __device__ __forceinline__ float3 de_stencil(uint32_t id, const float4* prm, float3 p, float h,
                                                  WorkCounters* wc = nullptr) {
   if (wc) wc->de_evals[id < PR_IS_COUNT ? id : 0] += 6;
   const float3 pt[6] = {f3(p.x + h, p.y, p.z), f3(p.x - h, p.y, p.z), f3(p.x, p.y + h, p.z),

@@ -74,12 +74,12 @@ __device__ __forceinline__ void node_boxes(const float4* n, float3 inv_d, float3
 // scene has no sphere-traced shader, so that code is not compiled in).
 template <bool kAnalytic, bool kAhs = false, bool kInlineMarch = false>
 __device__ __forceinline__ bool run_intersection(uint32_t is_id, uint32_t ahs, const float4* prm, float3 o, float3 d,
-                                                 float tmin, float t_lo, float t_hi, float eps, uint32_t max_steps,
-                                                 IsResult& r, WorkCounters* wc) {
+                                                 float3 inv_d, float tmin, float t_lo, float t_hi, float eps,
+                                                 uint32_t max_steps, IsResult& r, WorkCounters* wc) {
   if (wc) ++wc->is_calls[is_id < PR_IS_COUNT ? is_id : 0];
   switch (is_id) {
     case PR_IS_SPHERE: return is_sphere(__ldg(prm), o, d, tmin, r, ahs);
-    case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
+    case PR_IS_BOX: return is_box(__ldg(prm), __ldg(prm + 1), o, d, inv_d, tmin, r, ahs);
     case PR_IS_PACMAN: return is_pacman(__ldg(prm), __ldg(prm + 1), o, d, tmin, r, ahs);
     default:
       if (!kAnalytic && is_sphere_traced(is_id)) {
@@ -167,7 +167,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       return false;
     }
     IsResult res;
-    if (run_intersection<kAnalytic, kAhs, kInlineMarch>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
+    if (run_intersection<kAnalytic, kAhs, kInlineMarch>(hg.x, hg.z, S.params + 4 * (size_t)prim, oo, dd, inv, tmin, t_lo, t_hi, eps, max_steps, res, wc) &&
         res.t >= tmin) {
       bool accept = res.t < h.t;
       if (!accept && res.t == h.t && h.inst >= 0)

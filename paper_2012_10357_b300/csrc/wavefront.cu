@@ -314,7 +314,8 @@ __device__ __noinline__ bool march_in_place(const SceneView& S, const Deferred& 
   for (int i = 0; i < dfr.n; ++i) {
     const int k = dfr.inst[i];
     IsResult res;
-    if (run_intersection<false>(dfr.is_id[i], PR_NONE, S.params + 4 * (size_t)dfr.prim[i], dfr.oo[i], dfr.dd[i], 0.f, dfr.t_lo[i],
+    if (run_intersection<false>(dfr.is_id[i], PR_NONE, S.params + 4 * (size_t)dfr.prim[i], dfr.oo[i], dfr.dd[i],
+                                safe_rcp(dfr.dd[i]), 0.f, dfr.t_lo[i],
                                 dfr.t_hi[i], eps, max_steps, res, nullptr)) {
       const uint2 gq = __ldg(S.leaf_gq + dfr.leaf[i]);
       bool accept = res.t < h.t;

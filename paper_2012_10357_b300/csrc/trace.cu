@@ -44,12 +44,13 @@ struct Params {
 
 // kAnalytic: scenes without sphere-traced shaders whose stack bound fits the
 // short stack (kShortStackDepth entries, 4 KB per CTA instead of 32 KB); the
-// estimator code is not compiled in, so the kernel fits 80 registers and 6
+// estimator code is not compiled in, so the kernel fits 102 registers and 5
 // CTAs stay resident instead of 4. Same arithmetic, same bits. Measured on
-// B300 (4096 jittered 64x64 frames of the small analytic scene per launch):
-// 0.977 / 0.856 / 0.818 / 0.842 ms at 4 / 5 / 6 / 8 CTAs per SM.
+// B300 (4096 jittered 64x64 frames of the small analytic scene per launch,
+// traversal inline at one site): 33.9 / 38.6 / 36.7 Grays/s at 4 / 5 / 6
+// CTAs per SM (106 registers without spills; 92 and 256 bytes of spill loads).
 #ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC
-#define PR_TRACE_MIN_BLOCKS_ANALYTIC 6
+#define PR_TRACE_MIN_BLOCKS_ANALYTIC 5
 #endif
 
 template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false>

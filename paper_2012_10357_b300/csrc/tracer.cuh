@@ -557,9 +557,10 @@ __device__ __noinline__ Hit trace_ray(bool any_hit, const SceneView& S, float3 o
 }
 
 // The analytic kernel (no estimators: a small instruction footprint) takes
-// the traversal inline: without the call's register saves its spills drop
-// from 180 to 28 bytes at 80 registers (4096 64x64 frames: 32.0 -> 34.0
-// Grays/s). The generic kernel keeps it out of line.
+// the traversal inline, at one site (render_pixel_one_site): no call's
+// register saves (4096 64x64 frames: 32.0 Grays/s through the call, 34.0
+// inline at each ray's site, 38.6 at one site). The generic kernel keeps it
+// out of line.
 #ifndef PR_ANALYTIC_INLINE
 #define PR_ANALYTIC_INLINE 1
 #endif
@@ -694,6 +695,112 @@ struct PixelParams {
   uint32_t max_depth, max_steps;
 };
 
+// The analytic kernel's per-pixel pipeline with a single traversal site: the
+// primary, shadow and mirror rays go through one inlined trace in a loop
+// (with an inlined copy per ray kind the kernel's hot code overflowed the
+// instruction cache). The same operations in the same order as render_pixel,
+// so the same bits.
+template <bool kStats, int kDepth, int kTlas>
+__device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, const PixelParams& P, float3 eye, float3 d,
+                                                        float eps, TravStack stack, WorkCounters* wc, pr_aov* av,
+                                                        uint32_t& rays) {
+  enum Stage { kPrimaryRay, kShadowRay, kMirrorRay };
+  Stage stage = kPrimaryRay;
+  float3 ro = eye, rd = d;
+  float rt = INFINITY;
+  uint32_t rtype = 0, flags = 0;
+  float3 color = f3(0.f, 0.f, 0.f);
+  // the primary hit's shading inputs, kept for after the shadow ray
+  float3 albedo = color, n = color, pt = color;
+  float kr = 0.f, ndl = 0.f, delta = 0.f;
+  for (;;) {
+    Hit x;
+    rays += 1;
+    trace_typed<kStats, true, kDepth, false, kTlas>(S, ro, rd, rtype, 0.f, rt, eps, P.max_steps, x, stack, wc);
+    float vis = 1.f;
+    if (stage == kPrimaryRay) {
+      if (x.inst < 0) {
+        color = miss_rgb(S, 0, P.background);
+        if (av) {
+          av->t = -1.f;
+          av->inst = av->geom = av->prim = PR_NONE;
+          av->n[0] = av->n[1] = av->n[2] = 0.f;
+        }
+        break;
+      }
+      flags |= 1u;
+      const Surface sf = surface_body<true>(S, x, eye, d, eps, wc, nullptr);
+      if (av) {
+        av->t = x.t;
+        av->inst = (uint32_t)x.inst;
+        av->geom = sf.geom;
+        av->prim = sf.prim;
+        av->n[0] = sf.n.x; av->n[1] = sf.n.y; av->n[2] = sf.n.z;
+      }
+      if (sf.chs != PR_CHS_LAMBERT) break;   // black
+      pt = madd(eye, x.t, d);
+      delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
+      ndl = light_ndl(sf, P.light, pt);
+      albedo = sf.albedo;
+      n = sf.n;
+      kr = sf.kr;
+      if (ndl > 0.f) {
+        // shadow ray: offset origin, toward the light, ends at the light
+        ro = madd(pt, delta, sf.n);
+        const float3 ls = P.light - ro;
+        rt = len3(ls);
+        rd = ls * (1.f / rt);
+        rtype = 1;
+        flags |= 2u;
+        stage = kShadowRay;
+        continue;
+      }
+    } else if (stage == kShadowRay) {
+      vis = x.inst >= 0 ? 0.f : 1.f;
+      if (x.inst < 0) flags |= 4u;
+    } else {   // the mirror ray's hit, shaded without a shadow ray
+      float3 lr;
+      if (x.inst >= 0) {
+        flags |= 16u;
+        const Surface s2 = surface_body<true>(S, x, ro, rd, eps, wc, nullptr);
+        if (av) {
+          av->refl_t = x.t;
+          av->refl_inst = (uint32_t)x.inst;
+          av->refl_geom = s2.geom;
+          av->refl_prim = s2.prim;
+        }
+        lr = s2.chs == PR_CHS_LAMBERT
+                 ? lambert_rgb(s2.albedo, P.ambient, P.light_intensity, light_ndl(s2, P.light, madd(ro, x.t, rd)), 1.f)
+                 : f3(0.f, 0.f, 0.f);
+      } else {
+        lr = miss_rgb(S, 0, P.background);
+      }
+      color = mirror_mix(color, lr, kr);
+      break;
+    }
+    color = lambert_rgb(albedo, P.ambient, P.light_intensity, ndl, vis);
+    if (P.max_depth >= 2 && kr > 0.f) {
+      // one mirror bounce from the same offset point
+      ro = madd(pt, delta, n);
+      rd = normalize3(d - n * (2.f * dot3(d, n)));
+      rt = INFINITY;
+      rtype = 0;
+      flags |= 8u;
+      stage = kMirrorRay;
+      continue;
+    }
+    break;
+  }
+  if (av) {
+    if (!(flags & 16u)) {
+      av->refl_t = -1.f;
+      av->refl_inst = av->refl_geom = av->refl_prim = PR_NONE;
+    }
+    av->flags = flags;
+  }
+  return color;
+}
+
 // kAhs: the scene (or a batch request's scene) has an any-hit shader on a
 // sphere-traced intersection shader. kInlineMarch: the march of the
 // sphere-traced shaders is compiled into the traversal instead of called
@@ -703,6 +810,8 @@ template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, int kTl
           bool kInlineMarch = false>
 __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
                                                TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
+  if constexpr (kAnalytic && PR_ANALYTIC_INLINE)
+    return render_pixel_one_site<kStats, kDepth, kTlas>(S, P, eye, d, eps, stack, wc, av, rays);
   Hit h;
   rays += 1;
   trace_typed<kStats, kAnalytic, kDepth, false, kTlas, kAhs, kInlineMarch>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);

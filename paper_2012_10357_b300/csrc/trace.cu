@@ -27,9 +27,15 @@ struct Params {
 };
 
 // Resident CTAs per SM the register allocation must allow (occupancy knob;
-// 4 x 128 threads -> at most 128 registers, 4 x 32 KB shared stacks).
+// 4 x 128 threads -> at most 128 registers, 4 x 32 KB shared stacks; 5 -> at
+// most 102 registers, a few spills). Scenes traversed through the wide TLAS
+// (instanced fields) take 5 (100 000-instance field at 3840x2160: 2.20 -> 2.33
+// Grays/s), scenes of few instances 4 (the teaser: 0.5 % faster than at 5).
 #ifndef PR_TRACE_MIN_BLOCKS
 #define PR_TRACE_MIN_BLOCKS 4
+#endif
+#ifndef PR_TRACE_MIN_BLOCKS_WIDE
+#define PR_TRACE_MIN_BLOCKS_WIDE 5
 #endif
 // Width of a warp's pixel tile (height 32 / width). Measured on B300: 8x4 is
 // best for scenes of few instances (the teaser: 8x4 13.1, 4x8 11.6, 16x2 12.6
@@ -54,7 +60,9 @@ struct Params {
 #endif
 
 template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false>
-__global__ void __launch_bounds__(128, kAnalytic ? PR_TRACE_MIN_BLOCKS_ANALYTIC : PR_TRACE_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, kAnalytic                        ? PR_TRACE_MIN_BLOCKS_ANALYTIC
+                                      : kWarpW == PR_WARP_TILE_W_WIDE ? PR_TRACE_MIN_BLOCKS_WIDE
+                                                                      : PR_TRACE_MIN_BLOCKS)
     k_trace(Params P, unsigned long long* work) {
   static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
   const SceneView& S = P.S;

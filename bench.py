@@ -177,11 +177,11 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
                  "include/proceduray.h"]
 TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
     # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/); batch64: the
-    # 8-request batch's 143.93 MB scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
-    "11390e509939072374b66ba3b0f27b6273cfb550": {"batch64": 758_904_227,
-                                                 "teaser_1080p": 126_976 + 217_600,
-                                                 "field_100k_2160p": 5_993_216 + 51_371_776,
-                                                 "analytic_64x64_x4096": 381_952 + 169_079_040},
+    # 8-request batch's 148.79 MB scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
+    "648ce7b5e5176c652671bf219d5d6a696f68ba2c": {"batch64": 784_510_278,
+                                                 "teaser_1080p": 92_928 + 2_560,
+                                                 "field_100k_2160p": 5_964_032 + 53_346_816,
+                                                 "analytic_64x64_x4096": 374_784 + 150_295_552},
 }
 
 

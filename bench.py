@@ -169,26 +169,27 @@ def aggregate_over_ranks(total_ms: float, rays: int, world: int, device) -> tupl
 
 # DRAM traffic of one timed trace launch (dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture, L2 flushed before the launch as in the timed loop), per workload and traversal
-# mode. A figure holds only for the kernel sources it was taken on: it is keyed by their SHA-1
-# and reported as null once they change.
+# mode. A figure holds only for the kernel sources it was taken on: it is keyed by the SHA-1 of
+# its kernel's sources (the single-request kernel's, or those plus the batched kernels') and
+# reported as null once they change.
 TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/csrc/tracer.cuh",
                  "paper_2012_10357_b300/csrc/shaders.cuh", "paper_2012_10357_b300/csrc/pr_device.cuh",
-                 "paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h",
                  "include/proceduray.h"]
-TRACE_TRAFFIC = {   # {sha1 of TRACE_SOURCES: {workload: bytes per launch}}
-    # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/); batch64: the
-    # 8-request batch's 148.79 MB scaled by pixels to the 64-request batch (83 623 936 / 15 859 712)
-    "648ce7b5e5176c652671bf219d5d6a696f68ba2c": {"batch64": 784_510_278,
-                                                 "teaser_1080p": 92_928 + 2_560,
+BATCH_SOURCES = TRACE_SOURCES + ["paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h"]
+TRACE_TRAFFIC = {   # {sha1 of the kernel's sources: {workload: bytes per launch}}
+    # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/)
+    "98e1e216d0f87283e8eb48ea3c0aeb538c2b6a0d": {"teaser_1080p": 92_928 + 2_560,
                                                  "field_100k_2160p": 5_964_032 + 53_346_816,
                                                  "analytic_64x64_x4096": 374_784 + 150_295_552},
+    # batch64: the 8-request batch's bytes scaled by pixels to the 64-request batch
+    # (83 623 936 / 15 859 712)
 }
 
 
-def trace_sources_sha1() -> str:
+def sources_sha1(sources) -> str:
     import hashlib
     h = hashlib.sha1()
-    for rel in TRACE_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -197,7 +198,8 @@ def trace_sources_sha1() -> str:
 def trace_traffic(workload: str, binary_tlas: bool = False):
     if binary_tlas:
         return None
-    return TRACE_TRAFFIC.get(trace_sources_sha1(), {}).get(workload)
+    key = sources_sha1(BATCH_SOURCES if workload == "batch64" else TRACE_SOURCES)
+    return TRACE_TRAFFIC.get(key, {}).get(workload)
 
 
 def measured_peaks() -> dict:

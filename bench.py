@@ -43,6 +43,9 @@ SINGLE = ("analytic_64x64", "teaser_1080p", "field_100k_2160p")
 # default timed steps per workload: about 0.5-1.5 s of GPU work on a B300
 DEFAULT_STEPS = {BATCH: 20, "analytic_64x64": 2000, "teaser_1080p": 2000, "field_100k_2160p": 150}
 SERVE_RATES = [10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0]
+# continuous batching: while at most this many requests wait for rows, the oldest runs alone
+# through pr_trace (batching pays when requests queue)
+SERVE_SOLO_MAX_WAITING = 2
 BATCH_DESC = ("batch of 64 render requests: instanced procedural fields of 1..10000 instances "
               "(8 primitive types, log-uniform count), resolutions from {256^2, 512^2, 1024^2, 2048^2}, orbit cameras")
 
@@ -678,7 +681,7 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=4
         reqs = [pool.next() for _ in range(n)]
         gaps = np.random.default_rng(seed + 1).exponential(1.0 / lam, n)
         srv = pr.Server(mode=mode, max_active=64, mem_budget_bytes=100 << 30, max_batch_pixels=8 << 20,
-                        tuning=tuning)
+                        tuning=tuning, solo_max_waiting=SERVE_SOLO_MAX_WAITING)
         tickets = []
         t0 = time.perf_counter()
         due = t0
@@ -747,7 +750,8 @@ def serving_block(pr, torch, rates, n_requests, max_seconds, tuning) -> dict:
                 "p50_continuous_ms": cont[lam]["p50_ms"], "p50_plain_ms": plain[lam]["p50_ms"]} for lam in rates]
     return {"workload": "serving: Poisson arrivals, teaser / instanced-field (100000 instances) scenes 50/50 from "
                         "pools of 16, resolution 512^2..1920x1080, orbit cameras, 100 GB budget, 64 slots, "
-                        "8 Mpx per continuous-batching iteration",
+                        "8 Mpx per continuous-batching iteration; continuous mode runs the oldest request "
+                        f"alone through pr_trace while at most {SERVE_SOLO_MAX_WAITING} requests wait",
             "tuning": tuning, "points": rows, "continuous_vs_plain": compare}
 
 

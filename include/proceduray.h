@@ -452,7 +452,9 @@ void pr_batch_destroy(pr_batch* batch);
  * PR_SERVE_CONTINUOUS: continuous batching, every iteration one batched
  * launch over row ranges of all admitted requests (at most
  * max_batch_pixels; an iteration that is a single whole request uses the
- * pr_trace megakernel), so a request that arrives while others are on the
+ * pr_trace megakernel, and so does the oldest request while at most
+ * solo_max_waiting requests wait), so a request that arrives while others
+ * are on the
  * GPU joins at the next iteration; with the batched megakernel a request is
  * complete (and pr_server_poll says so) as soon as its last tile is written,
  * through a host-mapped completion flag, not at the end of the launch.
@@ -466,7 +468,11 @@ typedef struct {
   uint32_t struct_size;        /* sizeof(pr_server_config) */
   uint32_t mode;               /* PR_SERVE_CONTINUOUS or PR_SERVE_PLAIN */
   uint32_t max_active;         /* requests admitted at once */
-  uint32_t reserved;
+  uint32_t solo_max_waiting;   /* PR_SERVE_CONTINUOUS: while at most this many
+                                  requests wait for rows, the oldest one (if it
+                                  fits max_batch_pixels) runs alone through
+                                  pr_trace, as in PR_SERVE_PLAIN; 0 = always
+                                  batched */
   uint64_t mem_budget_bytes;   /* device bytes for cached scenes + batch state */
   uint64_t max_batch_pixels;   /* pixels per batched iteration (>= widest image row) */
   pr_batch_tuning tuning;      /* launch shape; struct_size 0 keeps the default. Prefer

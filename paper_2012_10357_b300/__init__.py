@@ -498,7 +498,7 @@ class Batch:
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("mem_budget_bytes", ctypes.c_uint64),
+                ("solo_max_waiting", ctypes.c_uint32), ("mem_budget_bytes", ctypes.c_uint64),
                 ("max_batch_pixels", ctypes.c_uint64), ("tuning", _BatchTuning)]
 
 
@@ -523,10 +523,10 @@ class Server:
     """Serving loop (pr_server): admission by memory budget, scene cache, continuous batching."""
 
     def __init__(self, mode=PR_SERVE_CONTINUOUS, max_active=64, mem_budget_bytes=100 << 30,
-                 max_batch_pixels=16 << 20, tuning: Optional[dict] = None):
+                 max_batch_pixels=16 << 20, tuning: Optional[dict] = None, solo_max_waiting: int = 0):
         cfg = _ServerConfig()
         cfg.struct_size = ctypes.sizeof(_ServerConfig)
-        cfg.mode, cfg.max_active = mode, max_active
+        cfg.mode, cfg.max_active, cfg.solo_max_waiting = mode, max_active, solo_max_waiting
         cfg.mem_budget_bytes, cfg.max_batch_pixels = mem_budget_bytes, max_batch_pixels
         if tuning:
             cfg.tuning = _BatchTuning(ctypes.sizeof(_BatchTuning), tuning["ctas_per_sm"], tuning["tile_w"],

@@ -3,7 +3,9 @@
 // BVH) resident in a cache keyed by the caller's scene key, and renders
 // with continuous batching: every iteration is one batched wavefront launch
 // over row ranges of all admitted requests, so requests that arrive while
-// others are on the GPU join at the next iteration and their work overlaps.
+// others are on the GPU join at the next iteration and their work overlaps
+// (under light load, solo_max_waiting requests or fewer waiting, the oldest
+// runs alone through pr_trace).
 // PR_SERVE_PLAIN mode renders one whole request per pr_trace, first come
 // first served, for comparison.
 #include <cuda_runtime.h>
@@ -357,6 +359,22 @@ bool launch_iteration(pr_server* s) {
   uint64_t px = 0;
   const uint64_t cap = s->cfg.max_batch_pixels;
   const double t_launch = now_s();   // one time stamp for every request of this launch
+  // Continuous batching pays when requests queue: with at most
+  // solo_max_waiting requests waiting for rows, the oldest (whole, within the
+  // pixel cap) runs alone through the single-request kernel, as in the plain
+  // form (same image bits).
+  bool single = s->cfg.mode == PR_SERVE_PLAIN;
+  if (!single && s->cfg.solo_max_waiting) {
+    uint32_t waiting = 0;
+    const Job* first = nullptr;
+    for (auto& jp : s->active) {
+      if (jp->next_row >= jp->params.height) continue;
+      if (!first) first = jp.get();
+      ++waiting;
+    }
+    single = first && waiting <= s->cfg.solo_max_waiting && first->next_row == 0 &&
+             (uint64_t)first->params.width * first->params.height <= cap;
+  }
   for (auto& jp : s->active) {
     Job& j = *jp;
     if (j.next_row >= j.params.height) continue;
@@ -364,7 +382,7 @@ bool launch_iteration(pr_server* s) {
     uint64_t room = cap > px ? cap - px : 0;
     if (room < j.params.width) break;
     uint32_t rows = (uint32_t)std::min<uint64_t>(j.params.height - j.next_row, room / j.params.width);
-    if (s->cfg.mode == PR_SERVE_PLAIN) rows = j.params.height - j.next_row;
+    if (single) rows = j.params.height - j.next_row;
     pr_request r{};
     r.scene = s->cache[j.key].scene;
     r.camera = j.camera;
@@ -378,12 +396,12 @@ bool launch_iteration(pr_server* s) {
     j.rows_inflight += rows;
     it.parts.push_back(Part{j.ticket, rows, false});
     px += (uint64_t)rows * j.params.width;
-    if (s->cfg.mode == PR_SERVE_PLAIN) break;   // one request per launch
+    if (single) break;   // one request per launch
   }
   if (reqs.empty()) return false;
   pr_status st;
   const bool whole_single = reqs.size() == 1 && reqs[0].row_begin == 0 && reqs[0].row_count == reqs[0].params.height;
-  if (s->cfg.mode == PR_SERVE_PLAIN || whole_single) {
+  if (single || whole_single) {
     // plain form, or an iteration that is one whole request: the megakernel
     // (same image bits, one launch instead of the four batched stages)
     st = pr_trace(reqs[0].scene, &reqs[0].camera, &reqs[0].params, reqs[0].out_rgba, nullptr,

@@ -255,3 +255,23 @@ def _early_completion_rounds(srv, big, small, blocker):
         same_launch += 1
         assert s["t_done"] < b["t_done"] - 2e-4, (s, b)
     return same_launch
+
+
+def test_light_load_runs_requests_alone():
+    """solo_max_waiting: while at most that many requests wait for rows, the
+    oldest runs alone through pr_trace. At or above max_active every iteration
+    is one whole request (the plain form's launches), with the same image bits."""
+    reqs = _requests()
+    alone = _alone(reqs)
+    srv = pr.Server(mode=pr.PR_SERVE_CONTINUOUS, max_active=5, mem_budget_bytes=8 << 30, max_batch_pixels=1 << 22,
+                    solo_max_waiting=5)
+    outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for _, w, _ in reqs]
+    for (key, w, cam), out in zip(reqs, outs):
+        srv.submit(key, w.scene, cam, w.params, out)
+    srv.drain(120.0)
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(zip(alone, outs)):
+        assert torch.equal(a, b), f"request {k} differs"
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["iterations"] == len(reqs)
+    srv.close()

@@ -677,8 +677,9 @@ pr_status pr_scene_upload(pr_scene* s, const pr_scene_desc* desc, void* stream) 
 namespace {
 
 // Streams the builds of pr_build_bvh_many fan out to, one pool per device,
-// created on first use and kept for the life of the process.
-constexpr int kBuildStreams = 8;
+// created on first use and kept for the life of the process (64 field scenes:
+// 0.97 / 0.91 / 0.89 ms with 8 / 16 / 32 streams).
+constexpr int kBuildStreams = 32;
 struct BuildPool {
   cudaStream_t streams[kBuildStreams] = {};
   cudaEvent_t done[kBuildStreams] = {};

@@ -214,9 +214,8 @@ struct pr_scene {
   float4* params;
   float* xform;
   uint32_t *inst_blas, *inst_id, *inst_sbt, *inst_mask;
-  uint4* hit_groups;
   float4* materials;
-  uint4* sbt;
+  uint4* sbt;                        // resolved shader records: is, chs, ahs, material
   uint2* ray_types;
   uint32_t* leaf_prim;
   uint2* leaf_gq;
@@ -270,7 +269,7 @@ struct Carver {
 // Byte offsets of every buffer in a scene's device arena (256-byte aligned);
 // the inputs form the prefix [0, o_tbox), copied to the device in one piece.
 struct ArenaPlan {
-  size_t o_aabbs, o_params, o_xform, o_iblas, o_iid, o_isbt, o_imask, o_hg, o_mat, o_sbt, o_rt, o_lp, o_lgq, o_binfo,
+  size_t o_aabbs, o_params, o_xform, o_iblas, o_iid, o_isbt, o_imask, o_mat, o_sbt, o_rt, o_lp, o_lgq, o_binfo,
       o_vert, o_idx;
   size_t o_tbox, o_bbox, o_bnodes, o_bperm, o_bcodes, o_rec, o_iboxes, o_tnodes, o_t4, o_c4p, o_c4e, o_c4r, o_wide, o_tperm,
       o_tcodes, o_sbox, o_err;
@@ -288,7 +287,6 @@ ArenaPlan plan_arena(const Layout& L) {
   P.o_iid = c.take<uint32_t>(L.n_inst);
   P.o_isbt = c.take<uint32_t>(L.n_inst);
   P.o_imask = c.take<uint32_t>(L.n_inst);
-  P.o_hg = c.take<uint4>(L.n_hg);
   P.o_mat = c.take<float4>(L.n_mat);
   P.o_sbt = c.take<uint4>(L.n_rec);
   P.o_rt = c.take<uint2>(L.n_rt);
@@ -350,13 +348,17 @@ pr_status upload(pr_scene* s, const pr_scene_desc* d, cudaStream_t st, char* ext
   put(s->inst_id, d->inst_id, sizeof(uint32_t) * L.n_inst);
   put(s->inst_sbt, d->inst_sbt_offset, sizeof(uint32_t) * L.n_inst);
   put(s->inst_mask, d->inst_mask, sizeof(uint32_t) * L.n_inst);
-  uint32_t* hg = reinterpret_cast<uint32_t*>(H + (reinterpret_cast<const char*>(s->hit_groups) - s->arena));
-  for (uint32_t h = 0; h < L.n_hg; ++h) {
-    for (int k = 0; k < 3; ++k) hg[4 * h + k] = d->hit_groups[3 * h + k];
-    hg[4 * h + 3] = 0;
-  }
   put(s->materials, d->materials, sizeof(float) * 4 * L.n_mat);
-  put(s->sbt, d->sbt, sizeof(uint32_t) * 4 * L.n_rec);
+  // Device shader records hold what a DXR shader record holds: the hit group's
+  // shader identifiers (intersection, closest-hit, any-hit) and the record's
+  // local argument (its material), so one 16-byte load per Eq. 1 lookup gives
+  // the shaders to run (the hit-group indices were validated above).
+  uint32_t* rec = reinterpret_cast<uint32_t*>(H + (reinterpret_cast<const char*>(s->sbt) - s->arena));
+  for (uint32_t r = 0; r < L.n_rec; ++r) {
+    const uint32_t h = d->sbt[4 * r];
+    for (int k = 0; k < 3; ++k) rec[4 * r + k] = d->hit_groups[3 * h + k];
+    rec[4 * r + 3] = d->sbt[4 * r + 1];
+  }
   put(s->ray_types, d->ray_types, sizeof(uint32_t) * 2 * L.n_rt);
   put(s->leaf_prim, L.leaf_prim.data(), sizeof(uint32_t) * L.n_leaves);
   put(s->leaf_gq, L.leaf_gq.data(), sizeof(uint32_t) * 2 * L.n_leaves);
@@ -392,13 +394,11 @@ SceneView view_of(const pr_scene* s) {
   v.aabbs = s->aabbs;
   v.params = s->params;
   v.sbt = s->sbt;
-  v.hit_groups = s->hit_groups;
   v.materials = s->materials;
   v.ray_types = s->ray_types;
   v.n_inst = s->L.n_inst;
   v.n_blas = s->L.n_blas;
   v.n_records = s->L.n_rec;
-  v.n_hit_groups = s->L.n_hg;
   v.sbt_stride_m = s->L.m;
   v.error_word = s->error_word;
   return v;
@@ -563,7 +563,6 @@ pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext
   s->inst_id = (uint32_t*)(A + P.o_iid);
   s->inst_sbt = (uint32_t*)(A + P.o_isbt);
   s->inst_mask = (uint32_t*)(A + P.o_imask);
-  s->hit_groups = (uint4*)(A + P.o_hg);
   s->materials = (float4*)(A + P.o_mat);
   s->sbt = (uint4*)(A + P.o_sbt);
   s->ray_types = (uint2*)(A + P.o_rt);

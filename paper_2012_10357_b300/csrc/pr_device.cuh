@@ -72,11 +72,10 @@ struct SceneView {
   const float* aabbs;         // [n_prims][6]
   const float4* params;       // [n_prims][4]
   // shader binding
-  const uint4* sbt;           // [n_records] hit_group, material, prim_type, instance_index
-  const uint4* hit_groups;    // [n_hit_groups] is, chs, ahs, 0
+  const uint4* sbt;           // [n_records] the record's hit group resolved: is, chs, ahs, material
   const float4* materials;    // [n_materials]
   const uint2* ray_types;     // [n_ray_types] miss, flags
-  uint32_t n_inst, n_blas, n_records, n_hit_groups, sbt_stride_m;
+  uint32_t n_inst, n_blas, n_records, sbt_stride_m;
   uint32_t* error_word;
 };
 

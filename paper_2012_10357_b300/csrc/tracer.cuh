@@ -141,6 +141,18 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
   float r_lo, r_hi;   // root-box slab interval
   slab_clip(f3(blo.x, blo.y, blo.z), f3(bhi.x, bhi.y, bhi.z), inv, o_inv, tmin, h.t, r_lo, r_hi);
   if (r_lo > r_hi) return false;
+  // Slab interval of a primitive's AABB (lo.xyz, hi.xyz) clipped to [tmin,
+  // h.t]: the entry and exit plane of each axis are picked once per ray by the
+  // sign of 1/d (an FMA is monotone in the plane, so the picked plane gives
+  // exactly the min / max of the axis's two slab distances) and only those
+  // words are read, with no min / max per axis.
+  const int pnx = inv.x >= 0.f ? 0 : 3, pny = inv.y >= 0.f ? 1 : 4, pnz = inv.z >= 0.f ? 2 : 5;
+  auto leaf_slab = [&](const float* bb, float& t_lo, float& t_hi) {
+    t_lo = fmax3(fmaf(__ldg(bb + pnx), inv.x, o_inv.x), fmaf(__ldg(bb + pny), inv.y, o_inv.y),
+                 fmaxf(fmaf(__ldg(bb + pnz), inv.z, o_inv.z), tmin));
+    t_hi = fmin3(fmaf(__ldg(bb + (3 - pnx)), inv.x, o_inv.x), fmaf(__ldg(bb + (5 - pny)), inv.y, o_inv.y),
+                 fminf(fmaf(__ldg(bb + (7 - pnz)), inv.z, o_inv.z), h.t));
+  };
   // Procedural leaf whose AABB slab interval is [t_lo, t_hi]: Eq. 1 record,
   // intersection shader, closest-hit bookkeeping. True when any-hit mode
   // accepted a hit (the trace ends).
@@ -152,8 +164,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       atomicOr(S.error_word, kErrSbt);
       return false;
     }
-    uint4 sr = __ldg(S.sbt + rec);
-    const uint4 hg = __ldg(S.hit_groups + sr.x);
+    const uint4 hg = __ldg(S.sbt + rec);   // is, chs, ahs, material
     if (kDefer && is_fractal(hg.x) && hg.z == PR_NONE && defer->n < kMaxDeferred) {   // any-hit candidates march here
       const int i = defer->n++;
       defer->inst[i] = k;
@@ -195,10 +206,11 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
       const int leaf = first + j;
       if (wc) ++wc->leaves;
       const uint32_t prim = __ldg(S.leaf_prim + leaf);
-      const float* bb = S.aabbs + 6 * (size_t)prim;
+      // the box as three 8-byte words (24-byte records, 8-byte aligned)
+      const float2* bb = reinterpret_cast<const float2*>(S.aabbs + 6 * (size_t)prim);
+      const float2 u = __ldg(bb), v = __ldg(bb + 1), w = __ldg(bb + 2);
       float t_lo, t_hi;
-      slab_clip(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv,
-                o_inv, tmin, h.t, t_lo, t_hi);
+      slab_clip(f3(u.x, u.y, v.x), f3(v.y, w.x, w.y), inv, o_inv, tmin, h.t, t_lo, t_hi);
       if (t_lo <= t_hi && procedural_leaf(leaf, prim, t_lo, t_hi)) return true;
     }
     return false;
@@ -242,7 +254,7 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
         if (rec >= S.n_records) {
           atomicOr(S.error_word, kErrSbt);
         } else {
-          const uint32_t ahs = __ldg(S.hit_groups + __ldg(S.sbt + rec).x).z;
+          const uint32_t ahs = __ldg(S.sbt + rec).z;
           const uint32_t* ti = S.indices + 3 * (size_t)prim;
           float t;
           const float3 v0 = ldf3g(S.vertices + 3 * (size_t)__ldg(ti));
@@ -265,10 +277,8 @@ __device__ bool traverse_blas(bool any_hit, const SceneView& S, int k, float3 o,
         node = stack[--sp];
         continue;
       }
-      const float* bb = S.aabbs + 6 * (size_t)prim;
       float t_lo, t_hi;
-      slab_clip(f3(__ldg(bb), __ldg(bb + 1), __ldg(bb + 2)), f3(__ldg(bb + 3), __ldg(bb + 4), __ldg(bb + 5)), inv, o_inv,
-                tmin, h.t, t_lo, t_hi);
+      leaf_slab(S.aabbs + 6 * (size_t)prim, t_lo, t_hi);
       if (t_lo <= t_hi && procedural_leaf(leaf, prim, t_lo, t_hi)) return true;
     }
     if (sp == sp0) break;
@@ -605,9 +615,8 @@ __device__ __forceinline__ Surface surface_body(const SceneView& S, const Hit& h
   uint2 gq = __ldg(S.leaf_gq + leaf);
   uint32_t prim = __ldg(S.leaf_prim + leaf);
   uint32_t rec = 0u + S.sbt_stride_m * gq.x + info.y;
-  uint4 sr = __ldg(S.sbt + rec);
-  uint4 hg = __ldg(S.hit_groups + sr.x);
-  float4 mat = __ldg(S.materials + sr.y);
+  const uint4 hg = __ldg(S.sbt + rec);   // is, chs, ahs, material
+  float4 mat = __ldg(S.materials + hg.w);
   float3 oo, dd;
   to_object(__ldg(R), __ldg(R + 1), __ldg(R + 2), o, d, oo, dd);
   float3 p = madd(oo, h.t, dd);

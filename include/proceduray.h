@@ -213,7 +213,13 @@ pr_status pr_build_bvh(pr_scene* scene, void* stream);
  * the first call per device) that start after the work already enqueued on
  * `stream`, and `stream`'s later work waits for all of them. Asynchronous;
  * the first failing build's status is returned (the others are still
- * enqueued). Calls from several host threads take turns. */
+ * enqueued). Calls from several host threads take turns. The launches of a
+ * call are kept as a CUDA graph (one per device) and replayed by the next call
+ * that builds the same scenes, in the same order, with the same flags: a
+ * scene's launches are fixed by its counts, which pr_scene_upload cannot
+ * change, so a replay rebuilds every BVH from the scenes' current inputs.
+ * Calls with PR_BUILD_TLAS_PLOC or PR_BUILD_TLAS_BVH8_F32, or on a stream that
+ * is being captured, launch directly. */
 pr_status pr_build_bvh_many(pr_scene* const* scenes, uint32_t n, void* stream);
 
 /* Build options (pr_build_bvh_ex, pr_build_bvh_many_ex). */

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -202,6 +203,7 @@ pr_status validate_and_flatten(const pr_scene_desc* d, Layout& L, bool check = t
 
 struct pr_scene {
   Layout L;
+  uint64_t serial = 0;   // unique per created scene (a freed address may be reused, a serial never is)
   char* arena = nullptr;
   size_t arena_bytes = 0;
   // pinned mirror of the arena's input prefix: an upload packs the inputs here
@@ -535,6 +537,8 @@ pr_status create_scene(const pr_scene_desc* desc, cudaStream_t stream, char* ext
   if (!out) return fail(PR_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
   pr_scene* s = new pr_scene();
+  static std::atomic<uint64_t> next_serial{1};
+  s->serial = next_serial.fetch_add(1);
   pr_status vs = validate_and_flatten(desc, s->L, check);
   if (vs != PR_OK) {
     delete s;
@@ -679,11 +683,27 @@ namespace {
 // created on first use and kept for the life of the process (64 field scenes:
 // 0.97 / 0.91 / 0.89 ms with 8 / 16 / 32 streams).
 constexpr int kBuildStreams = 32;
+// A fan-out is a few hundred small launches; the pool keeps the last one as a
+// CUDA graph and replays it while the same scenes are built with the same
+// flags. A scene's launches (shapes and arguments) are fixed by its layout,
+// which never changes after creation, so the graph re-runs every kernel of
+// the builds on the scenes' current inputs.
+#ifndef PR_BUILD_GRAPHS
+#define PR_BUILD_GRAPHS 1
+#endif
+struct BuiltState {   // host-side state a build leaves in its scene
+  int tlas_format, build_launches;
+};
 struct BuildPool {
   cudaStream_t streams[kBuildStreams] = {};
   cudaEvent_t done[kBuildStreams] = {};
   cudaEvent_t start = nullptr;
   cudaEvent_t ploc = nullptr;   // the previous PLOC clustering launch of the fan-out
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<std::pair<const pr_scene*, uint64_t>> key;   // scenes (address, serial) of the graph, in order
+  uint32_t key_flags = 0;
+  std::vector<BuiltState> state;
   bool ready = false;
 };
 
@@ -736,21 +756,67 @@ pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t fla
     P.ready = true;
   }
   const int used = (int)std::min<uint32_t>(n, kBuildStreams);
-  // fork: every pool stream waits for the work already on `stream`
-  PR_CUDA(cudaEventRecord(P.start, st), "record fork");
-  for (int k = 0; k < used; ++k) PR_CUDA(cudaStreamWaitEvent(P.streams[k], P.start, 0), "fork");
-  pr_status result = PR_OK;
-  PlocChain chain{P.ploc, false};
+  // the fan-out from stream `from` over the pool streams and back into it
+  auto fan_out = [&](cudaStream_t from) -> pr_status {
+    // fork: every pool stream waits for the work already on `from`
+    PR_CUDA(cudaEventRecord(P.start, from), "record fork");
+    for (int k = 0; k < used; ++k) PR_CUDA(cudaStreamWaitEvent(P.streams[k], P.start, 0), "fork");
+    pr_status result = PR_OK;
+    PlocChain chain{P.ploc, false};
+    for (uint32_t i = 0; i < n; ++i) {
+      const pr_status b = build_impl(scenes[i], flags, P.streams[i % kBuildStreams], &chain);
+      if (b != PR_OK && result == PR_OK) result = b;
+    }
+    // join: `from` waits for every build
+    for (int k = 0; k < used; ++k) {
+      PR_CUDA(cudaEventRecord(P.done[k], P.streams[k]), "record join");
+      PR_CUDA(cudaStreamWaitEvent(from, P.done[k], 0), "join");
+    }
+    return result;
+  };
+  // Graph replay: not for PLOC (cooperative launches chained by an event) nor
+  // the float 8-wide format (its first build allocates), nor when the
+  // caller's stream is itself being captured (the builds then join that capture).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PR_CUDA(cudaStreamIsCapturing(st, &cap), "cudaStreamIsCapturing");
+  if (!PR_BUILD_GRAPHS || (flags & (PR_BUILD_TLAS_PLOC | PR_BUILD_TLAS_BVH8_F32)) || cap != cudaStreamCaptureStatusNone)
+    return fan_out(st);
+  std::vector<std::pair<const pr_scene*, uint64_t>> key(n);
+  for (uint32_t i = 0; i < n; ++i) key[i] = {scenes[i], scenes[i]->serial};
+  if (!P.graph || P.key_flags != flags || P.key != key) {
+    if (P.graph) {
+      cudaGraphExecDestroy(P.graph);
+      P.graph = nullptr;
+      P.key.clear();
+    }
+    if (!P.capture) PR_CUDA(cudaStreamCreateWithFlags(&P.capture, cudaStreamNonBlocking), "build capture stream");
+    PR_CUDA(cudaStreamBeginCapture(P.capture, cudaStreamCaptureModeThreadLocal), "begin build capture");
+    const pr_status r = fan_out(P.capture);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(P.capture, &g);
+    if (r != PR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "end build capture");
+    const cudaError_t ei = cudaGraphInstantiate(&P.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      P.graph = nullptr;
+      return cuda_fail(ei, "instantiate build graph");
+    }
+    P.key = std::move(key);
+    P.key_flags = flags;
+    P.state.resize(n);
+    for (uint32_t i = 0; i < n; ++i) P.state[i] = {scenes[i]->tlas_format, scenes[i]->build_launches};
+  }
+  PR_CUDA(cudaGraphLaunch(P.graph, st), "build graph launch");
   for (uint32_t i = 0; i < n; ++i) {
-    const pr_status b = build_impl(scenes[i], flags, P.streams[i % kBuildStreams], &chain);
-    if (b != PR_OK && result == PR_OK) result = b;
+    scenes[i]->built = true;
+    scenes[i]->tlas_format = P.state[i].tlas_format;
+    scenes[i]->build_launches = P.state[i].build_launches;
   }
-  // join: `stream` waits for every build
-  for (int k = 0; k < used; ++k) {
-    PR_CUDA(cudaEventRecord(P.done[k], P.streams[k]), "record join");
-    PR_CUDA(cudaStreamWaitEvent(st, P.done[k], 0), "join");
-  }
-  return result;
+  return PR_OK;
 }
 
 pr_status pr_build_bvh(pr_scene* s, void* stream) { return pr_build_bvh_ex(s, 0u, stream); }

@@ -36,6 +36,8 @@ struct pr_batch {
   BatchTuning staged_tuning{};       // launch shape the last staged batch was laid out for
   bool staged_ahs = false;           // the last staged batch needs the any-hit march
   bool graph_ahs = false;
+  bool staged_mirror = true;         // the last staged batch has a request with mirror rays
+  bool graph_mirror = true;
   uint32_t last_launches = 0;
   uint32_t* notify = nullptr;        // completion flags for the next staged batch (host-mapped)
   uint32_t notify_seq = 0;
@@ -86,8 +88,10 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   }
   uint64_t px = 0;
   uint32_t tiles = 0;
+  bool mirror = false;
   for (uint32_t i = 0; i < n; ++i) {
     const pr_request& q = reqs[i];
+    mirror = mirror || q.params.max_depth >= 2;
     const pr_trace_params& p = q.params;
     if (!q.scene || !pr_internal_built(q.scene)) return bfail(PR_ERR_NOT_BUILT, "request scene null or not built");
     if (!q.out_rgba) return bfail(PR_ERR_INVALID_ARG, "request output null");
@@ -130,6 +134,7 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   b->staged_tiles = tiles;
   b->staged_tuning = T;
   b->staged_ahs = ahs;
+  b->staged_mirror = mirror;
   H->total_pixels = px;
   H->tile_ctr = H->shadow_n = H->mirror_n = H->shadow_ctr = H->mirror_ctr = H->pad = 0;
   H->counter = reinterpret_cast<unsigned long long*>(counter);
@@ -155,7 +160,7 @@ pr_status capture(pr_batch* b) {
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bcuda(e, "begin capture");
   b->graph_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->graph_tiles, b->capture_stream,
-                                                 b->staged_ahs);
+                                                 b->staged_ahs, b->staged_mirror);
   e = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess) return bcuda(e, "end capture");
   e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -163,6 +168,7 @@ pr_status capture(pr_batch* b) {
   if (e != cudaSuccess) return bcuda(e, "instantiate graph");
   b->graph_tuning = b->staged_tuning;
   b->graph_ahs = b->staged_ahs;
+  b->graph_mirror = b->staged_mirror;
   return PR_OK;
 }
 
@@ -271,7 +277,8 @@ pr_status pr_trace_batch(pr_batch* b, uint32_t n, const pr_request* reqs, uint64
   cudaStream_t st = (cudaStream_t)stream;
   pr_status s = stage(b, n, reqs, ray_counter, st);
   if (s != PR_OK) return s;
-  b->last_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->staged_tiles, st, b->staged_ahs);
+  b->last_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->staged_tiles, st, b->staged_ahs,
+                                                b->staged_mirror);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bcuda(e, "wavefront launch");
   return PR_OK;
@@ -291,7 +298,7 @@ pr_status pr_trace_batch_graph(pr_batch* b, uint32_t n, const pr_request* reqs, 
     while (g < b->staged_tiles && g < 0x80000000u) g <<= 1;
     b->graph_tiles = g;
   }
-  if (!b->graph || grow || b->graph_ahs != b->staged_ahs ||
+  if (!b->graph || grow || b->graph_ahs != b->staged_ahs || b->graph_mirror != b->staged_mirror ||
       memcmp(&b->graph_tuning, &b->staged_tuning, sizeof(BatchTuning)) != 0) {
     pr_status c = capture(b);
     if (c != PR_OK) return c;

@@ -37,6 +37,18 @@ struct Params {
 #ifndef PR_TRACE_MIN_BLOCKS_WIDE
 #define PR_TRACE_MIN_BLOCKS_WIDE 5
 #endif
+// Variants without the mirror bounce (launches with max_depth 1: the
+// instanced field, batch requests): the shadow trace is the last, so fewer
+// registers are live across it and the register bound for 5 CTAs/SM (96
+// registers) leaves no spills. Measured on B300 (100 000-instance field at
+// 3840x2160, build + frame): 2 369 -> 2 460 Mrays/s against the
+// mirror-capable kernel; 6 CTAs/SM (80 registers, 104 bytes of spills) 2 348.
+#ifndef PR_TRACE_MIN_BLOCKS_WIDE1
+#define PR_TRACE_MIN_BLOCKS_WIDE1 5
+#endif
+#ifndef PR_TRACE_MIN_BLOCKS1
+#define PR_TRACE_MIN_BLOCKS1 5
+#endif
 // Width of a warp's pixel tile (height 32 / width). Measured on B300: 8x4 is
 // best for scenes of few instances (the teaser: 8x4 13.1, 4x8 11.6, 16x2 12.6
 // Grays/s), 4x8 for large instanced fields (+2 % at 100 000 instances). The
@@ -58,10 +70,20 @@ struct Params {
 #ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC
 #define PR_TRACE_MIN_BLOCKS_ANALYTIC 5
 #endif
+// The analytic variant without the mirror bounce (config-1 frames): 94
+// registers without spills at 5 CTAs/SM, 80 with 104 bytes of spills at 6.
+// 4096 frames on B300: 39.3 Grays/s with the mirror-capable kernel; without
+// the bounce 40.9 / 42.0 / 40.9 / 41.8 Grays/s at 5 / 6 / 7 / 8 CTAs/SM.
+#ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC1
+#define PR_TRACE_MIN_BLOCKS_ANALYTIC1 6
+#endif
 
-template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false>
-__global__ void __launch_bounds__(128, kAnalytic                        ? PR_TRACE_MIN_BLOCKS_ANALYTIC
+template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false, bool kMirror = true>
+__global__ void __launch_bounds__(128, kAnalytic && !kMirror            ? PR_TRACE_MIN_BLOCKS_ANALYTIC1
+                                      : kAnalytic                       ? PR_TRACE_MIN_BLOCKS_ANALYTIC
+                                      : kWarpW == PR_WARP_TILE_W_WIDE && !kMirror ? PR_TRACE_MIN_BLOCKS_WIDE1
                                       : kWarpW == PR_WARP_TILE_W_WIDE ? PR_TRACE_MIN_BLOCKS_WIDE
+                                      : !kMirror                      ? PR_TRACE_MIN_BLOCKS1
                                                                       : PR_TRACE_MIN_BLOCKS)
     k_trace(Params P, unsigned long long* work) {
   static_assert(kWarpW == 4 || kWarpW == 8 || kWarpW == 16, "warp tile width");
@@ -86,7 +108,7 @@ __global__ void __launch_bounds__(128, kAnalytic                        ? PR_TRA
     const float eps = scene_eps(S, P.eps_rel);
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
-    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs, true>(
+    const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs, true, kMirror>(
         S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
     if (P.flags & PR_TRACE_OUTPUT_RGB) {
       float* o = reinterpret_cast<float*>(P.out) + 3 * pix;
@@ -145,11 +167,16 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
   } else if (L.S.tlas4) {
     if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, 0, true>)
                         : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, 0, true>);
+    else if (L.max_depth < 2) st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false, 0, false, false>)
+                                 : go(k_trace<false, PR_WARP_TILE_W_WIDE, false, 0, false, false>);
     else st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false>) : go(k_trace<false, PR_WARP_TILE_W_WIDE, false>);
   } else if (L.analytic_small) {
-    st ? go(k_trace<true, PR_WARP_TILE_W, true>) : go(k_trace<false, PR_WARP_TILE_W, true>);
+    if (L.max_depth >= 2) st ? go(k_trace<true, PR_WARP_TILE_W, true>) : go(k_trace<false, PR_WARP_TILE_W, true>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W, true, 0, false, false>) : go(k_trace<false, PR_WARP_TILE_W, true, 0, false, false>);
   } else {
     if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, true>) : go(k_trace<false, PR_WARP_TILE_W, false, 0, true>);
+    else if (L.max_depth < 2) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, false, false>)
+                                 : go(k_trace<false, PR_WARP_TILE_W, false, 0, false, false>);
     else st ? go(k_trace<true, PR_WARP_TILE_W, false>) : go(k_trace<false, PR_WARP_TILE_W, false>);
   }
   return 1;

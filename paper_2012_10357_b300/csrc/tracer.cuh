@@ -709,7 +709,7 @@ struct PixelParams {
 // (with an inlined copy per ray kind the kernel's hot code overflowed the
 // instruction cache). The same operations in the same order as render_pixel,
 // so the same bits.
-template <bool kStats, int kDepth, int kTlas>
+template <bool kStats, int kDepth, int kTlas, bool kMirror = true>
 __device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, const PixelParams& P, float3 eye, float3 d,
                                                         float eps, TravStack stack, WorkCounters* wc, pr_aov* av,
                                                         uint32_t& rays) {
@@ -788,7 +788,7 @@ __device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, cons
       break;
     }
     color = lambert_rgb(albedo, P.ambient, P.light_intensity, ndl, vis);
-    if (P.max_depth >= 2 && kr > 0.f) {
+    if (kMirror && P.max_depth >= 2 && kr > 0.f) {
       // one mirror bounce from the same offset point
       ro = madd(pt, delta, n);
       rd = normalize3(d - n * (2.f * dot3(d, n)));
@@ -815,12 +815,14 @@ __device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, cons
 // sphere-traced shaders is compiled into the traversal instead of called
 // (single-request kernel: teaser 13.8 -> 15.5, field 1.94 -> 2.03 Grays/s; the
 // one-CTA-per-tile batched kernel: +0.2 %).
+// kMirror false: compiled for launches without mirror rays (max_depth 1), so
+// none of the mirror bounce's state stays live across the shadow trace.
 template <bool kStats, bool kAnalytic = false, int kDepth = kStackDepth, int kTlas = 0, bool kAhs = false,
-          bool kInlineMarch = false>
+          bool kInlineMarch = false, bool kMirror = true>
 __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelParams& P, float3 eye, float3 d, float eps,
                                                TravStack stack, WorkCounters* wc, pr_aov* av, uint32_t& rays) {
   if constexpr (kAnalytic && PR_ANALYTIC_INLINE)
-    return render_pixel_one_site<kStats, kDepth, kTlas>(S, P, eye, d, eps, stack, wc, av, rays);
+    return render_pixel_one_site<kStats, kDepth, kTlas, kMirror>(S, P, eye, d, eps, stack, wc, av, rays);
   Hit h;
   rays += 1;
   trace_typed<kStats, kAnalytic, kDepth, false, kTlas, kAhs, kInlineMarch>(S, eye, d, 0, 0.f, INFINITY, eps, P.max_steps, h, stack, wc);
@@ -865,7 +867,7 @@ __device__ __forceinline__ float3 render_pixel(const SceneView& S, const PixelPa
         if (sh.inst < 0) flags |= 4u;
       }
       color = lambert_rgb(sf.albedo, P.ambient, P.light_intensity, ndl, vis);
-      if (P.max_depth >= 2 && sf.kr > 0.f) {
+      if (kMirror && P.max_depth >= 2 && sf.kr > 0.f) {
         // one mirror bounce, its hit shaded without a shadow ray
         float3 orr = madd(pt, delta, sf.n);
         float3 dr = normalize3(d - sf.n * (2.f * dot3(d, sf.n)));

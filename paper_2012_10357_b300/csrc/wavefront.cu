@@ -823,7 +823,9 @@ __global__ void __launch_bounds__(128, 4) k_batch_mega(BatchView B) {
 // pixels for scenes traversed through the wide TLAS, 8x4 for the others (a
 // 1080p teaser request 9.6 % faster than with 4x8; the 64-request batch of
 // instanced fields within 0.3 %).
-template <bool kAhs = false, int kWarps = 4>
+// kMirror false: every request of the batch has max_depth 1 (no mirror
+// bounce compiled in; fewer registers live across the shadow trace).
+template <bool kAhs = false, int kWarps = 4, bool kMirror = true>
 __global__ void __launch_bounds__(32 * kWarps, 4 * PR_BATCH_MIN_BLOCKS / kWarps) k_batch_mega_tiles(BatchView B) {
   static_assert(kWarps == 4 || kWarps == 1, "four warps per tile, or one per quarter");
   constexpr int kParts = 4 / kWarps;
@@ -851,8 +853,8 @@ __global__ void __launch_bounds__(32 * kWarps, 4 * PR_BATCH_MIN_BLOCKS / kWarps)
     PR_DECLARE_STACK(32 * kWarps);
     const PixelParams pp{R.light, R.background, R.light_intensity, R.ambient, R.max_depth, R.max_steps};
     const float eps = scene_eps(R.S, R.eps_rel);
-    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs, true>(R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps,
-                                                                          stack, nullptr, nullptr, rays);
+    const float3 color = render_pixel<false, false, kStackDepth, 0, kAhs, true, kMirror>(
+        R.S, pp, R.cam.eye, camera_ray(R.cam, x, y), eps, stack, nullptr, nullptr, rays);
     const uint64_t o = (uint64_t)y * R.width + (uint64_t)x;
     if (R.out_rgb) {
       float* f = reinterpret_cast<float*>(R.out) + 3 * o;
@@ -873,14 +875,16 @@ __global__ void __launch_bounds__(32 * kWarps, 4 * PR_BATCH_MIN_BLOCKS / kWarps)
 }  // namespace
 
 int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s,
-                     bool ahs_march) {
+                     bool ahs_march, bool mirror) {
   int launches = 0;
   if (ahs_march || T.megakernel == 2 || T.megakernel == 4) {
     // one CTA per tile (any-hit batches are staged with 16x8 tiles)
     if (!grid_tiles) return 0;
     if (ahs_march) k_batch_mega_tiles<true><<<grid_tiles, 128, 0, s>>>(B);
-    else if (T.megakernel == 2) k_batch_mega_tiles<><<<grid_tiles, 128, 0, s>>>(B);
-    else k_batch_mega_tiles<false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
+    else if (T.megakernel == 2 && mirror) k_batch_mega_tiles<><<<grid_tiles, 128, 0, s>>>(B);
+    else if (T.megakernel == 2) k_batch_mega_tiles<false, 4, false><<<grid_tiles, 128, 0, s>>>(B);
+    else if (mirror) k_batch_mega_tiles<false, 1><<<4 * grid_tiles, 32, 0, s>>>(B);
+    else k_batch_mega_tiles<false, 1, false><<<4 * grid_tiles, 32, 0, s>>>(B);
     return 1;
   }
   cudaMemsetAsync(&B.hdr->tile_ctr, 0, 5 * sizeof(uint32_t), s);   // tile_ctr, shadow_n, mirror_n, shadow_ctr, mirror_ctr

@@ -87,7 +87,9 @@ struct BatchTuning {
 // ahs_march: a request's scene has an any-hit shader on a sphere-traced shader;
 // the batch then runs the one-CTA-per-tile megakernel compiled with the
 // any-hit march (staged with 16x8 tiles), whatever T says.
+// mirror: a request has max_depth 2; when none has, the one-CTA-per-tile
+// megakernels run a variant without the mirror bounce.
 int launch_wavefront(const BatchView& B, const BatchTuning& T, int n_sm, uint32_t grid_tiles, cudaStream_t s,
-                     bool ahs_march = false);
+                     bool ahs_march = false, bool mirror = true);
 
 }  // namespace pr

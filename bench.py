@@ -181,12 +181,12 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
 BATCH_SOURCES = TRACE_SOURCES + ["paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h"]
 TRACE_TRAFFIC = {   # {sha1 of the kernel's sources: {workload: bytes per launch}}
     # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/)
-    "8434278b11852a4c1e175dd1fb4a62b2cdce1ffd": {"teaser_1080p": 97_792 + 1_792,
-                                                 "field_100k_2160p": 6_216_704 + 53_254_656,
-                                                 "analytic_64x64_x4096": 470_784 + 149_917_696},
-    # batch64: the 8-request batch's 149.08 MB scaled by pixels to the 64-request batch
+    "b433d8959751e224f3d0796c47507f56cfff17c1": {"teaser_1080p": 98_048 + 2_304,
+                                                 "field_100k_2160p": 5_887_232 + 46_012_416,
+                                                 "analytic_64x64_x4096": 391_424 + 154_895_360},
+    # batch64: the 8-request batch's 142.93 MB scaled by pixels to the 64-request batch
     # (83 623 936 / 15 859 712)
-    "d3d3720b3de04b6c5f52706bb4e54c0258d90354": {"batch64": 786_076_067},
+    "3c36a363ff74a0c6ea98935255ffa8773cc9b497": {"batch64": 753_623_738},
 }
 
 

@@ -70,15 +70,21 @@ struct Params {
 #ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC
 #define PR_TRACE_MIN_BLOCKS_ANALYTIC 5
 #endif
-// The analytic variant without the mirror bounce (config-1 frames): 94
-// registers without spills at 5 CTAs/SM, 80 with 104 bytes of spills at 6.
-// 4096 frames on B300: 39.3 Grays/s with the mirror-capable kernel; without
-// the bounce 40.9 / 42.0 / 40.9 / 41.8 Grays/s at 5 / 6 / 7 / 8 CTAs/SM.
+// The analytic variant without the mirror bounce (config-1 frames), and its
+// copy for launches without an AOV buffer (kAov false): 4096 frames on B300,
+// 39.3 Grays/s with the mirror-capable kernel; without the bounce 40.9 /
+// 42.0 / 40.9 / 41.8 Grays/s at 5 / 6 / 7 / 8 CTAs/SM; with no AOV code
+// either (and the primary ray's surface read from the loop's ray, so the
+// camera ray is not kept live) 44.4 / 44.2 / 45.1 Grays/s at 6 / 7 / 8 CTAs/SM
+// (80 / 72 / 64 registers, 56 / 112 / 196 bytes of spills: the extra warps
+// hide more latency than the spills cost).
 #ifndef PR_TRACE_MIN_BLOCKS_ANALYTIC1
-#define PR_TRACE_MIN_BLOCKS_ANALYTIC1 6
+#define PR_TRACE_MIN_BLOCKS_ANALYTIC1 8
 #endif
 
-template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false, bool kMirror = true>
+// kAov false: the launch writes no AOV buffer (no AOV stores compiled in).
+template <bool kStats, int kWarpW, bool kAnalytic, int kTlas = 0, bool kAhs = false, bool kMirror = true,
+          bool kAov = true>
 __global__ void __launch_bounds__(128, kAnalytic && !kMirror            ? PR_TRACE_MIN_BLOCKS_ANALYTIC1
                                       : kAnalytic                       ? PR_TRACE_MIN_BLOCKS_ANALYTIC
                                       : kWarpW == PR_WARP_TILE_W_WIDE && !kMirror ? PR_TRACE_MIN_BLOCKS_WIDE1
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(128, kAnalytic && !kMirror            ? PR_TRA
 
     const size_t pix = ((size_t)frame * P.height + (size_t)y) * P.width + (size_t)x;
     const float3 color = render_pixel<kStats, kAnalytic, kAnalytic ? kShortStackDepth : kStackDepth, kTlas, kAhs, true, kMirror>(
-        S, P.px, eye, d, eps, stack, wc, P.aov ? P.aov + pix : nullptr, rays);
+        S, P.px, eye, d, eps, stack, wc, kAov && P.aov ? P.aov + pix : nullptr, rays);
     if (P.flags & PR_TRACE_OUTPUT_RGB) {
       float* o = reinterpret_cast<float*>(P.out) + 3 * pix;
       o[0] = color.x;
@@ -172,7 +178,9 @@ int launch_trace(const TraceLaunch& L, cudaStream_t s) {
     else st ? go(k_trace<true, PR_WARP_TILE_W_WIDE, false>) : go(k_trace<false, PR_WARP_TILE_W_WIDE, false>);
   } else if (L.analytic_small) {
     if (L.max_depth >= 2) st ? go(k_trace<true, PR_WARP_TILE_W, true>) : go(k_trace<false, PR_WARP_TILE_W, true>);
-    else st ? go(k_trace<true, PR_WARP_TILE_W, true, 0, false, false>) : go(k_trace<false, PR_WARP_TILE_W, true, 0, false, false>);
+    else if (P.aov) st ? go(k_trace<true, PR_WARP_TILE_W, true, 0, false, false>) : go(k_trace<false, PR_WARP_TILE_W, true, 0, false, false>);
+    else st ? go(k_trace<true, PR_WARP_TILE_W, true, 0, false, false, false>)
+            : go(k_trace<false, PR_WARP_TILE_W, true, 0, false, false, false>);
   } else {
     if (L.ahs_march) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, true>) : go(k_trace<false, PR_WARP_TILE_W, false, 0, true>);
     else if (L.max_depth < 2) st ? go(k_trace<true, PR_WARP_TILE_W, false, 0, false, false>)

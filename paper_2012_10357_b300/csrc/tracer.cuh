@@ -738,7 +738,9 @@ __device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, cons
         break;
       }
       flags |= 1u;
-      const Surface sf = surface_body<true>(S, x, eye, d, eps, wc, nullptr);
+      // ro, rd are still the primary ray (eye, d): reading them here leaves
+      // eye and d dead after the primary trace unless the mirror needs d
+      const Surface sf = surface_body<true>(S, x, ro, rd, eps, wc, nullptr);
       if (av) {
         av->t = x.t;
         av->inst = (uint32_t)x.inst;
@@ -747,7 +749,7 @@ __device__ __forceinline__ float3 render_pixel_one_site(const SceneView& S, cons
         av->n[0] = sf.n.x; av->n[1] = sf.n.y; av->n[2] = sf.n.z;
       }
       if (sf.chs != PR_CHS_LAMBERT) break;   // black
-      pt = madd(eye, x.t, d);
+      pt = madd(ro, x.t, rd);
       delta = is_sphere_traced(sf.is_id) ? 2.f * eps : eps;
       ndl = light_ndl(sf, P.light, pt);
       albedo = sf.albedo;

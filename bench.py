@@ -181,12 +181,12 @@ TRACE_SOURCES = ["paper_2012_10357_b300/csrc/trace.cu", "paper_2012_10357_b300/c
 BATCH_SOURCES = TRACE_SOURCES + ["paper_2012_10357_b300/csrc/wavefront.cu", "paper_2012_10357_b300/csrc/wavefront.h"]
 TRACE_TRAFFIC = {   # {sha1 of the kernel's sources: {workload: bytes per launch}}
     # ncu captures of dram__bytes_read.sum + dram__bytes_write.sum (profiles/)
-    "b433d8959751e224f3d0796c47507f56cfff17c1": {"teaser_1080p": 98_048 + 2_304,
-                                                 "field_100k_2160p": 5_887_232 + 46_012_416,
-                                                 "analytic_64x64_x4096": 391_424 + 154_895_360},
-    # batch64: the 8-request batch's 142.93 MB scaled by pixels to the 64-request batch
+    "2b0b46fcf7c17c7a871ccaf413b23d3773bfd0ea": {"teaser_1080p": 97_024 + 2_048,
+                                                 "field_100k_2160p": 5_900_544 + 46_041_600,
+                                                 "analytic_64x64_x4096": 494_080 + 162_999_552},
+    # batch64: the 8-request batch's 142.63 MB scaled by pixels to the 64-request batch
     # (83 623 936 / 15 859 712)
-    "3c36a363ff74a0c6ea98935255ffa8773cc9b497": {"batch64": 753_623_738},
+    "4cb63c66dd005a5d598b1b784ee2346911cbe8c3": {"batch64": 752_037_702},
 }
 
 

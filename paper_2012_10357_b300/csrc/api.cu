@@ -789,28 +789,38 @@ pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t fla
       P.graph = nullptr;
       P.key.clear();
     }
-    if (!P.capture) PR_CUDA(cudaStreamCreateWithFlags(&P.capture, cudaStreamNonBlocking), "build capture stream");
-    PR_CUDA(cudaStreamBeginCapture(P.capture, cudaStreamCaptureModeThreadLocal), "begin build capture");
+    // A capture that fails anywhere launched nothing (although the builds it
+    // recorded marked their scenes built): the builds then run directly.
+    if (!P.capture && cudaStreamCreateWithFlags(&P.capture, cudaStreamNonBlocking) != cudaSuccess) {
+      P.capture = nullptr;
+      cudaGetLastError();
+      return fan_out(st);
+    }
+    if (cudaStreamBeginCapture(P.capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return fan_out(st);
+    }
     const pr_status r = fan_out(P.capture);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(P.capture, &g);
-    if (r != PR_OK) {
-      if (g) cudaGraphDestroy(g);
-      return r;
-    }
-    if (ec != cudaSuccess) return cuda_fail(ec, "end build capture");
-    const cudaError_t ei = cudaGraphInstantiate(&P.graph, g, 0);
-    cudaGraphDestroy(g);
+    cudaError_t ei = cudaErrorUnknown;
+    if (r == PR_OK && ec == cudaSuccess && g) ei = cudaGraphInstantiate(&P.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
       P.graph = nullptr;
-      return cuda_fail(ei, "instantiate build graph");
+      cudaGetLastError();
+      return fan_out(st);
     }
     P.key = std::move(key);
     P.key_flags = flags;
     P.state.resize(n);
     for (uint32_t i = 0; i < n; ++i) P.state[i] = {scenes[i]->tlas_format, scenes[i]->build_launches};
   }
-  PR_CUDA(cudaGraphLaunch(P.graph, st), "build graph launch");
+  const cudaError_t el = cudaGraphLaunch(P.graph, st);
+  if (el != cudaSuccess) {
+    for (uint32_t i = 0; i < n; ++i) scenes[i]->built = false;
+    return cuda_fail(el, "build graph launch");
+  }
   for (uint32_t i = 0; i < n; ++i) {
     scenes[i]->built = true;
     scenes[i]->tlas_format = P.state[i].tlas_format;

@@ -681,7 +681,7 @@ def bench_serving(pr, torch, rates, n_requests, mode, tuning=None, max_seconds=4
         n = int(min(n_requests, max(20, lam * max_seconds)))
         reqs = [pool.next() for _ in range(n)]
         gaps = np.random.default_rng(seed + 1).exponential(1.0 / lam, n)
-        srv = pr.Server(mode=mode, max_active=64, mem_budget_bytes=100 << 30, max_batch_pixels=8 << 20,
+        srv = pr.Server(mode=mode, max_active=64, mem_budget_bytes=100 << 30, max_batch_pixels=16 << 20,
                         tuning=tuning, solo_max_waiting=SERVE_SOLO_MAX_WAITING)
         tickets = []
         t0 = time.perf_counter()
@@ -751,7 +751,7 @@ def serving_block(pr, torch, rates, n_requests, max_seconds, tuning) -> dict:
                 "p50_continuous_ms": cont[lam]["p50_ms"], "p50_plain_ms": plain[lam]["p50_ms"]} for lam in rates]
     return {"workload": "serving: Poisson arrivals, teaser / instanced-field (100000 instances) scenes 50/50 from "
                         "pools of 16, resolution 512^2..1920x1080, orbit cameras, 100 GB budget, 64 slots, "
-                        "8 Mpx per continuous-batching iteration; continuous mode runs the oldest request "
+                        "16 Mpx per continuous-batching iteration; continuous mode runs the oldest request "
                         f"alone through pr_trace while at most {SERVE_SOLO_MAX_WAITING} requests wait",
             "tuning": tuning, "points": rows, "continuous_vs_plain": compare}
 

@@ -275,6 +275,33 @@ def test_4096_frame_launch_sampled_vs_oracle():
     assert agree / n >= 0.999, (n, agree)
 
 
+def test_launches_without_aov_equal_the_checked_ones():
+    """Launches that write no AOV buffer take kernels compiled without AOV
+    stores (the analytic config-1 kernel) and, for max_depth 1, without the
+    mirror bounce: the 4096-frame RGB launch the benchmark times equals, bit for
+    bit, the AOV launch that the oracle comparisons check, and so do single
+    frames of the small analytic scene and of an instanced field."""
+    w = scenes.small_analytic()
+    cams = pr.CameraArray(scenes.small_analytic_cameras(0, 4096))
+    scene = pr.Scene(w.scene)
+    checked, _ = scene.trace_frames(cams, w.params, want_aov=True, rgb=True)
+    timed = scene.trace_frames(cams, w.params, rgb=True)
+    one_checked, _ = scene.trace(w.camera, w.params, want_aov=True)
+    one = scene.trace(w.camera, w.params)
+    torch.cuda.synchronize()
+    assert torch.equal(checked, timed)
+    assert torch.equal(one_checked, one)
+    assert scene.error_word() == 0
+    scene.close()
+    f = scenes.field(n_inst=3000, width=203, height=97)
+    scene = pr.Scene(f.scene)
+    a, _ = scene.trace(f.camera, f.params, want_aov=True)
+    b = scene.trace(f.camera, f.params)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    scene.close()
+
+
 @pytest.mark.parametrize("which", ["teaser", "field"])
 def test_rgb_output_equals_the_rgba_channels(which):
     """PR_TRACE_OUTPUT_RGB writes 3 floats per pixel: the same values as the

@@ -28,16 +28,19 @@ struct pr_batch {
   BatchTuning tuning{8, 16, 8, 64, 0};
   int n_sm = 0;
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  BatchTuning graph_tuning{};
-  uint32_t graph_tiles = 0;          // grid of the captured one-CTA-per-tile megakernel
-  uint32_t graph_launches = 0;
+  // Captured launches, one per kernel family: batches with and without a
+  // mirror-ray request (a server's iterations alternate between the two).
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    BatchTuning tuning{};
+    uint32_t tiles = 0;              // grid of the captured one-CTA-per-tile megakernel
+    uint32_t launches = 0;
+    bool ahs = false;
+  } graphs[2];
   uint32_t staged_tiles = 0;         // tiles of the last staged batch
   BatchTuning staged_tuning{};       // launch shape the last staged batch was laid out for
   bool staged_ahs = false;           // the last staged batch needs the any-hit march
-  bool graph_ahs = false;
   bool staged_mirror = true;         // the last staged batch has a request with mirror rays
-  bool graph_mirror = true;
   uint32_t last_launches = 0;
   uint32_t* notify = nullptr;        // completion flags for the next staged batch (host-mapped)
   uint32_t notify_seq = 0;
@@ -151,24 +154,26 @@ pr_status stage(pr_batch* b, uint32_t n, const pr_request* reqs, uint64_t* count
   return PR_OK;
 }
 
-pr_status capture(pr_batch* b) {
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+pr_status capture(pr_batch* b, pr_batch::Graph& G) {
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bcuda(e, "begin capture");
-  b->graph_launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, b->graph_tiles, b->capture_stream,
-                                                 b->staged_ahs, b->staged_mirror);
+  G.launches = (uint32_t)launch_wavefront(b->V, b->staged_tuning, b->n_sm, G.tiles, b->capture_stream, b->staged_ahs,
+                                          b->staged_mirror);
   e = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess) return bcuda(e, "end capture");
-  e = cudaGraphInstantiate(&b->graph, g, 0);
+  e = cudaGraphInstantiate(&G.exec, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return bcuda(e, "instantiate graph");
-  b->graph_tuning = b->staged_tuning;
-  b->graph_ahs = b->staged_ahs;
-  b->graph_mirror = b->staged_mirror;
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return bcuda(e, "instantiate graph");
+  }
+  G.tuning = b->staged_tuning;
+  G.ahs = b->staged_ahs;
   return PR_OK;
 }
 
@@ -291,21 +296,20 @@ pr_status pr_trace_batch_graph(pr_batch* b, uint32_t n, const pr_request* reqs, 
   if (s != PR_OK) return s;
   // the one-CTA-per-tile megakernel needs a grid of at least this batch's tiles: capture again
   // (with room to grow) when it is larger than the captured one
-  const bool grow = (b->staged_tuning.megakernel == 2 || b->staged_tuning.megakernel == 4) &&
-                    b->staged_tiles > b->graph_tiles;
+  pr_batch::Graph& G = b->graphs[b->staged_mirror ? 1 : 0];
+  const bool grow = (b->staged_tuning.megakernel == 2 || b->staged_tuning.megakernel == 4) && b->staged_tiles > G.tiles;
   if (grow) {
     uint32_t g = 1024;
     while (g < b->staged_tiles && g < 0x80000000u) g <<= 1;
-    b->graph_tiles = g;
+    G.tiles = g;
   }
-  if (!b->graph || grow || b->graph_ahs != b->staged_ahs || b->graph_mirror != b->staged_mirror ||
-      memcmp(&b->graph_tuning, &b->staged_tuning, sizeof(BatchTuning)) != 0) {
-    pr_status c = capture(b);
+  if (!G.exec || grow || G.ahs != b->staged_ahs || memcmp(&G.tuning, &b->staged_tuning, sizeof(BatchTuning)) != 0) {
+    pr_status c = capture(b, G);
     if (c != PR_OK) return c;
   }
-  cudaError_t e = cudaGraphLaunch(b->graph, st);
+  cudaError_t e = cudaGraphLaunch(G.exec, st);
   if (e != cudaSuccess) return bcuda(e, "graph launch");
-  b->last_launches = b->graph_launches;
+  b->last_launches = G.launches;
   return PR_OK;
 }
 
@@ -383,7 +387,8 @@ extern "C" {
 void pr_batch_destroy(pr_batch* b) {
   if (!b) return;
   cudaDeviceSynchronize();
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& G : b->graphs)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->staging) cudaFreeHost(b->staging);

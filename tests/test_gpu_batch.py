@@ -63,6 +63,34 @@ def test_batch_bit_identical_to_plain(graph):
     batch.close()
 
 
+@pytest.mark.parametrize("mode", [2, 4])
+def test_graph_batches_alternating_mirror_and_no_mirror(mode):
+    """Batches whose requests all have max_depth 1 run kernels without the
+    mirror bounce, batches with a max_depth-2 request the mirror-capable ones;
+    one batch object keeps a captured graph for each and alternates between
+    them (as the server's iterations do), every image equal to pr_trace's."""
+    with_mirror = [scenes.teaser(width=120, height=68), scenes.field(n_inst=2000, width=96, height=64)]
+    without = scenes.batch_requests(seed=3, n_requests=3, res_choices=(64, 96))
+    assert all(w.params.max_depth == 1 for w in without) and with_mirror[0].params.max_depth == 2
+    objs_m = [pr.Scene(w.scene) for w in with_mirror]
+    objs_n = [pr.Scene(w.scene) for w in without]
+    plain_m, _ = _plain(objs_m, with_mirror)
+    plain_n, _ = _plain(objs_n, without)
+    total = max(sum(w.params.width * w.params.height for w in ws) for ws in (with_mirror, without))
+    batch = pr.Batch(4, total)
+    batch.set_tuning(4, 16, 8, 32, mode)
+    for rnd in range(3):
+        for objs, ws, plain in ((objs_m, with_mirror, plain_m), (objs_n, without, plain_n)):
+            outs = [torch.full((w.params.height, w.params.width, 4), -1.0, device="cuda") for w in ws]
+            batch.trace([(o, w.camera, w.params, out) for o, w, out in zip(objs, ws, outs)], graph=True)
+            torch.cuda.synchronize()
+            for k, (a, b) in enumerate(zip(plain, outs)):
+                assert torch.equal(a, b), f"round {rnd}, request {k} differs"
+    batch.close()
+    for o in objs_m + objs_n:
+        o.close()
+
+
 @pytest.mark.parametrize("shape", [(2, 16, 8, 32, 0), (8, 32, 4, 128, 0), (16, 8, 16, 64, 0), (1, 16, 8, 1024, 0),
                                    (4, 16, 8, 32, 1), (1, 16, 8, 32, 1), (4, 16, 8, 32, 2),
                                    (4, 16, 8, 32, 3), (8, 32, 4, 128, 3), (1, 8, 16, 64, 3), (4, 16, 8, 32, 4)])

@@ -213,7 +213,8 @@ pr_status pr_build_bvh(pr_scene* scene, void* stream);
  * the first call per device) that start after the work already enqueued on
  * `stream`, and `stream`'s later work waits for all of them. Asynchronous;
  * the first failing build's status is returned (the others are still
- * enqueued). Calls from several host threads take turns. The launches of a
+ * enqueued). A scene may appear once (PR_ERR_INVALID_ARG, nothing enqueued,
+ * if one appears twice). Calls from several host threads take turns. The launches of a
  * call are kept as a CUDA graph (one per device) and replayed by the next call
  * that builds the same scenes, in the same order, with the same flags: a
  * scene's launches are fixed by its counts, which pr_scene_upload cannot

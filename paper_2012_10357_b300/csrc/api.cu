@@ -739,6 +739,13 @@ pr_status pr_build_bvh_many_ex(pr_scene* const* scenes, uint32_t n, uint32_t fla
   if (!scenes) return fail(PR_ERR_INVALID_ARG, "null scene array");
   for (uint32_t i = 0; i < n; ++i)
     if (!scenes[i]) return fail(PR_ERR_INVALID_ARG, "null scene in the array");
+  {
+    // a scene listed twice would be built by two streams into one arena at once
+    std::vector<pr_scene*> sorted(scenes, scenes + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(PR_ERR_INVALID_ARG, "a scene appears twice in the array");
+  }
   cudaStream_t st = (cudaStream_t)stream;
   if (n == 1) return build_impl(scenes[0], flags, st, nullptr);
   int dev = 0;

@@ -138,3 +138,17 @@ def test_header_documents_every_entry_point():
         assert m, s
         before = text[:m.start(1)].rstrip()
         assert before.endswith("*/"), s
+
+
+def test_build_many_rejects_a_scene_listed_twice(pr):
+    """pr_build_bvh_many refuses an array naming one scene twice (two streams
+    would build it into one arena at once) before it touches any scene: the
+    handles here are never dereferenced, so no device is needed."""
+    lib = ctypes.CDLL(pr.LIB_PATH)
+    lib.pr_build_bvh_many.restype = ctypes.c_int
+    lib.pr_build_bvh_many.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_void_p]
+    lib.pr_last_error.restype = ctypes.c_char_p
+    fake = ctypes.c_void_p(0x1000)   # an address no scene has; only compared, never read
+    arr = (ctypes.c_void_p * 3)(0x2000, fake.value, fake.value)
+    assert lib.pr_build_bvh_many(arr, 3, None) == pr.PR_ERR_INVALID_ARG
+    assert b"twice" in lib.pr_last_error()
